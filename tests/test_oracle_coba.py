@@ -1,0 +1,153 @@
+"""Pins of the oracle's COBA E/I network step (Appendices E, F, N).
+
+What pins what:
+* synaptic decay            -> closed form g_n = g_0 exp(-n dt / tau) (Appendix E).
+* exponential Euler step    -> scipy's ODE solver on tau dV/dt = -(V - V_rest) + R I
+                               with I held fixed over the step (Appendix F).
+* COBA current              -> signs: an E event depolarises, an I event hyperpolarises.
+* threshold/reset/refractory-> closed-form interspike interval of an isolated
+                               neuron under constant input: first spike at step 139,
+                               then every 189 steps; no spike within 51 steps.
+* AlignPost merging         -> per-synapse conductances simulated one by one and
+                               summed equal the merged per-neuron conductance
+                               (Section 3.3: the merging is exact).
+* event delivery            -> events per step = sum of out-degrees of spiking rows.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy.integrate import solve_ivp
+
+import oracle as orc
+from paper_2311_05106_gb300 import workloads as wl
+
+
+def _empty_csr(n):
+    return ("csr", np.zeros(n + 1, np.int64), np.zeros(0, np.int32), None)
+
+
+def test_synaptic_decay_closed_form():
+    net = orc.CobaNet(4, 2, _empty_csr(4), np.full(4, -70.0))
+    net.ge[:] = [1.0, 2.0, 0.0, 3.0]
+    net.gi[:] = [5.0, 0.0, 1.0, 2.0]
+    g0e, g0i = net.ge.copy(), net.gi.copy()
+    for _ in range(137):
+        net.step()
+    np.testing.assert_allclose(net.ge, g0e * math.exp(-137 * 0.1 / 5.0), rtol=1e-12)
+    np.testing.assert_allclose(net.gi, g0i * math.exp(-137 * 0.1 / 10.0), rtol=1e-12)
+
+
+def test_exponential_euler_matches_ode_solver():
+    rng = np.random.default_rng(0)
+    for _ in range(5):
+        V0 = rng.uniform(-65, -52)
+        ge0, gi0 = rng.uniform(0, 3), rng.uniform(0, 5)
+        net = orc.CobaNet(1, 1, _empty_csr(1), np.array([V0]))
+        net.ge[:] = ge0
+        net.gi[:] = gi0
+        net.step()
+        ge1, gi1 = ge0 * math.exp(-0.1 / 5.0), gi0 * math.exp(-0.1 / 10.0)
+        I = ge1 * (0.0 - V0) + gi1 * (-80.0 - V0) + 20.0
+        sol = solve_ivp(lambda t, v: (-(v - (-60.0)) + 1.0 * I) / 20.0, (0, 0.1), [V0], rtol=1e-12, atol=1e-12)
+        expect = sol.y[0, -1]
+        if expect > -50.0:
+            assert net.V[0] == -60.0
+        else:
+            assert abs(net.V[0] - expect) < 1e-9
+
+
+def test_coba_current_signs():
+    def one_step(ce, ci):
+        net = orc.CobaNet(1, 1, _empty_csr(1), np.array([-58.0]), I_ext=0.0)
+        net.ye[:] = ce
+        net.yi[:] = ci
+        net.step()
+        return net.V[0]
+    base = one_step(0, 0)
+    assert one_step(3, 0) > base
+    assert one_step(0, 3) < base
+
+
+def test_isolated_neuron_interspike_interval():
+    n = 3
+    net = orc.CobaNet(n, 2, _empty_csr(n), np.full(n, -60.0))
+    out = net.run(2000, raster=True)
+    for i in range(n):
+        t = np.nonzero(out["raster"][:, i])[0] + 1            # 1-based step numbers
+        # V_m = -40 - 20 a^m crosses -50 when a^m < 1/2: m* = ceil(200 ln 2) = 139
+        assert t[0] == 139
+        assert np.all(np.diff(t) == 139 + 50)                  # 50 clamped steps + 139 integrating
+        assert len(t) == 1 + (2000 - 139) // 189
+
+
+def test_refractory_clamp_holds_reset_value():
+    net = orc.CobaNet(1, 1, _empty_csr(1), np.array([-60.0]))
+    for _ in range(139):
+        spk = net.step()
+    assert spk[0] == 1 and net.V[0] == -60.0 and net.ref[0] == 50
+    for k in range(50):
+        net.ye[:] = 5.0                                         # strong input does not move V
+        spk = net.step()
+        assert spk[0] == 0 and net.V[0] == -60.0
+    # the conductance built up during the clamp now drives the neuron over threshold at once
+    assert net.step()[0] == 1
+
+
+def test_alignpost_merging_exact():
+    n, n_e = 60, 48
+    ip, ix = wl.random_csr(n, n, 0.1, seed=3)
+    V0 = wl.coba_v0(n, seed=4).astype(np.float64)
+    net = orc.CobaNet(n, n_e, ("csr", ip, ix, None), V0)
+    T = 300
+    rows = np.repeat(np.arange(n), np.diff(ip))
+    g_syn = np.zeros(len(ix))                 # one conductance per synapse (Appendix F)
+    a_e, a_i = math.exp(-0.1 / 5.0), math.exp(-0.1 / 10.0)
+    is_e = rows < n_e
+    prev = np.zeros(n, np.uint8)
+    total = 0
+    for _ in range(T):
+        g_syn = np.where(is_e, g_syn * a_e, g_syn * a_i)
+        g_syn += np.where(prev[rows] == 1, np.where(is_e, 0.6, 6.7), 0.0)
+        spk = net.step()
+        ge_sum = np.bincount(ix[is_e], weights=g_syn[is_e], minlength=n)
+        gi_sum = np.bincount(ix[~is_e], weights=g_syn[~is_e], minlength=n)
+        np.testing.assert_allclose(net.ge, ge_sum, rtol=1e-12, atol=1e-12)
+        np.testing.assert_allclose(net.gi, gi_sum, rtol=1e-12, atol=1e-12)
+        prev = spk
+        total += spk.sum()
+    assert total > 0
+
+
+def test_event_totals_and_refractoriness_in_network():
+    n, n_e = 4000, 3200
+    K = orc.jit_K(0.02)
+    se, si = orc.projection_seed(2024, 0), orc.projection_seed(2024, 1)
+    net = orc.CobaNet(n, n_e, ("jit", se, si, K), wl.coba_v0(n, seed=7))
+    out = net.run(600, raster=True, events=True)
+    ras = out["raster"]
+    lens_e = orc.jit_row_lengths(se, K, n_e, n)
+    lens_i = orc.jit_row_lengths(si, K, n - n_e, n)
+    lens = np.concatenate([lens_e, lens_i])
+    assert np.array_equal(out["events"], ras.astype(np.int64) @ lens)
+    assert np.array_equal(out["spikes_e"], ras[:, :n_e].sum(1))
+    # no neuron fires twice within ref_steps + 1 = 51 steps
+    for i in range(0, n, 97):
+        t = np.nonzero(ras[:, i])[0]
+        assert np.all(np.diff(t) >= 51)
+    assert ras.sum() > 0
+
+
+def test_stored_csr_equals_jit_network():
+    """Materialising the JIT rows as a CSR gives the same trajectory bit for bit."""
+    n, n_e = 1000, 800
+    K = orc.jit_K(80.0 / n)
+    se, si = orc.projection_seed(5, 0), orc.projection_seed(5, 1)
+    ipe, ixe, _ = orc.jit_materialize(se, K, n_e, n)
+    ipi, ixi, _ = orc.jit_materialize(si, K, n - n_e, n)
+    ip = np.concatenate([ipe, ipi[1:] + ipe[-1]])
+    ix = np.concatenate([ixe, ixi])
+    V0 = wl.coba_v0(n, seed=7)
+    a = orc.CobaNet(n, n_e, ("jit", se, si, K), V0).run(300, raster=True)
+    b = orc.CobaNet(n, n_e, ("csr", ip, ix, None), V0).run(300, raster=True)
+    assert np.array_equal(a["raster"], b["raster"])
