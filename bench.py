@@ -1,0 +1,422 @@
+#!/usr/bin/env python3
+"""Benchmark: synaptic events/s and simulation steps/s of the scaled COBA E/I
+network (Appendix N Listing S6 scaled to N = 4e6 neurons, 80/20 E/I, fixed
+connection probability p = 80/N, i.e. 80 synapses per neuron on average,
+dt = 0.1 ms) on one GB300.
+
+One bench step = one simulated time step of the whole hot path: the fused
+LIF / conductance / threshold / compaction pass over all neurons and the
+event-driven delivery of that step's spikes through the connectivity.  The
+headline `value` uses stored CSR (int64 indptr, int32 indices, FP32 weights
+w_e = 0.6 / w_i = 6.7 stored per synapse, FP32 accumulation); the JIT form and
+the integer-count stored form are reported under `variants`.
+
+Timing: W warm-up steps, then exactly K steps run by bp_simulate (a captured
+CUDA graph), bracketed by a barrier and cuda.synchronize(), timed with CUDA
+events on the launching stream; max over ranks.  The connectivity (2.6 GB) and
+state (96 MB) exceed L2 together; the state is re-read every step, as in any
+time-stepped simulation, and L2 is not flushed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_NEURONS = 4_000_000
+N_EXC = 3_200_000
+SEED = 2024
+V0_SEED = 7
+DT_MS = 0.1
+WORKLOAD = "scaled COBA E/I network, N=4e6 (80/20), p=80/N, dt=0.1 ms"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10000)
+    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- helpers
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def lif_traffic_record():
+    """Per-launch DRAM traffic of the neuron pass from the committed ncu summary,
+    valid only while the kernel source is unchanged (hash recorded there)."""
+    src = os.path.join(ROOT, "paper_2311_05106_gb300", "csrc", "lif.cu")
+    rec = os.path.join(ROOT, "profiles", "lif_step_N4e6_traffic.txt")
+    if not (os.path.exists(src) and os.path.exists(rec)):
+        return None
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    vals = {}
+    for line in open(rec):
+        if ":" in line and not line.startswith("#"):
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("lif_cu_sha256_16") != h:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+# bytes the neuron pass must move per neuron: read V, g_e, g_i, ref, and the
+# two event accumulators (6 x 4 B); write V, g_e, g_i (3 x 4 B)
+LIF_BYTES_PER_NEURON = 36
+
+
+def build_network(torch, B, conn, weights):
+    import numpy as np
+    from paper_2311_05106_gb300 import workloads as wl
+    from paper_2311_05106_gb300.network import CobaNetwork, materialize_network_csr
+    V0 = wl.coba_v0(N_NEURONS, seed=V0_SEED)
+    p = 80.0 / N_NEURONS
+    csr = None
+    if conn == "csr":
+        csr = materialize_network_csr(SEED, p, N_NEURONS, N_EXC,
+                                      data_dtype=torch.float32 if weights == "f32" else None)
+    net = CobaNetwork(N_NEURONS, N_EXC, conn=conn, seed=SEED, p=p, V0=V0, csr=csr)
+    return net, np.asarray(V0)
+
+
+def time_simulate(torch, net, steps, warmup, dist=None):
+    stream = torch.cuda.current_stream()
+    net.simulate(warmup)
+    before = net.totals.clone()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    net.simulate(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    d = (net.totals - before).cpu().numpy()
+    return ms, int(d[2]), int(d[0] + d[1])
+
+
+def launches_in_simulate(steps, host_step_before):
+    """Kernels bp_simulate enqueues: two per step, one chunk-advance per 64-step
+    graph, one per leftover group, two record set-ups."""
+    n = 2
+    done = 0
+    if host_step_before % 2 == 1 and steps > 0:
+        n += 3
+        done = 1
+    chunks = (steps - done) // 64
+    n += chunks * (2 * 64 + 1)
+    rem = steps - done - chunks * 64
+    if rem > 0:
+        n += 2 * rem + 1
+    return n
+
+
+def lif_kernel_time(torch, B, net, reps=50):
+    """Average duration of the neuron-pass kernel (bp_lif_step on the network's
+    state), CUDA events around each launch on the launching stream."""
+    stream = torch.cuda.current_stream()
+    sl = torch.zeros(N_NEURONS, dtype=torch.int32, device="cuda")
+    ns = torch.zeros(1, dtype=torch.int32, device="cuda")
+    times = []
+    for _ in range(reps):
+        ns.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        B.bp_lif_step(net.params, N_EXC, net.V, net.ge, net.gi, net.ref, net.ye, net.yi, sl, ns)
+        b.record(stream)
+        times.append((a, b))
+    torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in times]
+    return statistics.mean(ms[5:]) if len(ms) > 5 else statistics.mean(ms)
+
+
+def e2e_run(torch, net, V0, steps):
+    """End to end through the public API: upload the initial state from pinned
+    host memory, simulate `steps`, download the per-step spike record and the
+    final potentials; all inside the timed region."""
+    import numpy as np
+    f32 = torch.float32
+    hV = torch.from_numpy(np.ascontiguousarray(V0, np.float32)).pin_memory()
+    hz = torch.zeros(N_NEURONS, dtype=f32).pin_memory()
+    hr = torch.zeros(N_NEURONS, dtype=torch.int32).pin_memory()
+    rec = torch.zeros((steps, 2), dtype=torch.int32, device="cuda")
+    hrec = torch.zeros((steps, 2), dtype=torch.int32).pin_memory()
+    hVout = torch.zeros(N_NEURONS, dtype=f32).pin_memory()
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    net.V.copy_(hV, non_blocking=True)
+    net.ge.copy_(hz, non_blocking=True)
+    net.gi.copy_(hz, non_blocking=True)
+    net.ref.copy_(hr, non_blocking=True)
+    net.reset_counters()
+    net.simulate(steps, rec)
+    hrec.copy_(rec, non_blocking=True)
+    hVout.copy_(net.V, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    events = int(net.totals[2].item())
+    h2d = 4 * 4 * N_NEURONS
+    d2h = 8 * steps + 4 * N_NEURONS
+    return ms, events, h2d, d2h
+
+
+# ----------------------------------------------------------------- oracle legs
+def oracle_sample(budget_s, n_sample=None):
+    """The FP64 oracle (single thread, as it stands) on the same E/I network:
+    JIT connectivity (the matrix the stored CSR materialises), from the same
+    seeded V0 recipe, for as many steps as fit `budget_s`."""
+    import numpy as np
+    import oracle as orc
+    from paper_2311_05106_gb300 import workloads as wl
+    n = N_NEURONS if n_sample is None else n_sample
+    n_e = (4 * n) // 5
+    p = 80.0 / n
+    K = orc.jit_K(p)
+    net = orc.CobaNet(n, n_e, ("jit", orc.projection_seed(SEED, 0), orc.projection_seed(SEED, 1), K),
+                      wl.coba_v0(n, seed=V0_SEED).astype(np.float64))
+    steps, events = 0, 0
+    t0 = time.perf_counter()
+    while True:
+        out = net.run(1, events=True)
+        events += int(out["events"][0])
+        steps += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return dict(value=events / dt, steps=steps, seconds=dt, n=n)
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    # each reference step is a bounded sample: one oracle step of the same
+    # network family (in-degree 80) at a size that keeps K steps within ~2 min
+    import numpy as np  # noqa: F401
+    import oracle as orc
+    from paper_2311_05106_gb300 import workloads as wl
+    budget = 120.0
+    per_neuron_step_s = 1.5e-7          # oracle cost per neuron-step incl. its events
+    n = int(budget / max(args.steps + args.warmup, 1) / per_neuron_step_s)
+    n = max(2000, min(N_NEURONS, n - n % 5))
+    n_e = (4 * n) // 5
+    p = 80.0 / n
+    K = orc.jit_K(p)
+    net = orc.CobaNet(n, n_e, ("jit", orc.projection_seed(SEED, 0), orc.projection_seed(SEED, 1), K),
+                      wl.coba_v0(n, seed=V0_SEED).astype("float64"))
+    net.run(args.warmup)
+    t0 = time.perf_counter()
+    out = net.run(args.steps, events=True)
+    dt = time.perf_counter() - t0
+    ev = int(out["events"].sum())
+    value = ev / dt
+    line = {
+        "impl": "reference", "metric": "synaptic_events_per_s", "value": value, "unit": "events/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample_neurons": n},
+        "cpu_baseline": {"value": value, "unit": "events/s", "cores": 1, "kind": "oracle",
+                         "sample": "FP64 oracle, one thread: the same E/I network family (in-degree 80, JIT rows) "
+                                   "at n=%d neurons, %d steps after %d warm-up steps" % (n, args.steps, args.warmup)},
+        "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ----------------------------------------------------------------- main
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    rank, world, local = dist_env()
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as tdist
+        torch.cuda.set_device(local)
+        tdist.init_process_group("nccl")
+        dist = tdist
+    else:
+        torch.cuda.set_device(0)
+    from paper_2311_05106_gb300 import binding as B
+    B.lib()
+
+    # ---- headline: stored CSR, FP32 weights
+    net, V0 = build_network(torch, B, "csr", "f32")
+    net.simulate(3)  # builds and caches the CUDA graph outside the timed region
+    net.reset_counters()
+    host_before = 3
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms, events, spikes = time_simulate(torch, net, args.steps, args.warmup, dist)
+    clk = clocks.stop()
+    launches = launches_in_simulate(args.steps, host_before + args.warmup)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        ev = torch.tensor([events], dtype=torch.float64, device="cuda")
+        dist.all_reduce(ev)
+        events = int(ev.item())
+    value = events / (ms * 1e-3)
+    steps_per_s = args.steps / (ms * 1e-3)
+
+    # ---- roofline of the dominant kernel (the neuron pass)
+    lif_ms = lif_kernel_time(torch, B, net)
+    alg_bytes = LIF_BYTES_PER_NEURON * N_NEURONS
+    achieved = alg_bytes / (lif_ms * 1e-3) / 1e9
+    peak, peak_kind = peaks()
+    roofline = {"bound": "hbm", "kernel": "k_lif_step", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": lif_traffic_record(), "peak_source": peak_kind,
+                "lif_us_per_launch": lif_ms * 1e3, "alg_bytes_per_launch": alg_bytes}
+
+    # ---- end to end through the public API (host buffers)
+    e2e_ms, e2e_events, h2d, d2h = e2e_run(torch, net, V0, args.steps)
+    e2e = {"value": e2e_events / (e2e_ms * 1e-3), "unit": "events/s",
+           "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps}
+    net.close()
+    del net
+    torch.cuda.empty_cache()
+
+    variants = {}
+    if not args.no_variants:
+        for name, conn, w in (("csr_counts", "csr", None), ("jit_counts", "jit", None)):
+            v, _ = build_network(torch, B, conn, w)
+            v.simulate(3)
+            v.reset_counters()
+            vms, vev, _ = time_simulate(torch, v, args.steps, args.warmup)
+            variants[name] = {"events_per_s": vev / (vms * 1e-3), "steps_per_s": args.steps / (vms * 1e-3),
+                              "ms_per_step": vms / args.steps}
+            v.close()
+            del v
+            torch.cuda.empty_cache()
+        variants["csr_f32"] = {"events_per_s": value, "steps_per_s": steps_per_s, "ms_per_step": ms / args.steps}
+        for k in variants:
+            variants[k]["vs_plain_f32"] = variants[k]["events_per_s"] / value
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        s = oracle_sample(15.0)
+        cpu = {"value": s["value"], "unit": "events/s", "cores": 1, "kind": "oracle",
+               "sample": "FP64 oracle, one thread, the same N=4e6 network (JIT rows = the stored matrix) from the "
+                         "same V0, first %d steps (%.1f s)" % (s["steps"], s["seconds"])}
+
+    line = {
+        "metric": "synaptic_events_per_s", "value": value, "unit": "events/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "connectivity": "stored CSR, int32 indices, FP32 weights",
+                   "neurons": N_NEURONS, "sim_steps": args.steps,
+                   "l2": "connectivity 2.6 GB + state 96 MB exceed L2; no flush between steps (state re-read each step)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "sim_steps_per_s": steps_per_s, "spikes_in_timed_region": spikes, "events_in_timed_region": events,
+        "firing_rate_hz": spikes / (N_NEURONS * args.steps * DT_MS * 1e-3),
+        "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk, "variants": variants,
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

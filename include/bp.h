@@ -1,0 +1,338 @@
+/*
+ * bp.h -- C ABI of libbp, a GB300 (sm_103a) library for the event-driven
+ * spiking-network hot path of BrainPy (Wang et al., ICLR 2024, "A
+ * differentiable brain simulator bridging brain simulation and brain-inspired
+ * computing").
+ *
+ * Conventions (apply to every entry point unless its comment says otherwise)
+ * ---------------------------------------------------------------------------
+ * Memory.    Every array pointer is DEVICE memory owned by the caller and must
+ *            stay valid until the stream work that uses it has finished.  The
+ *            library allocates device memory only inside the *_create calls
+ *            and frees it in the matching *_destroy.
+ * Streams.   Every call is asynchronous on `stream` (a cudaStream_t; NULL is
+ *            the legacy default stream) and returns after enqueueing.
+ * Layout.    Vectors are dense and contiguous.  Sparse matrices are CSR with
+ *            PRESYNAPTIC rows: indptr int64 [n_pre + 1] (indptr[0] = 0,
+ *            non-decreasing), indices int32 [nnz] in [0, n_post).  Calls that
+ *            use the post-column tile index also need each row's indices
+ *            sorted ascending (canonical CSR; the JIT materialiser produces it).
+ * Weights.   BP_W_HOMO (one scalar for every stored entry), BP_W_F32 or
+ *            BP_W_BF16 arrays [nnz]; accumulation is always FP32, or exact
+ *            int32 event counts where a call says so.
+ * Output.    Outputs ACCUMULATE (y += ...) unless BP_OVERWRITE is set in flags.
+ * Errors.    Every call returns a bp_status; nothing crosses the ABI as a C++
+ *            exception.  Argument errors are detected on the host before any
+ *            work is enqueued (BP_ERR_INVALID, nothing launched).  CUDA launch
+ *            errors return BP_ERR_CUDA.  Conditions detected on the device
+ *            (a bounded wait that ran out, a bounds check) set a sticky device
+ *            status word, reported by bp_sync_status().  bp_last_error()
+ *            returns a human-readable message for the calling thread's last
+ *            failure.
+ * Threads.   Calls on different streams may run concurrently if they write
+ *            disjoint memory.
+ */
+#ifndef BP_H
+#define BP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* bp_stream_t; /* identical to cudaStream_t */
+
+typedef enum {
+    BP_OK = 0,
+    BP_ERR_INVALID = 1,     /* bad argument (null pointer, size, kind) */
+    BP_ERR_CUDA = 2,        /* a CUDA runtime call failed */
+    BP_ERR_TIMEOUT = 3,     /* a bounded device-side wait ran out */
+    BP_ERR_OOM = 4,         /* a *_create could not allocate */
+    BP_ERR_UNSUPPORTED = 5, /* valid but not supported (e.g. no sm_103a device) */
+    BP_ERR_DEVICE = 6       /* a device-side check failed (see bp_last_error) */
+} bp_status;
+
+typedef enum { BP_W_HOMO = 0, BP_W_F32 = 1, BP_W_BF16 = 2 } bp_wkind;
+
+/* Weight law of a just-in-time (JIT) connectivity descriptor (Section 3.2,
+ * Appendix C): homogeneous w0; uniform in [w0, w1); normal with mean w0 and
+ * standard deviation w1. */
+typedef enum { BP_JIT_HOMO = 0, BP_JIT_UNIFORM = 1, BP_JIT_NORMAL = 2 } bp_jit_wkind;
+
+#define BP_OVERWRITE 1u     /* zero the output before accumulating */
+#define BP_ACC_GLOBAL 2u    /* force direct atomic accumulation in L2 (no shared-memory tiles) */
+#define BP_ACC_SHARED 4u    /* force shared-memory tile accumulation */
+
+/* --------------------------------------------------------------------------
+ * Library
+ * ------------------------------------------------------------------------ */
+
+/* Version string "bp <major>.<minor> sm_103a". Never NULL. */
+const char* bp_version(void);
+
+/* Message of the calling thread's most recent failure ("" if none). */
+const char* bp_last_error(void);
+
+/* Waits for `stream`, then reads and clears the library's sticky device
+ * status word.  Returns BP_ERR_TIMEOUT / BP_ERR_DEVICE if a kernel recorded a
+ * device-side failure since the last call, BP_ERR_CUDA if the stream reported
+ * an error, BP_OK otherwise. */
+bp_status bp_sync_status(bp_stream_t stream);
+
+/* Shared-memory accumulator capacity (post neurons per tile) the event
+ * products use for `wkind` outputs: int32 counts and FP32 sums both take 4
+ * bytes per post neuron. */
+int32_t bp_tile_cols(void);
+
+/* --------------------------------------------------------------------------
+ * a1-a4. LIF / exponential conductance synapse / COBA step.
+ * Appendix E (exponential synapse: g <- exp(-dt/tau) g, then g <- g + w per
+ * delivered spike), Appendix F (tau dV/dt = -(V - V_rest) + R G with
+ * G = -sum g (V - E); spike when V > V_th; V <- V_reset), Appendix N
+ * Listing S6 (E/I COBA network: tau = 20 ms, tau_ref = 5 ms, E_e = 0 mV with
+ * tau_e = 5 ms, E_i = -80 mV with tau_i = 10 ms, input 20 per step).
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    double dt;              /* ms */
+    double tau_m, tau_e, tau_i, tau_ref;    /* ms */
+    double V_rest, V_th, V_reset, E_e, E_i; /* mV */
+    double R;               /* membrane resistance */
+    double I_ext;           /* constant input added every step */
+    double w_e, w_i;        /* conductance increment per delivered E / I event */
+} bp_coba_params;
+
+/* Fills `p` with the COBA E/I parameters of Appendix N Listing S6
+ * (dt = 0.1 ms, V_rest = V_reset = -60, V_th = -50, tau_m = 20, tau_ref = 5,
+ * tau_e = 5, tau_i = 10, E_e = 0, E_i = -80, R = 1, I_ext = 20, w_e = 0.6,
+ * w_i = 6.7).  Returns BP_ERR_INVALID if p is NULL. */
+bp_status bp_coba_params_default(bp_coba_params* p);
+
+/* One time step for neurons [0, n), each neuron independently:
+ *   ge <- ge exp(-dt/tau_e) + dge,  gi <- gi exp(-dt/tau_i) + dgi,
+ *     where dge = w_e ye[i] and dgi = w_i yi[i] if y_is_count (ye, yi are
+ *     int32 event counts), else dge = ye[i], dgi = yi[i] (FP32 weighted sums);
+ *     ye[i] and yi[i] are then set to 0;
+ *   I = ge (E_e - V) + gi (E_i - V) + I_ext (+ I_vec[i] if I_vec != NULL),
+ *     with V from before this step;
+ *   if ref[i] > 0: ref[i] -= 1, V unchanged, no spike;
+ *   else V <- V_inf + (V - V_inf) exp(-dt/tau_m), V_inf = V_rest + R I
+ *     (exponential Euler, I held over the step); if V > V_th: spike,
+ *     V <- V_reset, ref[i] <- round(tau_ref / dt).
+ * The decay factors are evaluated in FP64 on the host and rounded to FP32;
+ * the state arithmetic is FP32.
+ * Arrays: V, ge, gi float [n]; ref int32 [n]; ye, yi int32 or float [n].
+ * Outputs: spk uint8 [n] (nullable) = 1 where the neuron spiked this step;
+ *   spike ids are APPENDED to spike_list int32 [n] at positions reserved by
+ *   an atomic add on *n_spikes (the caller zeroes *n_spikes beforehand; the
+ *   order of ids in the list is unspecified);
+ *   spike_totals int64 [2] (nullable) += number of spikes among neurons
+ *   [0, n_e) and [n_e, n).
+ * Errors: BP_ERR_INVALID for n < 0, n_e outside [0, n] or a required NULL. */
+bp_status bp_lif_step(const bp_coba_params* p, int64_t n, int64_t n_e,
+                      float* V, float* ge, float* gi, int32_t* ref,
+                      void* ye, void* yi, int32_t y_is_count,
+                      const float* I_vec,
+                      uint8_t* spk, int32_t* spike_list, int32_t* n_spikes,
+                      int64_t* spike_totals, bp_stream_t stream);
+
+/* Compacts a dense event vector (Appendix B's `events`) into a spike list:
+ * appends every i with events[i] != 0 to spike_list int32 [n] at positions
+ * reserved by an atomic add on *n_spikes (caller zeroes it; order
+ * unspecified). */
+bp_status bp_spike_compact(int64_t n, const uint8_t* events, int32_t* spike_list,
+                           int32_t* n_spikes, bp_stream_t stream);
+
+/* --------------------------------------------------------------------------
+ * a5. Event-driven CSR product (Appendix B; Section 4.1 operator benchmark).
+ * For every spiking presynaptic row i in spike_list[0 .. *n_spikes):
+ *   for j in [indptr[i], indptr[i+1]): y[indices[j]] += w_j
+ * i.e. y = W^T s with W stored presynaptic-row-major (Appendix B's listing,
+ * read with the synapse index j as the column subscript).
+ * w_j = data[j] (F32 / BF16) or w_homo (HOMO).  If y_is_count (HOMO only), y
+ * is int32 and receives exact event counts (w_homo is not applied);
+ * otherwise y is float.
+ * spike_list int32 [max_spikes] with distinct ids in [0, n_pre); *n_spikes is
+ * read on the device (at most max_spikes are used).
+ * tile_ptr/tile_cols: optional post-column tile index from
+ * bp_csr_tile_index() (NULL/0 if none); needed for shared-memory tile
+ * accumulation when n_post > bp_tile_cols().
+ * Accumulation order is unspecified: FP32 results are deterministic only up to
+ * rounding; int32 counts are exact.
+ * Errors: BP_ERR_INVALID for negative sizes, NULL required pointers,
+ * y_is_count with a non-HOMO kind, or a tile index built for other sizes. */
+bp_status bp_event_csrmv(int64_t n_pre, int64_t n_post,
+                         const int64_t* indptr, const int32_t* indices,
+                         const void* data, int32_t wkind, float w_homo,
+                         const int32_t* spike_list, const int32_t* n_spikes, int64_t max_spikes,
+                         void* y, int32_t y_is_count,
+                         const int32_t* tile_ptr, int32_t tile_cols,
+                         uint32_t flags, bp_stream_t stream);
+
+/* As bp_event_csrmv, but from the dense event vector events uint8 [n_pre]
+ * (the paper's form).  `workspace` is caller-owned device scratch of
+ * bp_event_csrmv_dense_workspace_bytes(n_pre) bytes (spike list + count). */
+size_t bp_event_csrmv_dense_workspace_bytes(int64_t n_pre);
+bp_status bp_event_csrmv_dense(int64_t n_pre, int64_t n_post,
+                               const int64_t* indptr, const int32_t* indices,
+                               const void* data, int32_t wkind, float w_homo,
+                               const uint8_t* events, void* workspace,
+                               void* y, int32_t y_is_count,
+                               const int32_t* tile_ptr, int32_t tile_cols,
+                               uint32_t flags, bp_stream_t stream);
+
+/* Post-column tile index for shared-memory accumulation.  With
+ * S = ceil(n_post / tile_cols) tiles, writes tile_ptr int32 [n_pre * (S + 1)]:
+ * tile_ptr[i (S+1) + s] = (first position in row i whose column is
+ * >= s tile_cols) - indptr[i], for s = 0..S (so entry S is the row length).
+ * Requires sorted rows and row lengths < 2^31.  tile_cols must be a positive
+ * multiple of 32 no larger than bp_tile_cols(). */
+int64_t bp_csr_tile_index_size(int64_t n_pre, int64_t n_post, int32_t tile_cols);
+bp_status bp_csr_tile_index(int64_t n_pre, int64_t n_post, const int64_t* indptr,
+                            const int32_t* indices, int32_t tile_cols, int32_t* tile_ptr,
+                            bp_stream_t stream);
+
+/* Gather ("transpose") form over the same CSR, all rows (Section 3.1: every
+ * operator has reverse-mode rules; this is the product with W rather than
+ * W^T):  y_pre[i] += sum_{j in row i} w_j x_post[indices[j]].
+ * x_post float [n_post], y_pre float [n_pre]. */
+bp_status bp_event_csrmv_t(int64_t n_pre, int64_t n_post,
+                           const int64_t* indptr, const int32_t* indices,
+                           const void* data, int32_t wkind, float w_homo,
+                           const float* x_post, float* y_pre,
+                           uint32_t flags, bp_stream_t stream);
+
+/* Reverse mode of bp_event_csrmv for a loss L with dy = dL/dy (Section 3.1):
+ *   dw[j] += dy[indices[j]] for every entry j of every spiking row (if dw is
+ *   non-NULL; float [nnz]; each spiking row must appear once);
+ *   dx_pre[i] += sum_j w_j dy[indices[j]] for every row i (if dx_pre is
+ *   non-NULL; float [n_pre]: the gradient with respect to the spike vector). */
+bp_status bp_event_csrmv_bwd(int64_t n_pre, int64_t n_post,
+                             const int64_t* indptr, const int32_t* indices,
+                             const void* data, int32_t wkind, float w_homo,
+                             const int32_t* spike_list, const int32_t* n_spikes, int64_t max_spikes,
+                             const float* dy, float* dw, float* dx_pre,
+                             bp_stream_t stream);
+
+/* --------------------------------------------------------------------------
+ * a6. Just-in-time connectivity (Section 3.2, Appendix C).
+ * Row i's targets are q_0 = U_0 - 1, q_{k+1} = q_k + U_{k+1} while
+ * q < n_post, with U_k = 1 + floor(x_k K / 2^32) uniform on [1, K],
+ * K = ceil(2/p - 1) (at least 1), and x_k word (k mod 4) of
+ * Philox4x32-10(key = seed, counter = (k div 4, i, 0, 0)).
+ * Weights: HOMO w0; UNIFORM w0 + (w1 - w0) u, u = (x'_k >> 8) 2^-24 from the
+ * stream-1 counter (k div 4, i, 1, 0); NORMAL w0 + w1 sqrt(-2 ln u1)
+ * cos(2 pi u2) from words 2(k mod 2), 2(k mod 2)+1 of the stream-2 block
+ * (k div 2, i, 2, 0), u1 = ((a >> 8) + 1) 2^-24, u2 = (b >> 8) 2^-24.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    uint64_t seed;
+    double p;       /* connection probability in (0, 1] */
+    int64_t K;      /* gap range, filled by bp_jit_desc_init */
+    int32_t wkind;  /* bp_jit_wkind */
+    float w0, w1;
+} bp_jit_desc;
+
+/* Fills d and computes K = ceil(2/p - 1) in FP64 (with a 1e-12 relative
+ * guard so that p = a/b representing 2/(K+1) yields K).  BP_ERR_INVALID if p
+ * is not in (0, 1] or wkind unknown. */
+bp_status bp_jit_desc_init(bp_jit_desc* d, uint64_t seed, double p, int32_t wkind, float w0, float w1);
+
+/* Event-driven JIT product (Appendix C listing, per-row streams):
+ * y[q] += w for every target q of every row in spike_list[0 .. *n_spikes).
+ * y int32 exact counts if y_is_count (HOMO only) else float. */
+bp_status bp_jitconn_event_mv(const bp_jit_desc* d, int64_t n_pre, int64_t n_post,
+                              const int32_t* spike_list, const int32_t* n_spikes, int64_t max_spikes,
+                              void* y, int32_t y_is_count, uint32_t flags, bp_stream_t stream);
+
+/* Reverse mode with respect to the spike vector (weights are static, so
+ * there is no weight gradient, Section 3.2): dx_pre[i] += sum over row i's
+ * targets q of w dy[q], for all rows i. */
+bp_status bp_jitconn_event_mv_bwd(const bp_jit_desc* d, int64_t n_pre, int64_t n_post,
+                                  const float* dy, float* dx_pre, bp_stream_t stream);
+
+/* Non-event JIT product with a dense vector (Section 4.2, mv_prob_uniform /
+ * mv_prob_normal): y_post[q] += w x_pre[i] for every target q of every row i. */
+bp_status bp_jitconn_mv(const bp_jit_desc* d, int64_t n_pre, int64_t n_post,
+                        const float* x_pre, float* y_post, uint32_t flags, bp_stream_t stream);
+
+/* Materialises the JIT matrix as CSR.  First call with indices == NULL: writes
+ * indptr int64 [n_pre + 1] (row lengths, then an in-place prefix sum).  Then
+ * call again with indices int32 [indptr[n_pre]] (and data float/bf16 [nnz] if
+ * data_kind != BP_W_HOMO) to fill the rows (sorted ascending). */
+bp_status bp_jit_materialize_csr(const bp_jit_desc* d, int64_t n_pre, int64_t n_post,
+                                 int64_t* indptr, int32_t* indices, void* data, int32_t data_kind,
+                                 bp_stream_t stream);
+
+/* Projection seed of the E/I network: output `projection` (0 = E rows,
+ * 1 = I rows) of SplitMix64 started at net_seed (Steele et al. 2014). */
+uint64_t bp_projection_seed(uint64_t net_seed, int32_t projection);
+
+/* --------------------------------------------------------------------------
+ * a7/a8. COBA E/I network: step and simulate (Appendix N Listing S6).
+ * Neurons [0, n_e) are excitatory, [n_e, n) inhibitory.  Each step is
+ * bp_lif_step followed by the delivery of this step's spikes: E rows into
+ * ye, I rows into yi (one merged conductance per neuron and synapse type,
+ * Section 3.3 AlignPost), to be consumed by the next step.
+ * ------------------------------------------------------------------------ */
+enum { BP_CONN_CSR = 0, BP_CONN_JIT = 1 };
+
+typedef struct {
+    int64_t n, n_e;
+    bp_coba_params coba;
+    int32_t conn_kind;              /* BP_CONN_CSR or BP_CONN_JIT */
+    /* BP_CONN_CSR: one CSR over all n presynaptic rows (row i < n_e: E
+     * projection row i; row i >= n_e: I projection row i - n_e). */
+    const int64_t* indptr;
+    const int32_t* indices;
+    const void* data;               /* NULL or wkind == BP_W_HOMO: weights w_e / w_i, int32 counts */
+    int32_t wkind;
+    const int32_t* tile_ptr;        /* optional, see bp_csr_tile_index */
+    int32_t tile_cols;
+    /* BP_CONN_JIT: homogeneous rows with seeds bp_projection_seed(seed, 0/1) */
+    uint64_t seed;
+    double p;
+    /* state, device, caller-owned */
+    float* V;                       /* [n] */
+    float* ge;                      /* [n] */
+    float* gi;                      /* [n] */
+    int32_t* ref;                   /* [n] */
+    void* ye;                       /* [n] int32 counts (homogeneous) or float sums */
+    void* yi;                       /* [n] */
+    int32_t* spike_list;            /* [n] scratch: spikes of the current step */
+    int32_t* n_spikes;              /* [2] scratch: spike counters (two alternating slots) */
+    int64_t* totals;                /* [4] cumulative: spikes E, spikes I, synaptic events, steps */
+    uint8_t* spk;                   /* [n] nullable: spike flags of the last step */
+} bp_net_desc;
+
+typedef struct bp_net bp_net;
+
+/* Validates `desc`, copies it, derives the decay factors and JIT seeds.
+ * Allocates only host memory (the CUDA graph of bp_simulate is built on its
+ * first call).  *out receives the handle. */
+bp_status bp_network_create(const bp_net_desc* desc, bp_net** out);
+
+/* Zeroes the counters (n_spikes, totals) and the event accumulators. */
+bp_status bp_network_reset_counters(bp_net* net, bp_stream_t stream);
+
+/* One time step (a1-a5/a6 above). */
+bp_status bp_network_step(bp_net* net, bp_stream_t stream);
+
+/* T steps.  On its first call builds and caches a CUDA graph of a chunk of
+ * steps (captured on a private stream), then launches it on `stream`;
+ * record int32 [T][2] (nullable) receives the E and I spike counts of each
+ * step. */
+bp_status bp_simulate(bp_net* net, int64_t T, int32_t* record, bp_stream_t stream);
+
+/* Population statistics in FP64 on the device (a8): out double [4] =
+ * {rate of all neurons, E rate, I rate (Hz), synaptic events per step}, from
+ * the int64 totals accumulated since the last reset. */
+bp_status bp_network_stats(bp_net* net, double* out, bp_stream_t stream);
+
+bp_status bp_network_destroy(bp_net* net);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BP_H */

@@ -85,7 +85,7 @@ def _load():
             "orc_event_csr_count": (None, [i64, P, P, P, P]),
             "orc_csrmv_t": (None, [i64, P, P, P, f64, P, P]),
             "orc_event_csrmv_dw": (None, [i64, P, P, P, P, P]),
-            "orc_coba_step": (i64, [P, P, P, P, P, P, P, P, P]),
+            "orc_coba_step": (i64, [P, P, P, P, P, P, P, P, P, P]),
             "orc_coba_run": (None, [P, P, i64, P, P, P, P, P, P, P, P, P, P]),
             "orc_rate_hz": (f64, [i64, i64, i64, f64]),
         }
@@ -264,11 +264,14 @@ class CobaNet:
         self.ye = np.zeros(self.n)
         self.yi = np.zeros(self.n)
 
-    def step(self):
+    def step(self, return_vdec=False):
+        """One step; returns the spike flags (and, if asked, the potential each
+        threshold test saw, NaN for refractory neurons)."""
         spk = np.zeros(self.n, np.uint8)
+        vdec = np.zeros(self.n) if return_vdec else None
         _load().orc_coba_step(ctypes.byref(self.P), ctypes.byref(self.C), _p(self.V), _p(self.ge), _p(self.gi),
-                              _p(self.ref), _p(self.ye), _p(self.yi), _p(spk))
-        return spk
+                              _p(self.ref), _p(self.ye), _p(self.yi), _p(spk), _p(vdec))
+        return (spk, vdec) if return_vdec else spk
 
     def run(self, T, raster=False, events=False):
         se = np.zeros(T, np.int64)

@@ -307,9 +307,11 @@ typedef struct {
 
 /* One time step.  ye / yi hold what the previous step delivered (counts in */
 /* the homogeneous case, weighted sums otherwise) and receive this step's    */
-/* deliveries.  Returns the number of spikes; spk[i] is set to 0/1.          */
+/* deliveries.  Returns the number of spikes; spk[i] is set to 0/1.  vdec    */
+/* (nullable) receives the potential the threshold test saw (NAN while      */
+/* refractory), so callers can tell how close each decision was.            */
 int64_t orc_coba_step(const orc_coba* P, const orc_conn* C, double* V, double* ge, double* gi,
-                      int32_t* ref, double* ye, double* yi, uint8_t* spk)
+                      int32_t* ref, double* ye, double* yi, uint8_t* spk, double* vdec)
 {
     const double a_m = exp(-P->dt / P->tau_m);
     const double a_e = exp(-P->dt / P->tau_e);
@@ -327,6 +329,7 @@ int64_t orc_coba_step(const orc_coba* P, const orc_conn* C, double* V, double* g
         /* COBA current with the pre-update potential */
         double I = ge[i] * (P->E_e - V[i]) + gi[i] * (P->E_i - V[i]) + P->I_ext;
         spk[i] = 0;
+        if (vdec) vdec[i] = NAN;
         if (ref[i] > 0) {
             ref[i] -= 1; /* R12: clamped, V unchanged */
             continue;
@@ -334,6 +337,7 @@ int64_t orc_coba_step(const orc_coba* P, const orc_conn* C, double* V, double* g
         /* R10: exact solution of the linear ODE with I held over the step */
         double V_inf = P->V_rest + P->R * I;
         V[i] = V_inf + (V[i] - V_inf) * a_m;
+        if (vdec) vdec[i] = V[i];
         if (V[i] > P->V_th) { /* R11 */
             spk[i] = 1;
             V[i] = P->V_reset;
@@ -374,7 +378,7 @@ void orc_coba_run(const orc_coba* P, const orc_conn* C, int64_t T, double* V, do
 {
     uint8_t* spk = (uint8_t*)malloc((size_t)P->n);
     for (int64_t t = 0; t < T; ++t) {
-        orc_coba_step(P, C, V, ge, gi, ref, ye, yi, spk);
+        orc_coba_step(P, C, V, ge, gi, ref, ye, yi, spk, NULL);
         int64_t ne = 0, ni = 0, ev = 0;
         for (int64_t i = 0; i < P->n; ++i) {
             if (!spk[i]) continue;

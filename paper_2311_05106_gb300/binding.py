@@ -1,0 +1,313 @@
+"""Thin Python binding of libbp's C ABI (include/bp.h).
+
+Argument marshalling only: every function takes torch CUDA tensors (device
+memory allocated by PyTorch), passes their data pointers and sizes to the C
+entry point of the same name on the current torch CUDA stream, and raises
+``BpError`` on a non-zero status.  No computation of the method happens here.
+
+The library is loaded from the package's ``_build`` directory; if it is
+missing the first call raises (there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+from . import _build
+
+BP_OK = 0
+BP_W_HOMO, BP_W_F32, BP_W_BF16 = 0, 1, 2
+BP_JIT_HOMO, BP_JIT_UNIFORM, BP_JIT_NORMAL = 0, 1, 2
+BP_OVERWRITE, BP_ACC_GLOBAL, BP_ACC_SHARED = 1, 2, 4
+BP_CONN_CSR, BP_CONN_JIT = 0, 1
+
+
+class BpError(RuntimeError):
+    def __init__(self, fn, status, msg):
+        super().__init__("%s returned status %d: %s" % (fn, status, msg))
+        self.status = status
+
+
+c_i64, c_i32, c_u32, c_u64, c_f32, c_f64 = (ctypes.c_int64, ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint64,
+                                            ctypes.c_float, ctypes.c_double)
+VP = ctypes.c_void_p
+
+
+class CobaParams(ctypes.Structure):
+    _fields_ = [("dt", c_f64), ("tau_m", c_f64), ("tau_e", c_f64), ("tau_i", c_f64), ("tau_ref", c_f64),
+                ("V_rest", c_f64), ("V_th", c_f64), ("V_reset", c_f64), ("E_e", c_f64), ("E_i", c_f64),
+                ("R", c_f64), ("I_ext", c_f64), ("w_e", c_f64), ("w_i", c_f64)]
+
+
+class JitDesc(ctypes.Structure):
+    _fields_ = [("seed", c_u64), ("p", c_f64), ("K", c_i64), ("wkind", c_i32), ("w0", c_f32), ("w1", c_f32)]
+
+
+class NetDesc(ctypes.Structure):
+    _fields_ = [("n", c_i64), ("n_e", c_i64), ("coba", CobaParams), ("conn_kind", c_i32),
+                ("indptr", VP), ("indices", VP), ("data", VP), ("wkind", c_i32),
+                ("tile_ptr", VP), ("tile_cols", c_i32),
+                ("seed", c_u64), ("p", c_f64),
+                ("V", VP), ("ge", VP), ("gi", VP), ("ref", VP), ("ye", VP), ("yi", VP),
+                ("spike_list", VP), ("n_spikes", VP), ("totals", VP), ("spk", VP)]
+
+
+_SIGS = {
+    "bp_version": (ctypes.c_char_p, []),
+    "bp_last_error": (ctypes.c_char_p, []),
+    "bp_sync_status": (c_i32, [VP]),
+    "bp_tile_cols": (c_i32, []),
+    "bp_coba_params_default": (c_i32, [ctypes.POINTER(CobaParams)]),
+    "bp_lif_step": (c_i32, [ctypes.POINTER(CobaParams), c_i64, c_i64, VP, VP, VP, VP, VP, VP, c_i32, VP, VP, VP, VP,
+                            VP, VP]),
+    "bp_spike_compact": (c_i32, [c_i64, VP, VP, VP, VP]),
+    "bp_event_csrmv": (c_i32, [c_i64, c_i64, VP, VP, VP, c_i32, c_f32, VP, VP, c_i64, VP, c_i32, VP, c_i32, c_u32,
+                               VP]),
+    "bp_event_csrmv_dense_workspace_bytes": (ctypes.c_size_t, [c_i64]),
+    "bp_event_csrmv_dense": (c_i32, [c_i64, c_i64, VP, VP, VP, c_i32, c_f32, VP, VP, VP, c_i32, VP, c_i32, c_u32,
+                                     VP]),
+    "bp_csr_tile_index_size": (c_i64, [c_i64, c_i64, c_i32]),
+    "bp_csr_tile_index": (c_i32, [c_i64, c_i64, VP, VP, c_i32, VP, VP]),
+    "bp_event_csrmv_t": (c_i32, [c_i64, c_i64, VP, VP, VP, c_i32, c_f32, VP, VP, c_u32, VP]),
+    "bp_event_csrmv_bwd": (c_i32, [c_i64, c_i64, VP, VP, VP, c_i32, c_f32, VP, VP, c_i64, VP, VP, VP, VP]),
+    "bp_jit_desc_init": (c_i32, [ctypes.POINTER(JitDesc), c_u64, c_f64, c_i32, c_f32, c_f32]),
+    "bp_jitconn_event_mv": (c_i32, [ctypes.POINTER(JitDesc), c_i64, c_i64, VP, VP, c_i64, VP, c_i32, c_u32, VP]),
+    "bp_jitconn_event_mv_bwd": (c_i32, [ctypes.POINTER(JitDesc), c_i64, c_i64, VP, VP, VP]),
+    "bp_jitconn_mv": (c_i32, [ctypes.POINTER(JitDesc), c_i64, c_i64, VP, VP, c_u32, VP]),
+    "bp_jit_materialize_csr": (c_i32, [ctypes.POINTER(JitDesc), c_i64, c_i64, VP, VP, VP, c_i32, VP]),
+    "bp_projection_seed": (c_u64, [c_u64, c_i32]),
+    "bp_network_create": (c_i32, [ctypes.POINTER(NetDesc), ctypes.POINTER(VP)]),
+    "bp_network_reset_counters": (c_i32, [VP, VP]),
+    "bp_network_step": (c_i32, [VP, VP]),
+    "bp_simulate": (c_i32, [VP, c_i64, VP, VP]),
+    "bp_network_stats": (c_i32, [VP, VP, VP]),
+    "bp_network_destroy": (c_i32, [VP]),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """The loaded libbp (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    with _lock:
+        if _lib is None:
+            path = library_path()
+            if not os.path.exists(path):
+                raise RuntimeError("libbp.so is not built (%s); run __graft_entry__.build() or "
+                                   "python -m paper_2311_05106_gb300._build" % path)
+            L = ctypes.CDLL(path)
+            for name, (res, args) in _SIGS.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return sorted(_SIGS)
+
+
+def _check(name, status):
+    if status != BP_OK:
+        raise BpError(name, status, lib().bp_last_error().decode())
+
+
+def _p(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor, got a %s tensor" % t.device)
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return VP(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return VP(s.cuda_stream)
+
+
+def _wkind(data):
+    if data is None:
+        return BP_W_HOMO
+    if data.dtype == torch.float32:
+        return BP_W_F32
+    if data.dtype == torch.bfloat16:
+        return BP_W_BF16
+    raise ValueError("weights must be float32 or bfloat16, got %s" % data.dtype)
+
+
+# ------------------------------------------------------------------ library
+def bp_version() -> str:
+    return lib().bp_version().decode()
+
+
+def bp_last_error() -> str:
+    return lib().bp_last_error().decode()
+
+
+def bp_sync_status(stream=None) -> int:
+    return int(lib().bp_sync_status(_stream(stream)))
+
+
+def bp_tile_cols() -> int:
+    return int(lib().bp_tile_cols())
+
+
+def bp_coba_params_default(**overrides) -> CobaParams:
+    p = CobaParams()
+    _check("bp_coba_params_default", lib().bp_coba_params_default(ctypes.byref(p)))
+    for k, v in overrides.items():
+        setattr(p, k, float(v))
+    return p
+
+
+# ------------------------------------------------------------------ a1-a4
+def bp_lif_step(p, n_e, V, ge, gi, ref, ye, yi, spike_list, n_spikes, I_vec=None, spk=None, spike_totals=None,
+                stream=None):
+    counts = 1 if ye.dtype == torch.int32 else 0
+    _check("bp_lif_step", lib().bp_lif_step(ctypes.byref(p), V.numel(), n_e, _p(V), _p(ge), _p(gi), _p(ref), _p(ye),
+                                            _p(yi), counts, _p(I_vec), _p(spk), _p(spike_list), _p(n_spikes),
+                                            _p(spike_totals), _stream(stream)))
+
+
+def bp_spike_compact(events, spike_list, n_spikes, stream=None):
+    _check("bp_spike_compact", lib().bp_spike_compact(events.numel(), _p(events), _p(spike_list), _p(n_spikes),
+                                                      _stream(stream)))
+
+
+# ------------------------------------------------------------------ a5
+def bp_event_csrmv(indptr, indices, data, w_homo, spike_list, n_spikes, y, n_post=None, tile_ptr=None, tile_cols=0,
+                   flags=0, max_spikes=None, stream=None):
+    n_pre = indptr.numel() - 1
+    n_post = y.numel() if n_post is None else n_post
+    counts = 1 if y.dtype == torch.int32 else 0
+    ms = n_pre if max_spikes is None else max_spikes
+    _check("bp_event_csrmv", lib().bp_event_csrmv(n_pre, n_post, _p(indptr), _p(indices), _p(data), _wkind(data),
+                                                  float(w_homo), _p(spike_list), _p(n_spikes), ms, _p(y), counts,
+                                                  _p(tile_ptr), int(tile_cols), int(flags), _stream(stream)))
+
+
+def bp_event_csrmv_dense_workspace_bytes(n_pre) -> int:
+    return int(lib().bp_event_csrmv_dense_workspace_bytes(n_pre))
+
+
+def bp_event_csrmv_dense(indptr, indices, data, w_homo, events, workspace, y, tile_ptr=None, tile_cols=0, flags=0,
+                         stream=None):
+    n_pre = indptr.numel() - 1
+    counts = 1 if y.dtype == torch.int32 else 0
+    _check("bp_event_csrmv_dense", lib().bp_event_csrmv_dense(n_pre, y.numel(), _p(indptr), _p(indices), _p(data),
+                                                              _wkind(data), float(w_homo), _p(events), _p(workspace),
+                                                              _p(y), counts, _p(tile_ptr), int(tile_cols), int(flags),
+                                                              _stream(stream)))
+
+
+def bp_csr_tile_index_size(n_pre, n_post, tile_cols) -> int:
+    return int(lib().bp_csr_tile_index_size(n_pre, n_post, tile_cols))
+
+
+def bp_csr_tile_index(indptr, indices, n_post, tile_cols, tile_ptr, stream=None):
+    _check("bp_csr_tile_index", lib().bp_csr_tile_index(indptr.numel() - 1, n_post, _p(indptr), _p(indices),
+                                                        int(tile_cols), _p(tile_ptr), _stream(stream)))
+
+
+def bp_event_csrmv_t(indptr, indices, data, w_homo, x_post, y_pre, flags=0, stream=None):
+    _check("bp_event_csrmv_t", lib().bp_event_csrmv_t(indptr.numel() - 1, x_post.numel(), _p(indptr), _p(indices),
+                                                      _p(data), _wkind(data), float(w_homo), _p(x_post), _p(y_pre),
+                                                      int(flags), _stream(stream)))
+
+
+def bp_event_csrmv_bwd(indptr, indices, data, w_homo, spike_list, n_spikes, dy, dw=None, dx_pre=None,
+                       max_spikes=None, stream=None):
+    n_pre = indptr.numel() - 1
+    ms = n_pre if max_spikes is None else max_spikes
+    _check("bp_event_csrmv_bwd", lib().bp_event_csrmv_bwd(n_pre, dy.numel(), _p(indptr), _p(indices), _p(data),
+                                                          _wkind(data), float(w_homo), _p(spike_list), _p(n_spikes),
+                                                          ms, _p(dy), _p(dw), _p(dx_pre), _stream(stream)))
+
+
+# ------------------------------------------------------------------ a6
+def bp_jit_desc_init(seed, p, wkind=BP_JIT_HOMO, w0=1.0, w1=0.0) -> JitDesc:
+    d = JitDesc()
+    _check("bp_jit_desc_init", lib().bp_jit_desc_init(ctypes.byref(d), int(seed) & (2**64 - 1), float(p), int(wkind),
+                                                      float(w0), float(w1)))
+    return d
+
+
+def bp_jitconn_event_mv(desc, n_pre, spike_list, n_spikes, y, flags=0, max_spikes=None, stream=None):
+    counts = 1 if y.dtype == torch.int32 else 0
+    ms = n_pre if max_spikes is None else max_spikes
+    _check("bp_jitconn_event_mv", lib().bp_jitconn_event_mv(ctypes.byref(desc), n_pre, y.numel(), _p(spike_list),
+                                                            _p(n_spikes), ms, _p(y), counts, int(flags),
+                                                            _stream(stream)))
+
+
+def bp_jitconn_event_mv_bwd(desc, dy, dx_pre, stream=None):
+    _check("bp_jitconn_event_mv_bwd", lib().bp_jitconn_event_mv_bwd(ctypes.byref(desc), dx_pre.numel(), dy.numel(),
+                                                                    _p(dy), _p(dx_pre), _stream(stream)))
+
+
+def bp_jitconn_mv(desc, x_pre, y_post, flags=0, stream=None):
+    _check("bp_jitconn_mv", lib().bp_jitconn_mv(ctypes.byref(desc), x_pre.numel(), y_post.numel(), _p(x_pre),
+                                                _p(y_post), int(flags), _stream(stream)))
+
+
+def bp_jit_materialize_csr(desc, n_pre, n_post, indptr, indices=None, data=None, stream=None):
+    dk = _wkind(data)
+    _check("bp_jit_materialize_csr", lib().bp_jit_materialize_csr(ctypes.byref(desc), n_pre, n_post, _p(indptr),
+                                                                  _p(indices), _p(data), dk, _stream(stream)))
+
+
+def bp_projection_seed(seed, projection) -> int:
+    return int(lib().bp_projection_seed(int(seed) & (2**64 - 1), int(projection)))
+
+
+def jit_materialize(desc, n_pre, n_post, data_dtype=None, device="cuda"):
+    """Allocates and fills a CSR copy of a JIT matrix (two library calls; the
+    row count is read back to size the index array)."""
+    indptr = torch.empty(n_pre + 1, dtype=torch.int64, device=device)
+    bp_jit_materialize_csr(desc, n_pre, n_post, indptr)
+    nnz = int(indptr[-1].item())
+    indices = torch.empty(max(nnz, 1), dtype=torch.int32, device=device)
+    data = None if data_dtype is None else torch.empty(max(nnz, 1), dtype=data_dtype, device=device)
+    bp_jit_materialize_csr(desc, n_pre, n_post, indptr, indices, data)
+    return indptr, indices[:nnz], (None if data is None else data[:nnz])
+
+
+# ------------------------------------------------------------------ a7/a8
+def bp_network_create(desc: NetDesc):
+    h = VP()
+    _check("bp_network_create", lib().bp_network_create(ctypes.byref(desc), ctypes.byref(h)))
+    return h
+
+
+def bp_network_reset_counters(net, stream=None):
+    _check("bp_network_reset_counters", lib().bp_network_reset_counters(net, _stream(stream)))
+
+
+def bp_network_step(net, stream=None):
+    _check("bp_network_step", lib().bp_network_step(net, _stream(stream)))
+
+
+def bp_simulate(net, T, record=None, stream=None):
+    _check("bp_simulate", lib().bp_simulate(net, int(T), _p(record), _stream(stream)))
+
+
+def bp_network_stats(net, out, stream=None):
+    _check("bp_network_stats", lib().bp_network_stats(net, _p(out), _stream(stream)))
+
+
+def bp_network_destroy(net):
+    _check("bp_network_destroy", lib().bp_network_destroy(net))

@@ -1,0 +1,77 @@
+// bp_internal.h -- declarations shared between libbp's translation units
+// (host-side launchers and parameter structs).  Not part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "bp.h"
+
+namespace bp {
+
+// Post neurons per shared-memory tile: 56 Ki 4-byte accumulators (224 KiB)
+// fit one CTA per SM under the 227 KiB opt-in limit with room for the
+// kernel's own bookkeeping.
+constexpr int32_t kTileCols = 57344;
+constexpr int kTileThreads = 1024;
+
+// FP32 constants of one COBA/LIF step; decay factors from FP64 exp().
+struct LifConst {
+    float a_m, a_e, a_i;
+    float V_rest, V_th, V_reset, E_e, E_i, R, I_ext, w_e, w_i;
+    int32_t ref_steps;
+};
+
+LifConst make_lif_const(const bp_coba_params& p);
+bp_status check_coba(const bp_coba_params* p);
+
+// Per-step control of a network simulation kept in device memory: kernels of
+// a captured CUDA graph read the record pointer and the step number from it.
+struct NetCtrl {
+    int64_t step;          // steps completed since the last reset
+    int64_t record_base;   // value of `step` when the current record began
+    int32_t* record;       // [T][2] or NULL
+    int64_t record_len;    // T
+};
+
+// ---- lif.cu
+bp_status launch_lif_step(const LifConst& c, int64_t n, int64_t n_e, float* V, float* ge, float* gi,
+                          int32_t* ref, void* ye, void* yi, bool counts, const float* I_vec, uint8_t* spk,
+                          int32_t* spike_list, int32_t* n_spikes, int32_t* clear_counter,
+                          int64_t* totals, const NetCtrl* ctrl, int32_t t_local, cudaStream_t s);
+bp_status launch_spike_compact(int64_t n, const uint8_t* events, int32_t* spike_list, int32_t* n_spikes,
+                               cudaStream_t s);
+
+// ---- csrmv.cu
+// Scatter of the spiking rows' entries.  Rows >= split go to y_hi (if
+// non-NULL), others to y.  events_total (nullable) += sum of spiking rows'
+// lengths.  mode: 0 auto, 1 direct (global atomics), 2 shared tiles.
+struct CsrArgs {
+    int64_t n_pre, n_post;
+    const int64_t* indptr;
+    const int32_t* indices;
+    const void* data;
+    int32_t wkind;
+    float w_homo;
+    const int32_t* tile_ptr;
+    int32_t tile_cols;
+};
+bp_status launch_event_csrmv(const CsrArgs& a, const int32_t* spike_list, const int32_t* n_spikes,
+                             int64_t max_spikes, void* y, void* y_hi, int64_t split, bool counts,
+                             int64_t* events_total, int mode, cudaStream_t s);
+
+// ---- jitconn.cu
+struct JitArgs {
+    uint64_t seed;
+    uint32_t K;
+    int32_t wkind;
+    float w0, w1;
+};
+// Scatter of JIT rows: spike ids < split use `lo` (row id = spike id) into y;
+// ids >= split use `hi` (row id = spike id - split) into y_hi.
+bp_status launch_jit_event_mv(const JitArgs& lo, const JitArgs& hi, int64_t split, int64_t n_post,
+                              const int32_t* spike_list, const int32_t* n_spikes, int64_t max_spikes,
+                              void* y, void* y_hi, bool counts, int64_t* events_total, int mode,
+                              cudaStream_t s);
+
+}  // namespace bp

@@ -1,0 +1,479 @@
+// csrmv.cu -- event-driven CSR products (a5): the scatter y = W^T s over the
+// spiking rows (Appendix B), its gather form y_pre = W x, the weight gradient,
+// and the post-column tile index.
+//
+// Work decomposition.  A "group" of G lanes (G in {4, 8, 16, 32}, chosen on
+// the device from the mean segment length) walks one spiking row's segment
+// with coalesced, evict-first loads of indices and weights, four strided
+// loads in flight per lane.  Two accumulation modes:
+//   direct  -- atomics straight into y in L2; right when the step delivers
+//              few events compared with n_post (the network steps).
+//   tiled   -- CTA (s, r) owns post columns [s W, (s+1) W) in shared memory
+//              (W <= 57344 4-byte accumulators) and rows r, r+R, ... of the
+//              spike list; segments come from the tile index (or the whole
+//              row when one tile covers n_post).  Shared-memory atomics absorb
+//              the scatter; the tile is flushed to y once, skipping zeros.
+// In auto mode each CTA reads the spike count and picks the mode from the
+// expected number of events, so no host synchronisation is needed.
+#include "bp_common.cuh"
+#include "bp_internal.h"
+
+namespace bp {
+namespace {
+
+constexpr int kDirectThreads = 256;
+
+// Lanes per row: enough that a segment is one to two passes of the group.
+__device__ __forceinline__ int pick_group(int64_t nnz, int64_t n_pre, int64_t tiles) {
+    const int64_t denom = (n_pre > 0 ? n_pre : 1) * (tiles > 0 ? tiles : 1);
+    const int64_t mean = nnz / denom;
+    if (mean >= 48) return 32;
+    if (mean >= 24) return 16;
+    if (mean >= 12) return 8;
+    return 4;
+}
+
+template <typename Acc>
+__device__ __forceinline__ Acc event_value(float w) {
+    if constexpr (std::is_same<Acc, int32_t>::value) {
+        return 1;
+    } else {
+        return w;
+    }
+}
+
+// out[indices[j] - col0] += value(w_j) for j = b0 + lane, b0 + lane + G, ...
+template <typename Acc, int WK>
+__device__ __forceinline__ void scatter_segment(const int32_t* __restrict__ indices, const void* __restrict__ data,
+                                                float w_homo, int64_t b0, int64_t b1, int lane, int G,
+                                                Acc* __restrict__ out, int64_t col0) {
+    int64_t j = b0 + lane;
+    for (; j + 3 * G < b1; j += 4 * G) {
+        int32_t c[4];
+        float w[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) c[u] = ld_stream(indices + j + u * G);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) w[u] = load_weight<WK>(data, j + u * G, w_homo);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc_add(out + (c[u] - col0), event_value<Acc>(w[u]));
+    }
+    for (; j < b1; j += G) {
+        const int32_t c = ld_stream(indices + j);
+        const float w = load_weight<WK>(data, j, w_homo);
+        acc_add(out + (c - col0), event_value<Acc>(w));
+    }
+}
+
+// Adds v (one value per thread) into *dst with one atomic per CTA.
+__device__ __forceinline__ void block_add_i64(int64_t v, int64_t* dst) {
+    __shared__ unsigned long long s_sum;
+    if (threadIdx.x == 0) s_sum = 0;
+    __syncthreads();
+    v = group_reduce_sum(v, 32);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(&s_sum, static_cast<unsigned long long>(v));
+    __syncthreads();
+    if (threadIdx.x == 0 && s_sum) atomicAdd(reinterpret_cast<unsigned long long*>(dst), s_sum);
+}
+
+// mode: 0 auto, 1 direct, 2 tiled.  W = tile width (post columns per tile),
+// S = number of tiles (the grid is S x R CTAs).  With SPLIT, rows >= split
+// go to y_hi and each CTA keeps two W-wide accumulators.
+template <typename Acc, int WK, bool SPLIT>
+__global__ void __launch_bounds__(kTileThreads, 1)
+    k_csr_scatter(CsrArgs a, const int32_t* __restrict__ spike_list, const int32_t* __restrict__ n_spikes,
+                  int64_t max_spikes, Acc* __restrict__ y, Acc* __restrict__ y_hi, int64_t split, int mode,
+                  int32_t W, int32_t S, int64_t* __restrict__ events_total) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Acc* acc = reinterpret_cast<Acc*>(smem_raw);
+    int64_t ns = *n_spikes;
+    ns = ns < max_spikes ? ns : max_spikes;
+    const int64_t nnz = a.indptr[a.n_pre];
+    if (mode == 0) {
+        // auto: shared tiles pay off once events clearly outnumber the
+        // accumulators each CTA has to zero and flush
+        const int64_t est = ns * (nnz / (a.n_pre > 0 ? a.n_pre : 1));
+        mode = (est >= 4 * static_cast<int64_t>(W) * S) ? 2 : 1;
+    }
+    int64_t ev = 0;
+    if (mode == 1) {
+        const int G = pick_group(nnz, a.n_pre, 1);
+        const int lane = threadIdx.x % G;
+        const int64_t ngroups = static_cast<int64_t>(gridDim.x) * blockDim.x / G;
+        for (int64_t u = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) / G; u < ns; u += ngroups) {
+            const int32_t i = spike_list[u];
+            if (static_cast<uint32_t>(i) >= static_cast<uint64_t>(a.n_pre)) continue;
+            const int64_t b0 = a.indptr[i], b1 = a.indptr[i + 1];
+            Acc* out = (SPLIT && i >= split) ? y_hi : y;
+            if (lane == 0) ev += b1 - b0;
+            scatter_segment<Acc, WK>(a.indices, a.data, a.w_homo, b0, b1, lane, G, out, 0);
+        }
+    } else {
+        const int s = blockIdx.x % S;
+        const int64_t r = blockIdx.x / S;
+        const int64_t R = gridDim.x / S;
+        const int64_t col0 = static_cast<int64_t>(s) * W;
+        const int nacc = SPLIT ? 2 * W : W;
+        for (int t = threadIdx.x; t < nacc; t += blockDim.x) acc[t] = Acc(0);
+        __syncthreads();
+        const int G = pick_group(nnz, a.n_pre, S);
+        const int lane = threadIdx.x % G;
+        const int64_t gid = threadIdx.x / G;
+        const int64_t ng = blockDim.x / G;
+        for (int64_t u = r + R * gid; u < ns; u += R * ng) {
+            const int32_t i = spike_list[u];
+            if (static_cast<uint32_t>(i) >= static_cast<uint64_t>(a.n_pre)) continue;
+            const int64_t rs = a.indptr[i];
+            int64_t b0, b1;
+            if (a.tile_ptr) {
+                const int32_t* tp = a.tile_ptr + static_cast<int64_t>(i) * (S + 1) + s;
+                b0 = rs + tp[0];
+                b1 = rs + tp[1];
+            } else {
+                b0 = rs;
+                b1 = a.indptr[i + 1];
+            }
+            if (events_total && s == 0 && lane == 0) ev += a.indptr[i + 1] - rs;
+            Acc* out = acc + ((SPLIT && i >= split) ? W : 0);
+            scatter_segment<Acc, WK>(a.indices, a.data, a.w_homo, b0, b1, lane, G, out, col0);
+        }
+        __syncthreads();
+        const int64_t rem = a.n_post - col0;
+        const int lim = static_cast<int>(rem < W ? rem : W);
+        for (int t = threadIdx.x; t < lim; t += blockDim.x) {
+            const Acc v = acc[t];
+            if (v != Acc(0)) acc_add(y + col0 + t, v);
+            if constexpr (SPLIT) {
+                const Acc v2 = acc[W + t];
+                if (v2 != Acc(0)) acc_add(y_hi + col0 + t, v2);
+            }
+        }
+    }
+    if (events_total) block_add_i64(ev, events_total);
+}
+
+// Direct-only variant without dynamic shared memory (more CTAs per SM).
+template <typename Acc, int WK, bool SPLIT>
+__global__ void __launch_bounds__(kDirectThreads)
+    k_csr_scatter_direct(CsrArgs a, const int32_t* __restrict__ spike_list, const int32_t* __restrict__ n_spikes,
+                         int64_t max_spikes, Acc* __restrict__ y, Acc* __restrict__ y_hi, int64_t split,
+                         int64_t* __restrict__ events_total) {
+    int64_t ns = *n_spikes;
+    ns = ns < max_spikes ? ns : max_spikes;
+    const int64_t nnz = a.indptr[a.n_pre];
+    const int G = pick_group(nnz, a.n_pre, 1);
+    const int lane = threadIdx.x % G;
+    const int64_t ngroups = static_cast<int64_t>(gridDim.x) * blockDim.x / G;
+    int64_t ev = 0;
+    for (int64_t u = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) / G; u < ns; u += ngroups) {
+        const int32_t i = spike_list[u];
+        if (static_cast<uint32_t>(i) >= static_cast<uint64_t>(a.n_pre)) continue;
+        const int64_t b0 = a.indptr[i], b1 = a.indptr[i + 1];
+        Acc* out = (SPLIT && i >= split) ? y_hi : y;
+        if (lane == 0) ev += b1 - b0;
+        scatter_segment<Acc, WK>(a.indices, a.data, a.w_homo, b0, b1, lane, G, out, 0);
+    }
+    if (events_total) block_add_i64(ev, events_total);
+}
+
+// Gather over all rows: y_pre[i] (+)= sum_j w_j x[indices[j]].
+template <int WK>
+__global__ void __launch_bounds__(256) k_csr_gather(CsrArgs a, const float* __restrict__ x, float* __restrict__ y,
+                                                    int overwrite) {
+    const int64_t nnz = a.indptr[a.n_pre];
+    const int G = pick_group(nnz, a.n_pre, 1);
+    const int lane = threadIdx.x % G;
+    const int64_t ngroups = static_cast<int64_t>(gridDim.x) * blockDim.x / G;
+    const int64_t g0 = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) / G;
+    // every lane of a warp runs the same number of iterations so that the
+    // group reduction's shuffles stay converged
+    const int64_t warp_groups = 32 / G;
+    const int64_t base0 = g0 - (g0 % warp_groups);
+    for (int64_t gb = base0; gb < a.n_pre; gb += ngroups) {
+        const int64_t i = gb + (g0 - base0);
+        float sum = 0.f;
+        if (i < a.n_pre) {
+            const int64_t b0 = a.indptr[i], b1 = a.indptr[i + 1];
+            int64_t j = b0 + lane;
+            for (; j + 3 * G < b1; j += 4 * G) {
+                int32_t c[4];
+                float w[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) c[u] = ld_stream(a.indices + j + u * G);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) w[u] = load_weight<WK>(a.data, j + u * G, a.w_homo);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) sum += w[u] * __ldg(x + c[u]);
+            }
+            for (; j < b1; j += G) sum += load_weight<WK>(a.data, j, a.w_homo) * __ldg(x + ld_stream(a.indices + j));
+        }
+        sum = group_reduce_sum(sum, G);
+        if (i < a.n_pre && lane == 0) y[i] = overwrite ? sum : y[i] + sum;
+    }
+}
+
+// dw[j] += dy[indices[j]] for the entries of each spiking row.
+__global__ void __launch_bounds__(256) k_csr_dw(CsrArgs a, const int32_t* __restrict__ spike_list,
+                                                const int32_t* __restrict__ n_spikes, int64_t max_spikes,
+                                                const float* __restrict__ dy, float* __restrict__ dw) {
+    int64_t ns = *n_spikes;
+    ns = ns < max_spikes ? ns : max_spikes;
+    const int64_t nnz = a.indptr[a.n_pre];
+    const int G = pick_group(nnz, a.n_pre, 1);
+    const int lane = threadIdx.x % G;
+    const int64_t ngroups = static_cast<int64_t>(gridDim.x) * blockDim.x / G;
+    for (int64_t u = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) / G; u < ns; u += ngroups) {
+        const int32_t i = spike_list[u];
+        if (static_cast<uint32_t>(i) >= static_cast<uint64_t>(a.n_pre)) continue;
+        const int64_t b0 = a.indptr[i], b1 = a.indptr[i + 1];
+        for (int64_t j = b0 + lane; j < b1; j += G) dw[j] += __ldg(dy + ld_stream(a.indices + j));
+    }
+}
+
+// tile_ptr[i (S+1) + s] = lower_bound(row i, s W) - indptr[i].
+__global__ void k_tile_index(int64_t n_pre, const int64_t* __restrict__ indptr, const int32_t* __restrict__ indices,
+                             int32_t W, int32_t S, int32_t* __restrict__ tile_ptr) {
+    const int64_t total = n_pre * (S + 1);
+    for (int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; t < total;
+         t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t i = t / (S + 1);
+        const int64_t s = t % (S + 1);
+        const int64_t rs = indptr[i], re = indptr[i + 1];
+        int64_t lo = rs, hi = re;
+        if (s < S) {
+            const int64_t key = s * static_cast<int64_t>(W);
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                if (indices[mid] < key) lo = mid + 1; else hi = mid;
+            }
+        } else {
+            lo = re;
+        }
+        tile_ptr[t] = static_cast<int32_t>(lo - rs);
+    }
+}
+
+template <typename Acc, int WK, bool SPLIT>
+bp_status launch_scatter_t(const CsrArgs& a, const int32_t* spike_list, const int32_t* n_spikes, int64_t max_spikes,
+                           void* y, void* y_hi, int64_t split, int64_t* events_total, int mode, cudaStream_t s) {
+    Acc* yy = static_cast<Acc*>(y);
+    Acc* yh = static_cast<Acc*>(y_hi);
+    // tile geometry: one tile covers n_post if it fits, otherwise the tile index's width
+    const int32_t cap = SPLIT ? kTileCols / 2 : kTileCols;
+    int32_t W = 0, S = 0;
+    if (a.n_post <= cap) {
+        W = static_cast<int32_t>(a.n_post > 0 ? a.n_post : 1);
+        W = (W + 31) & ~31;
+        S = 1;
+    } else if (a.tile_ptr && a.tile_cols > 0 && a.tile_cols <= cap) {
+        W = a.tile_cols;
+        S = static_cast<int32_t>((a.n_post + W - 1) / W);
+    }
+    const bool can_tile = S > 0;
+    if (!can_tile) mode = 1;
+    CsrArgs at = a;
+    if (S == 1) at.tile_ptr = nullptr;  // one tile covers every column: whole rows
+    if (mode == 1) {
+        const int grid = sm_count() * 8;
+        k_csr_scatter_direct<Acc, WK, SPLIT><<<grid, kDirectThreads, 0, s>>>(a, spike_list, n_spikes, max_spikes, yy,
+                                                                             yh, split, events_total);
+        BP_LAUNCHED();
+        return BP_OK;
+    }
+    const size_t smem = static_cast<size_t>(SPLIT ? 2 * W : W) * sizeof(Acc);
+    static bool attr_set = false;  // per instantiation
+    if (!attr_set) {
+        BP_CUDA(cudaFuncSetAttribute(k_csr_scatter<Acc, WK, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     static_cast<int>(SPLIT ? 2 * cap * sizeof(Acc) : cap * sizeof(Acc))));
+        attr_set = true;
+    }
+    // one 1024-thread CTA per SM: R row groups per tile so that S x R covers the SMs
+    int64_t R = static_cast<int64_t>(sm_count()) / S;
+    if (R < 1) R = 1;
+    const int64_t grid = R * S;
+    k_csr_scatter<Acc, WK, SPLIT><<<static_cast<unsigned>(grid), kTileThreads, smem, s>>>(
+        at, spike_list, n_spikes, max_spikes, yy, yh, split, mode, W, S, events_total);
+    BP_LAUNCHED();
+    return BP_OK;
+}
+
+template <typename Acc, bool SPLIT>
+bp_status launch_scatter_wk(const CsrArgs& a, const int32_t* sl, const int32_t* ns, int64_t mx, void* y, void* yh,
+                            int64_t split, int64_t* ev, int mode, cudaStream_t s) {
+    switch (a.wkind) {
+        case BP_W_F32: return launch_scatter_t<Acc, WK_F32, SPLIT>(a, sl, ns, mx, y, yh, split, ev, mode, s);
+        case BP_W_BF16: return launch_scatter_t<Acc, WK_BF16, SPLIT>(a, sl, ns, mx, y, yh, split, ev, mode, s);
+        default: return launch_scatter_t<Acc, WK_HOMO, SPLIT>(a, sl, ns, mx, y, yh, split, ev, mode, s);
+    }
+}
+
+bp_status check_csr(const CsrArgs& a) {
+    BP_REQUIRE(a.n_pre >= 0 && a.n_post >= 0, "negative matrix size");
+    BP_REQUIRE(a.n_pre <= INT32_MAX && a.n_post <= INT32_MAX, "matrix side exceeds 2^31 - 1");
+    BP_REQUIRE(a.indptr != nullptr, "indptr is NULL");
+    BP_REQUIRE(a.wkind >= BP_W_HOMO && a.wkind <= BP_W_BF16, "unknown weight kind %d", a.wkind);
+    BP_REQUIRE(a.wkind == BP_W_HOMO || a.data != nullptr, "weights are NULL for a non-homogeneous kind");
+    BP_REQUIRE(a.tile_ptr == nullptr || (a.tile_cols > 0 && a.tile_cols % 32 == 0 && a.tile_cols <= kTileCols),
+               "tile_cols %d must be a positive multiple of 32 <= %d", a.tile_cols, kTileCols);
+    return BP_OK;
+}
+
+int gather_grid(int64_t n_pre) {
+    const int64_t need = (n_pre * 8 + 255) / 256;  // at least 8 lanes per row
+    const int64_t cap = static_cast<int64_t>(sm_count()) * 16;
+    const int64_t g = need < cap ? need : cap;
+    return static_cast<int>(g > 0 ? g : 1);
+}
+
+}  // namespace
+
+bp_status launch_event_csrmv(const CsrArgs& a, const int32_t* spike_list, const int32_t* n_spikes, int64_t max_spikes,
+                             void* y, void* y_hi, int64_t split, bool counts, int64_t* events_total, int mode,
+                             cudaStream_t s) {
+    if (max_spikes <= 0 || a.n_post == 0) return BP_OK;
+    const bool sp = y_hi != nullptr;
+    if (counts) {
+        return sp ? launch_scatter_wk<int32_t, true>(a, spike_list, n_spikes, max_spikes, y, y_hi, split,
+                                                     events_total, mode, s)
+                  : launch_scatter_wk<int32_t, false>(a, spike_list, n_spikes, max_spikes, y, y_hi, split,
+                                                      events_total, mode, s);
+    }
+    return sp ? launch_scatter_wk<float, true>(a, spike_list, n_spikes, max_spikes, y, y_hi, split, events_total,
+                                               mode, s)
+              : launch_scatter_wk<float, false>(a, spike_list, n_spikes, max_spikes, y, y_hi, split, events_total,
+                                                mode, s);
+}
+
+}  // namespace bp
+
+namespace {
+
+int mode_from_flags(uint32_t flags) {
+    if (flags & BP_ACC_GLOBAL) return 1;
+    if (flags & BP_ACC_SHARED) return 2;
+    return 0;
+}
+
+bp::CsrArgs make_csr(int64_t n_pre, int64_t n_post, const int64_t* indptr, const int32_t* indices, const void* data,
+                     int32_t wkind, float w_homo, const int32_t* tile_ptr, int32_t tile_cols) {
+    bp::CsrArgs a;
+    a.n_pre = n_pre;
+    a.n_post = n_post;
+    a.indptr = indptr;
+    a.indices = indices;
+    a.data = data;
+    a.wkind = wkind;
+    a.w_homo = w_homo;
+    a.tile_ptr = tile_ptr;
+    a.tile_cols = tile_cols;
+    return a;
+}
+
+}  // namespace
+
+extern "C" {
+
+bp_status bp_event_csrmv(int64_t n_pre, int64_t n_post, const int64_t* indptr, const int32_t* indices,
+                         const void* data, int32_t wkind, float w_homo, const int32_t* spike_list,
+                         const int32_t* n_spikes, int64_t max_spikes, void* y, int32_t y_is_count,
+                         const int32_t* tile_ptr, int32_t tile_cols, uint32_t flags, bp_stream_t stream) {
+    bp::clear_error();
+    const bp::CsrArgs a = make_csr(n_pre, n_post, indptr, indices, data, wkind, w_homo, tile_ptr, tile_cols);
+    BP_TRY(bp::check_csr(a));
+    BP_REQUIRE(!y_is_count || wkind == BP_W_HOMO, "integer counts need homogeneous weights");
+    BP_REQUIRE(max_spikes >= 0 && max_spikes <= n_pre, "max_spikes %lld not in [0, n_pre]", (long long)max_spikes);
+    BP_REQUIRE(n_post == 0 || y != nullptr, "y is NULL");
+    BP_REQUIRE(max_spikes == 0 || (spike_list && n_spikes && indices), "spike list, count or indices is NULL");
+    if (flags & BP_OVERWRITE) BP_CUDA(cudaMemsetAsync(y, 0, static_cast<size_t>(n_post) * 4, stream));
+    return bp::launch_event_csrmv(a, spike_list, n_spikes, max_spikes, y, nullptr, n_pre, y_is_count != 0, nullptr,
+                                  mode_from_flags(flags), stream);
+}
+
+size_t bp_event_csrmv_dense_workspace_bytes(int64_t n_pre) {
+    return 16 + static_cast<size_t>(n_pre > 0 ? n_pre : 0) * sizeof(int32_t);
+}
+
+bp_status bp_event_csrmv_dense(int64_t n_pre, int64_t n_post, const int64_t* indptr, const int32_t* indices,
+                               const void* data, int32_t wkind, float w_homo, const uint8_t* events,
+                               void* workspace, void* y, int32_t y_is_count, const int32_t* tile_ptr,
+                               int32_t tile_cols, uint32_t flags, bp_stream_t stream) {
+    bp::clear_error();
+    const bp::CsrArgs a = make_csr(n_pre, n_post, indptr, indices, data, wkind, w_homo, tile_ptr, tile_cols);
+    BP_TRY(bp::check_csr(a));
+    BP_REQUIRE(!y_is_count || wkind == BP_W_HOMO, "integer counts need homogeneous weights");
+    BP_REQUIRE(n_post == 0 || y != nullptr, "y is NULL");
+    BP_REQUIRE(n_pre == 0 || (events && workspace && indices), "events, workspace or indices is NULL");
+    BP_REQUIRE((reinterpret_cast<uintptr_t>(workspace) & 15) == 0, "workspace must be 16-byte aligned");
+    if (flags & BP_OVERWRITE) BP_CUDA(cudaMemsetAsync(y, 0, static_cast<size_t>(n_post) * 4, stream));
+    if (n_pre == 0) return BP_OK;
+    int32_t* cnt = static_cast<int32_t*>(workspace);
+    int32_t* list = reinterpret_cast<int32_t*>(static_cast<char*>(workspace) + 16);
+    BP_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t), stream));
+    BP_TRY(bp::launch_spike_compact(n_pre, events, list, cnt, stream));
+    return bp::launch_event_csrmv(a, list, cnt, n_pre, y, nullptr, n_pre, y_is_count != 0, nullptr,
+                                  mode_from_flags(flags), stream);
+}
+
+int64_t bp_csr_tile_index_size(int64_t n_pre, int64_t n_post, int32_t tile_cols) {
+    if (n_pre < 0 || n_post < 0 || tile_cols <= 0) return -1;
+    const int64_t S = (n_post + tile_cols - 1) / tile_cols;
+    return n_pre * (S + 1);
+}
+
+bp_status bp_csr_tile_index(int64_t n_pre, int64_t n_post, const int64_t* indptr, const int32_t* indices,
+                            int32_t tile_cols, int32_t* tile_ptr, bp_stream_t stream) {
+    bp::clear_error();
+    BP_REQUIRE(n_pre >= 0 && n_post >= 0 && n_pre <= INT32_MAX && n_post <= INT32_MAX, "bad sizes");
+    BP_REQUIRE(tile_cols > 0 && tile_cols % 32 == 0 && tile_cols <= bp::kTileCols,
+               "tile_cols %d must be a positive multiple of 32 <= %d", tile_cols, bp::kTileCols);
+    BP_REQUIRE(n_pre == 0 || (indptr && indices && tile_ptr), "a required pointer is NULL");
+    if (n_pre == 0) return BP_OK;
+    const int32_t S = static_cast<int32_t>((n_post + tile_cols - 1) / tile_cols);
+    const int64_t total = n_pre * (S + 1);
+    int64_t grid = (total + 255) / 256;
+    if (grid > bp::sm_count() * 32) grid = bp::sm_count() * 32;
+    bp::k_tile_index<<<static_cast<unsigned>(grid), 256, 0, stream>>>(n_pre, indptr, indices, tile_cols, S,
+                                                                       tile_ptr);
+    BP_LAUNCHED();
+    return BP_OK;
+}
+
+bp_status bp_event_csrmv_t(int64_t n_pre, int64_t n_post, const int64_t* indptr, const int32_t* indices,
+                           const void* data, int32_t wkind, float w_homo, const float* x_post, float* y_pre,
+                           uint32_t flags, bp_stream_t stream) {
+    bp::clear_error();
+    const bp::CsrArgs a = make_csr(n_pre, n_post, indptr, indices, data, wkind, w_homo, nullptr, 0);
+    BP_TRY(bp::check_csr(a));
+    BP_REQUIRE(n_pre == 0 || (y_pre && x_post && indices), "x_post, y_pre or indices is NULL");
+    if (n_pre == 0) return BP_OK;
+    const int ow = (flags & BP_OVERWRITE) ? 1 : 0;
+    const int grid = bp::gather_grid(n_pre);
+    switch (wkind) {
+        case BP_W_F32: bp::k_csr_gather<bp::WK_F32><<<grid, 256, 0, stream>>>(a, x_post, y_pre, ow); break;
+        case BP_W_BF16: bp::k_csr_gather<bp::WK_BF16><<<grid, 256, 0, stream>>>(a, x_post, y_pre, ow); break;
+        default: bp::k_csr_gather<bp::WK_HOMO><<<grid, 256, 0, stream>>>(a, x_post, y_pre, ow); break;
+    }
+    BP_LAUNCHED();
+    return BP_OK;
+}
+
+bp_status bp_event_csrmv_bwd(int64_t n_pre, int64_t n_post, const int64_t* indptr, const int32_t* indices,
+                             const void* data, int32_t wkind, float w_homo, const int32_t* spike_list,
+                             const int32_t* n_spikes, int64_t max_spikes, const float* dy, float* dw, float* dx_pre,
+                             bp_stream_t stream) {
+    bp::clear_error();
+    const bp::CsrArgs a = make_csr(n_pre, n_post, indptr, indices, data, wkind, w_homo, nullptr, 0);
+    BP_TRY(bp::check_csr(a));
+    BP_REQUIRE(max_spikes >= 0 && max_spikes <= n_pre, "max_spikes out of range");
+    BP_REQUIRE(dy != nullptr || n_post == 0, "dy is NULL");
+    if (dw && max_spikes > 0) {
+        BP_REQUIRE(spike_list && n_spikes && indices, "spike list, count or indices is NULL");
+        const int grid = bp::sm_count() * 8;
+        bp::k_csr_dw<<<grid, 256, 0, stream>>>(a, spike_list, n_spikes, max_spikes, dy, dw);
+        BP_LAUNCHED();
+    }
+    if (dx_pre) return bp_event_csrmv_t(n_pre, n_post, indptr, indices, data, wkind, w_homo, dy, dx_pre, 0, stream);
+    return BP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,183 @@
+// lib.cu -- library-wide entry points: version, error reporting, the sticky
+// device status word, parameter defaults and small host-side helpers.
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "bp_common.cuh"
+#include "bp_internal.h"
+
+namespace {
+thread_local char g_msg[1024] = {0};
+
+// Sticky device status word (one per device that loads the library).
+__device__ int g_device_status = 0;
+
+constexpr int kMaxDevices = 64;
+int* g_status_addr[kMaxDevices] = {nullptr};
+int g_sm_count[kMaxDevices] = {0};
+int g_smem_optin[kMaxDevices] = {0};
+std::mutex g_mu;
+
+int current_device() {
+    int d = 0;
+    if (cudaGetDevice(&d) != cudaSuccess) return 0;
+    return d < kMaxDevices ? d : 0;
+}
+}  // namespace
+
+namespace bp {
+
+void set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_msg, sizeof(g_msg), fmt, ap);
+    va_end(ap);
+}
+
+void clear_error() { g_msg[0] = 0; }
+
+int* device_status_ptr() {
+    const int d = current_device();
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_status_addr[d]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_device_status) != cudaSuccess) return nullptr;
+        g_status_addr[d] = static_cast<int*>(p);
+    }
+    return g_status_addr[d];
+}
+
+int sm_count() {
+    const int d = current_device();
+    if (!g_sm_count[d]) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, d);
+        g_sm_count[d] = v > 0 ? v : 1;
+    }
+    return g_sm_count[d];
+}
+
+int max_smem_optin() {
+    const int d = current_device();
+    if (!g_smem_optin[d]) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, d);
+        g_smem_optin[d] = v > 0 ? v : 48 * 1024;
+    }
+    return g_smem_optin[d];
+}
+
+LifConst make_lif_const(const bp_coba_params& p) {
+    LifConst c;
+    c.a_m = static_cast<float>(std::exp(-p.dt / p.tau_m));
+    c.a_e = static_cast<float>(std::exp(-p.dt / p.tau_e));
+    c.a_i = static_cast<float>(std::exp(-p.dt / p.tau_i));
+    c.V_rest = static_cast<float>(p.V_rest);
+    c.V_th = static_cast<float>(p.V_th);
+    c.V_reset = static_cast<float>(p.V_reset);
+    c.E_e = static_cast<float>(p.E_e);
+    c.E_i = static_cast<float>(p.E_i);
+    c.R = static_cast<float>(p.R);
+    c.I_ext = static_cast<float>(p.I_ext);
+    c.w_e = static_cast<float>(p.w_e);
+    c.w_i = static_cast<float>(p.w_i);
+    c.ref_steps = static_cast<int32_t>(std::llround(p.tau_ref / p.dt));
+    return c;
+}
+
+bp_status check_coba(const bp_coba_params* p) {
+    BP_REQUIRE(p != nullptr, "coba params are NULL");
+    BP_REQUIRE(p->dt > 0 && p->tau_m > 0 && p->tau_e > 0 && p->tau_i > 0 && p->tau_ref >= 0,
+               "coba params: dt and time constants must be positive");
+    return BP_OK;
+}
+
+}  // namespace bp
+
+extern "C" {
+
+const char* bp_version(void) { return "bp 0.1 sm_103a"; }
+
+const char* bp_last_error(void) { return g_msg; }
+
+int32_t bp_tile_cols(void) { return bp::kTileCols; }
+
+bp_status bp_sync_status(bp_stream_t stream) {
+    bp::clear_error();
+    cudaError_t e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) {
+        bp::set_error("stream error: %s", cudaGetErrorString(e));
+        return BP_ERR_CUDA;
+    }
+    int* addr = bp::device_status_ptr();
+    if (!addr) {
+        bp::set_error("cannot resolve the device status word");
+        return BP_ERR_CUDA;
+    }
+    int v = 0;
+    BP_CUDA(cudaMemcpy(&v, addr, sizeof(int), cudaMemcpyDeviceToHost));
+    if (v != 0) {
+        int zero = 0;
+        BP_CUDA(cudaMemcpy(addr, &zero, sizeof(int), cudaMemcpyHostToDevice));
+        if (v == BP_ERR_TIMEOUT) {
+            bp::set_error("a bounded device-side wait ran out");
+            return BP_ERR_TIMEOUT;
+        }
+        bp::set_error("device-side check failed (code %d)", v);
+        return BP_ERR_DEVICE;
+    }
+    return BP_OK;
+}
+
+bp_status bp_coba_params_default(bp_coba_params* p) {
+    BP_REQUIRE(p != nullptr, "p is NULL");
+    p->dt = 0.1;
+    p->tau_m = 20.0;
+    p->tau_e = 5.0;
+    p->tau_i = 10.0;
+    p->tau_ref = 5.0;
+    p->V_rest = -60.0;
+    p->V_th = -50.0;
+    p->V_reset = -60.0;
+    p->E_e = 0.0;
+    p->E_i = -80.0;
+    p->R = 1.0;
+    p->I_ext = 20.0;
+    p->w_e = 0.6;
+    p->w_i = 6.7;
+    return BP_OK;
+}
+
+// SplitMix64 (Steele, Lea and Flood 2014): the state advances by the golden
+// ratio increment; the output is the state passed through two xor-shift /
+// multiply mixing rounds and a final xor-shift.
+uint64_t bp_projection_seed(uint64_t net_seed, int32_t projection) {
+    uint64_t x = net_seed + 0x9E3779B97F4A7C15ull * (static_cast<uint64_t>(projection) + 1ull);
+    x ^= x >> 30;
+    x *= 0xBF58476D1CE4E5B9ull;
+    x ^= x >> 27;
+    x *= 0x94D049BB133111EBull;
+    x ^= x >> 31;
+    return x;
+}
+
+bp_status bp_jit_desc_init(bp_jit_desc* d, uint64_t seed, double p, int32_t wkind, float w0, float w1) {
+    bp::clear_error();
+    BP_REQUIRE(d != nullptr, "desc is NULL");
+    BP_REQUIRE(p > 0.0 && p <= 1.0, "connection probability %g not in (0, 1]", p);
+    BP_REQUIRE(wkind >= BP_JIT_HOMO && wkind <= BP_JIT_NORMAL, "unknown JIT weight kind %d", wkind);
+    const double x = 2.0 / p - 1.0;
+    double K = std::ceil(x - 1e-12 * std::fabs(x));
+    if (K < 1.0) K = 1.0;
+    BP_REQUIRE(K < 4294967296.0, "gap range K = %.0f exceeds 32 bits (p too small)", K);
+    d->seed = seed;
+    d->p = p;
+    d->K = static_cast<int64_t>(K);
+    d->wkind = wkind;
+    d->w0 = w0;
+    d->w1 = w1;
+    return BP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,263 @@
+// network.cu -- the COBA E/I network step and the T-step simulation loop
+// (a7), plus the FP64 population statistics (a8).
+//
+// A step is two launches: the fused neuron pass (lif.cu), which also compacts
+// this step's spikes, and the delivery of those spikes through the stored CSR
+// or the JIT rows into the merged E and I event accumulators (AlignPost,
+// Section 3.3), consumed by the next step's neuron pass (zero delay,
+// Appendix N Listing S6).  The spike counter alternates between two slots:
+// each neuron pass appends to slot t mod 2 and clears the other, so the loop
+// needs no memset node.  bp_simulate captures a chunk of steps once in a CUDA
+// graph and replays it; per-step indices that differ between replays (the
+// record row) are read from a small device control block.
+#include <cmath>
+#include <new>
+
+#include "bp_common.cuh"
+#include "bp_internal.h"
+
+struct bp_net {
+    bp_net_desc d;
+    bp::LifConst c;
+    bp::CsrArgs csr;
+    bp::JitArgs je, ji;
+    bool counts;
+    int64_t host_step;
+    bp::NetCtrl* ctrl;  // device
+    cudaStream_t cap_stream;
+    cudaGraphExec_t graph;
+    int chunk;
+};
+
+namespace bp {
+namespace {
+
+constexpr int kChunk = 64;  // steps per captured graph (even: the counter slots alternate)
+
+__global__ void k_advance(NetCtrl* ctrl, int64_t* totals, int64_t k) {
+    ctrl->step += k;
+    totals[3] += k;
+}
+
+__global__ void k_set_record(NetCtrl* ctrl, int32_t* record, int64_t len) {
+    ctrl->record = record;
+    ctrl->record_base = ctrl->step;
+    ctrl->record_len = len;
+}
+
+__global__ void k_reset_ctrl(NetCtrl* ctrl) {
+    ctrl->step = 0;
+    ctrl->record = nullptr;
+    ctrl->record_base = 0;
+    ctrl->record_len = 0;
+}
+
+// FP64 rates from the exact integer totals.
+__global__ void k_stats(const int64_t* totals, int64_t n, int64_t n_e, double dt_ms, double* out) {
+    const double steps = static_cast<double>(totals[3]);
+    const double secs = steps * dt_ms * 1e-3;
+    const double se = static_cast<double>(totals[0]), si = static_cast<double>(totals[1]);
+    out[0] = (n > 0 && secs > 0) ? (se + si) / (static_cast<double>(n) * secs) : 0.0;
+    out[1] = (n_e > 0 && secs > 0) ? se / (static_cast<double>(n_e) * secs) : 0.0;
+    out[2] = (n - n_e > 0 && secs > 0) ? si / (static_cast<double>(n - n_e) * secs) : 0.0;
+    out[3] = steps > 0 ? static_cast<double>(totals[2]) / steps : 0.0;
+}
+
+bp_status enqueue_step(bp_net* net, int parity, int32_t t_local, cudaStream_t s) {
+    const bp_net_desc& d = net->d;
+    int32_t* cnt = d.n_spikes + parity;
+    int32_t* other = d.n_spikes + (parity ^ 1);
+    BP_TRY(launch_lif_step(net->c, d.n, d.n_e, d.V, d.ge, d.gi, d.ref, d.ye, d.yi, net->counts, nullptr, d.spk,
+                           d.spike_list, cnt, other, d.totals, net->ctrl, t_local, s));
+    if (d.conn_kind == BP_CONN_CSR) {
+        BP_TRY(launch_event_csrmv(net->csr, d.spike_list, cnt, d.n, d.ye, d.yi, d.n_e, net->counts, d.totals + 2, 0,
+                                  s));
+    } else {
+        BP_TRY(launch_jit_event_mv(net->je, net->ji, d.n_e, d.n, d.spike_list, cnt, d.n, d.ye, d.yi, net->counts,
+                                   d.totals + 2, 0, s));
+    }
+    return BP_OK;
+}
+
+bp_status advance(bp_net* net, int64_t k, cudaStream_t s) {
+    k_advance<<<1, 1, 0, s>>>(net->ctrl, net->d.totals, k);
+    BP_LAUNCHED();
+    return BP_OK;
+}
+
+bp_status build_graph(bp_net* net) {
+    if (net->graph) return BP_OK;
+    if (!net->cap_stream) BP_CUDA(cudaStreamCreateWithFlags(&net->cap_stream, cudaStreamNonBlocking));
+    BP_CUDA(cudaStreamBeginCapture(net->cap_stream, cudaStreamCaptureModeThreadLocal));
+    bp_status st = BP_OK;
+    for (int t = 0; t < net->chunk && st == BP_OK; ++t) st = enqueue_step(net, t & 1, t, net->cap_stream);
+    if (st == BP_OK) st = advance(net, net->chunk, net->cap_stream);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(net->cap_stream, &g);
+    if (st != BP_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) {
+        set_error("graph capture failed: %s", cudaGetErrorString(e));
+        return BP_ERR_CUDA;
+    }
+    e = cudaGraphInstantiate(&net->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        net->graph = nullptr;
+        set_error("graph instantiation failed: %s", cudaGetErrorString(e));
+        return BP_ERR_CUDA;
+    }
+    return BP_OK;
+}
+
+}  // namespace
+}  // namespace bp
+
+extern "C" {
+
+bp_status bp_network_create(const bp_net_desc* desc, bp_net** out) {
+    bp::clear_error();
+    BP_REQUIRE(desc && out, "desc or out is NULL");
+    const bp_net_desc& d = *desc;
+    BP_REQUIRE(d.n > 0 && d.n <= INT32_MAX, "n = %lld out of range", (long long)d.n);
+    BP_REQUIRE(d.n_e >= 0 && d.n_e <= d.n, "n_e not in [0, n]");
+    BP_TRY(bp::check_coba(&d.coba));
+    BP_REQUIRE(d.V && d.ge && d.gi && d.ref && d.ye && d.yi && d.spike_list && d.n_spikes && d.totals,
+               "a required state pointer is NULL");
+    BP_REQUIRE(d.conn_kind == BP_CONN_CSR || d.conn_kind == BP_CONN_JIT, "unknown connectivity kind %d",
+               d.conn_kind);
+    bool counts = true;
+    bp::CsrArgs csr{};
+    bp::JitArgs je{}, ji{};
+    if (d.conn_kind == BP_CONN_CSR) {
+        BP_REQUIRE(d.indptr && d.indices, "CSR indptr or indices is NULL");
+        BP_REQUIRE(d.wkind >= BP_W_HOMO && d.wkind <= BP_W_BF16, "unknown weight kind");
+        counts = (d.wkind == BP_W_HOMO) || d.data == nullptr;
+        csr.n_pre = d.n;
+        csr.n_post = d.n;
+        csr.indptr = d.indptr;
+        csr.indices = d.indices;
+        csr.data = counts ? nullptr : d.data;
+        csr.wkind = counts ? BP_W_HOMO : d.wkind;
+        csr.w_homo = 1.0f;
+        csr.tile_ptr = d.tile_ptr;
+        csr.tile_cols = d.tile_ptr ? d.tile_cols : 0;
+    } else {
+        bp_jit_desc de, di;
+        BP_TRY(bp_jit_desc_init(&de, bp_projection_seed(d.seed, 0), d.p, BP_JIT_HOMO, 1.0f, 0.0f));
+        BP_TRY(bp_jit_desc_init(&di, bp_projection_seed(d.seed, 1), d.p, BP_JIT_HOMO, 1.0f, 0.0f));
+        je = {de.seed, static_cast<uint32_t>(de.K), BP_JIT_HOMO, 1.0f, 0.0f};
+        ji = {di.seed, static_cast<uint32_t>(di.K), BP_JIT_HOMO, 1.0f, 0.0f};
+    }
+    bp_net* net = new (std::nothrow) bp_net();
+    if (!net) {
+        bp::set_error("host allocation failed");
+        return BP_ERR_OOM;
+    }
+    net->d = d;
+    net->c = bp::make_lif_const(d.coba);
+    net->csr = csr;
+    net->je = je;
+    net->ji = ji;
+    net->counts = counts;
+    net->host_step = 0;
+    net->chunk = bp::kChunk;
+    net->graph = nullptr;
+    net->cap_stream = nullptr;
+    cudaError_t e = cudaMalloc(&net->ctrl, sizeof(bp::NetCtrl));
+    if (e != cudaSuccess) {
+        delete net;
+        bp::set_error("cudaMalloc of the control block failed: %s", cudaGetErrorString(e));
+        return BP_ERR_OOM;
+    }
+    e = cudaMemset(net->ctrl, 0, sizeof(bp::NetCtrl));
+    if (e != cudaSuccess) {
+        cudaFree(net->ctrl);
+        delete net;
+        bp::set_error("cudaMemset failed: %s", cudaGetErrorString(e));
+        return BP_ERR_CUDA;
+    }
+    *out = net;
+    return BP_OK;
+}
+
+bp_status bp_network_reset_counters(bp_net* net, bp_stream_t stream) {
+    bp::clear_error();
+    BP_REQUIRE(net, "net is NULL");
+    const bp_net_desc& d = net->d;
+    BP_CUDA(cudaMemsetAsync(d.n_spikes, 0, 2 * sizeof(int32_t), stream));
+    BP_CUDA(cudaMemsetAsync(d.totals, 0, 4 * sizeof(int64_t), stream));
+    BP_CUDA(cudaMemsetAsync(d.ye, 0, static_cast<size_t>(d.n) * 4, stream));
+    BP_CUDA(cudaMemsetAsync(d.yi, 0, static_cast<size_t>(d.n) * 4, stream));
+    bp::k_reset_ctrl<<<1, 1, 0, stream>>>(net->ctrl);
+    BP_LAUNCHED();
+    net->host_step = 0;
+    return BP_OK;
+}
+
+bp_status bp_network_step(bp_net* net, bp_stream_t stream) {
+    bp::clear_error();
+    BP_REQUIRE(net, "net is NULL");
+    BP_TRY(bp::enqueue_step(net, static_cast<int>(net->host_step & 1), 0, stream));
+    BP_TRY(bp::advance(net, 1, stream));
+    net->host_step += 1;
+    return BP_OK;
+}
+
+bp_status bp_simulate(bp_net* net, int64_t T, int32_t* record, bp_stream_t stream) {
+    bp::clear_error();
+    BP_REQUIRE(net, "net is NULL");
+    BP_REQUIRE(T >= 0, "T < 0");
+    if (T == 0) return BP_OK;
+    if (record) BP_CUDA(cudaMemsetAsync(record, 0, static_cast<size_t>(T) * 2 * sizeof(int32_t), stream));
+    bp::k_set_record<<<1, 1, 0, stream>>>(net->ctrl, record, record ? T : 0);
+    BP_LAUNCHED();
+    int64_t done = 0;
+    // the captured chunk starts on an even counter slot
+    if (net->host_step & 1) {
+        BP_TRY(bp::enqueue_step(net, 1, 0, stream));
+        BP_TRY(bp::advance(net, 1, stream));
+        net->host_step += 1;
+        done = 1;
+    }
+    const int64_t chunks = (T - done) / net->chunk;
+    if (chunks > 0) {
+        BP_TRY(bp::build_graph(net));
+        for (int64_t k = 0; k < chunks; ++k) BP_CUDA(cudaGraphLaunch(net->graph, stream));
+        net->host_step += chunks * net->chunk;
+        done += chunks * net->chunk;
+    }
+    const int64_t rem = T - done;
+    for (int64_t t = 0; t < rem; ++t)
+        BP_TRY(bp::enqueue_step(net, static_cast<int>((net->host_step + t) & 1), static_cast<int32_t>(t), stream));
+    if (rem > 0) {
+        BP_TRY(bp::advance(net, rem, stream));
+        net->host_step += rem;
+    }
+    // detach the record so that later steps do not write into it
+    bp::k_set_record<<<1, 1, 0, stream>>>(net->ctrl, nullptr, 0);
+    BP_LAUNCHED();
+    return BP_OK;
+}
+
+bp_status bp_network_stats(bp_net* net, double* out, bp_stream_t stream) {
+    bp::clear_error();
+    BP_REQUIRE(net && out, "net or out is NULL");
+    bp::k_stats<<<1, 1, 0, stream>>>(net->d.totals, net->d.n, net->d.n_e, net->d.coba.dt, out);
+    BP_LAUNCHED();
+    return BP_OK;
+}
+
+bp_status bp_network_destroy(bp_net* net) {
+    bp::clear_error();
+    if (!net) return BP_OK;
+    if (net->graph) cudaGraphExecDestroy(net->graph);
+    if (net->cap_stream) cudaStreamDestroy(net->cap_stream);
+    if (net->ctrl) cudaFree(net->ctrl);
+    delete net;
+    return BP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,123 @@
+"""COBA E/I network object over the C ABI (Appendix N, Listing S6).
+
+Allocates the network state with PyTorch on the GPU, fills a ``NetDesc`` and
+drives ``bp_network_*`` / ``bp_simulate``.  All per-step work runs in libbp.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import binding as B
+
+
+def materialize_network_csr(seed, p, n, n_e, data_dtype=None, device="cuda"):
+    """Stored-CSR form of the network's JIT connectivity: rows [0, n_e) are the
+    excitatory projection's rows, rows [n_e, n) the inhibitory ones (row
+    i - n_e of that projection); identical to what the JIT path regenerates."""
+    de = B.bp_jit_desc_init(B.bp_projection_seed(seed, 0), p)
+    di = B.bp_jit_desc_init(B.bp_projection_seed(seed, 1), p)
+    ipe, ixe, _ = B.jit_materialize(de, n_e, n, device=device)
+    ipi, ixi, _ = B.jit_materialize(di, n - n_e, n, device=device)
+    indptr = torch.cat([ipe, ipi[1:] + ipe[-1]])
+    indices = torch.cat([ixe, ixi])
+    data = None
+    if data_dtype is not None:
+        # equal weights stored per synapse: w_e on E rows, w_i on I rows
+        data = torch.empty(indices.numel(), dtype=data_dtype, device=device)
+        data[: ixe.numel()] = 0.6
+        data[ixe.numel():] = 6.7
+    return indptr, indices, data
+
+
+class CobaNetwork:
+    """E/I COBA network of n LIF neurons (first n_e excitatory).
+
+    conn="jit": connectivity regenerated every step from `seed` with
+    probability p (default 80/n).  conn="csr": a stored CSR (indptr, indices,
+    data) over all n presynaptic rows; data None means homogeneous weights
+    w_e / w_i with exact integer event counts.
+    """
+
+    def __init__(self, n, n_e=None, conn="jit", seed=2024, p=None, V0=None, csr=None, tile_cols=0,
+                 params=None, keep_spk=False, device="cuda"):
+        self.n = int(n)
+        self.n_e = int(n_e if n_e is not None else (4 * self.n) // 5)
+        self.p = float(p if p is not None else 80.0 / self.n)
+        self.seed = int(seed)
+        self.device = device
+        self.params = params if params is not None else B.bp_coba_params_default()
+        f32, i32 = torch.float32, torch.int32
+        if V0 is None:
+            V0 = np.full(self.n, -60.0, np.float32)
+        self.V = torch.as_tensor(np.asarray(V0, np.float32), device=device).contiguous()
+        self.ge = torch.zeros(self.n, dtype=f32, device=device)
+        self.gi = torch.zeros(self.n, dtype=f32, device=device)
+        self.ref = torch.zeros(self.n, dtype=i32, device=device)
+        self.spike_list = torch.zeros(self.n, dtype=i32, device=device)
+        self.n_spikes = torch.zeros(2, dtype=i32, device=device)
+        self.totals = torch.zeros(4, dtype=torch.int64, device=device)
+        self.spk = torch.zeros(self.n, dtype=torch.uint8, device=device) if keep_spk else None
+        self.tile_ptr = None
+        desc = B.NetDesc()
+        desc.n, desc.n_e = self.n, self.n_e
+        desc.coba = self.params
+        if conn == "jit":
+            desc.conn_kind = B.BP_CONN_JIT
+            desc.seed = self.seed & (2**64 - 1)
+            desc.p = self.p
+            counts = True
+        elif conn == "csr":
+            if csr is None:
+                csr = materialize_network_csr(self.seed, self.p, self.n, self.n_e, device=device)
+            self.indptr, self.indices, self.data = csr
+            desc.conn_kind = B.BP_CONN_CSR
+            desc.indptr = self.indptr.data_ptr()
+            desc.indices = self.indices.data_ptr()
+            desc.data = None if self.data is None else self.data.data_ptr()
+            desc.wkind = B._wkind(self.data)
+            counts = self.data is None
+            if tile_cols:
+                size = B.bp_csr_tile_index_size(self.n, self.n, tile_cols)
+                self.tile_ptr = torch.empty(size, dtype=i32, device=device)
+                B.bp_csr_tile_index(self.indptr, self.indices, self.n, tile_cols, self.tile_ptr)
+                desc.tile_ptr = self.tile_ptr.data_ptr()
+                desc.tile_cols = tile_cols
+        else:
+            raise ValueError("conn must be 'jit' or 'csr'")
+        ydt = i32 if counts else f32
+        self.ye = torch.zeros(self.n, dtype=ydt, device=device)
+        self.yi = torch.zeros(self.n, dtype=ydt, device=device)
+        desc.V, desc.ge, desc.gi, desc.ref = (t.data_ptr() for t in (self.V, self.ge, self.gi, self.ref))
+        desc.ye, desc.yi = self.ye.data_ptr(), self.yi.data_ptr()
+        desc.spike_list, desc.n_spikes = self.spike_list.data_ptr(), self.n_spikes.data_ptr()
+        desc.totals = self.totals.data_ptr()
+        desc.spk = None if self.spk is None else self.spk.data_ptr()
+        self.desc = desc
+        self.handle = B.bp_network_create(desc)
+        B.bp_network_reset_counters(self.handle)
+
+    def reset_counters(self):
+        B.bp_network_reset_counters(self.handle)
+
+    def step(self):
+        B.bp_network_step(self.handle)
+
+    def simulate(self, T, record=None):
+        B.bp_simulate(self.handle, T, record)
+
+    def stats(self):
+        out = torch.zeros(4, dtype=torch.float64, device=self.device)
+        B.bp_network_stats(self.handle, out)
+        return out.cpu().numpy()
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            B.bp_network_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,313 @@
+"""GPU parity of the operators (a1-a6) against the FP64 oracle, through the C ABI.
+
+Tolerances: integer event counts and index work are bit-exact; FP32 results
+must be within 1e-5 of the oracle in the relative-to-max norm
+max|gpu - ref| / max|ref| (per array); BF16-stored weights are compared with
+the oracle fed the same BF16-rounded weights (1e-5) and with the unrounded
+FP32 weights (1e-2).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as orc
+from paper_2311_05106_gb300 import binding as B
+from paper_2311_05106_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+RTOL_F32 = 1e-5
+RTOL_BF16 = 1e-2
+
+
+def rel_err(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    if a.size == 0:
+        return 0.0
+    return float(np.max(np.abs(a - b)) / max(float(np.max(np.abs(b))), 1e-30))
+
+
+def cuda(x, dtype=None):
+    t = torch.as_tensor(np.ascontiguousarray(x))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def spike_list_of(events):
+    ids = np.nonzero(events)[0].astype(np.int32)
+    sl = torch.zeros(max(len(events), 1), dtype=torch.int32, device="cuda")
+    if len(ids):
+        sl[: len(ids)] = cuda(ids)
+    ns = torch.tensor([len(ids)], dtype=torch.int32, device="cuda")
+    return sl, ns
+
+
+# ---------------------------------------------------------------------- a1-a4
+@pytest.mark.parametrize("n,counts", [(1, True), (255, True), (70001, True), (70001, False), (300000, True)])
+def test_lif_step_matches_oracle(n, counts):
+    st = wl.lif_state(n, seed=n)
+    n_e = (4 * n) // 5
+    empty = ("csr", np.zeros(n + 1, np.int64), np.zeros(1, np.int32), None if counts else np.zeros(1))
+    net = orc.CobaNet(n, n_e, empty, st["V"].astype(np.float64))
+    net.ge[:] = st["ge"]
+    net.gi[:] = st["gi"]
+    net.ref[:] = st["ref"]
+    ye_in = st["ce"] if counts else (st["ce"] * 0.37).astype(np.float32)
+    yi_in = st["ci"] if counts else (st["ci"] * 1.9).astype(np.float32)
+    net.ye[:] = ye_in
+    net.yi[:] = yi_in
+    spk_ref, vdec = net.step(return_vdec=True)
+
+    p = B.bp_coba_params_default()
+    V, ge, gi, ref = cuda(st["V"]), cuda(st["ge"]), cuda(st["gi"]), cuda(st["ref"])
+    ye, yi = cuda(ye_in), cuda(yi_in)
+    spk = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    sl = torch.zeros(n, dtype=torch.int32, device="cuda")
+    ns = torch.zeros(1, dtype=torch.int32, device="cuda")
+    tot = torch.zeros(2, dtype=torch.int64, device="cuda")
+    B.bp_lif_step(p, n_e, V, ge, gi, ref, ye, yi, sl, ns, spk=spk, spike_totals=tot)
+    torch.cuda.synchronize()
+
+    assert rel_err(ge.cpu().numpy(), net.ge) < RTOL_F32
+    assert rel_err(gi.cpu().numpy(), net.gi) < RTOL_F32
+    near = np.abs(np.nan_to_num(vdec, nan=1e9) - (-50.0)) < 1e-4
+    s_gpu = spk.cpu().numpy()
+    assert np.array_equal(s_gpu[~near], spk_ref[~near])
+    ok = ~near
+    assert rel_err(V.cpu().numpy()[ok], net.V[ok]) < RTOL_F32
+    assert np.array_equal(ref.cpu().numpy()[ok], net.ref[ok])
+    assert not ye.any().item() and not yi.any().item()
+    k = int(ns.item())
+    ids = np.sort(sl[:k].cpu().numpy())
+    assert np.array_equal(ids, np.nonzero(s_gpu)[0])
+    t = tot.cpu().numpy()
+    assert t[0] == s_gpu[:n_e].sum() and t[1] == s_gpu[n_e:].sum()
+
+
+def test_spike_compact():
+    for n, rho in [(1, 1.0), (1000, 0.0), (123457, 0.01), (500000, 0.5)]:
+        ev = wl.bernoulli_spikes(n, rho, seed=n)
+        sl = torch.zeros(n, dtype=torch.int32, device="cuda")
+        ns = torch.zeros(1, dtype=torch.int32, device="cuda")
+        B.bp_spike_compact(cuda(ev), sl, ns)
+        k = int(ns.item())
+        assert k == ev.sum()
+        assert np.array_equal(np.sort(sl[:k].cpu().numpy()), np.nonzero(ev)[0])
+
+
+# ---------------------------------------------------------------------- a5
+CSR_CASES = [
+    # n_pre, n_post, p, rho
+    (1, 1, 1.0, 1.0),
+    (300, 257, 0.1, 0.3),
+    (5000, 4001, 0.02, 0.05),
+    (2000, 150001, 0.004, 0.2),     # several post tiles and a ragged tail
+    (20000, 30000, 0.001, 0.0),     # no spikes
+]
+
+
+def _csr(n_pre, n_post, p, seed):
+    ip, ix = wl.random_csr(n_pre, n_post, p, seed)
+    return ip, ix
+
+
+@pytest.mark.parametrize("case", CSR_CASES)
+@pytest.mark.parametrize("flags", [0, B.BP_ACC_GLOBAL, B.BP_ACC_SHARED])
+def test_event_csrmv_counts_bit_exact(case, flags):
+    n_pre, n_post, p, rho = case
+    ip, ix = _csr(n_pre, n_post, p, seed=n_pre)
+    ev = wl.bernoulli_spikes(n_pre, rho, seed=n_pre + 1)
+    expect = orc.event_csr_count(ip, ix, ev, n_post)
+    dip, dix = cuda(ip), cuda(ix)
+    tcols = B.bp_tile_cols() if n_post > B.bp_tile_cols() else 0
+    tp = None
+    if tcols:
+        tp = torch.empty(B.bp_csr_tile_index_size(n_pre, n_post, tcols), dtype=torch.int32, device="cuda")
+        B.bp_csr_tile_index(dip, dix, n_post, tcols, tp)
+    sl, ns = spike_list_of(ev)
+    y = torch.zeros(n_post, dtype=torch.int32, device="cuda")
+    B.bp_event_csrmv(dip, dix, None, 1.0, sl, ns, y, tile_ptr=tp, tile_cols=tcols, flags=flags)
+    assert np.array_equal(y.cpu().numpy(), expect)
+    # accumulate semantics: a second call doubles; BP_OVERWRITE resets
+    B.bp_event_csrmv(dip, dix, None, 1.0, sl, ns, y, tile_ptr=tp, tile_cols=tcols, flags=flags)
+    assert np.array_equal(y.cpu().numpy(), 2 * expect)
+    B.bp_event_csrmv(dip, dix, None, 1.0, sl, ns, y, tile_ptr=tp, tile_cols=tcols, flags=flags | B.BP_OVERWRITE)
+    assert np.array_equal(y.cpu().numpy(), expect)
+
+
+@pytest.mark.parametrize("case", CSR_CASES[1:4])
+@pytest.mark.parametrize("flags", [0, B.BP_ACC_GLOBAL, B.BP_ACC_SHARED])
+def test_event_csrmv_float_weights(case, flags):
+    n_pre, n_post, p, rho = case
+    ip, ix = _csr(n_pre, n_post, p, seed=n_pre + 7)
+    w = wl.normal_weights(len(ix), 0.5, 0.1, seed=3)
+    ev = wl.bernoulli_spikes(n_pre, rho, seed=11)
+    dip, dix = cuda(ip), cuda(ix)
+    tcols = B.bp_tile_cols() if n_post > B.bp_tile_cols() else 0
+    tp = None
+    if tcols:
+        tp = torch.empty(B.bp_csr_tile_index_size(n_pre, n_post, tcols), dtype=torch.int32, device="cuda")
+        B.bp_csr_tile_index(dip, dix, n_post, tcols, tp)
+    sl, ns = spike_list_of(ev)
+    # FP32 weights
+    y = torch.zeros(n_post, dtype=torch.float32, device="cuda")
+    B.bp_event_csrmv(dip, dix, cuda(w), 0.0, sl, ns, y, tile_ptr=tp, tile_cols=tcols, flags=flags)
+    ref = orc.event_csrmv(ip, ix, w.astype(np.float64), ev, n_post)
+    assert rel_err(y.cpu().numpy(), ref) < RTOL_F32
+    # BF16 weights
+    wb = cuda(w).to(torch.bfloat16)
+    yb = torch.zeros(n_post, dtype=torch.float32, device="cuda")
+    B.bp_event_csrmv(dip, dix, wb, 0.0, sl, ns, yb, tile_ptr=tp, tile_cols=tcols, flags=flags)
+    ref_b = orc.event_csrmv(ip, ix, wb.float().cpu().numpy().astype(np.float64), ev, n_post)
+    assert rel_err(yb.cpu().numpy(), ref_b) < RTOL_F32
+    assert rel_err(yb.cpu().numpy(), ref) < RTOL_BF16
+    # homogeneous float weight
+    yh = torch.zeros(n_post, dtype=torch.float32, device="cuda")
+    B.bp_event_csrmv(dip, dix, None, 0.6, sl, ns, yh, tile_ptr=tp, tile_cols=tcols, flags=flags)
+    assert rel_err(yh.cpu().numpy(), orc.event_csrmv(ip, ix, None, ev, n_post, w_homo=0.6)) < RTOL_F32
+
+
+def test_event_csrmv_dense_events():
+    n_pre, n_post = 7000, 9000
+    ip, ix = _csr(n_pre, n_post, 0.01, seed=5)
+    ev = wl.bernoulli_spikes(n_pre, 0.1, seed=6)
+    ws = torch.zeros(B.bp_event_csrmv_dense_workspace_bytes(n_pre), dtype=torch.uint8, device="cuda")
+    y = torch.zeros(n_post, dtype=torch.int32, device="cuda")
+    B.bp_event_csrmv_dense(cuda(ip), cuda(ix), None, 1.0, cuda(ev), ws, y)
+    assert np.array_equal(y.cpu().numpy(), orc.event_csr_count(ip, ix, ev, n_post))
+
+
+def test_tile_index_matches_searchsorted():
+    n_pre, n_post, tc = 3000, 200000, 57344
+    ip, ix = _csr(n_pre, n_post, 0.002, seed=9)
+    tp = torch.empty(B.bp_csr_tile_index_size(n_pre, n_post, tc), dtype=torch.int32, device="cuda")
+    B.bp_csr_tile_index(cuda(ip), cuda(ix), n_post, tc, tp)
+    S = -(-n_post // tc)
+    got = tp.cpu().numpy().reshape(n_pre, S + 1)
+    for i in range(0, n_pre, 37):
+        row = ix[ip[i]:ip[i + 1]]
+        bounds = np.searchsorted(row, np.arange(S) * tc, side="left")
+        assert np.array_equal(got[i, :S], bounds)
+        assert got[i, S] == len(row)
+
+
+@pytest.mark.parametrize("wdt", [None, torch.float32, torch.bfloat16])
+def test_csrmv_t_gather(wdt):
+    n_pre, n_post = 6000, 5000
+    ip, ix = _csr(n_pre, n_post, 0.01, seed=13)
+    w = wl.normal_weights(len(ix), 0.0, 1.0, seed=14)
+    x = np.random.default_rng(1).normal(size=n_post).astype(np.float32)
+    dw = None if wdt is None else cuda(w).to(wdt)
+    wref = None if wdt is None else dw.float().cpu().numpy().astype(np.float64)
+    y = torch.full((n_pre,), 0.25, dtype=torch.float32, device="cuda")
+    B.bp_event_csrmv_t(cuda(ip), cuda(ix), dw, 0.6, cuda(x), y)
+    ref = 0.25 + orc.csrmv_t(ip, ix, wref, x.astype(np.float64), w_homo=0.6)
+    assert rel_err(y.cpu().numpy(), ref) < RTOL_F32
+
+
+def test_csrmv_bwd():
+    n_pre, n_post = 3000, 4000
+    ip, ix = _csr(n_pre, n_post, 0.02, seed=15)
+    w = wl.normal_weights(len(ix), 0.0, 1.0, seed=16)
+    ev = wl.bernoulli_spikes(n_pre, 0.2, seed=17)
+    dy = np.random.default_rng(2).normal(size=n_post).astype(np.float32)
+    sl, ns = spike_list_of(ev)
+    dwt = torch.zeros(len(ix), dtype=torch.float32, device="cuda")
+    dx = torch.zeros(n_pre, dtype=torch.float32, device="cuda")
+    B.bp_event_csrmv_bwd(cuda(ip), cuda(ix), cuda(w), 0.0, sl, ns, cuda(dy), dw=dwt, dx_pre=dx)
+    # each entry receives exactly one addition onto zero: bit-exact
+    assert np.array_equal(dwt.cpu().numpy(), orc.event_csrmv_dw(ip, ix, ev, dy.astype(np.float64)).astype(np.float32))
+    assert rel_err(dx.cpu().numpy(), orc.csrmv_t(ip, ix, w.astype(np.float64), dy.astype(np.float64))) < RTOL_F32
+
+
+# ---------------------------------------------------------------------- a6
+@pytest.mark.parametrize("n_pre,n_post,p", [(1, 1, 1.0), (3000, 2500, 0.05), (4000, 4000, 0.02), (500, 100000, 0.01)])
+def test_jit_materialize_bit_exact(n_pre, n_post, p):
+    seed = 1234 + n_pre
+    d = B.bp_jit_desc_init(seed, p)
+    K = orc.jit_K(p)
+    assert d.K == K
+    ip, ix, _ = B.jit_materialize(d, n_pre, n_post)
+    eip, eix, _ = orc.jit_materialize(seed, K, n_pre, n_post)
+    assert np.array_equal(ip.cpu().numpy(), eip)
+    assert np.array_equal(ix.cpu().numpy(), eix)
+
+
+@pytest.mark.parametrize("wkind,w0,w1", [(B.BP_JIT_UNIFORM, -0.5, 1.5), (B.BP_JIT_NORMAL, 0.5, 0.1)])
+def test_jit_materialized_weights(wkind, w0, w1):
+    n_pre, n_post, p, seed = 800, 3000, 0.05, 77
+    d = B.bp_jit_desc_init(seed, p, wkind, w0, w1)
+    ip, ix, data = B.jit_materialize(d, n_pre, n_post, data_dtype=torch.float32)
+    eip, eix, edata = orc.jit_materialize(seed, orc.jit_K(p), n_pre, n_post, wkind, w0, w1)
+    assert np.array_equal(ix.cpu().numpy(), eix)
+    assert rel_err(data.cpu().numpy(), edata) < RTOL_F32
+
+
+@pytest.mark.parametrize("n_pre,n_post,p,rho", [(3000, 3000, 0.05, 0.1), (2000, 100000, 0.01, 0.05),
+                                                (50000, 60000, 0.001, 0.01)])
+@pytest.mark.parametrize("flags", [0, B.BP_ACC_GLOBAL])
+def test_jitconn_event_mv_counts_bit_exact(n_pre, n_post, p, rho, flags):
+    seed = 99 + n_pre
+    d = B.bp_jit_desc_init(seed, p)
+    ev = wl.bernoulli_spikes(n_pre, rho, seed=3)
+    sl, ns = spike_list_of(ev)
+    y = torch.zeros(n_post, dtype=torch.int32, device="cuda")
+    B.bp_jitconn_event_mv(d, n_pre, sl, ns, y, flags=flags)
+    expect = orc.jitconn_event_mv(seed, orc.jit_K(p), n_pre, n_post, ev)
+    assert np.array_equal(y.cpu().numpy(), expect.astype(np.int64))
+
+
+@pytest.mark.parametrize("wkind,w0,w1", [(B.BP_JIT_HOMO, 0.6, 0.0), (B.BP_JIT_UNIFORM, 0.0, 1.0),
+                                         (B.BP_JIT_NORMAL, 0.5, 0.1)])
+def test_jitconn_float_products(wkind, w0, w1):
+    n_pre, n_post, p, seed = 4000, 5000, 0.02, 5
+    K = orc.jit_K(p)
+    d = B.bp_jit_desc_init(seed, p, wkind, w0, w1)
+    ev = wl.bernoulli_spikes(n_pre, 0.1, seed=8)
+    sl, ns = spike_list_of(ev)
+    y = torch.zeros(n_post, dtype=torch.float32, device="cuda")
+    B.bp_jitconn_event_mv(d, n_pre, sl, ns, y)
+    assert rel_err(y.cpu().numpy(), orc.jitconn_event_mv(seed, K, n_pre, n_post, ev, wkind, w0, w1)) < RTOL_F32
+    x = np.random.default_rng(3).normal(size=n_pre).astype(np.float32)
+    yy = torch.zeros(n_post, dtype=torch.float32, device="cuda")
+    B.bp_jitconn_mv(d, cuda(x), yy)
+    assert rel_err(yy.cpu().numpy(), orc.jitconn_mv(seed, K, n_pre, n_post, x.astype(np.float64), wkind, w0,
+                                                    w1)) < RTOL_F32
+    dy = np.random.default_rng(4).normal(size=n_post).astype(np.float32)
+    dx = torch.zeros(n_pre, dtype=torch.float32, device="cuda")
+    B.bp_jitconn_event_mv_bwd(d, cuda(dy), dx)
+    assert rel_err(dx.cpu().numpy(), orc.jitconn_mv_t(seed, K, n_pre, n_post, dy.astype(np.float64), wkind, w0,
+                                                      w1)) < RTOL_F32
+
+
+def test_jit_and_stored_csr_agree_on_gpu():
+    n_pre, n_post, p, seed = 20000, 20000, 0.004, 31
+    d = B.bp_jit_desc_init(seed, p)
+    ip, ix, _ = B.jit_materialize(d, n_pre, n_post)
+    ev = wl.bernoulli_spikes(n_pre, 0.05, seed=32)
+    sl, ns = spike_list_of(ev)
+    a = torch.zeros(n_post, dtype=torch.int32, device="cuda")
+    b = torch.zeros(n_post, dtype=torch.int32, device="cuda")
+    B.bp_jitconn_event_mv(d, n_pre, sl, ns, a)
+    B.bp_event_csrmv(ip, ix, None, 1.0, sl, ns, b)
+    assert torch.equal(a, b)
+
+
+def test_invalid_arguments_rejected_on_host():
+    d = B.bp_jit_desc_init(1, 0.1)
+    y = torch.zeros(10, dtype=torch.float32, device="cuda")
+    sl = torch.zeros(10, dtype=torch.int32, device="cuda")
+    ns = torch.zeros(1, dtype=torch.int32, device="cuda")
+    with pytest.raises(B.BpError):
+        B.bp_jit_desc_init(1, 0.0)
+    with pytest.raises(B.BpError):
+        B.bp_jit_desc_init(1, 1.5)
+    with pytest.raises(B.BpError):   # counts with non-homogeneous weights
+        B.bp_event_csrmv(cuda(np.zeros(11, np.int64)), cuda(np.zeros(1, np.int32)), cuda(np.zeros(1, np.float32)),
+                         0.0, sl, ns, torch.zeros(10, dtype=torch.int32, device="cuda"))
+    with pytest.raises(B.BpError):   # max_spikes beyond n_pre
+        B.bp_jitconn_event_mv(d, 10, sl, ns, y, max_spikes=11)
+    assert B.bp_sync_status() == 0
