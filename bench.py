@@ -50,6 +50,11 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    # profiling cases (ncu): headline path only, with another connectivity / size
+    ap.add_argument("--conn", default="csr", choices=["csr", "jit"])
+    ap.add_argument("--weights", default="f32", choices=["f32", "counts"])
+    ap.add_argument("--neurons", type=int, default=N_NEURONS)
+    ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
 
 
@@ -152,17 +157,17 @@ def lif_traffic_record():
 LIF_BYTES_PER_NEURON = 36
 
 
-def build_network(torch, B, conn, weights):
+def build_network(torch, B, conn, weights, n=N_NEURONS):
     import numpy as np
     from paper_2311_05106_gb300 import workloads as wl
     from paper_2311_05106_gb300.network import CobaNetwork, materialize_network_csr
-    V0 = wl.coba_v0(N_NEURONS, seed=V0_SEED)
-    p = 80.0 / N_NEURONS
+    n_e = (4 * n) // 5
+    V0 = wl.coba_v0(n, seed=V0_SEED)
+    p = 80.0 / n
     csr = None
     if conn == "csr":
-        csr = materialize_network_csr(SEED, p, N_NEURONS, N_EXC,
-                                      data_dtype=torch.float32 if weights == "f32" else None)
-    net = CobaNetwork(N_NEURONS, N_EXC, conn=conn, seed=SEED, p=p, V0=V0, csr=csr)
+        csr = materialize_network_csr(SEED, p, n, n_e, data_dtype=torch.float32 if weights == "f32" else None)
+    net = CobaNetwork(n, n_e, conn=conn, seed=SEED, p=p, V0=V0, csr=csr)
     return net, np.asarray(V0)
 
 
@@ -187,24 +192,25 @@ def time_simulate(torch, net, steps, warmup, dist=None):
 
 
 def launches_in_simulate(steps, host_step_before):
-    """Kernels bp_simulate enqueues: two per step, one chunk-advance per 64-step
-    graph, one per leftover group, two record set-ups."""
+    """Kernels bp_simulate enqueues: one fused step kernel per step, one
+    chunk-advance per 64-step graph and per leftover group, two record set-ups."""
     n = 2
     done = 0
     if host_step_before % 2 == 1 and steps > 0:
-        n += 3
+        n += 2
         done = 1
     chunks = (steps - done) // 64
-    n += chunks * (2 * 64 + 1)
+    n += chunks * (64 + 1)
     rem = steps - done - chunks * 64
     if rem > 0:
-        n += 2 * rem + 1
+        n += rem + 1
     return n
 
 
 def lif_kernel_time(torch, B, net, reps=50):
-    """Average duration of the neuron-pass kernel (bp_lif_step on the network's
-    state), CUDA events around each launch on the launching stream."""
+    """Average duration of the neuron pass alone (bp_lif_step on the network's
+    state: the fused step kernel without delivery), CUDA events around each
+    launch on the launching stream."""
     stream = torch.cuda.current_stream()
     sl = torch.zeros(N_NEURONS, dtype=torch.int32, device="cuda")
     ns = torch.zeros(1, dtype=torch.int32, device="cuda")
@@ -338,8 +344,11 @@ def main():
     from paper_2311_05106_gb300 import binding as B
     B.lib()
 
-    # ---- headline: stored CSR, FP32 weights
-    net, V0 = build_network(torch, B, "csr", "f32")
+    # ---- headline: stored CSR, FP32 weights (other cases only for profiling)
+    global N_NEURONS, N_EXC
+    if args.neurons != N_NEURONS:
+        N_NEURONS, N_EXC = args.neurons, (4 * args.neurons) // 5
+    net, V0 = build_network(torch, B, args.conn, args.weights, N_NEURONS)
     net.simulate(3)  # builds and caches the CUDA graph outside the timed region
     net.reset_counters()
     host_before = 3
@@ -363,20 +372,23 @@ def main():
     alg_bytes = LIF_BYTES_PER_NEURON * N_NEURONS
     achieved = alg_bytes / (lif_ms * 1e-3) / 1e9
     peak, peak_kind = peaks()
-    roofline = {"bound": "hbm", "kernel": "k_lif_step", "achieved": achieved, "peak": peak, "unit": "GB/s",
+    roofline = {"bound": "hbm", "kernel": "k_step (neuron pass)", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": lif_traffic_record(), "peak_source": peak_kind,
                 "lif_us_per_launch": lif_ms * 1e3, "alg_bytes_per_launch": alg_bytes}
 
     # ---- end to end through the public API (host buffers)
-    e2e_ms, e2e_events, h2d, d2h = e2e_run(torch, net, V0, args.steps)
-    e2e = {"value": e2e_events / (e2e_ms * 1e-3), "unit": "events/s",
-           "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps}
+    e2e = None
+    if not args.no_e2e:
+        e2e_ms, e2e_events, h2d, d2h = e2e_run(torch, net, V0, args.steps)
+        e2e = {"value": e2e_events / (e2e_ms * 1e-3), "unit": "events/s",
+               "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps}
     net.close()
     del net
     torch.cuda.empty_cache()
 
     variants = {}
-    if not args.no_variants:
+    headline = args.conn == "csr" and args.weights == "f32" and args.neurons == 4_000_000
+    if not args.no_variants and headline:
         for name, conn, w in (("csr_counts", "csr", None), ("jit_counts", "jit", None)):
             v, _ = build_network(torch, B, conn, w)
             v.simulate(3)
@@ -392,7 +404,7 @@ def main():
             variants[k]["vs_plain_f32"] = variants[k]["events_per_s"] / value
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and headline:
         s = oracle_sample(15.0)
         cpu = {"value": s["value"], "unit": "events/s", "cores": 1, "kind": "oracle",
                "sample": "FP64 oracle, one thread, the same N=4e6 network (JIT rows = the stored matrix) from the "
@@ -402,7 +414,9 @@ def main():
         "metric": "synaptic_events_per_s", "value": value, "unit": "events/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "connectivity": "stored CSR, int32 indices, FP32 weights",
+        "config": {"workload": WORKLOAD if headline else "profiling case (not the headline workload)",
+                   "connectivity": {"csr": "stored CSR, int32 indices, ", "jit": "JIT rows, "}[args.conn]
+                   + {"f32": "FP32 weights", "counts": "homogeneous weights, int32 event counts"}[args.weights],
                    "neurons": N_NEURONS, "sim_steps": args.steps,
                    "l2": "connectivity 2.6 GB + state 96 MB exceed L2; no flush between steps (state re-read each step)",
                    "parallelism": "replicas" if world > 1 else "single"},

@@ -124,9 +124,9 @@ bp_status bp_coba_params_default(bp_coba_params* p);
  * the state arithmetic is FP32.
  * Arrays: V, ge, gi float [n]; ref int32 [n]; ye, yi int32 or float [n].
  * Outputs: spk uint8 [n] (nullable) = 1 where the neuron spiked this step;
- *   spike ids are APPENDED to spike_list int32 [n] at positions reserved by
- *   an atomic add on *n_spikes (the caller zeroes *n_spikes beforehand; the
- *   order of ids in the list is unspecified);
+ *   spike ids are APPENDED to spike_list int32 [n] (nullable together with
+ *   n_spikes) at positions reserved by an atomic add on *n_spikes (the caller
+ *   zeroes *n_spikes beforehand; the order of ids in the list is unspecified);
  *   spike_totals int64 [2] (nullable) += number of spikes among neurons
  *   [0, n_e) and [n_e, n).
  * Errors: BP_ERR_INVALID for n < 0, n_e outside [0, n] or a required NULL. */
@@ -271,10 +271,13 @@ uint64_t bp_projection_seed(uint64_t net_seed, int32_t projection);
 
 /* --------------------------------------------------------------------------
  * a7/a8. COBA E/I network: step and simulate (Appendix N Listing S6).
- * Neurons [0, n_e) are excitatory, [n_e, n) inhibitory.  Each step is
- * bp_lif_step followed by the delivery of this step's spikes: E rows into
- * ye, I rows into yi (one merged conductance per neuron and synapse type,
- * Section 3.3 AlignPost), to be consumed by the next step.
+ * Neurons [0, n_e) are excitatory, [n_e, n) inhibitory.  Each step is the
+ * bp_lif_step update followed by the delivery of this step's spikes: E rows
+ * into ye, I rows into yi (one merged conductance per neuron and synapse
+ * type, Section 3.3 AlignPost), consumed by the next step.  The event
+ * accumulators are double-buffered ([2n] each): step t reads and clears
+ * elements [(t mod 2) n, (t mod 2 + 1) n) and delivers into the other half,
+ * which lets one kernel do both.
  * ------------------------------------------------------------------------ */
 enum { BP_CONN_CSR = 0, BP_CONN_JIT = 1 };
 
@@ -298,10 +301,10 @@ typedef struct {
     float* ge;                      /* [n] */
     float* gi;                      /* [n] */
     int32_t* ref;                   /* [n] */
-    void* ye;                       /* [n] int32 counts (homogeneous) or float sums */
-    void* yi;                       /* [n] */
-    int32_t* spike_list;            /* [n] scratch: spikes of the current step */
-    int32_t* n_spikes;              /* [2] scratch: spike counters (two alternating slots) */
+    void* ye;                       /* [2n] int32 counts (homogeneous) or float sums, two halves */
+    void* yi;                       /* [2n] */
+    int32_t* spike_list;            /* [n] nullable: spike ids of the last step (order unspecified) */
+    int32_t* n_spikes;              /* [2] with spike_list: the last step t's count is n_spikes[t mod 2] */
     int64_t* totals;                /* [4] cumulative: spikes E, spikes I, synaptic events, steps */
     uint8_t* spk;                   /* [n] nullable: spike flags of the last step */
 } bp_net_desc;
@@ -313,7 +316,8 @@ typedef struct bp_net bp_net;
  * first call).  *out receives the handle. */
 bp_status bp_network_create(const bp_net_desc* desc, bp_net** out);
 
-/* Zeroes the counters (n_spikes, totals) and the event accumulators. */
+/* Zeroes the counters (n_spikes, totals) and both halves of the event
+ * accumulators, and restarts the step count at 0. */
 bp_status bp_network_reset_counters(bp_net* net, bp_stream_t stream);
 
 /* One time step (a1-a5/a6 above). */

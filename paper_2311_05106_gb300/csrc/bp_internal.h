@@ -34,18 +34,7 @@ struct NetCtrl {
     int64_t record_len;    // T
 };
 
-// ---- lif.cu
-bp_status launch_lif_step(const LifConst& c, int64_t n, int64_t n_e, float* V, float* ge, float* gi,
-                          int32_t* ref, void* ye, void* yi, bool counts, const float* I_vec, uint8_t* spk,
-                          int32_t* spike_list, int32_t* n_spikes, int32_t* clear_counter,
-                          int64_t* totals, const NetCtrl* ctrl, int32_t t_local, cudaStream_t s);
-bp_status launch_spike_compact(int64_t n, const uint8_t* events, int32_t* spike_list, int32_t* n_spikes,
-                               cudaStream_t s);
-
-// ---- csrmv.cu
-// Scatter of the spiking rows' entries.  Rows >= split go to y_hi (if
-// non-NULL), others to y.  events_total (nullable) += sum of spiking rows'
-// lengths.  mode: 0 auto, 1 direct (global atomics), 2 shared tiles.
+// Stored CSR operand of the event products.
 struct CsrArgs {
     int64_t n_pre, n_post;
     const int64_t* indptr;
@@ -56,17 +45,57 @@ struct CsrArgs {
     const int32_t* tile_ptr;
     int32_t tile_cols;
 };
-bp_status launch_event_csrmv(const CsrArgs& a, const int32_t* spike_list, const int32_t* n_spikes,
-                             int64_t max_spikes, void* y, void* y_hi, int64_t split, bool counts,
-                             int64_t* events_total, int mode, cudaStream_t s);
 
-// ---- jitconn.cu
+// JIT operand (Appendix C): key, gap range, weight law.
 struct JitArgs {
     uint64_t seed;
     uint32_t K;
     int32_t wkind;
     float w0, w1;
 };
+
+// One fused network step: neuron pass over [0, n) reading half `parity` of
+// the double-buffered accumulators ye2 / yi2 ([2n] each) and delivering the
+// step's spikes into the other half.
+struct NetStepLaunch {
+    LifConst c;
+    int64_t n, n_e;
+    float* V;
+    float* ge;
+    float* gi;
+    int32_t* ref;
+    void* ye2;
+    void* yi2;
+    uint8_t* spk;
+    int32_t* spike_list;   // nullable
+    int32_t* n_spikes;     // [2], used with spike_list
+    int64_t* totals;
+    const NetCtrl* ctrl;
+    bool counts;
+    bool jit;
+    CsrArgs csr;
+    int32_t group;         // lanes per CSR row in the delivery (4, 8, 16 or 32)
+    JitArgs je, ji;
+};
+
+// ---- lif.cu
+bp_status launch_lif_step(const LifConst& c, int64_t n, int64_t n_e, float* V, float* ge, float* gi,
+                          int32_t* ref, void* ye, void* yi, bool counts, const float* I_vec, uint8_t* spk,
+                          int32_t* spike_list, int32_t* n_spikes, int32_t* clear_counter,
+                          int64_t* totals, const NetCtrl* ctrl, int32_t t_local, cudaStream_t s);
+bp_status launch_network_step(const NetStepLaunch& L, int parity, int32_t t_local, cudaStream_t s);
+bp_status launch_spike_compact(int64_t n, const uint8_t* events, int32_t* spike_list, int32_t* n_spikes,
+                               cudaStream_t s);
+
+// ---- csrmv.cu
+// Scatter of the spiking rows' entries.  Rows >= split go to y_hi (if
+// non-NULL), others to y.  events_total (nullable) += sum of spiking rows'
+// lengths.  mode: 0 auto, 1 direct (global atomics), 2 shared tiles.
+bp_status launch_event_csrmv(const CsrArgs& a, const int32_t* spike_list, const int32_t* n_spikes,
+                             int64_t max_spikes, void* y, void* y_hi, int64_t split, bool counts,
+                             int64_t* events_total, int mode, cudaStream_t s);
+
+// ---- jitconn.cu
 // Scatter of JIT rows: spike ids < split use `lo` (row id = spike id) into y;
 // ids >= split use `hi` (row id = spike id - split) into y_hi.
 bp_status launch_jit_event_mv(const JitArgs& lo, const JitArgs& hi, int64_t split, int64_t n_post,

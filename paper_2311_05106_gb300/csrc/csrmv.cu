@@ -17,64 +17,12 @@
 // expected number of events, so no host synchronisation is needed.
 #include "bp_common.cuh"
 #include "bp_internal.h"
+#include "bp_rows.cuh"
 
 namespace bp {
 namespace {
 
 constexpr int kDirectThreads = 256;
-
-// Lanes per row: enough that a segment is one to two passes of the group.
-__device__ __forceinline__ int pick_group(int64_t nnz, int64_t n_pre, int64_t tiles) {
-    const int64_t denom = (n_pre > 0 ? n_pre : 1) * (tiles > 0 ? tiles : 1);
-    const int64_t mean = nnz / denom;
-    if (mean >= 48) return 32;
-    if (mean >= 24) return 16;
-    if (mean >= 12) return 8;
-    return 4;
-}
-
-template <typename Acc>
-__device__ __forceinline__ Acc event_value(float w) {
-    if constexpr (std::is_same<Acc, int32_t>::value) {
-        return 1;
-    } else {
-        return w;
-    }
-}
-
-// out[indices[j] - col0] += value(w_j) for j = b0 + lane, b0 + lane + G, ...
-template <typename Acc, int WK>
-__device__ __forceinline__ void scatter_segment(const int32_t* __restrict__ indices, const void* __restrict__ data,
-                                                float w_homo, int64_t b0, int64_t b1, int lane, int G,
-                                                Acc* __restrict__ out, int64_t col0) {
-    int64_t j = b0 + lane;
-    for (; j + 3 * G < b1; j += 4 * G) {
-        int32_t c[4];
-        float w[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) c[u] = ld_stream(indices + j + u * G);
-#pragma unroll
-        for (int u = 0; u < 4; ++u) w[u] = load_weight<WK>(data, j + u * G, w_homo);
-#pragma unroll
-        for (int u = 0; u < 4; ++u) acc_add(out + (c[u] - col0), event_value<Acc>(w[u]));
-    }
-    for (; j < b1; j += G) {
-        const int32_t c = ld_stream(indices + j);
-        const float w = load_weight<WK>(data, j, w_homo);
-        acc_add(out + (c - col0), event_value<Acc>(w));
-    }
-}
-
-// Adds v (one value per thread) into *dst with one atomic per CTA.
-__device__ __forceinline__ void block_add_i64(int64_t v, int64_t* dst) {
-    __shared__ unsigned long long s_sum;
-    if (threadIdx.x == 0) s_sum = 0;
-    __syncthreads();
-    v = group_reduce_sum(v, 32);
-    if ((threadIdx.x & 31) == 0 && v) atomicAdd(&s_sum, static_cast<unsigned long long>(v));
-    __syncthreads();
-    if (threadIdx.x == 0 && s_sum) atomicAdd(reinterpret_cast<unsigned long long*>(dst), s_sum);
-}
 
 // mode: 0 auto, 1 direct, 2 tiled.  W = tile width (post columns per tile),
 // S = number of tiles (the grid is S x R CTAs).  With SPLIT, rows >= split

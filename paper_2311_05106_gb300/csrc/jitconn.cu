@@ -12,96 +12,13 @@
 // (flushed once per CTA, skipping zeros), otherwise atomics into L2.
 #include "bp_common.cuh"
 #include "bp_internal.h"
+#include "bp_rows.cuh"
 
 namespace bp {
 namespace {
 
 constexpr int kJitThreads = 512;
 constexpr int kJitWarps = kJitThreads / 32;
-
-// Weight of synapses 4 blk + m (m = 0..3) of `row`.
-template <int WK>
-__device__ __forceinline__ void jit_weights(const JitArgs& d, uint32_t blk, uint32_t row, float w[4]) {
-    if constexpr (WK == BP_JIT_UNIFORM) {
-        const uint4 x = Philox::block(make_uint4(blk, row, 1u, 0u), static_cast<uint32_t>(d.seed),
-                                      static_cast<uint32_t>(d.seed >> 32));
-        const float span = d.w1 - d.w0;
-        const float s24 = 1.0f / 16777216.0f;
-        w[0] = d.w0 + span * (static_cast<float>(x.x >> 8) * s24);
-        w[1] = d.w0 + span * (static_cast<float>(x.y >> 8) * s24);
-        w[2] = d.w0 + span * (static_cast<float>(x.z >> 8) * s24);
-        w[3] = d.w0 + span * (static_cast<float>(x.w >> 8) * s24);
-    } else if constexpr (WK == BP_JIT_NORMAL) {
-        const float s24 = 1.0f / 16777216.0f;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const uint4 x = Philox::block(make_uint4(2u * blk + h, row, 2u, 0u), static_cast<uint32_t>(d.seed),
-                                          static_cast<uint32_t>(d.seed >> 32));
-            const float u1a = static_cast<float>((x.x >> 8) + 1u) * s24;
-            const float u2a = static_cast<float>(x.y >> 8) * s24;
-            const float u1b = static_cast<float>((x.z >> 8) + 1u) * s24;
-            const float u2b = static_cast<float>(x.w >> 8) * s24;
-            w[2 * h] = d.w0 + d.w1 * (sqrtf(-2.0f * logf(u1a)) * cospif(2.0f * u2a));
-            w[2 * h + 1] = d.w0 + d.w1 * (sqrtf(-2.0f * logf(u1b)) * cospif(2.0f * u2b));
-        }
-    } else {
-        w[0] = w[1] = w[2] = w[3] = d.w0;
-    }
-}
-
-// Walks row `row` with the calling warp; f(q, k, w) runs for every target
-// q < n_post (k = synapse index within the row).  Returns this lane's count.
-template <int WK, typename F>
-__device__ __forceinline__ int64_t jit_walk(const JitArgs& d, uint32_t row, int64_t n_post, F&& f) {
-    const uint32_t lane = threadIdx.x & 31u;
-    const uint32_t k0 = static_cast<uint32_t>(d.seed), k1 = static_cast<uint32_t>(d.seed >> 32);
-    int64_t carry = -1;
-    int64_t count = 0;
-    for (uint32_t c = 0;; c += 32u) {
-        const uint32_t blk = c + lane;
-        const uint4 x = Philox::block(make_uint4(blk, row, 0u, 0u), k0, k1);
-        const uint32_t g0 = 1u + __umulhi(x.x, d.K);
-        const uint32_t g1 = 1u + __umulhi(x.y, d.K);
-        const uint32_t g2 = 1u + __umulhi(x.z, d.K);
-        const uint32_t g3 = 1u + __umulhi(x.w, d.K);
-        const uint64_t s4 = static_cast<uint64_t>(g0) + g1 + g2 + g3;
-        const uint64_t incl = warp_inclusive_scan(s4);
-        const int64_t q0 = carry + static_cast<int64_t>(incl - s4) + g0;
-        const int64_t q1 = q0 + g1, q2 = q1 + g2, q3 = q2 + g3;
-        if (q0 < n_post) {
-            float w[4];
-            jit_weights<WK>(d, blk, row, w);
-            const uint64_t kb = 4ull * blk;
-            f(q0, kb, w[0]);
-            ++count;
-            if (q1 < n_post) { f(q1, kb + 1, w[1]); ++count; }
-            if (q2 < n_post) { f(q2, kb + 2, w[2]); ++count; }
-            if (q3 < n_post) { f(q3, kb + 3, w[3]); ++count; }
-        }
-        carry += static_cast<int64_t>(__shfl_sync(FULL_MASK, incl, 31));
-        if (carry >= n_post - 1) break;
-    }
-    return count;
-}
-
-template <typename Acc>
-__device__ __forceinline__ Acc jit_value(float w) {
-    if constexpr (std::is_same<Acc, int32_t>::value) {
-        return 1;
-    } else {
-        return w;
-    }
-}
-
-__device__ __forceinline__ void block_add_i64(int64_t v, int64_t* dst) {
-    __shared__ unsigned long long s_sum;
-    if (threadIdx.x == 0) s_sum = 0;
-    __syncthreads();
-    v = group_reduce_sum(v, 32);
-    if ((threadIdx.x & 31) == 0 && v) atomicAdd(&s_sum, static_cast<unsigned long long>(v));
-    __syncthreads();
-    if (threadIdx.x == 0 && s_sum) atomicAdd(reinterpret_cast<unsigned long long*>(dst), s_sum);
-}
 
 // Event scatter of JIT rows.  SMEM: the CTA accumulates all n_post columns
 // (two vectors with SPLIT) in shared memory of `wpad` entries each.
@@ -129,7 +46,7 @@ __global__ void __launch_bounds__(kJitThreads) k_jit_scatter(JitArgs lo, JitArgs
         const JitArgs& d = upper ? hi : lo;
         const uint32_t row = static_cast<uint32_t>(upper ? i - split : i);
         Acc* out = SMEM ? (acc + (upper ? wpad : 0)) : (upper ? y_hi : y);
-        ev += jit_walk<WK>(d, row, n_post, [&](int64_t q, uint64_t, float w) { acc_add(out + q, jit_value<Acc>(w)); });
+        ev += jit_walk<WK>(d, row, n_post, [&](int64_t q, uint64_t, float w) { acc_add(out + q, event_value<Acc>(w)); });
     }
     if constexpr (SMEM) {
         __syncthreads();

@@ -1,174 +1,375 @@
-// lif.cu -- fused COBA / exponential-synapse / LIF step with spike-list
-// compaction (a1-a4), and dense-event compaction.
+// lif.cu -- the fused neuron step (a1-a4) and, for the network, the delivery
+// of the step's spikes in the same kernel (a5/a6).
 //
-// One pass over the neuron state (structure of arrays, FP32): decay and event
-// add of both conductances (Appendix E), COBA current with the pre-update
-// potential (Appendix F), exponential-Euler membrane update with refractory
-// clamp, threshold and reset.  Spiking neurons are compacted per CTA into a
-// shared-memory buffer (warp ballot + popcount, block prefix) and appended to
-// the global spike list with one atomic per CTA flush, so the list costs a
-// handful of L2 atomics per step instead of one per warp.
+// Neuron pass.  Structure-of-arrays FP32 state; each thread updates VEC = 4
+// consecutive neurons per grid-stride iteration with 16-byte loads and
+// stores: decay and event add of both conductances (Appendix E), COBA
+// current with the pre-update potential (Appendix F), exponential-Euler
+// membrane update with refractory clamp, threshold and reset.  Spike flags
+// stay in a 32-bit register mask (bit = iteration * VEC + element), so the
+// loop has no barrier; the grid is sized so that no thread runs more than
+// 32 / VEC iterations.  One block-wide prefix over the masks then compacts
+// the CTA's spikes into shared memory.
+//
+// Delivery.  In the network step each CTA then delivers its own spikes:
+// groups of lanes walk the stored CSR rows, or whole warps regenerate the
+// JIT rows, with atomics into the OTHER half of the double-buffered event
+// accumulators (the half this step did not read), which the next step reads
+// (zero delay).  The spike list and the per-step record are optional outputs.
+#include <mutex>
+#include <unordered_map>
+
 #include "bp_common.cuh"
 #include "bp_internal.h"
+#include "bp_rows.cuh"
 
 namespace bp {
 namespace {
 
-constexpr int kLifThreads = 256;
-constexpr int kLifWarps = kLifThreads / 32;
-constexpr int kSpikeBuf = 2048;
+constexpr int kStepThreads = 256;
+constexpr int kStepWarps = kStepThreads / 32;
+constexpr int kMaskBits = 32;
 
-struct SpikeStage {
-    int32_t ids[kSpikeBuf];
-    int32_t warp_cnt[kLifWarps];
-    int32_t base;
-    int32_t red[2][kLifWarps];
+enum { CONN_NONE = 0, CONN_CSR = 1, CONN_JIT = 2 };
+
+struct StepArgs {
+    LifConst c;
+    int64_t n, n_e;
+    float* V;
+    float* ge;
+    float* gi;
+    int32_t* ref;
+    void* ye_in;   // read and zeroed this step
+    void* yi_in;
+    void* ye_out;  // receive this step's deliveries
+    void* yi_out;
+    const float* I_vec;
+    uint8_t* spk;
+    int32_t* spike_list;
+    int32_t* n_spikes;
+    int32_t* clear_counter;
+    int64_t* totals;  // [0] E spikes, [1] I spikes, [2] events (nullable)
+    const NetCtrl* ctrl;
+    int32_t t_local;
+    CsrArgs csr;
+    int32_t group;  // lanes per CSR row in the delivery
+    JitArgs je, ji;
 };
 
-// Adds this iteration's spikes (flag s, id i) to the CTA buffer; `count` is
-// the buffer fill, identical in every thread.  Ends with a barrier.
-__device__ __forceinline__ void stage_spikes(SpikeStage& st, bool s, int64_t i, int& count) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const unsigned m = __ballot_sync(FULL_MASK, s);
-    if (lane == 0) st.warp_cnt[warp] = __popc(m);
-    __syncthreads();
-    int off = 0, total = 0;
-#pragma unroll
-    for (int w = 0; w < kLifWarps; ++w) {
-        const int c = st.warp_cnt[w];
-        off += (w < warp) ? c : 0;
-        total += c;
-    }
-    if (s) st.ids[count + off + __popc(m & lanemask_lt())] = static_cast<int32_t>(i);
-    count += total;
-    __syncthreads();
-}
+struct StepSmem {
+    int32_t ids[kStepThreads * kMaskBits];
+    int32_t warp_sum[kStepWarps];
+    int32_t total;
+    int32_t base;
+    long long red[3][kStepWarps];
+};
 
-// Appends the CTA buffer to the global list (one atomic) and empties it.
-// Positions at or beyond `cap` (a counter that was not zeroed) are dropped.
-__device__ __forceinline__ void flush_spikes(SpikeStage& st, int& count, int32_t* spike_list, int32_t* n_spikes,
-                                             int64_t cap) {
-    if (count == 0) return;  // uniform across the CTA
-    if (threadIdx.x == 0) st.base = atomicAdd(n_spikes, count);
-    __syncthreads();
-    const int64_t base = st.base;
-    for (int k = threadIdx.x; k < count; k += kLifThreads)
-        if (base + k >= 0 && base + k < cap) spike_list[base + k] = st.ids[k];
-    count = 0;
-    __syncthreads();
+// One neuron; returns true if it spikes.
+__device__ __forceinline__ bool neuron_update(const LifConst& c, float& v, float& g_e, float& g_i, int32_t& r,
+                                              float add_e, float add_i, float I_add) {
+    g_e = g_e * c.a_e + add_e;
+    g_i = g_i * c.a_i + add_i;
+    const float I = g_e * (c.E_e - v) + g_i * (c.E_i - v) + c.I_ext + I_add;
+    if (r > 0) {
+        r -= 1;
+        return false;
+    }
+    const float v_inf = c.V_rest + c.R * I;
+    v = v_inf + (v - v_inf) * c.a_m;
+    if (v > c.V_th) {
+        v = c.V_reset;
+        r = c.ref_steps;
+        return true;
+    }
+    return false;
 }
 
 template <bool COUNTS>
-__global__ void __launch_bounds__(kLifThreads) k_lif_step(
-    LifConst c, int64_t n, int64_t n_e, float* __restrict__ V, float* __restrict__ ge,
-    float* __restrict__ gi, int32_t* __restrict__ ref, void* __restrict__ ye_, void* __restrict__ yi_,
-    const float* __restrict__ I_vec, uint8_t* __restrict__ spk, int32_t* __restrict__ spike_list,
-    int32_t* __restrict__ n_spikes, int32_t* __restrict__ clear_counter, int64_t* __restrict__ totals,
-    const NetCtrl* __restrict__ ctrl, int32_t t_local) {
-    __shared__ SpikeStage st;
-    using Y = typename std::conditional<COUNTS, int32_t, float>::type;
-    Y* __restrict__ ye = static_cast<Y*>(ye_);
-    Y* __restrict__ yi = static_cast<Y*>(yi_);
-    if (clear_counter && blockIdx.x == 0 && threadIdx.x == 0) *clear_counter = 0;
+__device__ __forceinline__ float event_add(typename std::conditional<COUNTS, int32_t, float>::type y, float w) {
+    if constexpr (COUNTS) {
+        return w * static_cast<float>(y);
+    } else {
+        return y;
+    }
+}
 
-    int count = 0;
+template <bool COUNTS, int VEC, int CONN, int WK>
+__global__ void __launch_bounds__(kStepThreads, 4) k_step(StepArgs a) {
+    __shared__ StepSmem sm;
+    using Y = typename std::conditional<COUNTS, int32_t, float>::type;
+    using Y4 = typename std::conditional<COUNTS, int4, float4>::type;
+    const LifConst& c = a.c;
+    Y* __restrict__ ye = static_cast<Y*>(a.ye_in);
+    Y* __restrict__ yi = static_cast<Y*>(a.yi_in);
+    if (a.clear_counter && blockIdx.x == 0 && threadIdx.x == 0) *a.clear_counter = 0;
+
+    uint32_t mask = 0;
     int cnt_e = 0, cnt_i = 0;
-    const int64_t stride = static_cast<int64_t>(gridDim.x) * kLifThreads;
-    for (int64_t base = static_cast<int64_t>(blockIdx.x) * kLifThreads; base < n; base += stride) {
-        const int64_t i = base + threadIdx.x;
-        bool s = false;
-        if (i < n) {
-            const Y ce = ye[i], ci = yi[i];
-            float add_e, add_i;
-            if constexpr (COUNTS) {
-                add_e = c.w_e * static_cast<float>(ce);
-                add_i = c.w_i * static_cast<float>(ci);
-            } else {
-                add_e = ce;
-                add_i = ci;
+    const int64_t nq = (a.n + VEC - 1) / VEC;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * kStepThreads;
+    const int64_t q0 = static_cast<int64_t>(blockIdx.x) * kStepThreads + threadIdx.x;
+    int it = 0;
+    for (int64_t q = q0; q < nq; q += stride, ++it) {
+        const int64_t i0 = q * VEC;
+        uint32_t bits = 0;
+        if (VEC == 4 && i0 + 4 <= a.n) {
+            float4 v = *reinterpret_cast<const float4*>(a.V + i0);
+            float4 g_e = *reinterpret_cast<const float4*>(a.ge + i0);
+            float4 g_i = *reinterpret_cast<const float4*>(a.gi + i0);
+            int4 r = *reinterpret_cast<const int4*>(a.ref + i0);
+            const Y4 ce = *reinterpret_cast<const Y4*>(ye + i0);
+            const Y4 ci = *reinterpret_cast<const Y4*>(yi + i0);
+            float4 Iv = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (a.I_vec) Iv = *reinterpret_cast<const float4*>(a.I_vec + i0);
+            const int4 r_old = r;
+            bits |= neuron_update(c, v.x, g_e.x, g_i.x, r.x, event_add<COUNTS>(ce.x, c.w_e), event_add<COUNTS>(ci.x, c.w_i), Iv.x) ? 1u : 0u;
+            bits |= neuron_update(c, v.y, g_e.y, g_i.y, r.y, event_add<COUNTS>(ce.y, c.w_e), event_add<COUNTS>(ci.y, c.w_i), Iv.y) ? 2u : 0u;
+            bits |= neuron_update(c, v.z, g_e.z, g_i.z, r.z, event_add<COUNTS>(ce.z, c.w_e), event_add<COUNTS>(ci.z, c.w_i), Iv.z) ? 4u : 0u;
+            bits |= neuron_update(c, v.w, g_e.w, g_i.w, r.w, event_add<COUNTS>(ce.w, c.w_e), event_add<COUNTS>(ci.w, c.w_i), Iv.w) ? 8u : 0u;
+            *reinterpret_cast<float4*>(a.V + i0) = v;
+            *reinterpret_cast<float4*>(a.ge + i0) = g_e;
+            *reinterpret_cast<float4*>(a.gi + i0) = g_i;
+            if (r.x != r_old.x || r.y != r_old.y || r.z != r_old.z || r.w != r_old.w)
+                *reinterpret_cast<int4*>(a.ref + i0) = r;
+            if (ce.x != Y(0) || ce.y != Y(0) || ce.z != Y(0) || ce.w != Y(0))
+                *reinterpret_cast<Y4*>(ye + i0) = Y4{};
+            if (ci.x != Y(0) || ci.y != Y(0) || ci.z != Y(0) || ci.w != Y(0))
+                *reinterpret_cast<Y4*>(yi + i0) = Y4{};
+            if (a.spk) {
+                const uint32_t packed = (bits & 1u) | ((bits & 2u) << 7) | ((bits & 4u) << 14) | ((bits & 8u) << 21);
+                *reinterpret_cast<uint32_t*>(a.spk + i0) = packed;
             }
-            if (ce != Y(0)) ye[i] = Y(0);
-            if (ci != Y(0)) yi[i] = Y(0);
-            const float g_e = ge[i] * c.a_e + add_e;
-            const float g_i = gi[i] * c.a_i + add_i;
-            ge[i] = g_e;
-            gi[i] = g_i;
-            float v = V[i];
-            float I = g_e * (c.E_e - v) + g_i * (c.E_i - v) + c.I_ext;
-            if (I_vec) I += I_vec[i];
-            const int32_t r = ref[i];
-            if (r > 0) {
-                ref[i] = r - 1;
-            } else {
-                const float v_inf = c.V_rest + c.R * I;
-                v = v_inf + (v - v_inf) * c.a_m;
-                if (v > c.V_th) {
-                    s = true;
-                    v = c.V_reset;
-                    ref[i] = c.ref_steps;
-                }
-                V[i] = v;
-            }
-            if (spk) spk[i] = s ? 1 : 0;
-            if (s) {
-                if (i < n_e) ++cnt_e; else ++cnt_i;
+        } else {
+#pragma unroll
+            for (int k = 0; k < VEC; ++k) {
+                const int64_t i = i0 + k;
+                if (i >= a.n) break;
+                float v = a.V[i], g_e = a.ge[i], g_i = a.gi[i];
+                int32_t r = a.ref[i];
+                const int32_t r_old = r;
+                const Y ce = ye[i], ci = yi[i];
+                const float Iv = a.I_vec ? a.I_vec[i] : 0.f;
+                const bool s = neuron_update(c, v, g_e, g_i, r, event_add<COUNTS>(ce, c.w_e),
+                                             event_add<COUNTS>(ci, c.w_i), Iv);
+                a.V[i] = v;
+                a.ge[i] = g_e;
+                a.gi[i] = g_i;
+                if (r != r_old) a.ref[i] = r;
+                if (ce != Y(0)) ye[i] = Y(0);
+                if (ci != Y(0)) yi[i] = Y(0);
+                if (a.spk) a.spk[i] = s ? 1 : 0;
+                bits |= s ? (1u << k) : 0u;
             }
         }
-        if (count + kLifThreads > kSpikeBuf) flush_spikes(st, count, spike_list, n_spikes, n);
-        stage_spikes(st, s, i, count);
+        if (bits) {
+            mask |= bits << (it * VEC);
+#pragma unroll
+            for (int k = 0; k < VEC; ++k)
+                if (bits & (1u << k)) {
+                    if (i0 + k < a.n_e) ++cnt_e; else ++cnt_i;
+                    // the delivery below reads this row's extent: start the fetch now
+                    if constexpr (CONN == CONN_CSR)
+                        asm volatile("prefetch.global.L2 [%0];" ::"l"(a.csr.indptr + i0 + k));
+                }
+        }
     }
-    flush_spikes(st, count, spike_list, n_spikes, n);
 
-    if (totals || ctrl) {
-        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        cnt_e = group_reduce_sum(cnt_e, 32);
-        cnt_i = group_reduce_sum(cnt_i, 32);
+    // ---- compaction of the CTA's spikes into shared memory
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int mine = __popc(mask);
+    int incl = mine;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int o = __shfl_up_sync(FULL_MASK, incl, d);
+        if (lane >= d) incl += o;
+    }
+    if (lane == 31) sm.warp_sum[warp] = incl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int w = 0; w < kStepWarps; ++w) {
+            const int v = sm.warp_sum[w];
+            sm.warp_sum[w] = run;
+            run += v;
+        }
+        sm.total = run;
+    }
+    __syncthreads();
+    int off = sm.warp_sum[warp] + incl - mine;
+    for (uint32_t m = mask; m; m &= m - 1) {
+        const int b = __ffs(m) - 1;
+        const int64_t i = (q0 + static_cast<int64_t>(b / VEC) * stride) * VEC + (b % VEC);
+        sm.ids[off++] = static_cast<int32_t>(i);
+    }
+    __syncthreads();
+    const int total = sm.total;
+
+    // ---- optional global spike list (one atomic per CTA)
+    if (a.spike_list && total > 0) {
+        if (threadIdx.x == 0) sm.base = atomicAdd(a.n_spikes, total);
+        __syncthreads();
+        const int64_t base = sm.base;
+        for (int k = threadIdx.x; k < total; k += kStepThreads)
+            if (base + k >= 0 && base + k < a.n) a.spike_list[base + k] = sm.ids[k];
+    }
+
+    // ---- delivery of this CTA's spikes (network step)
+    int64_t ev = 0;
+    if constexpr (CONN == CONN_CSR) {
+        const CsrArgs& A = a.csr;
+        const int G = a.group;
+        const int gl = threadIdx.x % G;
+        const int ng = kStepThreads / G;
+        Y* out_e = static_cast<Y*>(a.ye_out);
+        Y* out_i = static_cast<Y*>(a.yi_out);
+        for (int k = threadIdx.x / G; k < total; k += ng) {
+            const int32_t i = sm.ids[k];
+            const int64_t b0 = A.indptr[i], b1 = A.indptr[i + 1];
+            if (gl == 0) ev += b1 - b0;
+            scatter_segment<Y, WK>(A.indices, A.data, A.w_homo, b0, b1, gl, G, i < a.n_e ? out_e : out_i, 0);
+        }
+    } else if constexpr (CONN == CONN_JIT) {
+        Y* out_e = static_cast<Y*>(a.ye_out);
+        Y* out_i = static_cast<Y*>(a.yi_out);
+        for (int k = warp; k < total; k += kStepWarps) {
+            const int32_t i = sm.ids[k];
+            const bool upper = i >= a.n_e;
+            const JitArgs& d = upper ? a.ji : a.je;
+            Y* out = upper ? out_i : out_e;
+            ev += jit_walk<BP_JIT_HOMO>(d, static_cast<uint32_t>(upper ? i - a.n_e : i), a.n,
+                                        [&](int64_t q, uint64_t, float w) { acc_add(out + q, event_value<Y>(w)); });
+        }
+    }
+
+    // ---- totals and the per-step record
+    if (a.totals || a.ctrl) {
+        long long v0 = group_reduce_sum(static_cast<long long>(cnt_e), 32);
+        long long v1 = group_reduce_sum(static_cast<long long>(cnt_i), 32);
+        long long v2 = group_reduce_sum(static_cast<long long>(ev), 32);
         if (lane == 0) {
-            st.red[0][warp] = cnt_e;
-            st.red[1][warp] = cnt_i;
+            sm.red[0][warp] = v0;
+            sm.red[1][warp] = v1;
+            sm.red[2][warp] = v2;
         }
         __syncthreads();
         if (threadIdx.x == 0) {
-            int se = 0, si = 0;
-            for (int w = 0; w < kLifWarps; ++w) {
-                se += st.red[0][w];
-                si += st.red[1][w];
+            long long se = 0, si = 0, sv = 0;
+            for (int w = 0; w < kStepWarps; ++w) {
+                se += sm.red[0][w];
+                si += sm.red[1][w];
+                sv += sm.red[2][w];
             }
-            if (totals && (se | si)) {
-                atomicAdd(reinterpret_cast<unsigned long long*>(totals + 0), static_cast<unsigned long long>(se));
-                atomicAdd(reinterpret_cast<unsigned long long*>(totals + 1), static_cast<unsigned long long>(si));
+            if (a.totals) {
+                if (se) atomicAdd(reinterpret_cast<unsigned long long*>(a.totals + 0), static_cast<unsigned long long>(se));
+                if (si) atomicAdd(reinterpret_cast<unsigned long long*>(a.totals + 1), static_cast<unsigned long long>(si));
+                if (sv && CONN != CONN_NONE)
+                    atomicAdd(reinterpret_cast<unsigned long long*>(a.totals + 2), static_cast<unsigned long long>(sv));
             }
-            if (ctrl && ctrl->record && (se | si)) {
-                const int64_t idx = ctrl->step + t_local - ctrl->record_base;
-                if (idx >= 0 && idx < ctrl->record_len) {
-                    atomicAdd(ctrl->record + 2 * idx, se);
-                    atomicAdd(ctrl->record + 2 * idx + 1, si);
+            if (a.ctrl && a.ctrl->record && (se | si)) {
+                const int64_t idx = a.ctrl->step + a.t_local - a.ctrl->record_base;
+                if (idx >= 0 && idx < a.ctrl->record_len) {
+                    atomicAdd(a.ctrl->record + 2 * idx, static_cast<int32_t>(se));
+                    atomicAdd(a.ctrl->record + 2 * idx + 1, static_cast<int32_t>(si));
                 }
             }
         }
     }
 }
 
-__global__ void __launch_bounds__(kLifThreads) k_spike_compact(int64_t n, const uint8_t* __restrict__ events,
-                                                              int32_t* __restrict__ spike_list,
-                                                              int32_t* __restrict__ n_spikes) {
-    __shared__ SpikeStage st;
-    int count = 0;
-    const int64_t stride = static_cast<int64_t>(gridDim.x) * kLifThreads;
-    for (int64_t base = static_cast<int64_t>(blockIdx.x) * kLifThreads; base < n; base += stride) {
+// Dense event flags -> spike list (Appendix B's `events` to the compact form).
+__global__ void __launch_bounds__(kStepThreads) k_spike_compact(int64_t n, const uint8_t* __restrict__ events,
+                                                               int32_t* __restrict__ spike_list,
+                                                               int32_t* __restrict__ n_spikes) {
+    __shared__ int32_t warp_sum[kStepWarps];
+    __shared__ int32_t s_base;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * kStepThreads;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int64_t base = static_cast<int64_t>(blockIdx.x) * kStepThreads; base < n; base += stride) {
         const int64_t i = base + threadIdx.x;
         const bool s = (i < n) && events[i] != 0;
-        if (count + kLifThreads > kSpikeBuf) flush_spikes(st, count, spike_list, n_spikes, n);
-        stage_spikes(st, s, i, count);
+        const unsigned m = __ballot_sync(FULL_MASK, s);
+        if (lane == 0) warp_sum[warp] = __popc(m);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int run = 0;
+            for (int w = 0; w < kStepWarps; ++w) {
+                const int v = warp_sum[w];
+                warp_sum[w] = run;
+                run += v;
+            }
+            s_base = run ? atomicAdd(n_spikes, run) : 0;
+        }
+        __syncthreads();
+        if (s) {
+            const int64_t pos = static_cast<int64_t>(s_base) + warp_sum[warp] + __popc(m & lanemask_lt());
+            if (pos < n) spike_list[pos] = static_cast<int32_t>(i);
+        }
+        __syncthreads();
     }
-    flush_spikes(st, count, spike_list, n_spikes, n);
 }
 
-int lif_grid(int64_t n) {
-    const int64_t need = (n + kLifThreads - 1) / kLifThreads;
-    const int64_t cap = static_cast<int64_t>(sm_count()) * 8;
-    const int64_t g = need < cap ? need : cap;
-    return static_cast<int>(g > 0 ? g : 1);
+bool aligned(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
+
+// Resident CTAs per SM of a kernel instantiation (cached per kernel).
+int resident_per_sm(const void* kernel) {
+    static std::mutex mu;
+    static std::unordered_map<const void*, int> cache;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(kernel);
+    if (it != cache.end()) return it->second;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, kStepThreads, 0) != cudaSuccess || nb < 1) nb = 1;
+    cache[kernel] = nb;
+    return nb;
+}
+
+// One resident wave when it covers the state (so each CTA's delivery tail is
+// paid once per step), more CTAs only when the 32-bit spike mask needs them.
+template <typename K>
+bp_status launch_k(K kernel, const StepArgs& a, int vec, cudaStream_t s) {
+    const int64_t nq = (a.n + vec - 1) / vec;
+    const int64_t per_thread = kMaskBits / vec;
+    int64_t grid = static_cast<int64_t>(sm_count()) * resident_per_sm(reinterpret_cast<const void*>(kernel));
+    const int64_t need_min = (nq + kStepThreads * per_thread - 1) / (kStepThreads * per_thread);
+    const int64_t need_max = (nq + kStepThreads - 1) / kStepThreads;
+    if (grid > need_max) grid = need_max;
+    if (grid < need_min) grid = need_min;
+    if (grid < 1) grid = 1;
+    kernel<<<static_cast<unsigned>(grid), kStepThreads, 0, s>>>(a);
+    BP_LAUNCHED();
+    return BP_OK;
+}
+
+template <bool COUNTS, int VEC>
+bp_status launch_step_vec(const StepArgs& a, int conn, int wk, cudaStream_t s) {
+    if (conn == CONN_NONE) return launch_k(k_step<COUNTS, VEC, CONN_NONE, WK_HOMO>, a, VEC, s);
+    if (conn == CONN_JIT) return launch_k(k_step<COUNTS, VEC, CONN_JIT, WK_HOMO>, a, VEC, s);
+    if (wk == WK_F32) return launch_k(k_step<COUNTS, VEC, CONN_CSR, WK_F32>, a, VEC, s);
+    if (wk == WK_BF16) return launch_k(k_step<COUNTS, VEC, CONN_CSR, WK_BF16>, a, VEC, s);
+    return launch_k(k_step<COUNTS, VEC, CONN_CSR, WK_HOMO>, a, VEC, s);
+}
+
+bp_status launch_step(const StepArgs& a, bool counts, int conn, int wk, cudaStream_t s) {
+    if (a.n == 0) {
+        if (a.clear_counter) BP_CUDA(cudaMemsetAsync(a.clear_counter, 0, sizeof(int32_t), s));
+        return BP_OK;
+    }
+    const bool vec = aligned(a.V, 16) && aligned(a.ge, 16) && aligned(a.gi, 16) && aligned(a.ref, 16) &&
+                     aligned(a.ye_in, 16) && aligned(a.yi_in, 16) && aligned(a.I_vec, 16) && aligned(a.spk, 4);
+    if (counts) return vec ? launch_step_vec<true, 4>(a, conn, wk, s) : launch_step_vec<true, 1>(a, conn, wk, s);
+    return vec ? launch_step_vec<false, 4>(a, conn, wk, s) : launch_step_vec<false, 1>(a, conn, wk, s);
+}
+
+StepArgs base_args(const LifConst& c, int64_t n, int64_t n_e, float* V, float* ge, float* gi, int32_t* ref) {
+    StepArgs a{};
+    a.c = c;
+    a.n = n;
+    a.n_e = n_e;
+    a.V = V;
+    a.ge = ge;
+    a.gi = gi;
+    a.ref = ref;
+    return a;
 }
 
 }  // namespace
@@ -177,25 +378,51 @@ bp_status launch_lif_step(const LifConst& c, int64_t n, int64_t n_e, float* V, f
                           int32_t* ref, void* ye, void* yi, bool counts, const float* I_vec, uint8_t* spk,
                           int32_t* spike_list, int32_t* n_spikes, int32_t* clear_counter, int64_t* totals,
                           const NetCtrl* ctrl, int32_t t_local, cudaStream_t s) {
-    if (n == 0) {
-        if (clear_counter) BP_CUDA(cudaMemsetAsync(clear_counter, 0, sizeof(int32_t), s));
-        return BP_OK;
-    }
-    const int grid = lif_grid(n);
-    if (counts)
-        k_lif_step<true><<<grid, kLifThreads, 0, s>>>(c, n, n_e, V, ge, gi, ref, ye, yi, I_vec, spk, spike_list,
-                                                      n_spikes, clear_counter, totals, ctrl, t_local);
-    else
-        k_lif_step<false><<<grid, kLifThreads, 0, s>>>(c, n, n_e, V, ge, gi, ref, ye, yi, I_vec, spk, spike_list,
-                                                       n_spikes, clear_counter, totals, ctrl, t_local);
-    BP_LAUNCHED();
-    return BP_OK;
+    StepArgs a = base_args(c, n, n_e, V, ge, gi, ref);
+    a.ye_in = ye;
+    a.yi_in = yi;
+    a.I_vec = I_vec;
+    a.spk = spk;
+    a.spike_list = spike_list;
+    a.n_spikes = n_spikes;
+    a.clear_counter = clear_counter;
+    a.totals = totals;
+    a.ctrl = ctrl;
+    a.t_local = t_local;
+    return launch_step(a, counts, CONN_NONE, WK_HOMO, s);
+}
+
+bp_status launch_network_step(const NetStepLaunch& L, int parity, int32_t t_local, cudaStream_t s) {
+    StepArgs a = base_args(L.c, L.n, L.n_e, L.V, L.ge, L.gi, L.ref);
+    const size_t half = static_cast<size_t>(L.n) * 4;
+    char* ye = static_cast<char*>(L.ye2);
+    char* yi = static_cast<char*>(L.yi2);
+    a.ye_in = ye + (parity ? half : 0);
+    a.yi_in = yi + (parity ? half : 0);
+    a.ye_out = ye + (parity ? 0 : half);
+    a.yi_out = yi + (parity ? 0 : half);
+    a.spk = L.spk;
+    a.spike_list = L.spike_list;
+    a.n_spikes = L.spike_list ? L.n_spikes + parity : nullptr;
+    a.clear_counter = L.spike_list ? L.n_spikes + (parity ^ 1) : nullptr;
+    a.totals = L.totals;
+    a.ctrl = L.ctrl;
+    a.t_local = t_local;
+    a.csr = L.csr;
+    a.group = L.group;
+    a.je = L.je;
+    a.ji = L.ji;
+    const int conn = L.jit ? CONN_JIT : CONN_CSR;
+    return launch_step(a, L.counts, conn, L.csr.wkind, s);
 }
 
 bp_status launch_spike_compact(int64_t n, const uint8_t* events, int32_t* spike_list, int32_t* n_spikes,
                                cudaStream_t s) {
     if (n == 0) return BP_OK;
-    k_spike_compact<<<lif_grid(n), kLifThreads, 0, s>>>(n, events, spike_list, n_spikes);
+    int64_t grid = (n + kStepThreads - 1) / kStepThreads;
+    const int64_t cap = static_cast<int64_t>(sm_count()) * 8;
+    if (grid > cap) grid = cap;
+    k_spike_compact<<<static_cast<unsigned>(grid), kStepThreads, 0, s>>>(n, events, spike_list, n_spikes);
     BP_LAUNCHED();
     return BP_OK;
 }
@@ -211,8 +438,8 @@ bp_status bp_lif_step(const bp_coba_params* p, int64_t n, int64_t n_e, float* V,
     BP_TRY(bp::check_coba(p));
     BP_REQUIRE(n >= 0 && n <= INT32_MAX, "n = %lld out of range", (long long)n);
     BP_REQUIRE(n_e >= 0 && n_e <= n, "n_e = %lld not in [0, n]", (long long)n_e);
-    BP_REQUIRE(n == 0 || (V && ge && gi && ref && ye && yi && spike_list && n_spikes),
-               "a required state pointer is NULL");
+    BP_REQUIRE(n == 0 || (V && ge && gi && ref && ye && yi), "a required state pointer is NULL");
+    BP_REQUIRE(!spike_list == !n_spikes, "spike_list and n_spikes must both be given or both be NULL");
     const bp::LifConst c = bp::make_lif_const(*p);
     return bp::launch_lif_step(c, n, n_e, V, ge, gi, ref, ye, yi, y_is_count != 0, I_vec, spk, spike_list,
                                n_spikes, nullptr, spike_totals, nullptr, 0, stream);

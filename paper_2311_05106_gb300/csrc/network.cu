@@ -1,15 +1,16 @@
 // network.cu -- the COBA E/I network step and the T-step simulation loop
 // (a7), plus the FP64 population statistics (a8).
 //
-// A step is two launches: the fused neuron pass (lif.cu), which also compacts
-// this step's spikes, and the delivery of those spikes through the stored CSR
+// A step is one launch (lif.cu, k_step): the neuron pass, the CTA-local
+// compaction of the step's spikes and their delivery through the stored CSR
 // or the JIT rows into the merged E and I event accumulators (AlignPost,
-// Section 3.3), consumed by the next step's neuron pass (zero delay,
-// Appendix N Listing S6).  The spike counter alternates between two slots:
-// each neuron pass appends to slot t mod 2 and clears the other, so the loop
-// needs no memset node.  bp_simulate captures a chunk of steps once in a CUDA
-// graph and replays it; per-step indices that differ between replays (the
-// record row) are read from a small device control block.
+// Section 3.3).  The accumulators are double-buffered: step t reads and
+// clears half t mod 2 and delivers into the other half, which step t + 1
+// reads (zero delay, Appendix N Listing S6), so delivery can run in the same
+// kernel as the neuron pass.  The optional spike-list counter alternates
+// between two slots the same way.  bp_simulate captures a chunk of steps once
+// in a CUDA graph and replays it; per-step indices that differ between
+// replays (the record row) are read from a small device control block.
 #include <cmath>
 #include <new>
 
@@ -18,10 +19,7 @@
 
 struct bp_net {
     bp_net_desc d;
-    bp::LifConst c;
-    bp::CsrArgs csr;
-    bp::JitArgs je, ji;
-    bool counts;
+    bp::NetStepLaunch L;
     int64_t host_step;
     bp::NetCtrl* ctrl;  // device
     cudaStream_t cap_stream;
@@ -64,19 +62,7 @@ __global__ void k_stats(const int64_t* totals, int64_t n, int64_t n_e, double dt
 }
 
 bp_status enqueue_step(bp_net* net, int parity, int32_t t_local, cudaStream_t s) {
-    const bp_net_desc& d = net->d;
-    int32_t* cnt = d.n_spikes + parity;
-    int32_t* other = d.n_spikes + (parity ^ 1);
-    BP_TRY(launch_lif_step(net->c, d.n, d.n_e, d.V, d.ge, d.gi, d.ref, d.ye, d.yi, net->counts, nullptr, d.spk,
-                           d.spike_list, cnt, other, d.totals, net->ctrl, t_local, s));
-    if (d.conn_kind == BP_CONN_CSR) {
-        BP_TRY(launch_event_csrmv(net->csr, d.spike_list, cnt, d.n, d.ye, d.yi, d.n_e, net->counts, d.totals + 2, 0,
-                                  s));
-    } else {
-        BP_TRY(launch_jit_event_mv(net->je, net->ji, d.n_e, d.n, d.spike_list, cnt, d.n, d.ye, d.yi, net->counts,
-                                   d.totals + 2, 0, s));
-    }
-    return BP_OK;
+    return launch_network_step(net->L, parity, t_local, s);
 }
 
 bp_status advance(bp_net* net, int64_t k, cudaStream_t s) {
@@ -124,32 +110,50 @@ bp_status bp_network_create(const bp_net_desc* desc, bp_net** out) {
     BP_REQUIRE(d.n > 0 && d.n <= INT32_MAX, "n = %lld out of range", (long long)d.n);
     BP_REQUIRE(d.n_e >= 0 && d.n_e <= d.n, "n_e not in [0, n]");
     BP_TRY(bp::check_coba(&d.coba));
-    BP_REQUIRE(d.V && d.ge && d.gi && d.ref && d.ye && d.yi && d.spike_list && d.n_spikes && d.totals,
-               "a required state pointer is NULL");
+    BP_REQUIRE(d.V && d.ge && d.gi && d.ref && d.ye && d.yi && d.totals, "a required state pointer is NULL");
+    BP_REQUIRE(!d.spike_list || d.n_spikes, "spike_list needs n_spikes");
     BP_REQUIRE(d.conn_kind == BP_CONN_CSR || d.conn_kind == BP_CONN_JIT, "unknown connectivity kind %d",
                d.conn_kind);
-    bool counts = true;
-    bp::CsrArgs csr{};
-    bp::JitArgs je{}, ji{};
+    bp::NetStepLaunch L{};
+    L.c = bp::make_lif_const(d.coba);
+    L.n = d.n;
+    L.n_e = d.n_e;
+    L.V = d.V;
+    L.ge = d.ge;
+    L.gi = d.gi;
+    L.ref = d.ref;
+    L.ye2 = d.ye;
+    L.yi2 = d.yi;
+    L.spk = d.spk;
+    L.spike_list = d.spike_list;
+    L.n_spikes = d.n_spikes;
+    L.totals = d.totals;
+    L.counts = true;
     if (d.conn_kind == BP_CONN_CSR) {
         BP_REQUIRE(d.indptr && d.indices, "CSR indptr or indices is NULL");
         BP_REQUIRE(d.wkind >= BP_W_HOMO && d.wkind <= BP_W_BF16, "unknown weight kind");
-        counts = (d.wkind == BP_W_HOMO) || d.data == nullptr;
-        csr.n_pre = d.n;
-        csr.n_post = d.n;
-        csr.indptr = d.indptr;
-        csr.indices = d.indices;
-        csr.data = counts ? nullptr : d.data;
-        csr.wkind = counts ? BP_W_HOMO : d.wkind;
-        csr.w_homo = 1.0f;
-        csr.tile_ptr = d.tile_ptr;
-        csr.tile_cols = d.tile_ptr ? d.tile_cols : 0;
+        L.counts = (d.wkind == BP_W_HOMO) || d.data == nullptr;
+        L.jit = false;
+        L.csr.n_pre = d.n;
+        L.csr.n_post = d.n;
+        L.csr.indptr = d.indptr;
+        L.csr.indices = d.indices;
+        L.csr.data = L.counts ? nullptr : d.data;
+        L.csr.wkind = L.counts ? BP_W_HOMO : d.wkind;
+        L.csr.w_homo = 1.0f;
+        // lanes per delivered row from the mean row length (one synchronous
+        // 8-byte read at set-up)
+        int64_t nnz = 0;
+        BP_CUDA(cudaMemcpy(&nnz, d.indptr + d.n, sizeof(int64_t), cudaMemcpyDeviceToHost));
+        const int64_t mean = nnz / d.n;
+        L.group = mean >= 48 ? 32 : mean >= 24 ? 16 : mean >= 12 ? 8 : 4;
     } else {
         bp_jit_desc de, di;
         BP_TRY(bp_jit_desc_init(&de, bp_projection_seed(d.seed, 0), d.p, BP_JIT_HOMO, 1.0f, 0.0f));
         BP_TRY(bp_jit_desc_init(&di, bp_projection_seed(d.seed, 1), d.p, BP_JIT_HOMO, 1.0f, 0.0f));
-        je = {de.seed, static_cast<uint32_t>(de.K), BP_JIT_HOMO, 1.0f, 0.0f};
-        ji = {di.seed, static_cast<uint32_t>(di.K), BP_JIT_HOMO, 1.0f, 0.0f};
+        L.jit = true;
+        L.je = {de.seed, static_cast<uint32_t>(de.K), BP_JIT_HOMO, 1.0f, 0.0f};
+        L.ji = {di.seed, static_cast<uint32_t>(di.K), BP_JIT_HOMO, 1.0f, 0.0f};
     }
     bp_net* net = new (std::nothrow) bp_net();
     if (!net) {
@@ -157,11 +161,7 @@ bp_status bp_network_create(const bp_net_desc* desc, bp_net** out) {
         return BP_ERR_OOM;
     }
     net->d = d;
-    net->c = bp::make_lif_const(d.coba);
-    net->csr = csr;
-    net->je = je;
-    net->ji = ji;
-    net->counts = counts;
+    net->L = L;
     net->host_step = 0;
     net->chunk = bp::kChunk;
     net->graph = nullptr;
@@ -172,6 +172,7 @@ bp_status bp_network_create(const bp_net_desc* desc, bp_net** out) {
         bp::set_error("cudaMalloc of the control block failed: %s", cudaGetErrorString(e));
         return BP_ERR_OOM;
     }
+    net->L.ctrl = net->ctrl;
     e = cudaMemset(net->ctrl, 0, sizeof(bp::NetCtrl));
     if (e != cudaSuccess) {
         cudaFree(net->ctrl);
@@ -187,10 +188,10 @@ bp_status bp_network_reset_counters(bp_net* net, bp_stream_t stream) {
     bp::clear_error();
     BP_REQUIRE(net, "net is NULL");
     const bp_net_desc& d = net->d;
-    BP_CUDA(cudaMemsetAsync(d.n_spikes, 0, 2 * sizeof(int32_t), stream));
+    if (d.n_spikes) BP_CUDA(cudaMemsetAsync(d.n_spikes, 0, 2 * sizeof(int32_t), stream));
     BP_CUDA(cudaMemsetAsync(d.totals, 0, 4 * sizeof(int64_t), stream));
-    BP_CUDA(cudaMemsetAsync(d.ye, 0, static_cast<size_t>(d.n) * 4, stream));
-    BP_CUDA(cudaMemsetAsync(d.yi, 0, static_cast<size_t>(d.n) * 4, stream));
+    BP_CUDA(cudaMemsetAsync(d.ye, 0, static_cast<size_t>(d.n) * 8, stream));
+    BP_CUDA(cudaMemsetAsync(d.yi, 0, static_cast<size_t>(d.n) * 8, stream));
     bp::k_reset_ctrl<<<1, 1, 0, stream>>>(net->ctrl);
     BP_LAUNCHED();
     net->host_step = 0;

@@ -40,7 +40,7 @@ class CobaNetwork:
     """
 
     def __init__(self, n, n_e=None, conn="jit", seed=2024, p=None, V0=None, csr=None, tile_cols=0,
-                 params=None, keep_spk=False, device="cuda"):
+                 params=None, keep_spk=False, keep_spikes=False, device="cuda"):
         self.n = int(n)
         self.n_e = int(n_e if n_e is not None else (4 * self.n) // 5)
         self.p = float(p if p is not None else 80.0 / self.n)
@@ -54,7 +54,7 @@ class CobaNetwork:
         self.ge = torch.zeros(self.n, dtype=f32, device=device)
         self.gi = torch.zeros(self.n, dtype=f32, device=device)
         self.ref = torch.zeros(self.n, dtype=i32, device=device)
-        self.spike_list = torch.zeros(self.n, dtype=i32, device=device)
+        self.spike_list = torch.zeros(self.n, dtype=i32, device=device) if keep_spikes else None
         self.n_spikes = torch.zeros(2, dtype=i32, device=device)
         self.totals = torch.zeros(4, dtype=torch.int64, device=device)
         self.spk = torch.zeros(self.n, dtype=torch.uint8, device=device) if keep_spk else None
@@ -86,11 +86,13 @@ class CobaNetwork:
         else:
             raise ValueError("conn must be 'jit' or 'csr'")
         ydt = i32 if counts else f32
-        self.ye = torch.zeros(self.n, dtype=ydt, device=device)
-        self.yi = torch.zeros(self.n, dtype=ydt, device=device)
+        # two halves: step t reads half t mod 2 and delivers into the other
+        self.ye = torch.zeros(2 * self.n, dtype=ydt, device=device)
+        self.yi = torch.zeros(2 * self.n, dtype=ydt, device=device)
         desc.V, desc.ge, desc.gi, desc.ref = (t.data_ptr() for t in (self.V, self.ge, self.gi, self.ref))
         desc.ye, desc.yi = self.ye.data_ptr(), self.yi.data_ptr()
-        desc.spike_list, desc.n_spikes = self.spike_list.data_ptr(), self.n_spikes.data_ptr()
+        desc.spike_list = None if self.spike_list is None else self.spike_list.data_ptr()
+        desc.n_spikes = self.n_spikes.data_ptr()
         desc.totals = self.totals.data_ptr()
         desc.spk = None if self.spk is None else self.spk.data_ptr()
         self.desc = desc
