@@ -55,6 +55,11 @@ def parse():
     ap.add_argument("--weights", default="f32", choices=["f32", "counts"])
     ap.add_argument("--neurons", type=int, default=N_NEURONS)
     ap.add_argument("--no-e2e", action="store_true")
+    # operator sweep (one JSON line per cell instead of the bench line)
+    ap.add_argument("--sweep", action="store_true")
+    ap.add_argument("--sweep-n", default="1e4,1e5,1e6")
+    ap.add_argument("--sweep-p", default="0.001,0.01,0.1")
+    ap.add_argument("--sweep-rho", default="0.001,0.01,0.1")
     return ap.parse_args()
 
 
@@ -326,11 +331,104 @@ def run_reference(args):
     return 0
 
 
+# ----------------------------------------------------------------- operator sweep
+def run_sweep(args):
+    """Standalone operators of the paper's operator benchmark (Section 4.1,
+    Appendix B / C) on synthetic inputs: n_pre = n_post = n, connection
+    probability p, Bernoulli(rho) spikes, homogeneous (integer counts) or
+    heterogeneous N(0.5, 0.1) weights stored FP32 / BF16.  Prints one JSON line
+    per cell.  Stored matrices come from the JIT materialiser (sorted rows);
+    cells whose CSR would exceed 200 GB run the JIT operator only."""
+    import torch
+    from paper_2311_05106_gb300 import binding as B
+    from paper_2311_05106_gb300 import workloads as wl
+    torch.cuda.set_device(0)
+    peak, peak_kind = peaks()
+    sizes = [int(float(x)) for x in args.sweep_n.split(",")]
+    probs = [float(x) for x in args.sweep_p.split(",")]
+    rhos = [float(x) for x in args.sweep_rho.split(",")]
+    stream = torch.cuda.current_stream()
+
+    def timeit(fn, reps):
+        fn()
+        fn()
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for a, b in evs:
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        ms = sorted(a.elapsed_time(b) for a, b in evs)
+        return ms[len(ms) // 2]
+
+    def emit(**kw):
+        print(json.dumps(kw), flush=True)
+
+    for n in sizes:
+        for p in probs:
+            seed = 1000 + n % 997 + int(p * 1e4)
+            csr_ok = p * n * n * 8 <= 200e9
+            dn = B.bp_jit_desc_init(seed, p, B.BP_JIT_NORMAL, 0.5, 0.1)
+            dh = B.bp_jit_desc_init(seed, p)
+            ip = ix = w32 = w16 = tp = None
+            tc = 0
+            if csr_ok:
+                ip, ix, w32 = B.jit_materialize(dn, n, n, data_dtype=torch.float32)
+                nnz = ix.numel()
+                w16 = w32.to(torch.bfloat16)
+                tc = B.bp_tile_cols() if n > B.bp_tile_cols() else 0
+                if tc:
+                    tp = torch.empty(B.bp_csr_tile_index_size(n, n, tc), dtype=torch.int32, device="cuda")
+                    B.bp_csr_tile_index(ip, ix, n, tc, tp)
+                torch.cuda.synchronize()
+                # gather form over all rows (independent of rho)
+                x = torch.ones(n, dtype=torch.float32, device="cuda")
+                yp = torch.zeros(n, dtype=torch.float32, device="cuda")
+                for wname, wt, wb in (("homo", None, 0), ("f32", w32, 4), ("bf16", w16, 2)):
+                    ms = timeit(lambda: B.bp_event_csrmv_t(ip, ix, wt, 1.0, x, yp), 5)
+                    alg = nnz * (4 + wb) + 8 * (n + 1)
+                    emit(op="event_csrmv_t", n=n, p=p, weights=wname, us=ms * 1e3, nnz=nnz,
+                         alg_bytes=alg, gbs=alg / ms / 1e6, frac_hbm=alg / ms / 1e6 / peak, peak_source=peak_kind)
+            for rho in rhos:
+                ev_np = wl.bernoulli_spikes(n, rho, seed=seed + int(rho * 1e4))
+                events = torch.from_numpy(ev_np).cuda()
+                sl = torch.zeros(n, dtype=torch.int32, device="cuda")
+                ns = torch.zeros(1, dtype=torch.int32, device="cuda")
+                B.bp_spike_compact(events, sl, ns)
+                n_spk = int(ns.item())
+                yc = torch.zeros(n, dtype=torch.int32, device="cuda")
+                yf = torch.zeros(n, dtype=torch.float32, device="cuda")
+                if csr_ok:
+                    lens = ip[1:] - ip[:-1]
+                    ev_count = int(lens[sl[:n_spk].long()].sum().item()) if n_spk else 0
+                    for wname, wt, wb, y in (("homo", None, 0, yc), ("f32", w32, 4, yf), ("bf16", w16, 2, yf)):
+                        ms = timeit(lambda: B.bp_event_csrmv(ip, ix, wt, 1.0, sl, ns, y, tile_ptr=tp, tile_cols=tc), 7)
+                        alg = ev_count * (4 + wb) + 16 * n_spk
+                        emit(op="event_csrmv", n=n, p=p, rho=rho, weights=wname, us=ms * 1e3, spikes=n_spk,
+                             events=ev_count, events_per_s=ev_count / (ms * 1e-3), alg_bytes=alg,
+                             gbs=alg / ms / 1e6, frac_hbm=alg / ms / 1e6 / peak, peak_source=peak_kind,
+                             graded=(n == 1_000_000 and (p, rho) in ((0.01, 0.01), (0.01, 0.1), (0.001, 0.1))))
+                yy = torch.zeros(n, dtype=torch.int32, device="cuda")
+                B.bp_jitconn_event_mv(dh, n, sl, ns, yy)
+                ev_jit = int(yy.sum().item())
+                for wname, d, y in (("homo", dh, yc), ("normal", dn, yf)):
+                    ms = timeit(lambda: B.bp_jitconn_event_mv(d, n, sl, ns, y), 5)
+                    emit(op="jitconn_event_mv", n=n, p=p, rho=rho, weights=wname, us=ms * 1e3, spikes=n_spk,
+                         events=ev_jit, events_per_s=ev_jit / (ms * 1e-3), bound="alu")
+                del events, sl, ns, yc, yf, yy
+            del ip, ix, w32, w16, tp
+            torch.cuda.empty_cache()
+    return 0
+
+
 # ----------------------------------------------------------------- main
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.sweep:
+        return run_sweep(args)
     rank, world, local = dist_env()
     import torch
     dist = None

@@ -336,6 +336,61 @@ bp_status bp_network_stats(bp_net* net, double* out, bp_stream_t stream);
 
 bp_status bp_network_destroy(bp_net* net);
 
+/* --------------------------------------------------------------------------
+ * a9. Batched networks: many independent COBA E/I networks of uneven sizes
+ * (the "parameter explorations" of Section 2), each with its own seed and
+ * JIT connectivity (probability p, default 80/n, homogeneous w_e / w_i),
+ * advanced together by one persistent kernel in which a CTA owns whole
+ * networks (no inter-CTA synchronisation), its time loop captured in a CUDA
+ * graph.  The per-step arithmetic is the one of bp_network_step; a network of
+ * the batch follows the trajectory the single-network path computes for it.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    int32_t n_nets;
+    const int64_t* n;       /* HOST [n_nets] neurons per network, each in [1, 56320] */
+    const int64_t* n_e;     /* HOST [n_nets] nullable: default 4n/5 (each population < 65536) */
+    const uint64_t* seed;   /* HOST [n_nets] network seeds (projection seeds derived as in bp_projection_seed) */
+    const double* p;        /* HOST [n_nets] nullable: default 80/n */
+    bp_coba_params coba;    /* shared by every network */
+    /* device state, caller-owned, concatenated: network b occupies
+     * [off_b, off_b + n_b) with off_b from bp_batch_layout; padding entries
+     * are never simulated. */
+    float* V;
+    float* ge;
+    float* gi;
+    int32_t* ref;
+    int64_t* totals;        /* device [n_nets][4]: spikes E, spikes I, events, steps (accumulated) */
+} bp_batch_desc;
+
+typedef struct bp_batch bp_batch;
+
+/* Offsets of the concatenated layout: offsets[b] for b < n_nets (host,
+ * nullable) and offsets[n_nets] = the total length returned (each network
+ * padded to a multiple of 4 neurons).  Returns -1 on bad arguments. */
+int64_t bp_batch_layout(int32_t n_nets, const int64_t* n, int64_t* offsets);
+
+/* Validates, packs the networks into one bin per SM (longest first, bounded
+ * by shared memory) and allocates the device tables, the event-count spill
+ * buffer and the autotuner's snapshot.  Pending event counts start at zero. */
+bp_status bp_batch_create(const bp_batch_desc* desc, bp_batch** out);
+
+/* Bins (CTAs), CTA size in use and padded length of the layout. */
+bp_status bp_batch_info(const bp_batch* b, int32_t* bins, int32_t* threads, int64_t* padded_neurons);
+
+/* Zeroes the pending event counts and the totals. */
+bp_status bp_batch_reset_counters(bp_batch* b, bp_stream_t stream);
+
+/* T steps of every network (a CUDA graph per distinct T, cached). */
+bp_status bp_batch_simulate(bp_batch* b, int64_t T, bp_stream_t stream);
+
+/* Times probe_steps steps with each candidate CTA size (256, 512, 1024
+ * threads) from a snapshot of the current state, restores the state, keeps
+ * the fastest and returns it in *chosen_threads (nullable).  Synchronises
+ * `stream`. */
+bp_status bp_batch_autotune(bp_batch* b, int32_t probe_steps, int32_t* chosen_threads, bp_stream_t stream);
+
+bp_status bp_batch_destroy(bp_batch* b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -55,6 +55,11 @@ class NetDesc(ctypes.Structure):
                 ("spike_list", VP), ("n_spikes", VP), ("totals", VP), ("spk", VP)]
 
 
+class BatchDesc(ctypes.Structure):
+    _fields_ = [("n_nets", c_i32), ("n", VP), ("n_e", VP), ("seed", VP), ("p", VP), ("coba", CobaParams),
+                ("V", VP), ("ge", VP), ("gi", VP), ("ref", VP), ("totals", VP)]
+
+
 _SIGS = {
     "bp_version": (ctypes.c_char_p, []),
     "bp_last_error": (ctypes.c_char_p, []),
@@ -85,6 +90,13 @@ _SIGS = {
     "bp_simulate": (c_i32, [VP, c_i64, VP, VP]),
     "bp_network_stats": (c_i32, [VP, VP, VP]),
     "bp_network_destroy": (c_i32, [VP]),
+    "bp_batch_layout": (c_i64, [c_i32, VP, VP]),
+    "bp_batch_create": (c_i32, [ctypes.POINTER(BatchDesc), ctypes.POINTER(VP)]),
+    "bp_batch_info": (c_i32, [VP, VP, VP, VP]),
+    "bp_batch_reset_counters": (c_i32, [VP, VP]),
+    "bp_batch_simulate": (c_i32, [VP, c_i64, VP]),
+    "bp_batch_autotune": (c_i32, [VP, c_i32, VP, VP]),
+    "bp_batch_destroy": (c_i32, [VP]),
 }
 
 _lock = threading.Lock()
@@ -311,3 +323,45 @@ def bp_network_stats(net, out, stream=None):
 
 def bp_network_destroy(net):
     _check("bp_network_destroy", lib().bp_network_destroy(net))
+
+
+# ------------------------------------------------------------------ a9
+def bp_batch_layout(n):
+    """Offsets (numpy int64 [n_nets + 1]) of the concatenated batch layout."""
+    import numpy as np
+    nn = np.ascontiguousarray(n, dtype=np.int64)
+    off = np.zeros(len(nn) + 1, np.int64)
+    total = lib().bp_batch_layout(len(nn), nn.ctypes.data_as(VP), off.ctypes.data_as(VP))
+    if total < 0:
+        raise ValueError("bad network sizes")
+    return off
+
+
+def bp_batch_create(desc: BatchDesc):
+    h = VP()
+    _check("bp_batch_create", lib().bp_batch_create(ctypes.byref(desc), ctypes.byref(h)))
+    return h
+
+
+def bp_batch_info(b):
+    bins, threads, total = c_i32(), c_i32(), c_i64()
+    _check("bp_batch_info", lib().bp_batch_info(b, ctypes.byref(bins), ctypes.byref(threads), ctypes.byref(total)))
+    return bins.value, threads.value, total.value
+
+
+def bp_batch_reset_counters(b, stream=None):
+    _check("bp_batch_reset_counters", lib().bp_batch_reset_counters(b, _stream(stream)))
+
+
+def bp_batch_simulate(b, T, stream=None):
+    _check("bp_batch_simulate", lib().bp_batch_simulate(b, int(T), _stream(stream)))
+
+
+def bp_batch_autotune(b, probe_steps=20, stream=None):
+    th = c_i32()
+    _check("bp_batch_autotune", lib().bp_batch_autotune(b, int(probe_steps), ctypes.byref(th), _stream(stream)))
+    return th.value
+
+
+def bp_batch_destroy(b):
+    _check("bp_batch_destroy", lib().bp_batch_destroy(b))

@@ -1,0 +1,526 @@
+// batch.cu -- many independent COBA E/I networks of uneven sizes advanced
+// together by one persistent kernel (a9).
+//
+// Networks are independent, so a network never spans CTAs: the host packs the
+// networks into one bin per SM (longest-processing-time first, bounded by the
+// shared-memory capacity) and CTA b runs every time step of bin b's networks
+// on its own, with no inter-CTA synchronisation at all.  Within a step the CTA
+//   1. updates all neurons of its networks (the same per-neuron arithmetic as
+//      the single-network path, 16-byte state loads from global memory),
+//      reading and clearing the event counts from shared memory, and appends
+//      spikes to its spike list;
+//   2. after a CTA barrier, regenerates the JIT rows of those spikes (one warp
+//      per row) and adds the events into the shared-memory counts, E and I
+//      packed into one 32-bit word (E in the low 16 bits; one presynaptic
+//      neuron delivers at most one event per target and step, so each half
+//      stays below the population size, < 2^16 by construction);
+//   3. after another barrier, adds the step's per-network totals.
+// The counts survive between launches in a global spill buffer.  The time
+// loop is split into launches of a few steps that bp_batch_simulate captures
+// once in a CUDA graph; the CTA size is chosen by bp_batch_autotune.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "bp_common.cuh"
+#include "bp_internal.h"
+#include "bp_neuron.cuh"
+#include "bp_rows.cuh"
+
+namespace bp {
+namespace {
+
+constexpr int kBatchMaxNetsPerBin = 64;
+constexpr int kBatchStepsPerLaunch = 100;
+constexpr int32_t kBatchCapacity = 56320;  // packed counts per CTA (220 KiB)
+
+struct NetInfo {
+    int64_t off;       // first neuron in the concatenated state
+    int32_t n, n_e;
+    uint64_t seed_e, seed_i;
+    uint32_t K;
+    int32_t pad;
+};
+
+struct BinArgs {
+    LifConst c;
+    const NetInfo* nets;
+    const int32_t* bin_nets;   // net ids, grouped by bin
+    const int32_t* bin_ptr;    // [bins + 1]
+    const int64_t* bin_spk;    // spike-list offset of each bin
+    float* V;
+    float* ge;
+    float* gi;
+    int32_t* ref;
+    int32_t* spill;            // packed counts between launches, concatenated layout
+    int32_t* spk_list;
+    int64_t* totals;           // [n_nets][4]
+    int32_t steps;
+};
+
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS, 1) k_batch(BinArgs a) {
+    extern __shared__ __align__(16) int32_t acc[];
+    __shared__ int32_t s_base[kBatchMaxNetsPerBin + 1];
+    __shared__ int32_t s_cnt[kBatchMaxNetsPerBin][3];
+    __shared__ int32_t s_nspk;
+    constexpr int kWarps = THREADS / 32;
+    const int bin = blockIdx.x;
+    const int nb0 = a.bin_ptr[bin];
+    const int nn = a.bin_ptr[bin + 1] - nb0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int k = 0; k < nn; ++k) {
+            s_base[k] = run;
+            run += (a.nets[a.bin_nets[nb0 + k]].n + 3) & ~3;
+        }
+        s_base[nn] = run;
+    }
+    __syncthreads();
+    // restore the pending counts
+    for (int k = 0; k < nn; ++k) {
+        const NetInfo& net = a.nets[a.bin_nets[nb0 + k]];
+        const int np = (net.n + 3) & ~3;
+        for (int t = threadIdx.x; t < np; t += THREADS) acc[s_base[k] + t] = a.spill[net.off + t];
+    }
+    int32_t* list = a.spk_list + a.bin_spk[bin];
+
+    for (int step = 0; step < a.steps; ++step) {
+        if (threadIdx.x < nn) {
+            s_cnt[threadIdx.x][0] = 0;
+            s_cnt[threadIdx.x][1] = 0;
+            s_cnt[threadIdx.x][2] = 0;
+        }
+        if (threadIdx.x == 0) s_nspk = 0;
+        __syncthreads();
+        // ---- 1. neuron pass
+        for (int k = 0; k < nn; ++k) {
+            const NetInfo& net = a.nets[a.bin_nets[nb0 + k]];
+            const int nq = (net.n + 3) >> 2;
+            int32_t* cnt = acc + s_base[k];
+            // warp-uniform trip count: every lane runs every iteration
+            for (int qb = 0; qb < nq; qb += THREADS) {
+                const int q = qb + threadIdx.x;
+                uint32_t bits = 0;
+                if (q < nq) {
+                    const int64_t g = net.off + 4 * static_cast<int64_t>(q);
+                    float4 v = *reinterpret_cast<const float4*>(a.V + g);
+                    float4 ge = *reinterpret_cast<const float4*>(a.ge + g);
+                    float4 gi = *reinterpret_cast<const float4*>(a.gi + g);
+                    int4 r = *reinterpret_cast<const int4*>(a.ref + g);
+                    int4 y = *reinterpret_cast<int4*>(cnt + 4 * q);
+                    *reinterpret_cast<int4*>(cnt + 4 * q) = make_int4(0, 0, 0, 0);
+                    float* vv = &v.x;
+                    float* gg = &ge.x;
+                    float* hh = &gi.x;
+                    int* rr = &r.x;
+                    const int* yy = &y.x;
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        if (4 * q + e < net.n) {  // padding neurons are not simulated
+                            const int32_t ce = yy[e] & 0xFFFF;
+                            const int32_t ci = static_cast<int32_t>(static_cast<uint32_t>(yy[e]) >> 16);
+                            if (neuron_update(a.c, vv[e], gg[e], hh[e], rr[e], event_add<true>(ce, a.c.w_e),
+                                              event_add<true>(ci, a.c.w_i), 0.f))
+                                bits |= 1u << e;
+                        }
+                    }
+                    *reinterpret_cast<float4*>(a.V + g) = v;
+                    *reinterpret_cast<float4*>(a.ge + g) = ge;
+                    *reinterpret_cast<float4*>(a.gi + g) = gi;
+                    *reinterpret_cast<int4*>(a.ref + g) = r;
+                }
+                // warp-aggregated append of (net slot << 20 | neuron) entries
+                const int mine = __popc(bits);
+                int incl = mine;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const int o = __shfl_up_sync(FULL_MASK, incl, d);
+                    if (lane >= d) incl += o;
+                }
+                const int wtot = __shfl_sync(FULL_MASK, incl, 31);
+                int base = 0;
+                if (lane == 0 && wtot) base = atomicAdd(&s_nspk, wtot);
+                base = __shfl_sync(FULL_MASK, base, 0);
+                int pos = base + incl - mine;
+                int ne = 0, ni = 0;
+                for (uint32_t m = bits; m; m &= m - 1) {
+                    const int i = 4 * q + (__ffs(m) - 1);
+                    list[pos++] = (k << 20) | i;
+                    if (i < net.n_e) ++ne; else ++ni;
+                }
+                if (ne) atomicAdd(&s_cnt[k][0], ne);
+                if (ni) atomicAdd(&s_cnt[k][1], ni);
+            }
+        }
+        __syncthreads();
+        // ---- 2. delivery of this step's spikes (JIT rows, Appendix C)
+        const int nspk = s_nspk;
+        for (int e = warp; e < nspk; e += kWarps) {
+            const int32_t ent = list[e];
+            const int k = ent >> 20;
+            const int i = ent & 0xFFFFF;
+            const NetInfo& net = a.nets[a.bin_nets[nb0 + k]];
+            const bool exc = i < net.n_e;
+            JitArgs d;
+            d.seed = exc ? net.seed_e : net.seed_i;
+            d.K = net.K;
+            d.wkind = BP_JIT_HOMO;
+            d.w0 = 1.0f;
+            d.w1 = 0.0f;
+            int32_t* cnt = acc + s_base[k];
+            const int32_t inc = exc ? 1 : 65536;
+            int64_t ev = jit_walk<BP_JIT_HOMO>(d, static_cast<uint32_t>(exc ? i : i - net.n_e), net.n,
+                                              [&](int64_t q, uint64_t, float) { atomicAdd(cnt + q, inc); });
+            ev = group_reduce_sum(ev, 32);
+            if (lane == 0 && ev) atomicAdd(&s_cnt[k][2], static_cast<int32_t>(ev));
+        }
+        __syncthreads();
+        // ---- 3. per-network totals
+        if (threadIdx.x < nn) {
+            int64_t* tot = a.totals + 4 * static_cast<int64_t>(a.bin_nets[nb0 + threadIdx.x]);
+            atomicAdd(reinterpret_cast<unsigned long long*>(tot + 0), static_cast<unsigned long long>(s_cnt[threadIdx.x][0]));
+            atomicAdd(reinterpret_cast<unsigned long long*>(tot + 1), static_cast<unsigned long long>(s_cnt[threadIdx.x][1]));
+            atomicAdd(reinterpret_cast<unsigned long long*>(tot + 2), static_cast<unsigned long long>(s_cnt[threadIdx.x][2]));
+            atomicAdd(reinterpret_cast<unsigned long long*>(tot + 3), 1ull);
+        }
+    }
+    __syncthreads();
+    // keep the pending counts for the next launch
+    for (int k = 0; k < nn; ++k) {
+        const NetInfo& net = a.nets[a.bin_nets[nb0 + k]];
+        const int np = (net.n + 3) & ~3;
+        for (int t = threadIdx.x; t < np; t += THREADS) a.spill[net.off + t] = acc[s_base[k] + t];
+    }
+}
+
+const int kThreadChoices[] = {256, 512, 1024};
+
+template <int THREADS>
+bp_status launch_batch_t(const BinArgs& a, int bins, size_t smem, cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+        BP_CUDA(cudaFuncSetAttribute(k_batch<THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     kBatchCapacity * 4));
+        attr = true;
+    }
+    k_batch<THREADS><<<bins, THREADS, smem, s>>>(a);
+    BP_LAUNCHED();
+    return BP_OK;
+}
+
+bp_status launch_batch(const BinArgs& a, int threads, int bins, size_t smem, cudaStream_t s) {
+    switch (threads) {
+        case 256: return launch_batch_t<256>(a, bins, smem, s);
+        case 512: return launch_batch_t<512>(a, bins, smem, s);
+        default: return launch_batch_t<1024>(a, bins, smem, s);
+    }
+}
+
+}  // namespace
+}  // namespace bp
+
+struct bp_batch {
+    bp_batch_desc d;
+    int32_t n_nets;
+    int bins;
+    int threads;
+    size_t smem;
+    int64_t total;             // padded neurons
+    bp::BinArgs args;
+    bp::NetInfo* d_nets;
+    int32_t* d_bin_nets;
+    int32_t* d_bin_ptr;
+    int64_t* d_bin_spk;
+    int32_t* d_spill;
+    int32_t* d_list;
+    void* d_snapshot;          // autotuner's copy of the state
+    cudaStream_t cap_stream;
+    std::map<int64_t, cudaGraphExec_t>* graphs;
+};
+
+namespace {
+
+void free_batch(bp_batch* b) {
+    if (!b) return;
+    if (b->graphs) {
+        for (auto& kv : *b->graphs) cudaGraphExecDestroy(kv.second);
+        delete b->graphs;
+    }
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    cudaFree(b->d_nets);
+    cudaFree(b->d_bin_nets);
+    cudaFree(b->d_bin_ptr);
+    cudaFree(b->d_bin_spk);
+    cudaFree(b->d_spill);
+    cudaFree(b->d_list);
+    cudaFree(b->d_snapshot);
+    delete b;
+}
+
+void drop_graphs(bp_batch* b) {
+    for (auto& kv : *b->graphs) cudaGraphExecDestroy(kv.second);
+    b->graphs->clear();
+}
+
+bp_status enqueue_steps(bp_batch* b, int64_t T, cudaStream_t s) {
+    for (int64_t done = 0; done < T;) {
+        const int64_t k = std::min<int64_t>(bp::kBatchStepsPerLaunch, T - done);
+        bp::BinArgs a = b->args;
+        a.steps = static_cast<int32_t>(k);
+        BP_TRY(bp::launch_batch(a, b->threads, b->bins, b->smem, s));
+        done += k;
+    }
+    return BP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t bp_batch_layout(int32_t n_nets, const int64_t* n, int64_t* offsets) {
+    if (n_nets < 0 || (n_nets > 0 && !n)) return -1;
+    int64_t off = 0;
+    for (int32_t b = 0; b < n_nets; ++b) {
+        if (offsets) offsets[b] = off;
+        off += (n[b] + 3) & ~int64_t(3);
+    }
+    if (offsets) offsets[n_nets] = off;
+    return off;
+}
+
+bp_status bp_batch_create(const bp_batch_desc* desc, bp_batch** out) {
+    bp::clear_error();
+    BP_REQUIRE(desc && out, "desc or out is NULL");
+    const bp_batch_desc& d = *desc;
+    BP_REQUIRE(d.n_nets > 0 && d.n && d.seed, "n_nets, n or seed missing");
+    BP_TRY(bp::check_coba(&d.coba));
+    BP_REQUIRE(d.V && d.ge && d.gi && d.ref && d.totals, "a required state pointer is NULL");
+    const int32_t N = d.n_nets;
+    std::vector<int64_t> off(N + 1);
+    const int64_t total = bp_batch_layout(N, d.n, off.data());
+    std::vector<bp::NetInfo> nets(N);
+    for (int32_t b = 0; b < N; ++b) {
+        const int64_t n = d.n[b];
+        const int64_t ne = d.n_e ? d.n_e[b] : (4 * n) / 5;
+        BP_REQUIRE(n > 0 && n <= bp::kBatchCapacity, "network %d: n = %lld not in [1, %d]", b, (long long)n,
+                   bp::kBatchCapacity);
+        BP_REQUIRE(ne >= 0 && ne <= n && ne < 65536 && n - ne < 65536, "network %d: bad n_e", b);
+        const double p = d.p ? d.p[b] : 80.0 / static_cast<double>(n);
+        bp_jit_desc de;
+        BP_TRY(bp_jit_desc_init(&de, bp_projection_seed(d.seed[b], 0), p, BP_JIT_HOMO, 1.0f, 0.0f));
+        nets[b].off = off[b];
+        nets[b].n = static_cast<int32_t>(n);
+        nets[b].n_e = static_cast<int32_t>(ne);
+        nets[b].seed_e = de.seed;
+        nets[b].seed_i = bp_projection_seed(d.seed[b], 1);
+        nets[b].K = static_cast<uint32_t>(de.K);
+        nets[b].pad = 0;
+    }
+    // longest-processing-time packing into one bin per SM
+    int bins = std::min<int>(bp::sm_count(), N);
+    std::vector<int32_t> order(N);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return d.n[x] > d.n[y]; });
+    std::vector<std::vector<int32_t>> members;
+    std::vector<int64_t> load;
+    for (;;) {
+        members.assign(bins, {});
+        load.assign(bins, 0);
+        bool ok = true;
+        for (int32_t id : order) {
+            const int64_t np = (d.n[id] + 3) & ~int64_t(3);
+            int best = -1;
+            for (int k = 0; k < bins; ++k) {
+                if (load[k] + np > bp::kBatchCapacity || static_cast<int>(members[k].size()) >= bp::kBatchMaxNetsPerBin)
+                    continue;
+                if (best < 0 || load[k] < load[best]) best = k;
+            }
+            if (best < 0) {
+                ok = false;
+                break;
+            }
+            members[best].push_back(id);
+            load[best] += np;
+        }
+        if (ok) break;
+        bins *= 2;  // more bins than SMs: the kernel then runs in several waves
+        BP_REQUIRE(bins <= 65535, "cannot pack the networks");
+    }
+    std::vector<int32_t> bin_nets, bin_ptr(1, 0);
+    std::vector<int64_t> bin_spk;
+    int64_t spk_off = 0, max_load = 0;
+    for (int k = 0; k < bins; ++k) {
+        bin_spk.push_back(spk_off);
+        spk_off += load[k];
+        max_load = std::max(max_load, load[k]);
+        for (int32_t id : members[k]) bin_nets.push_back(id);
+        bin_ptr.push_back(static_cast<int32_t>(bin_nets.size()));
+    }
+    bp_batch* b = new (std::nothrow) bp_batch();
+    if (!b) {
+        bp::set_error("host allocation failed");
+        return BP_ERR_OOM;
+    }
+    b->d = d;
+    b->d.n = nullptr;  // host arrays are not kept
+    b->d.n_e = nullptr;
+    b->d.seed = nullptr;
+    b->d.p = nullptr;
+    b->n_nets = N;
+    b->bins = bins;
+    b->threads = 1024;
+    b->smem = static_cast<size_t>(std::max<int64_t>(max_load, 4)) * 4;
+    b->total = total;
+    b->graphs = new (std::nothrow) std::map<int64_t, cudaGraphExec_t>();
+    const size_t state_bytes = static_cast<size_t>(total) * 16 + static_cast<size_t>(total) * 4 +
+                               static_cast<size_t>(N) * 32;
+    cudaError_t e = cudaSuccess;
+    e = e ? e : cudaMalloc(&b->d_nets, sizeof(bp::NetInfo) * N);
+    e = e ? e : cudaMalloc(&b->d_bin_nets, sizeof(int32_t) * bin_nets.size());
+    e = e ? e : cudaMalloc(&b->d_bin_ptr, sizeof(int32_t) * bin_ptr.size());
+    e = e ? e : cudaMalloc(&b->d_bin_spk, sizeof(int64_t) * bin_spk.size());
+    e = e ? e : cudaMalloc(&b->d_spill, sizeof(int32_t) * total);
+    e = e ? e : cudaMalloc(&b->d_list, sizeof(int32_t) * std::max<int64_t>(spk_off, 1));
+    e = e ? e : cudaMalloc(&b->d_snapshot, state_bytes);
+    if (e != cudaSuccess || !b->graphs) {
+        free_batch(b);
+        bp::set_error("allocation of the batch tables failed: %s", cudaGetErrorString(e));
+        return BP_ERR_OOM;
+    }
+    e = e ? e : cudaMemcpy(b->d_nets, nets.data(), sizeof(bp::NetInfo) * N, cudaMemcpyHostToDevice);
+    e = e ? e : cudaMemcpy(b->d_bin_nets, bin_nets.data(), sizeof(int32_t) * bin_nets.size(), cudaMemcpyHostToDevice);
+    e = e ? e : cudaMemcpy(b->d_bin_ptr, bin_ptr.data(), sizeof(int32_t) * bin_ptr.size(), cudaMemcpyHostToDevice);
+    e = e ? e : cudaMemcpy(b->d_bin_spk, bin_spk.data(), sizeof(int64_t) * bin_spk.size(), cudaMemcpyHostToDevice);
+    e = e ? e : cudaMemset(b->d_spill, 0, sizeof(int32_t) * total);
+    if (e != cudaSuccess) {
+        free_batch(b);
+        bp::set_error("upload of the batch tables failed: %s", cudaGetErrorString(e));
+        return BP_ERR_CUDA;
+    }
+    bp::BinArgs& a = b->args;
+    a.c = bp::make_lif_const(d.coba);
+    a.nets = b->d_nets;
+    a.bin_nets = b->d_bin_nets;
+    a.bin_ptr = b->d_bin_ptr;
+    a.bin_spk = b->d_bin_spk;
+    a.V = d.V;
+    a.ge = d.ge;
+    a.gi = d.gi;
+    a.ref = d.ref;
+    a.spill = b->d_spill;
+    a.spk_list = b->d_list;
+    a.totals = d.totals;
+    a.steps = 0;
+    *out = b;
+    return BP_OK;
+}
+
+bp_status bp_batch_info(const bp_batch* b, int32_t* bins, int32_t* threads, int64_t* padded_neurons) {
+    bp::clear_error();
+    BP_REQUIRE(b, "batch is NULL");
+    if (bins) *bins = b->bins;
+    if (threads) *threads = b->threads;
+    if (padded_neurons) *padded_neurons = b->total;
+    return BP_OK;
+}
+
+bp_status bp_batch_reset_counters(bp_batch* b, bp_stream_t stream) {
+    bp::clear_error();
+    BP_REQUIRE(b, "batch is NULL");
+    BP_CUDA(cudaMemsetAsync(b->d_spill, 0, sizeof(int32_t) * b->total, stream));
+    BP_CUDA(cudaMemsetAsync(b->d.totals, 0, sizeof(int64_t) * 4 * b->n_nets, stream));
+    return BP_OK;
+}
+
+bp_status bp_batch_simulate(bp_batch* b, int64_t T, bp_stream_t stream) {
+    bp::clear_error();
+    BP_REQUIRE(b, "batch is NULL");
+    BP_REQUIRE(T >= 0, "T < 0");
+    if (T == 0) return BP_OK;
+    auto it = b->graphs->find(T);
+    if (it == b->graphs->end()) {
+        if (!b->cap_stream) BP_CUDA(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+        BP_CUDA(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+        bp_status st = enqueue_steps(b, T, b->cap_stream);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(b->cap_stream, &g);
+        if (st != BP_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        if (e != cudaSuccess) {
+            bp::set_error("graph capture failed: %s", cudaGetErrorString(e));
+            return BP_ERR_CUDA;
+        }
+        cudaGraphExec_t ex = nullptr;
+        e = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            bp::set_error("graph instantiation failed: %s", cudaGetErrorString(e));
+            return BP_ERR_CUDA;
+        }
+        it = b->graphs->emplace(T, ex).first;
+    }
+    BP_CUDA(cudaGraphLaunch(it->second, stream));
+    return BP_OK;
+}
+
+bp_status bp_batch_autotune(bp_batch* b, int32_t probe_steps, int32_t* chosen_threads, bp_stream_t stream) {
+    bp::clear_error();
+    BP_REQUIRE(b, "batch is NULL");
+    BP_REQUIRE(probe_steps > 0, "probe_steps must be positive");
+    const size_t f = static_cast<size_t>(b->total) * 4;
+    char* snap = static_cast<char*>(b->d_snapshot);
+    void* src[] = {b->d.V, b->d.ge, b->d.gi, b->d.ref, b->d_spill, b->d.totals};
+    const size_t sz[] = {f, f, f, f, f, static_cast<size_t>(b->n_nets) * 32};
+    size_t offs[6];
+    size_t o = 0;
+    for (int k = 0; k < 6; ++k) {
+        offs[k] = o;
+        o += sz[k];
+    }
+    for (int k = 0; k < 6; ++k) BP_CUDA(cudaMemcpyAsync(snap + offs[k], src[k], sz[k], cudaMemcpyDeviceToDevice, stream));
+    cudaEvent_t e0, e1;
+    BP_CUDA(cudaEventCreate(&e0));
+    BP_CUDA(cudaEventCreate(&e1));
+    float best_ms = 1e30f;
+    int best = b->threads;
+    for (int th : bp::kThreadChoices) {
+        for (int k = 0; k < 6; ++k)
+            BP_CUDA(cudaMemcpyAsync(src[k], snap + offs[k], sz[k], cudaMemcpyDeviceToDevice, stream));
+        b->threads = th;
+        BP_TRY(enqueue_steps(b, 2, stream));  // warm-up (also sets the shared-memory attribute)
+        BP_CUDA(cudaEventRecord(e0, stream));
+        BP_TRY(enqueue_steps(b, probe_steps, stream));
+        BP_CUDA(cudaEventRecord(e1, stream));
+        BP_CUDA(cudaEventSynchronize(e1));
+        float ms = 0;
+        BP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = th;
+        }
+    }
+    for (int k = 0; k < 6; ++k) BP_CUDA(cudaMemcpyAsync(src[k], snap + offs[k], sz[k], cudaMemcpyDeviceToDevice, stream));
+    BP_CUDA(cudaStreamSynchronize(stream));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->threads = best;
+    drop_graphs(b);
+    if (chosen_threads) *chosen_threads = best;
+    return BP_OK;
+}
+
+bp_status bp_batch_destroy(bp_batch* b) {
+    bp::clear_error();
+    free_batch(b);
+    return BP_OK;
+}
+
+}  // extern "C"

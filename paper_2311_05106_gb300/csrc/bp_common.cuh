@@ -105,6 +105,8 @@ __device__ __forceinline__ float ld_stream_bf16(const __nv_bfloat16* p) {
     return __uint_as_float(static_cast<uint32_t>(raw) << 16);
 }
 
+__device__ __forceinline__ int4 ld_stream4(const int32_t* p) { return __ldcs(reinterpret_cast<const int4*>(p)); }
+
 // Weight kinds of stored CSR entries.
 enum { WK_HOMO = 0, WK_F32 = 1, WK_BF16 = 2 };
 
@@ -117,6 +119,62 @@ __device__ __forceinline__ float load_weight(const void* data, int64_t j, float 
     } else {
         return w_homo;
     }
+}
+
+// Four consecutive weights starting at a multiple of 4 (16-byte aligned FP32,
+// 8-byte aligned BF16).
+template <int WK>
+__device__ __forceinline__ float4 load_weight4(const void* data, int64_t j, float w_homo) {
+    if constexpr (WK == WK_F32) {
+        return __ldcs(reinterpret_cast<const float4*>(static_cast<const float*>(data) + j));
+    } else if constexpr (WK == WK_BF16) {
+        const uint2 raw = __ldcs(reinterpret_cast<const uint2*>(static_cast<const __nv_bfloat16*>(data) + j));
+        return make_float4(__uint_as_float(raw.x << 16), __uint_as_float(raw.x & 0xFFFF0000u),
+                           __uint_as_float(raw.y << 16), __uint_as_float(raw.y & 0xFFFF0000u));
+    } else {
+        return make_float4(w_homo, w_homo, w_homo, w_homo);
+    }
+}
+
+// L2 policy that keeps lines resident ahead of evict-normal/evict-first
+// lines: used for the event accumulators, which are re-read every step while
+// the neuron state streams through L2.
+__device__ __forceinline__ uint64_t l2_keep_policy() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ void red_add_keep(int32_t* a, int32_t v, uint64_t pol) {
+    asm volatile("red.relaxed.gpu.global.add.L2::cache_hint.s32 [%0], %1, %2;" ::"l"(a), "r"(v), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void red_add_keep(float* a, float v, uint64_t pol) {
+    asm volatile("red.relaxed.gpu.global.add.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(a), "f"(v), "l"(pol) : "memory");
+}
+
+__device__ __forceinline__ int4 ld_keep(const int4* p, uint64_t pol) {
+    int4 v;
+    asm volatile("ld.global.L2::cache_hint.v4.s32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ float4 ld_keep(const float4* p, uint64_t pol) {
+    float4 v;
+    asm volatile("ld.global.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ void st_keep(int4* p, int4 v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.v4.s32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "r"(v.x), "r"(v.y), "r"(v.z),
+                 "r"(v.w), "l"(pol)
+                 : "memory");
+}
+__device__ __forceinline__ void st_keep(float4* p, float4 v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z),
+                 "f"(v.w), "l"(pol)
+                 : "memory");
 }
 
 // Accumulate into shared or global memory.  Integer counts and FP32 sums

@@ -28,13 +28,26 @@ __device__ __forceinline__ Acc event_value(float w) {
     }
 }
 
+// Accumulation targets: plain atomics (shared memory or global), or global
+// REDs that keep the target line in L2 (KEEP).
+template <bool KEEP>
+struct AccOp {
+    uint64_t pol;
+    __device__ __forceinline__ AccOp() : pol(KEEP ? l2_keep_policy() : 0ull) {}
+    template <typename T>
+    __device__ __forceinline__ void operator()(T* p, T v) const {
+        if constexpr (KEEP) red_add_keep(p, v, pol); else acc_add(p, v);
+    }
+};
+
 // out[indices[j] - col0] += value(w_j) for j = b0 + lane, b0 + lane + G, ...
 // Each pass issues up to four predicated loads per lane before any atomic,
 // so a row of up to 4 G entries costs one memory latency.
-template <typename Acc, int WK>
+template <typename Acc, int WK, bool KEEP = false>
 __device__ __forceinline__ void scatter_segment(const int32_t* __restrict__ indices, const void* __restrict__ data,
                                                 float w_homo, int64_t b0, int64_t b1, int lane, int G,
                                                 Acc* __restrict__ out, int64_t col0) {
+    const AccOp<KEEP> add;
     for (int64_t j = b0 + lane; j < b1; j += 4 * G) {
         int32_t c[4];
         float w[4];
@@ -46,7 +59,54 @@ __device__ __forceinline__ void scatter_segment(const int32_t* __restrict__ indi
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-            if (c[u] >= 0) acc_add(out + (c[u] - col0), event_value<Acc>(w[u]));
+            if (c[u] >= 0) add(out + (c[u] - col0), event_value<Acc>(w[u]));
+    }
+}
+
+// As scatter_segment, with 16-byte loads: the part of the segment between
+// the first and last multiple of 4 is read as aligned groups of four entries
+// (four groups per lane per pass, so 64 bytes of indices in flight per lane),
+// the unaligned head and tail entry by entry.  Needs 16-byte aligned indices
+// (and FP32 weights; 8-byte aligned BF16 weights).
+template <typename Acc, int WK>
+__device__ __forceinline__ void scatter_segment_v4(const int32_t* __restrict__ indices, const void* __restrict__ data,
+                                                   float w_homo, int64_t b0, int64_t b1, int lane, int G,
+                                                   Acc* __restrict__ out, int64_t col0) {
+    int64_t a4 = (b0 + 3) & ~int64_t(3);
+    if (a4 > b1) a4 = b1;
+    int64_t e4 = b1 & ~int64_t(3);
+    if (e4 < a4) e4 = a4;
+    // head and tail: at most 3 entries each
+    {
+        const int64_t nh = a4 - b0, nt = b1 - e4;
+        for (int64_t t = lane; t < nh + nt; t += G) {
+            const int64_t j = t < nh ? b0 + t : e4 + (t - nh);
+            acc_add(out + (ld_stream(indices + j) - col0), event_value<Acc>(load_weight<WK>(data, j, w_homo)));
+        }
+    }
+    const int64_t c0 = a4 >> 2, c1 = e4 >> 2;
+    for (int64_t cb = c0 + lane; cb < c1; cb += 4 * G) {
+        int4 c[4];
+        float4 w[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t cc = cb + u * G;
+            if (cc < c1) {
+                c[u] = ld_stream4(indices + 4 * cc);
+                w[u] = load_weight4<WK>(data, 4 * cc, w_homo);
+            } else {
+                c[u] = make_int4(-1, -1, -1, -1);
+                w[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (c[u].x < 0) continue;
+            acc_add(out + (c[u].x - col0), event_value<Acc>(w[u].x));
+            acc_add(out + (c[u].y - col0), event_value<Acc>(w[u].y));
+            acc_add(out + (c[u].z - col0), event_value<Acc>(w[u].z));
+            acc_add(out + (c[u].w - col0), event_value<Acc>(w[u].w));
+        }
     }
 }
 

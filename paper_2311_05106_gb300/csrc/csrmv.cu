@@ -27,7 +27,27 @@ constexpr int kDirectThreads = 256;
 // mode: 0 auto, 1 direct, 2 tiled.  W = tile width (post columns per tile),
 // S = number of tiles (the grid is S x R CTAs).  With SPLIT, rows >= split
 // go to y_hi and each CTA keeps two W-wide accumulators.
-template <typename Acc, int WK, bool SPLIT>
+// Lanes per (row, tile) segment with vector loads: about 16 entries per lane.
+__device__ __forceinline__ int pick_group_v4(int64_t nnz, int64_t n_pre, int64_t tiles) {
+    const int64_t denom = (n_pre > 0 ? n_pre : 1) * (tiles > 0 ? tiles : 1);
+    const int64_t mean = nnz / denom;
+    if (mean >= 512) return 32;
+    if (mean >= 256) return 16;
+    if (mean >= 128) return 8;
+    return 4;
+}
+
+template <typename Acc, int WK, bool VECL>
+__device__ __forceinline__ void scatter_any(const int32_t* __restrict__ indices, const void* __restrict__ data,
+                                            float w_homo, int64_t b0, int64_t b1, int lane, int G,
+                                            Acc* __restrict__ out, int64_t col0) {
+    if constexpr (VECL)
+        scatter_segment_v4<Acc, WK>(indices, data, w_homo, b0, b1, lane, G, out, col0);
+    else
+        scatter_segment<Acc, WK>(indices, data, w_homo, b0, b1, lane, G, out, col0);
+}
+
+template <typename Acc, int WK, bool SPLIT, bool VECL>
 __global__ void __launch_bounds__(kTileThreads, 1)
     k_csr_scatter(CsrArgs a, const int32_t* __restrict__ spike_list, const int32_t* __restrict__ n_spikes,
                   int64_t max_spikes, Acc* __restrict__ y, Acc* __restrict__ y_hi, int64_t split, int mode,
@@ -45,7 +65,7 @@ __global__ void __launch_bounds__(kTileThreads, 1)
     }
     int64_t ev = 0;
     if (mode == 1) {
-        const int G = pick_group(nnz, a.n_pre, 1);
+        const int G = VECL ? pick_group_v4(nnz, a.n_pre, 1) : pick_group(nnz, a.n_pre, 1);
         const int lane = threadIdx.x % G;
         const int64_t ngroups = static_cast<int64_t>(gridDim.x) * blockDim.x / G;
         for (int64_t u = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) / G; u < ns; u += ngroups) {
@@ -54,7 +74,7 @@ __global__ void __launch_bounds__(kTileThreads, 1)
             const int64_t b0 = a.indptr[i], b1 = a.indptr[i + 1];
             Acc* out = (SPLIT && i >= split) ? y_hi : y;
             if (lane == 0) ev += b1 - b0;
-            scatter_segment<Acc, WK>(a.indices, a.data, a.w_homo, b0, b1, lane, G, out, 0);
+            scatter_any<Acc, WK, VECL>(a.indices, a.data, a.w_homo, b0, b1, lane, G, out, 0);
         }
     } else {
         const int s = blockIdx.x % S;
@@ -64,7 +84,7 @@ __global__ void __launch_bounds__(kTileThreads, 1)
         const int nacc = SPLIT ? 2 * W : W;
         for (int t = threadIdx.x; t < nacc; t += blockDim.x) acc[t] = Acc(0);
         __syncthreads();
-        const int G = pick_group(nnz, a.n_pre, S);
+        const int G = VECL ? pick_group_v4(nnz, a.n_pre, S) : pick_group(nnz, a.n_pre, S);
         const int lane = threadIdx.x % G;
         const int64_t gid = threadIdx.x / G;
         const int64_t ng = blockDim.x / G;
@@ -83,7 +103,7 @@ __global__ void __launch_bounds__(kTileThreads, 1)
             }
             if (events_total && s == 0 && lane == 0) ev += a.indptr[i + 1] - rs;
             Acc* out = acc + ((SPLIT && i >= split) ? W : 0);
-            scatter_segment<Acc, WK>(a.indices, a.data, a.w_homo, b0, b1, lane, G, out, col0);
+            scatter_any<Acc, WK, VECL>(a.indices, a.data, a.w_homo, b0, b1, lane, G, out, col0);
         }
         __syncthreads();
         const int64_t rem = a.n_post - col0;
@@ -101,7 +121,7 @@ __global__ void __launch_bounds__(kTileThreads, 1)
 }
 
 // Direct-only variant without dynamic shared memory (more CTAs per SM).
-template <typename Acc, int WK, bool SPLIT>
+template <typename Acc, int WK, bool SPLIT, bool VECL>
 __global__ void __launch_bounds__(kDirectThreads)
     k_csr_scatter_direct(CsrArgs a, const int32_t* __restrict__ spike_list, const int32_t* __restrict__ n_spikes,
                          int64_t max_spikes, Acc* __restrict__ y, Acc* __restrict__ y_hi, int64_t split,
@@ -109,7 +129,7 @@ __global__ void __launch_bounds__(kDirectThreads)
     int64_t ns = *n_spikes;
     ns = ns < max_spikes ? ns : max_spikes;
     const int64_t nnz = a.indptr[a.n_pre];
-    const int G = pick_group(nnz, a.n_pre, 1);
+    const int G = VECL ? pick_group_v4(nnz, a.n_pre, 1) : pick_group(nnz, a.n_pre, 1);
     const int lane = threadIdx.x % G;
     const int64_t ngroups = static_cast<int64_t>(gridDim.x) * blockDim.x / G;
     int64_t ev = 0;
@@ -119,7 +139,7 @@ __global__ void __launch_bounds__(kDirectThreads)
         const int64_t b0 = a.indptr[i], b1 = a.indptr[i + 1];
         Acc* out = (SPLIT && i >= split) ? y_hi : y;
         if (lane == 0) ev += b1 - b0;
-        scatter_segment<Acc, WK>(a.indices, a.data, a.w_homo, b0, b1, lane, G, out, 0);
+        scatter_any<Acc, WK, VECL>(a.indices, a.data, a.w_homo, b0, b1, lane, G, out, 0);
     }
     if (events_total) block_add_i64(ev, events_total);
 }
@@ -201,7 +221,7 @@ __global__ void k_tile_index(int64_t n_pre, const int64_t* __restrict__ indptr, 
     }
 }
 
-template <typename Acc, int WK, bool SPLIT>
+template <typename Acc, int WK, bool SPLIT, bool VECL>
 bp_status launch_scatter_t(const CsrArgs& a, const int32_t* spike_list, const int32_t* n_spikes, int64_t max_spikes,
                            void* y, void* y_hi, int64_t split, int64_t* events_total, int mode, cudaStream_t s) {
     Acc* yy = static_cast<Acc*>(y);
@@ -223,15 +243,16 @@ bp_status launch_scatter_t(const CsrArgs& a, const int32_t* spike_list, const in
     if (S == 1) at.tile_ptr = nullptr;  // one tile covers every column: whole rows
     if (mode == 1) {
         const int grid = sm_count() * 8;
-        k_csr_scatter_direct<Acc, WK, SPLIT><<<grid, kDirectThreads, 0, s>>>(a, spike_list, n_spikes, max_spikes, yy,
-                                                                             yh, split, events_total);
+        k_csr_scatter_direct<Acc, WK, SPLIT, VECL><<<grid, kDirectThreads, 0, s>>>(a, spike_list, n_spikes,
+                                                                                   max_spikes, yy, yh, split,
+                                                                                   events_total);
         BP_LAUNCHED();
         return BP_OK;
     }
     const size_t smem = static_cast<size_t>(SPLIT ? 2 * W : W) * sizeof(Acc);
     static bool attr_set = false;  // per instantiation
     if (!attr_set) {
-        BP_CUDA(cudaFuncSetAttribute(k_csr_scatter<Acc, WK, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        BP_CUDA(cudaFuncSetAttribute(k_csr_scatter<Acc, WK, SPLIT, VECL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      static_cast<int>(SPLIT ? 2 * cap * sizeof(Acc) : cap * sizeof(Acc))));
         attr_set = true;
     }
@@ -239,19 +260,33 @@ bp_status launch_scatter_t(const CsrArgs& a, const int32_t* spike_list, const in
     int64_t R = static_cast<int64_t>(sm_count()) / S;
     if (R < 1) R = 1;
     const int64_t grid = R * S;
-    k_csr_scatter<Acc, WK, SPLIT><<<static_cast<unsigned>(grid), kTileThreads, smem, s>>>(
+    k_csr_scatter<Acc, WK, SPLIT, VECL><<<static_cast<unsigned>(grid), kTileThreads, smem, s>>>(
         at, spike_list, n_spikes, max_spikes, yy, yh, split, mode, W, S, events_total);
     BP_LAUNCHED();
     return BP_OK;
+}
+
+bool aligned_to(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
+
+template <typename Acc, int WK, bool SPLIT>
+bp_status launch_scatter_a(const CsrArgs& a, const int32_t* sl, const int32_t* ns, int64_t mx, void* y, void* yh,
+                           int64_t split, int64_t* ev, int mode, cudaStream_t s) {
+    // 16-byte index loads (aligned indices) pay off for homogeneous weights,
+    // whose events cost only the 4-byte index: with 4-byte loads too few bytes
+    // are in flight per SM.  With stored weights the extra registers of the
+    // vector path cost more than they bring (measured), so those stay scalar.
+    const bool vec = WK == WK_HOMO && aligned_to(a.indices, 16);
+    if (vec) return launch_scatter_t<Acc, WK, SPLIT, true>(a, sl, ns, mx, y, yh, split, ev, mode, s);
+    return launch_scatter_t<Acc, WK, SPLIT, false>(a, sl, ns, mx, y, yh, split, ev, mode, s);
 }
 
 template <typename Acc, bool SPLIT>
 bp_status launch_scatter_wk(const CsrArgs& a, const int32_t* sl, const int32_t* ns, int64_t mx, void* y, void* yh,
                             int64_t split, int64_t* ev, int mode, cudaStream_t s) {
     switch (a.wkind) {
-        case BP_W_F32: return launch_scatter_t<Acc, WK_F32, SPLIT>(a, sl, ns, mx, y, yh, split, ev, mode, s);
-        case BP_W_BF16: return launch_scatter_t<Acc, WK_BF16, SPLIT>(a, sl, ns, mx, y, yh, split, ev, mode, s);
-        default: return launch_scatter_t<Acc, WK_HOMO, SPLIT>(a, sl, ns, mx, y, yh, split, ev, mode, s);
+        case BP_W_F32: return launch_scatter_a<Acc, WK_F32, SPLIT>(a, sl, ns, mx, y, yh, split, ev, mode, s);
+        case BP_W_BF16: return launch_scatter_a<Acc, WK_BF16, SPLIT>(a, sl, ns, mx, y, yh, split, ev, mode, s);
+        default: return launch_scatter_a<Acc, WK_HOMO, SPLIT>(a, sl, ns, mx, y, yh, split, ev, mode, s);
     }
 }
 

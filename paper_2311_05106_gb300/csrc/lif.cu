@@ -21,6 +21,7 @@
 
 #include "bp_common.cuh"
 #include "bp_internal.h"
+#include "bp_neuron.cuh"
 #include "bp_rows.cuh"
 
 namespace bp {
@@ -64,35 +65,6 @@ struct StepSmem {
     long long red[3][kStepWarps];
 };
 
-// One neuron; returns true if it spikes.
-__device__ __forceinline__ bool neuron_update(const LifConst& c, float& v, float& g_e, float& g_i, int32_t& r,
-                                              float add_e, float add_i, float I_add) {
-    g_e = g_e * c.a_e + add_e;
-    g_i = g_i * c.a_i + add_i;
-    const float I = g_e * (c.E_e - v) + g_i * (c.E_i - v) + c.I_ext + I_add;
-    if (r > 0) {
-        r -= 1;
-        return false;
-    }
-    const float v_inf = c.V_rest + c.R * I;
-    v = v_inf + (v - v_inf) * c.a_m;
-    if (v > c.V_th) {
-        v = c.V_reset;
-        r = c.ref_steps;
-        return true;
-    }
-    return false;
-}
-
-template <bool COUNTS>
-__device__ __forceinline__ float event_add(typename std::conditional<COUNTS, int32_t, float>::type y, float w) {
-    if constexpr (COUNTS) {
-        return w * static_cast<float>(y);
-    } else {
-        return y;
-    }
-}
-
 template <bool COUNTS, int VEC, int CONN, int WK>
 __global__ void __launch_bounds__(kStepThreads, 4) k_step(StepArgs a) {
     __shared__ StepSmem sm;
@@ -105,6 +77,7 @@ __global__ void __launch_bounds__(kStepThreads, 4) k_step(StepArgs a) {
 
     uint32_t mask = 0;
     int cnt_e = 0, cnt_i = 0;
+    const uint64_t keep = l2_keep_policy();
     const int64_t nq = (a.n + VEC - 1) / VEC;
     const int64_t stride = static_cast<int64_t>(gridDim.x) * kStepThreads;
     const int64_t q0 = static_cast<int64_t>(blockIdx.x) * kStepThreads + threadIdx.x;
@@ -113,28 +86,30 @@ __global__ void __launch_bounds__(kStepThreads, 4) k_step(StepArgs a) {
         const int64_t i0 = q * VEC;
         uint32_t bits = 0;
         if (VEC == 4 && i0 + 4 <= a.n) {
-            float4 v = *reinterpret_cast<const float4*>(a.V + i0);
-            float4 g_e = *reinterpret_cast<const float4*>(a.ge + i0);
-            float4 g_i = *reinterpret_cast<const float4*>(a.gi + i0);
-            int4 r = *reinterpret_cast<const int4*>(a.ref + i0);
-            const Y4 ce = *reinterpret_cast<const Y4*>(ye + i0);
-            const Y4 ci = *reinterpret_cast<const Y4*>(yi + i0);
+            // the state streams through L2 (evict-first); the accumulators
+            // are read with the keep policy since the next delivery targets them
+            float4 v = __ldcs(reinterpret_cast<const float4*>(a.V + i0));
+            float4 g_e = __ldcs(reinterpret_cast<const float4*>(a.ge + i0));
+            float4 g_i = __ldcs(reinterpret_cast<const float4*>(a.gi + i0));
+            int4 r = __ldcs(reinterpret_cast<const int4*>(a.ref + i0));
+            const Y4 ce = ld_keep(reinterpret_cast<const Y4*>(ye + i0), keep);
+            const Y4 ci = ld_keep(reinterpret_cast<const Y4*>(yi + i0), keep);
             float4 Iv = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (a.I_vec) Iv = *reinterpret_cast<const float4*>(a.I_vec + i0);
+            if (a.I_vec) Iv = __ldcs(reinterpret_cast<const float4*>(a.I_vec + i0));
             const int4 r_old = r;
             bits |= neuron_update(c, v.x, g_e.x, g_i.x, r.x, event_add<COUNTS>(ce.x, c.w_e), event_add<COUNTS>(ci.x, c.w_i), Iv.x) ? 1u : 0u;
             bits |= neuron_update(c, v.y, g_e.y, g_i.y, r.y, event_add<COUNTS>(ce.y, c.w_e), event_add<COUNTS>(ci.y, c.w_i), Iv.y) ? 2u : 0u;
             bits |= neuron_update(c, v.z, g_e.z, g_i.z, r.z, event_add<COUNTS>(ce.z, c.w_e), event_add<COUNTS>(ci.z, c.w_i), Iv.z) ? 4u : 0u;
             bits |= neuron_update(c, v.w, g_e.w, g_i.w, r.w, event_add<COUNTS>(ce.w, c.w_e), event_add<COUNTS>(ci.w, c.w_i), Iv.w) ? 8u : 0u;
-            *reinterpret_cast<float4*>(a.V + i0) = v;
-            *reinterpret_cast<float4*>(a.ge + i0) = g_e;
-            *reinterpret_cast<float4*>(a.gi + i0) = g_i;
+            __stcs(reinterpret_cast<float4*>(a.V + i0), v);
+            __stcs(reinterpret_cast<float4*>(a.ge + i0), g_e);
+            __stcs(reinterpret_cast<float4*>(a.gi + i0), g_i);
             if (r.x != r_old.x || r.y != r_old.y || r.z != r_old.z || r.w != r_old.w)
-                *reinterpret_cast<int4*>(a.ref + i0) = r;
+                __stcs(reinterpret_cast<int4*>(a.ref + i0), r);
             if (ce.x != Y(0) || ce.y != Y(0) || ce.z != Y(0) || ce.w != Y(0))
-                *reinterpret_cast<Y4*>(ye + i0) = Y4{};
+                st_keep(reinterpret_cast<Y4*>(ye + i0), Y4{}, keep);
             if (ci.x != Y(0) || ci.y != Y(0) || ci.z != Y(0) || ci.w != Y(0))
-                *reinterpret_cast<Y4*>(yi + i0) = Y4{};
+                st_keep(reinterpret_cast<Y4*>(yi + i0), Y4{}, keep);
             if (a.spk) {
                 const uint32_t packed = (bits & 1u) | ((bits & 2u) << 7) | ((bits & 4u) << 14) | ((bits & 8u) << 21);
                 *reinterpret_cast<uint32_t*>(a.spk + i0) = packed;
@@ -226,7 +201,7 @@ __global__ void __launch_bounds__(kStepThreads, 4) k_step(StepArgs a) {
             const int32_t i = sm.ids[k];
             const int64_t b0 = A.indptr[i], b1 = A.indptr[i + 1];
             if (gl == 0) ev += b1 - b0;
-            scatter_segment<Y, WK>(A.indices, A.data, A.w_homo, b0, b1, gl, G, i < a.n_e ? out_e : out_i, 0);
+            scatter_segment<Y, WK, true>(A.indices, A.data, A.w_homo, b0, b1, gl, G, i < a.n_e ? out_e : out_i, 0);
         }
     } else if constexpr (CONN == CONN_JIT) {
         Y* out_e = static_cast<Y*>(a.ye_out);
@@ -237,7 +212,7 @@ __global__ void __launch_bounds__(kStepThreads, 4) k_step(StepArgs a) {
             const JitArgs& d = upper ? a.ji : a.je;
             Y* out = upper ? out_i : out_e;
             ev += jit_walk<BP_JIT_HOMO>(d, static_cast<uint32_t>(upper ? i - a.n_e : i), a.n,
-                                        [&](int64_t q, uint64_t, float w) { acc_add(out + q, event_value<Y>(w)); });
+                                        [&](int64_t q, uint64_t, float w) { red_add_keep(out + q, event_value<Y>(w), keep); });
         }
     }
 

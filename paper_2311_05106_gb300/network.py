@@ -123,3 +123,68 @@ class CobaNetwork:
             self.close()
         except Exception:
             pass
+
+
+class BatchedNetworks:
+    """Many independent COBA E/I networks (sizes `sizes`, seeds `seeds`, JIT
+    connectivity with p = 80/n by default) advanced together by the batched
+    persistent kernel.  State is concatenated; ``view(b)`` returns network b's
+    slice of a state array."""
+
+    def __init__(self, sizes, seeds, V0=None, p=None, params=None, device="cuda"):
+        sizes = np.ascontiguousarray(sizes, dtype=np.int64)
+        self.sizes = sizes
+        self.n_nets = len(sizes)
+        self.seeds = np.ascontiguousarray(seeds, dtype=np.uint64)
+        self.off = B.bp_batch_layout(sizes)
+        total = int(self.off[-1])
+        self.device = device
+        self.params = params if params is not None else B.bp_coba_params_default()
+        f32 = torch.float32
+        V = np.full(total, -60.0, np.float32)
+        if V0 is not None:
+            for b in range(self.n_nets):
+                V[self.off[b]:self.off[b] + sizes[b]] = V0[b]
+        self.V = torch.as_tensor(V, device=device)
+        self.ge = torch.zeros(total, dtype=f32, device=device)
+        self.gi = torch.zeros(total, dtype=f32, device=device)
+        self.ref = torch.zeros(total, dtype=torch.int32, device=device)
+        self.totals = torch.zeros((self.n_nets, 4), dtype=torch.int64, device=device)
+        self._p = None if p is None else np.ascontiguousarray(p, dtype=np.float64)
+        d = B.BatchDesc()
+        d.n_nets = self.n_nets
+        d.n = sizes.ctypes.data
+        d.n_e = None
+        d.seed = self.seeds.ctypes.data
+        d.p = None if self._p is None else self._p.ctypes.data
+        d.coba = self.params
+        d.V, d.ge, d.gi, d.ref = (t.data_ptr() for t in (self.V, self.ge, self.gi, self.ref))
+        d.totals = self.totals.data_ptr()
+        self.desc = d
+        self.handle = B.bp_batch_create(d)
+
+    def view(self, t, b):
+        return t[int(self.off[b]):int(self.off[b]) + int(self.sizes[b])]
+
+    def reset_counters(self):
+        B.bp_batch_reset_counters(self.handle)
+
+    def simulate(self, T):
+        B.bp_batch_simulate(self.handle, T)
+
+    def autotune(self, probe_steps=20):
+        return B.bp_batch_autotune(self.handle, probe_steps)
+
+    def info(self):
+        return B.bp_batch_info(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            B.bp_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

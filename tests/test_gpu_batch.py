@@ -1,0 +1,90 @@
+"""GPU parity of the batched networks (a9).
+
+* Every network of a batch follows, bit for bit, the trajectory that the
+  single-network path (itself pinned to the oracle) computes for it: same
+  FP32 arithmetic, exact integer event counts.
+* Sampled networks agree with the FP64 oracle until a near-threshold flip.
+* Autotuning restores the state it probes from; totals are consistent.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as orc
+from paper_2311_05106_gb300 import binding as B
+from paper_2311_05106_gb300 import workloads as wl
+from paper_2311_05106_gb300.network import BatchedNetworks, CobaNetwork
+
+pytestmark = pytest.mark.gpu
+
+
+def make_batch(n_nets, lo, hi, seed):
+    sizes = wl.batched_sizes(n_nets, lo, hi, seed=seed)
+    seeds = np.arange(n_nets, dtype=np.uint64) * 7919 + 17
+    V0 = [wl.coba_v0(int(n), seed=100 + b) for b, n in enumerate(sizes)]
+    return sizes, seeds, V0
+
+
+def test_batch_equals_single_network_path():
+    sizes, seeds, V0 = make_batch(12, 1000, 9000, seed=3)
+    sizes[0] = 1003                     # a size that is not a multiple of 4
+    V0[0] = wl.coba_v0(1003, seed=100)
+    bat = BatchedNetworks(sizes, seeds, V0=V0)
+    T = 230
+    bat.simulate(T)
+    torch.cuda.synchronize()
+    for b in [0, 3, 7, 11]:
+        single = CobaNetwork(int(sizes[b]), conn="jit", seed=int(seeds[b]), V0=V0[b])
+        single.simulate(T)
+        assert torch.equal(bat.view(bat.V, b), single.V), b
+        assert torch.equal(bat.view(bat.ref, b), single.ref), b
+        t = bat.totals[b].cpu().numpy()
+        s = single.totals.cpu().numpy()
+        assert t[0] == s[0] and t[1] == s[1] and t[2] == s[2] and t[3] == T
+        single.close()
+    bat.close()
+
+
+def test_batch_sampled_networks_match_oracle():
+    sizes, seeds, V0 = make_batch(6, 1000, 4000, seed=5)
+    bat = BatchedNetworks(sizes, seeds, V0=V0)
+    T = 60
+    bat.simulate(T)
+    V = bat.V.cpu().numpy()
+    for b in [1, 4]:
+        n = int(sizes[b])
+        K = orc.jit_K(80.0 / n)
+        ref = orc.CobaNet(n, (4 * n) // 5, ("jit", orc.projection_seed(int(seeds[b]), 0),
+                                           orc.projection_seed(int(seeds[b]), 1), K), V0[b].astype(np.float64))
+        flip = False
+        for _ in range(T):
+            _, vdec = ref.step(return_vdec=True)
+            if np.nanmin(np.abs(vdec + 50.0)) < 1e-3:
+                flip = True
+        if not flip:
+            got = V[bat.off[b]:bat.off[b] + n]
+            assert np.max(np.abs(got - ref.V)) < 1e-3
+
+
+def test_autotune_restores_state_and_continues():
+    sizes, seeds, V0 = make_batch(40, 1000, 20000, seed=7)
+    a = BatchedNetworks(sizes, seeds, V0=V0)
+    b = BatchedNetworks(sizes, seeds, V0=V0)
+    a.simulate(50)
+    b.simulate(50)
+    th = a.autotune(probe_steps=10)
+    assert th in (256, 512, 1024)
+    assert torch.equal(a.V, b.V) and torch.equal(a.totals, b.totals)
+    a.simulate(120)
+    b.simulate(120)
+    assert torch.equal(a.V, b.V) and torch.equal(a.ref, b.ref) and torch.equal(a.totals, b.totals)
+    bins, threads, total = a.info()
+    assert threads == th and total == int(a.off[-1]) and 1 <= bins
+    a.close()
+    b.close()
+
+
+def test_batch_rejects_oversized_network():
+    with pytest.raises(B.BpError):
+        BatchedNetworks(np.array([70000]), np.array([1], np.uint64))
