@@ -182,6 +182,29 @@ bp_status bp_event_csrmv_dense(int64_t n_pre, int64_t n_post,
                                const int32_t* tile_ptr, int32_t tile_cols,
                                uint32_t flags, bp_stream_t stream);
 
+/* bp_event_csrmv_dense for callers that cannot allocate device memory.
+ * The paper has no counterpart: this is an interface convenience of this
+ * library.  It computes exactly what bp_event_csrmv_dense computes (same
+ * arguments, without `workspace`), keeping the compacted spike list in a
+ * fixed scratch array built into the library instead of a caller-owned
+ * workspace.  It is meant for code that runs inside a framework owning the
+ * whole device memory pool, and for real-time loops in which cudaMalloc /
+ * cudaFree could synchronise the device; it calls no allocating routine.
+ * Limits: n_pre <= bp_event_csrmv_dense_noalloc_max_pre() (2^20); larger
+ * inputs return BP_ERR_INVALID with a message and enqueue nothing.  The
+ * scratch (about 4 MiB) exists on every GPU that loads the library until the
+ * process exits.  The first call on each device looks up the scratch
+ * array's device address; make that first call before any stream capture.
+ * All calls on a device share the scratch, so calls that may overlap on the
+ * GPU (other streams or host threads) race and must be serialised by the
+ * caller. */
+int64_t bp_event_csrmv_dense_noalloc_max_pre(void);
+bp_status bp_event_csrmv_dense_noalloc(int64_t n_pre, int64_t n_post,
+                                       const int64_t* indptr, const int32_t* indices,
+                                       const void* data, int32_t wkind, float w_homo,
+                                       const uint8_t* events, void* y, int32_t y_is_count,
+                                       uint32_t flags, bp_stream_t stream);
+
 /* Post-column tile index for shared-memory accumulation.  With
  * S = ceil(n_post / tile_cols) tiles, writes tile_ptr int32 [n_pre * (S + 1)]:
  * tile_ptr[i (S+1) + s] = (first position in row i whose column is

@@ -74,6 +74,8 @@ _SIGS = {
     "bp_event_csrmv_dense_workspace_bytes": (ctypes.c_size_t, [c_i64]),
     "bp_event_csrmv_dense": (c_i32, [c_i64, c_i64, VP, VP, VP, c_i32, c_f32, VP, VP, VP, c_i32, VP, c_i32, c_u32,
                                      VP]),
+    "bp_event_csrmv_dense_noalloc_max_pre": (c_i64, []),
+    "bp_event_csrmv_dense_noalloc": (c_i32, [c_i64, c_i64, VP, VP, VP, c_i32, c_f32, VP, VP, c_i32, c_u32, VP]),
     "bp_csr_tile_index_size": (c_i64, [c_i64, c_i64, c_i32]),
     "bp_csr_tile_index": (c_i32, [c_i64, c_i64, VP, VP, c_i32, VP, VP]),
     "bp_event_csrmv_t": (c_i32, [c_i64, c_i64, VP, VP, VP, c_i32, c_f32, VP, VP, c_u32, VP]),
@@ -224,6 +226,20 @@ def bp_event_csrmv_dense(indptr, indices, data, w_homo, events, workspace, y, ti
                                                               _wkind(data), float(w_homo), _p(events), _p(workspace),
                                                               _p(y), counts, _p(tile_ptr), int(tile_cols), int(flags),
                                                               _stream(stream)))
+
+
+def bp_event_csrmv_dense_noalloc_max_pre() -> int:
+    return int(lib().bp_event_csrmv_dense_noalloc_max_pre())
+
+
+def bp_event_csrmv_dense_noalloc(indptr, indices, data, w_homo, events, y, flags=0, stream=None):
+    """bp_event_csrmv_dense without a workspace argument: the library's fixed
+    scratch holds the spike list (for callers that cannot allocate)."""
+    n_pre = indptr.numel() - 1
+    counts = 1 if y.dtype == torch.int32 else 0
+    _check("bp_event_csrmv_dense_noalloc",
+           lib().bp_event_csrmv_dense_noalloc(n_pre, y.numel(), _p(indptr), _p(indices), _p(data), _wkind(data),
+                                              float(w_homo), _p(events), _p(y), counts, int(flags), _stream(stream)))
 
 
 def bp_csr_tile_index_size(n_pre, n_post, tile_cols) -> int:
