@@ -267,6 +267,150 @@ def e2e_run(torch, net, V0, steps):
     return ms, events, h2d, d2h
 
 
+# ----------------------------------------------------------------- other configurations
+def bench_small_net(torch, steps=1000):
+    """COBA E/I network of 4000 neurons (Appendix N scale 1), p = 0.02, 1000
+    steps: the multi-kernel CUDA-graph path and the persistent single-CTA path
+    (a batch of one network)."""
+    import numpy as np
+    from paper_2311_05106_gb300 import workloads as wl
+    from paper_2311_05106_gb300.network import BatchedNetworks, CobaNetwork
+    n = 4000
+    V0 = wl.coba_v0(n, seed=V0_SEED)
+    out = {}
+    stream = torch.cuda.current_stream()
+    for name, conn in (("graph_jit", "jit"), ("graph_csr", "csr")):
+        net = CobaNetwork(n, conn=conn, seed=SEED, p=0.02, V0=V0)
+        net.simulate(64)
+        net.reset_counters()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        net.simulate(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        t = net.totals.cpu().numpy()
+        out[name] = {"ms_per_run": ms, "steps_per_s": steps / (ms * 1e-3), "events_per_s": t[2] / (ms * 1e-3),
+                     "rate_hz": (t[0] + t[1]) / (n * steps * DT_MS * 1e-3)}
+        net.close()
+    bat = BatchedNetworks(np.array([n]), np.array([SEED], np.uint64), V0=[V0])
+    bat.simulate(64)
+    bat.reset_counters()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    bat.simulate(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    t = bat.totals.cpu().numpy()[0]
+    out["persistent_jit"] = {"ms_per_run": ms, "steps_per_s": steps / (ms * 1e-3), "events_per_s": t[2] / (ms * 1e-3)}
+    bat.close()
+    return out
+
+
+def bench_batched(torch, steps=2000, n_nets=256):
+    """256 independent COBA E/I networks, N ~ U[1000, 50000] (seed 11), JIT
+    connectivity p = 80/N, per-network seeds: the persistent batched kernel
+    (autotuned CTA size) against the single-network path run network after
+    network (the plain FP32 path, one CUDA graph per network)."""
+    import numpy as np
+    from paper_2311_05106_gb300 import workloads as wl
+    from paper_2311_05106_gb300.network import BatchedNetworks, CobaNetwork
+    sizes = wl.batched_sizes(n_nets, 1000, 50000, seed=11)
+    seeds = (np.arange(n_nets, dtype=np.uint64) * np.uint64(7919) + np.uint64(SEED))
+    V0 = [wl.coba_v0(int(n), seed=1000 + b) for b, n in enumerate(sizes)]
+    stream = torch.cuda.current_stream()
+    bat = BatchedNetworks(sizes, seeds, V0=V0)
+    threads = bat.autotune(probe_steps=20)
+    bat.simulate(steps)  # graph build + warm-up
+    bat.reset_counters()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    bat.simulate(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    tot = bat.totals.cpu().numpy()
+    bins = bat.info()[0]
+    bat.close()
+    # the plain single-network path, one network after the other (sampled: 100 steps each)
+    seq_steps = 100
+    seq_ms = 0.0
+    for b in range(n_nets):
+        net = CobaNetwork(int(sizes[b]), conn="jit", seed=int(seeds[b]), V0=V0[b])
+        net.simulate(64)
+        a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        net.simulate(seq_steps)
+        c.record(stream)
+        torch.cuda.synchronize()
+        seq_ms += a.elapsed_time(c)
+        net.close()
+    seq_ms_per_step = seq_ms / seq_steps
+    return {"networks": n_nets, "neurons": int(sizes.sum()), "steps": steps, "bins": bins, "cta_threads": threads,
+            "ms_per_step": ms / steps, "events_per_s": float(tot[:, 2].sum()) / (ms * 1e-3),
+            "sequential_single_net_ms_per_step": seq_ms_per_step,
+            "speedup_vs_sequential": seq_ms_per_step / (ms / steps)}
+
+
+def bench_bptt(torch, reps=3):
+    """Differentiable network of Appendix I at the configured size: batch 128,
+    700 Poisson inputs (5-50 Hz), 1024 recurrent LIF with 10 % recurrent CSR
+    weights N(0, 1/sqrt(102)), 20 leaky readouts, T = 1000, dt = 1 ms,
+    checkpoints every 100 steps: forward + loss + backward per iteration, BF16
+    and FP32 recurrent weights."""
+    import math
+
+    import numpy as np
+    from paper_2311_05106_gb300 import binding as B
+    from paper_2311_05106_gb300 import workloads as wl
+    from paper_2311_05106_gb300.snn import make_desc
+    Bsz, T, n_in, n_rec, n_out = 128, 1000, 700, 1024, 20
+    u = torch.from_numpy(wl.poisson_inputs(Bsz, T, n_in, seed=5)).cuda()
+    w = wl.snn_weights(n_in, n_rec, n_out, 0.1, seed=6, rec_std=1.0 / math.sqrt(102.0))
+    labels = torch.from_numpy(wl.labels(Bsz, n_out, seed=7)).cuda()
+    dev = "cuda"
+    T_ = lambda x: torch.as_tensor(np.ascontiguousarray(x)).to(dev)
+    ip, ix = T_(w["indptr"]).long(), T_(w["indices"]).int()
+    W_in, W_out, b = (T_(w[k]).float() for k in ("W_in", "W_out", "b_out"))
+    stream = torch.cuda.current_stream()
+    out = {}
+    for name, wr in (("bf16", T_(w["w_rec"]).to(torch.bfloat16)), ("f32", T_(w["w_rec"]).float())):
+        d = make_desc(Bsz, T, n_in, n_rec, n_out, W_in, ip, ix, wr, W_out, b, 100)
+        ws = torch.empty(B.bp_snn_workspace_bytes(d), dtype=torch.uint8, device=dev)
+        m = torch.empty((Bsz, n_out), dtype=torch.float32, device=dev)
+        loss = torch.empty(1, dtype=torch.float32, device=dev)
+        gm = torch.empty_like(m)
+        gs = [torch.zeros_like(W_in), torch.zeros(ix.numel(), device=dev), torch.zeros_like(W_out),
+              torch.zeros_like(b)]
+
+        def it():
+            B.bp_snn_forward(d, u, m, ws)
+            B.bp_snn_loss(m, labels, loss, gm)
+            B.bp_snn_backward(d, u, gm, ws, *gs)
+        it()
+        torch.cuda.synchronize()
+        fw_ms, tot_ms = [], []
+        for _ in range(reps):
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream)
+            B.bp_snn_forward(d, u, m, ws)
+            B.bp_snn_loss(m, labels, loss, gm)
+            e1.record(stream)
+            B.bp_snn_backward(d, u, gm, ws, *gs)
+            e2.record(stream)
+            torch.cuda.synchronize()
+            fw_ms.append(e0.elapsed_time(e1))
+            tot_ms.append(e0.elapsed_time(e2))
+        out[name] = {"forward_ms": min(fw_ms), "fwd_bwd_ms": min(tot_ms), "loss": float(loss.item()),
+                     "workspace_mb": ws.numel() / 2**20}
+    out["bf16_vs_f32"] = out["f32"]["fwd_bwd_ms"] / out["bf16"]["fwd_bwd_ms"]
+    return out
+
+
 # ----------------------------------------------------------------- oracle legs
 def oracle_sample(budget_s, n_sample=None):
     """The FP64 oracle (single thread, as it stands) on the same E/I network:
@@ -500,6 +644,9 @@ def main():
         variants["csr_f32"] = {"events_per_s": value, "steps_per_s": steps_per_s, "ms_per_step": ms / args.steps}
         for k in variants:
             variants[k]["vs_plain_f32"] = variants[k]["events_per_s"] / value
+        variants["coba_4k_1000_steps"] = bench_small_net(torch)
+        variants["batched_256_nets"] = bench_batched(torch)
+        variants["bptt_b128_t1000"] = bench_bptt(torch)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and headline:

@@ -414,6 +414,65 @@ bp_status bp_batch_autotune(bp_batch* b, int32_t probe_steps, int32_t* chosen_th
 
 bp_status bp_batch_destroy(bp_batch* b);
 
+/* --------------------------------------------------------------------------
+ * a10. Differentiable recurrent spiking network and its BPTT adjoint
+ * (Appendix I: LIF recurrent layer with exponential synaptic current, leaky
+ * readout, cross-entropy on the readout, surrogate-gradient training;
+ * Section 3.1: every operator has a reverse-mode rule).  Per batch element,
+ * t = 1..T, starting from I = V = y = 0 and no spikes:
+ *   I_t  = a_s I_{t-1} + W_rec^T z_{t-1} + W_in^T u_t     (a_s = exp(-dt/tau_s))
+ *   Vp_t = a_m V_{t-1} + (1 - a_m)(V_rest + R I_t)        (exponential Euler)
+ *   z_t  = [Vp_t > V_th];  V_t = z_t ? V_reset : Vp_t      (reset detached)
+ *   y_t  = a_o y_{t-1} + dt (W_out^T z_t + b_out);  m = mean_t y_t
+ * Gradients use dz/dVp ~ slope s(slope x)(1 - s(slope x)), x = Vp - V_th,
+ * s the logistic function.  W_rec is CSR with presynaptic rows (event-driven
+ * delivery of z_{t-1}); its stored values are FP32 or BF16, all arithmetic is
+ * FP32.  Checkpoints every ckpt_every steps; the backward pass recomputes
+ * each segment from its checkpoint, replaying the spikes the forward
+ * recorded.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    int32_t B, T, n_in, n_rec, n_out;  /* n_in, n_rec <= 4096, n_out <= 64 */
+    double dt, tau_m, tau_s, tau_o;    /* ms */
+    double V_rest, V_reset, V_th, R, slope;
+    int32_t ckpt_every;                /* K >= 1; 0 = a single segment (store everything) */
+    const float* W_in;                 /* [n_in][n_rec] */
+    const int64_t* indptr;             /* [n_rec + 1] */
+    const int32_t* indices;            /* [nnz] */
+    const void* w_rec;                 /* [nnz] FP32 or BF16 */
+    int32_t w_rec_kind;                /* BP_W_F32 or BP_W_BF16 */
+    const float* W_out;                /* [n_rec][n_out] */
+    const float* b_out;                /* [n_out] */
+} bp_snn_desc;
+
+/* dt = 1 ms, tau_m = 20, tau_s = 100, tau_o = 20 ms, V_rest = V_reset = 0,
+ * V_th = 1, R = 1, slope = 4, ckpt_every = 100, F32 recurrent weights; sizes
+ * and pointers zero. */
+bp_status bp_snn_desc_default(bp_snn_desc* d);
+
+/* Device workspace (bytes, 256-byte aligned) shared by forward and backward:
+ * checkpoints, the recorded spike bits of every step and one segment of
+ * potentials per batch element.  0 for an invalid desc. */
+size_t bp_snn_workspace_bytes(const bp_snn_desc* d);
+
+/* Forward pass over T steps: u uint8 [B][T][n_in] (input spikes), m float
+ * [B][n_out] (mean readout).  Fills the workspace for bp_snn_backward. */
+bp_status bp_snn_forward(const bp_snn_desc* d, const uint8_t* u, float* m, void* workspace, bp_stream_t stream);
+
+/* Mean over the batch of the cross-entropy of softmax(m_b) with label_b
+ * (labels int64 [B]), written to loss[0], and its gradient g_m = dL/dm
+ * [B][n_out]. */
+bp_status bp_snn_loss(int32_t B, int32_t n_out, const float* m, const int64_t* labels, float* loss, float* g_m,
+                      bp_stream_t stream);
+
+/* Backward pass (BPTT with checkpointed recomputation) for an upstream
+ * gradient g_m = dL/dm [B][n_out], after bp_snn_forward with the same desc,
+ * inputs and workspace.  ACCUMULATES dW_in [n_in][n_rec], dw_rec [nnz] (one
+ * gradient per stored recurrent weight), dW_out [n_rec][n_out] and
+ * db_out [n_out]. */
+bp_status bp_snn_backward(const bp_snn_desc* d, const uint8_t* u, const float* g_m, void* workspace, float* dW_in,
+                          float* dw_rec, float* dW_out, float* db_out, bp_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -60,6 +60,15 @@ class BatchDesc(ctypes.Structure):
                 ("V", VP), ("ge", VP), ("gi", VP), ("ref", VP), ("totals", VP)]
 
 
+class SnnDesc(ctypes.Structure):
+    _fields_ = [("B", c_i32), ("T", c_i32), ("n_in", c_i32), ("n_rec", c_i32), ("n_out", c_i32),
+                ("dt", c_f64), ("tau_m", c_f64), ("tau_s", c_f64), ("tau_o", c_f64),
+                ("V_rest", c_f64), ("V_reset", c_f64), ("V_th", c_f64), ("R", c_f64), ("slope", c_f64),
+                ("ckpt_every", c_i32),
+                ("W_in", VP), ("indptr", VP), ("indices", VP), ("w_rec", VP), ("w_rec_kind", c_i32),
+                ("W_out", VP), ("b_out", VP)]
+
+
 _SIGS = {
     "bp_version": (ctypes.c_char_p, []),
     "bp_last_error": (ctypes.c_char_p, []),
@@ -99,6 +108,11 @@ _SIGS = {
     "bp_batch_simulate": (c_i32, [VP, c_i64, VP]),
     "bp_batch_autotune": (c_i32, [VP, c_i32, VP, VP]),
     "bp_batch_destroy": (c_i32, [VP]),
+    "bp_snn_desc_default": (c_i32, [ctypes.POINTER(SnnDesc)]),
+    "bp_snn_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(SnnDesc)]),
+    "bp_snn_forward": (c_i32, [ctypes.POINTER(SnnDesc), VP, VP, VP, VP]),
+    "bp_snn_loss": (c_i32, [c_i32, c_i32, VP, VP, VP, VP, VP]),
+    "bp_snn_backward": (c_i32, [ctypes.POINTER(SnnDesc), VP, VP, VP, VP, VP, VP, VP, VP]),
 }
 
 _lock = threading.Lock()
@@ -381,3 +395,28 @@ def bp_batch_autotune(b, probe_steps=20, stream=None):
 
 def bp_batch_destroy(b):
     _check("bp_batch_destroy", lib().bp_batch_destroy(b))
+
+
+# ------------------------------------------------------------------ a10
+def bp_snn_desc_default() -> SnnDesc:
+    d = SnnDesc()
+    _check("bp_snn_desc_default", lib().bp_snn_desc_default(ctypes.byref(d)))
+    return d
+
+
+def bp_snn_workspace_bytes(desc) -> int:
+    return int(lib().bp_snn_workspace_bytes(ctypes.byref(desc)))
+
+
+def bp_snn_forward(desc, u, m, workspace, stream=None):
+    _check("bp_snn_forward", lib().bp_snn_forward(ctypes.byref(desc), _p(u), _p(m), _p(workspace), _stream(stream)))
+
+
+def bp_snn_loss(m, labels, loss, g_m, stream=None):
+    B, n_out = m.shape
+    _check("bp_snn_loss", lib().bp_snn_loss(B, n_out, _p(m), _p(labels), _p(loss), _p(g_m), _stream(stream)))
+
+
+def bp_snn_backward(desc, u, g_m, workspace, dW_in, dw_rec, dW_out, db_out, stream=None):
+    _check("bp_snn_backward", lib().bp_snn_backward(ctypes.byref(desc), _p(u), _p(g_m), _p(workspace), _p(dW_in),
+                                                    _p(dw_rec), _p(dW_out), _p(db_out), _stream(stream)))

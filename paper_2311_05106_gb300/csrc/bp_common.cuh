@@ -177,6 +177,13 @@ __device__ __forceinline__ void st_keep(float4* p, float4 v, uint64_t pol) {
                  : "memory");
 }
 
+// Four consecutive FP32 reductions in one 16-byte global operation (the
+// address must be 16-byte aligned).
+__device__ __forceinline__ void red_add_v4(float* a, float4 v) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(a), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
+                 : "memory");
+}
+
 // Accumulate into shared or global memory.  Integer counts and FP32 sums
 // both use the native red/atom paths.
 __device__ __forceinline__ void acc_add(int32_t* p, int32_t v) { atomicAdd(p, v); }

@@ -1,0 +1,490 @@
+// snn.cu -- the differentiable recurrent spiking network and its BPTT
+// adjoint (a10; Appendix I, Section 3.1: operators with reverse-mode rules).
+//
+// Model (per batch element; t = 1..T):
+//   I_t  = a_s I_{t-1} + W_rec^T z_{t-1} + W_in^T u_t
+//   Vp_t = a_m V_{t-1} + (1 - a_m)(V_rest + R I_t),  z_t = [Vp_t > V_th],
+//   V_t  = z_t ? V_reset : Vp_t (reset detached from the gradient),
+//   y_t  = a_o y_{t-1} + dt (W_out^T z_t + b),  m = mean_t y_t.
+// Adjoint (t = T..1), with surrogate dz/dVp = k s(kx)(1 - s(kx)):
+//   ybar_t = a_o ybar_{t+1} + g_m / T
+//   zbar_t = dt W_out ybar_t + W_rec Ibar_{t+1}          (gather over rows)
+//   Vpbar_t = Vbar_t (1 - z_t) + zbar_t s'(Vp_t - V_th)
+//   Ibar_t = (1 - a_m) R Vpbar_t + a_s Ibar_{t+1},  Vbar_{t-1} = a_m Vpbar_t
+//   dW_out += dt z_t ybar_t^T, db += dt ybar_t, dW_in += u_t Ibar_t^T,
+//   dw_rec[j] += Ibar_t[col j] for every entry j of rows spiking at t - 1.
+//
+// One CTA per batch element, the neuron state in shared memory.  Forward:
+// input spikes of the step are compacted (ballot) and their W_in rows summed
+// per neuron; the previous step's spikes are delivered through the CSR rows
+// (one warp per row) into a shared-memory accumulator; the readout sums the
+// W_out rows of the step's spikes.  Every K steps the state (I, V, y) is
+// checkpointed, and every step's spike bits are recorded (n_rec / 8 bytes per
+// step).  Backward: for each K-step segment, last first, the forward is
+// recomputed from its checkpoint storing Vp_t, with the recorded spikes
+// replayed rather than re-decided (the shared-memory float atomics may round
+// differently from the forward, and a near-threshold neuron must not take
+// the other branch); the adjoint then runs back through the segment.
+// Recurrent weights are FP32 or BF16 (FP32 arithmetic); gradients are FP32,
+// accumulated with atomics across batch elements.
+#include <cmath>
+
+#include "bp_common.cuh"
+#include "bp_internal.h"
+
+namespace bp {
+namespace {
+
+constexpr int kSnnThreads = 1024;
+constexpr int kSnnMaxRec = 4096;
+constexpr int kSnnMaxIn = 4096;
+constexpr int kSnnMaxOut = 64;
+
+struct SnnK {
+    int32_t B, T, n_in, n_rec, n_out, K;
+    float a_s, a_m, a_o, dt, V_rest, V_reset, V_th, R, slope;
+    const float* W_in;
+    const int64_t* indptr;
+    const int32_t* indices;
+    const void* w_rec;
+    const float* W_out;
+    const float* b_out;
+    // workspace
+    float* ck_I;         // [B][n_ck][n_rec]
+    float* ck_V;         // [B][n_ck][n_rec]
+    float* ck_y;         // [B][n_ck][n_out]
+    uint32_t* z_all;     // [B][T][zw]  spike bits of every step (recorded by the forward)
+    float* seg_Vp;       // [B][K][n_rec]
+    int32_t n_ck, zw;
+    int32_t vec_red;     // dW_in rows 16-byte aligned: vector reductions
+};
+
+template <int WK>
+__device__ __forceinline__ float w_at(const void* w, int64_t j) {
+    if constexpr (WK == BP_W_BF16) {
+        const unsigned short raw = static_cast<const unsigned short*>(w)[j];
+        return __uint_as_float(static_cast<uint32_t>(raw) << 16);
+    } else {
+        return static_cast<const float*>(w)[j];
+    }
+}
+
+// Compacts the active inputs of step t into list (shared), returns the count.
+__device__ __forceinline__ int gather_inputs(const uint8_t* __restrict__ ut, int n_in, int32_t* list,
+                                             int32_t* counter) {
+    if (threadIdx.x == 0) *counter = 0;
+    __syncthreads();
+    for (int base = 0; base < n_in; base += kSnnThreads) {
+        const int k = base + threadIdx.x;
+        const bool on = k < n_in && ut[k] != 0;
+        const unsigned m = __ballot_sync(FULL_MASK, on);
+        int pos = 0;
+        if ((threadIdx.x & 31) == 0 && m) pos = atomicAdd(counter, __popc(m));
+        pos = __shfl_sync(FULL_MASK, pos, 0);
+        if (on) list[pos + __popc(m & lanemask_lt())] = k;
+    }
+    __syncthreads();
+    return *counter;
+}
+
+// One step of the neuron state held in shared memory.  racc holds
+// W_rec^T z_{t-1} and is cleared.  Spikes are decided by the threshold, or,
+// when force_z is given, taken from those recorded bits (the backward pass
+// replays the forward's spikes so that its recomputation cannot take another
+// branch).  The step's spikes are appended to spk; zbits (nullable) receives
+// their bits; Vp_out (nullable) the potentials before reset.
+__device__ __forceinline__ void neuron_step(const SnnK& p, float* I, float* V, float* racc, const int32_t* in_list,
+                                            int n_act, int32_t* spk, int32_t* n_spk, float* Vp_out,
+                                            uint32_t* zbits, const uint32_t* force_z) {
+    for (int jb = 0; jb < p.n_rec; jb += kSnnThreads) {
+        const int j = jb + threadIdx.x;
+        bool z = false;
+        if (j < p.n_rec) {
+            float in = 0.f;
+            for (int a = 0; a < n_act; ++a) in += __ldg(p.W_in + static_cast<int64_t>(in_list[a]) * p.n_rec + j);
+            const float Ij = p.a_s * I[j] + racc[j] + in;
+            racc[j] = 0.f;
+            I[j] = Ij;
+            const float vp = p.a_m * V[j] + (1.f - p.a_m) * (p.V_rest + p.R * Ij);
+            z = force_z ? ((force_z[j >> 5] >> (j & 31)) & 1u) != 0 : vp > p.V_th;
+            V[j] = z ? p.V_reset : vp;
+            if (Vp_out) Vp_out[j] = vp;
+        }
+        const unsigned m = __ballot_sync(FULL_MASK, z);
+        if ((threadIdx.x & 31) == 0) {
+            if (zbits && jb + threadIdx.x < p.n_rec) zbits[(jb + threadIdx.x) >> 5] = m;
+            if (m) {
+                int pos = atomicAdd(n_spk, __popc(m));
+                for (unsigned mm = m; mm; mm &= mm - 1) spk[pos++] = jb + threadIdx.x + __ffs(mm) - 1;
+            }
+        }
+    }
+}
+
+// racc[col] += w for every entry of the rows in spk[0..n) (one warp per row).
+template <int WK>
+__device__ __forceinline__ void deliver(const SnnK& p, const int32_t* spk, int n, float* racc) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int e = warp; e < n; e += kSnnThreads / 32) {
+        const int i = spk[e];
+        const int64_t b0 = p.indptr[i], b1 = p.indptr[i + 1];
+        for (int64_t j = b0 + lane; j < b1; j += 32) atomicAdd(racc + p.indices[j], w_at<WK>(p.w_rec, j));
+    }
+}
+
+template <int WK>
+__global__ void __launch_bounds__(kSnnThreads, 1) k_snn_forward(SnnK p, const uint8_t* __restrict__ u,
+                                                               float* __restrict__ m_out) {
+    extern __shared__ __align__(16) float sh[];
+    float* I = sh;
+    float* V = I + p.n_rec;
+    float* racc = V + p.n_rec;
+    int32_t* spk = reinterpret_cast<int32_t*>(racc + p.n_rec);
+    int32_t* in_list = spk + p.n_rec;
+    __shared__ int32_t s_cnt[2];
+    __shared__ float s_y[kSnnMaxOut], s_m[kSnnMaxOut];
+    const int b = blockIdx.x;
+    for (int j = threadIdx.x; j < p.n_rec; j += kSnnThreads) I[j] = V[j] = racc[j] = 0.f;
+    if (threadIdx.x < p.n_out) s_y[threadIdx.x] = s_m[threadIdx.x] = 0.f;
+    __syncthreads();
+    for (int t = 0; t < p.T; ++t) {
+        if (t % p.K == 0) {  // checkpoint of the state before step t
+            const int64_t o = static_cast<int64_t>(b) * p.n_ck + t / p.K;
+            for (int j = threadIdx.x; j < p.n_rec; j += kSnnThreads) {
+                p.ck_I[o * p.n_rec + j] = I[j];
+                p.ck_V[o * p.n_rec + j] = V[j];
+            }
+            if (threadIdx.x < p.n_out) p.ck_y[o * p.n_out + threadIdx.x] = s_y[threadIdx.x];
+        }
+        const int n_act = gather_inputs(u + (static_cast<int64_t>(b) * p.T + t) * p.n_in, p.n_in, in_list, &s_cnt[0]);
+        if (threadIdx.x == 0) s_cnt[1] = 0;
+        __syncthreads();
+        neuron_step(p, I, V, racc, in_list, n_act, spk, &s_cnt[1], nullptr,
+                    p.z_all + (static_cast<int64_t>(b) * p.T + t) * p.zw, nullptr);
+        __syncthreads();
+        const int n = s_cnt[1];
+        deliver<WK>(p, spk, n, racc);
+        if (threadIdx.x < p.n_out) {
+            const int o = threadIdx.x;
+            float acc = 0.f;
+            for (int e = 0; e < n; ++e) acc += __ldg(p.W_out + static_cast<int64_t>(spk[e]) * p.n_out + o);
+            const float y = p.a_o * s_y[o] + p.dt * (acc + p.b_out[o]);
+            s_y[o] = y;
+            s_m[o] += y;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < p.n_out) m_out[static_cast<int64_t>(b) * p.n_out + threadIdx.x] = s_m[threadIdx.x] / p.T;
+}
+
+template <int WK>
+__global__ void __launch_bounds__(kSnnThreads, 1) k_snn_backward(SnnK p, const uint8_t* __restrict__ u,
+                                                                const float* __restrict__ g_m, float* __restrict__ dW_in,
+                                                                float* __restrict__ dw_rec, float* __restrict__ dW_out,
+                                                                float* __restrict__ db_out) {
+    extern __shared__ __align__(16) float sh[];
+    float* I = sh;                    // recompute state
+    float* V = I + p.n_rec;
+    float* racc = V + p.n_rec;
+    float* Ib_next = racc + p.n_rec;  // Ibar_{t+1}
+    float* Ib = Ib_next + p.n_rec;    // Ibar_t
+    float* Vb = Ib + p.n_rec;         // Vbar_t
+    int32_t* spk = reinterpret_cast<int32_t*>(Vb + p.n_rec);
+    int32_t* in_list = spk + p.n_rec;
+    __shared__ int32_t s_cnt[2];
+    __shared__ float s_yb[kSnnMaxOut], s_gm[kSnnMaxOut];
+    const int b = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int j = threadIdx.x; j < p.n_rec; j += kSnnThreads) Ib_next[j] = Vb[j] = 0.f;
+    if (threadIdx.x < p.n_out) {
+        s_yb[threadIdx.x] = 0.f;
+        s_gm[threadIdx.x] = g_m[static_cast<int64_t>(b) * p.n_out + threadIdx.x];
+    }
+    float db_acc = 0.f;
+    float* segVp = p.seg_Vp + static_cast<int64_t>(b) * p.K * p.n_rec;
+    const uint32_t* zall = p.z_all + static_cast<int64_t>(b) * p.T * p.zw;
+    const int nseg = (p.T + p.K - 1) / p.K;
+    for (int seg = nseg - 1; seg >= 0; --seg) {
+        const int t0 = seg * p.K;
+        const int t1 = min(p.T, t0 + p.K);
+        const int64_t o = static_cast<int64_t>(b) * p.n_ck + seg;
+        // ---- recompute the segment from its checkpoint
+        __syncthreads();
+        for (int j = threadIdx.x; j < p.n_rec; j += kSnnThreads) {
+            I[j] = p.ck_I[o * p.n_rec + j];
+            V[j] = p.ck_V[o * p.n_rec + j];
+            racc[j] = 0.f;
+        }
+        if (threadIdx.x == 0) s_cnt[1] = 0;
+        __syncthreads();
+        if (t0 > 0) {  // pending input of the spikes of step t0 - 1
+            const uint32_t* zp = zall + static_cast<int64_t>(t0 - 1) * p.zw;
+            for (int w = threadIdx.x; w < p.zw; w += kSnnThreads) {
+                uint32_t bits = zp[w];
+                if (bits) {
+                    int q = atomicAdd(&s_cnt[1], __popc(bits));
+                    for (; bits; bits &= bits - 1) spk[q++] = 32 * w + __ffs(bits) - 1;
+                }
+            }
+        }
+        __syncthreads();
+        deliver<WK>(p, spk, s_cnt[1], racc);
+        __syncthreads();
+        for (int t = t0; t < t1; ++t) {
+            const int n_act = gather_inputs(u + (static_cast<int64_t>(b) * p.T + t) * p.n_in, p.n_in, in_list, &s_cnt[0]);
+            if (threadIdx.x == 0) s_cnt[1] = 0;
+            __syncthreads();
+            neuron_step(p, I, V, racc, in_list, n_act, spk, &s_cnt[1], segVp + static_cast<int64_t>(t - t0) * p.n_rec,
+                        nullptr, zall + static_cast<int64_t>(t) * p.zw);
+            __syncthreads();
+            deliver<WK>(p, spk, s_cnt[1], racc);
+            __syncthreads();
+        }
+        // ---- adjoint, t = t1-1 .. t0
+        for (int t = t1 - 1; t >= t0; --t) {
+            if (threadIdx.x < p.n_out) {
+                const float yb = p.a_o * s_yb[threadIdx.x] + s_gm[threadIdx.x] / p.T;
+                s_yb[threadIdx.x] = yb;
+                db_acc += p.dt * yb;
+            }
+            __syncthreads();
+            const float* Vp = segVp + static_cast<int64_t>(t - t0) * p.n_rec;
+            const uint32_t* zb = zall + static_cast<int64_t>(t) * p.zw;
+            // zbar_j: readout part per neuron, recurrent part by one warp per row
+            for (int j = warp; j < p.n_rec; j += kSnnThreads / 32) {
+                const int64_t r0 = p.indptr[j], r1 = p.indptr[j + 1];
+                float acc = 0.f;
+                for (int64_t e = r0 + lane; e < r1; e += 32) acc += w_at<WK>(p.w_rec, e) * Ib_next[p.indices[e]];
+                for (int oo = lane; oo < p.n_out; oo += 32) acc += p.dt * __ldg(p.W_out + static_cast<int64_t>(j) * p.n_out + oo) * s_yb[oo];
+                acc = group_reduce_sum(acc, 32);
+                if (lane == 0) Ib[j] = acc;  // zbar_j for now
+            }
+            __syncthreads();
+            for (int j = threadIdx.x; j < p.n_rec; j += kSnnThreads) {
+                const float zbar = Ib[j];
+                const bool z = (zb[j >> 5] >> (j & 31)) & 1u;
+                const float x = Vp[j] - p.V_th;
+                const float s = 1.f / (1.f + expf(-p.slope * x));
+                const float vpb = Vb[j] * (z ? 0.f : 1.f) + zbar * (p.slope * s * (1.f - s));
+                const float ib = (1.f - p.a_m) * p.R * vpb + p.a_s * Ib_next[j];
+                Ib[j] = ib;
+                Vb[j] = p.a_m * vpb;
+                if (z) {
+                    for (int oo = 0; oo < p.n_out; ++oo)
+                        atomicAdd(dW_out + static_cast<int64_t>(j) * p.n_out + oo, p.dt * s_yb[oo]);
+                }
+            }
+            __syncthreads();
+            // dW_in += u_t Ibar_t^T (inputs active at t)
+            const int n_act = gather_inputs(u + (static_cast<int64_t>(b) * p.T + t) * p.n_in, p.n_in, in_list, &s_cnt[0]);
+            for (int a = 0; a < n_act; ++a) {
+                float* row = dW_in + static_cast<int64_t>(in_list[a]) * p.n_rec;
+                if (p.vec_red) {
+                    for (int j4 = 4 * threadIdx.x; j4 < p.n_rec; j4 += 4 * kSnnThreads)
+                        red_add_v4(row + j4, make_float4(Ib[j4], Ib[j4 + 1], Ib[j4 + 2], Ib[j4 + 3]));
+                } else {
+                    for (int j = threadIdx.x; j < p.n_rec; j += kSnnThreads) atomicAdd(row + j, Ib[j]);
+                }
+            }
+            // dw_rec: rows spiking at t - 1
+            if (t > 0) {
+                const uint32_t* zp = zall + static_cast<int64_t>(t - 1) * p.zw;
+                for (int w = warp; w < p.zw; w += kSnnThreads / 32) {
+                    uint32_t bits = zp[w];
+                    for (; bits; bits &= bits - 1) {
+                        const int i = 32 * w + __ffs(bits) - 1;
+                        const int64_t r0 = p.indptr[i], r1 = p.indptr[i + 1];
+                        for (int64_t e = r0 + lane; e < r1; e += 32) atomicAdd(dw_rec + e, Ib[p.indices[e]]);
+                    }
+                }
+            }
+            __syncthreads();
+            for (int j = threadIdx.x; j < p.n_rec; j += kSnnThreads) Ib_next[j] = Ib[j];
+            __syncthreads();
+        }
+    }
+    if (threadIdx.x < p.n_out) atomicAdd(db_out + threadIdx.x, db_acc);
+}
+
+// Mean cross-entropy of softmax(m) over the batch and its gradient.
+__global__ void k_snn_loss(int32_t B, int32_t n_out, const float* __restrict__ m, const int64_t* __restrict__ labels,
+                           float* __restrict__ loss, float* __restrict__ g_m) {
+    __shared__ double s_sum;
+    if (threadIdx.x == 0) s_sum = 0.0;
+    __syncthreads();
+    for (int b = threadIdx.x; b < B; b += blockDim.x) {
+        const float* mb = m + static_cast<int64_t>(b) * n_out;
+        double mx = mb[0];
+        for (int o = 1; o < n_out; ++o) mx = fmax(mx, static_cast<double>(mb[o]));
+        double se = 0.0;
+        for (int o = 0; o < n_out; ++o) se += exp(static_cast<double>(mb[o]) - mx);
+        const int64_t lab = labels[b];
+        const double lse = log(se) + mx;
+        atomicAdd(&s_sum, lse - mb[lab]);
+        for (int o = 0; o < n_out; ++o) {
+            const double sm = exp(static_cast<double>(mb[o]) - mx) / se;
+            g_m[static_cast<int64_t>(b) * n_out + o] = static_cast<float>((sm - (o == lab ? 1.0 : 0.0)) / B);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *loss = static_cast<float>(s_sum / B);
+}
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct SnnLayout {
+    size_t ck_I, ck_V, ck_y, z_all, seg_Vp, total;
+    int32_t n_ck, zw;
+};
+
+SnnLayout snn_layout(const bp_snn_desc& d) {
+    SnnLayout L{};
+    const int K = d.ckpt_every > 0 ? d.ckpt_every : d.T;
+    L.n_ck = (d.T + K - 1) / K;
+    if (L.n_ck < 1) L.n_ck = 1;
+    L.zw = (d.n_rec + 31) / 32;
+    size_t o = 0;
+    const size_t B = d.B;
+    L.ck_I = o; o = align256(o + B * L.n_ck * d.n_rec * 4);
+    L.ck_V = o; o = align256(o + B * L.n_ck * d.n_rec * 4);
+    L.ck_y = o; o = align256(o + B * L.n_ck * d.n_out * 4);
+    L.z_all = o; o = align256(o + B * static_cast<size_t>(d.T) * L.zw * 4);
+    L.seg_Vp = o; o = align256(o + B * static_cast<size_t>(K) * d.n_rec * 4);
+    L.total = o;
+    return L;
+}
+
+bp_status snn_check(const bp_snn_desc* d) {
+    BP_REQUIRE(d != nullptr, "desc is NULL");
+    BP_REQUIRE(d->B > 0 && d->T > 0, "B and T must be positive");
+    BP_REQUIRE(d->n_in > 0 && d->n_in <= kSnnMaxIn, "n_in must be in [1, %d]", kSnnMaxIn);
+    BP_REQUIRE(d->n_rec > 0 && d->n_rec <= kSnnMaxRec, "n_rec must be in [1, %d]", kSnnMaxRec);
+    BP_REQUIRE(d->n_out > 0 && d->n_out <= kSnnMaxOut, "n_out must be in [1, %d]", kSnnMaxOut);
+    BP_REQUIRE(d->ckpt_every >= 0, "ckpt_every < 0");
+    BP_REQUIRE(d->w_rec_kind == BP_W_F32 || d->w_rec_kind == BP_W_BF16, "recurrent weights must be F32 or BF16");
+    BP_REQUIRE(d->W_in && d->indptr && d->indices && d->w_rec && d->W_out && d->b_out, "a parameter pointer is NULL");
+    BP_REQUIRE(d->tau_m > 0 && d->tau_s > 0 && d->tau_o > 0 && d->dt > 0, "time constants must be positive");
+    return BP_OK;
+}
+
+SnnK snn_kernel_args(const bp_snn_desc& d, void* ws) {
+    const SnnLayout L = snn_layout(d);
+    SnnK p;
+    p.B = d.B;
+    p.T = d.T;
+    p.n_in = d.n_in;
+    p.n_rec = d.n_rec;
+    p.n_out = d.n_out;
+    p.K = d.ckpt_every > 0 ? d.ckpt_every : d.T;
+    p.a_s = static_cast<float>(std::exp(-d.dt / d.tau_s));
+    p.a_m = static_cast<float>(std::exp(-d.dt / d.tau_m));
+    p.a_o = static_cast<float>(std::exp(-d.dt / d.tau_o));
+    p.dt = static_cast<float>(d.dt);
+    p.V_rest = static_cast<float>(d.V_rest);
+    p.V_reset = static_cast<float>(d.V_reset);
+    p.V_th = static_cast<float>(d.V_th);
+    p.R = static_cast<float>(d.R);
+    p.slope = static_cast<float>(d.slope);
+    p.W_in = d.W_in;
+    p.indptr = d.indptr;
+    p.indices = d.indices;
+    p.w_rec = d.w_rec;
+    p.W_out = d.W_out;
+    p.b_out = d.b_out;
+    char* w = static_cast<char*>(ws);
+    p.ck_I = reinterpret_cast<float*>(w + L.ck_I);
+    p.ck_V = reinterpret_cast<float*>(w + L.ck_V);
+    p.ck_y = reinterpret_cast<float*>(w + L.ck_y);
+    p.z_all = reinterpret_cast<uint32_t*>(w + L.z_all);
+    p.seg_Vp = reinterpret_cast<float*>(w + L.seg_Vp);
+    p.n_ck = L.n_ck;
+    p.zw = L.zw;
+    p.vec_red = 0;
+    return p;
+}
+
+template <typename Kern>
+bp_status set_smem(Kern k, size_t bytes) {
+    BP_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes)));
+    return BP_OK;
+}
+
+}  // namespace
+}  // namespace bp
+
+extern "C" {
+
+bp_status bp_snn_desc_default(bp_snn_desc* d) {
+    bp::clear_error();
+    BP_REQUIRE(d != nullptr, "desc is NULL");
+    *d = bp_snn_desc{};
+    d->dt = 1.0;
+    d->tau_m = 20.0;
+    d->tau_s = 100.0;
+    d->tau_o = 20.0;
+    d->V_rest = 0.0;
+    d->V_reset = 0.0;
+    d->V_th = 1.0;
+    d->R = 1.0;
+    d->slope = 4.0;
+    d->ckpt_every = 100;
+    d->w_rec_kind = BP_W_F32;
+    return BP_OK;
+}
+
+size_t bp_snn_workspace_bytes(const bp_snn_desc* d) {
+    if (!d || d->B <= 0 || d->T <= 0 || d->n_rec <= 0 || d->n_out <= 0) return 0;
+    return bp::snn_layout(*d).total;
+}
+
+bp_status bp_snn_forward(const bp_snn_desc* d, const uint8_t* u, float* m, void* workspace, bp_stream_t stream) {
+    bp::clear_error();
+    BP_TRY(bp::snn_check(d));
+    BP_REQUIRE(u && m && workspace, "u, m or workspace is NULL");
+    BP_REQUIRE((reinterpret_cast<uintptr_t>(workspace) & 255) == 0, "workspace must be 256-byte aligned");
+    const bp::SnnK p = bp::snn_kernel_args(*d, workspace);
+    const size_t smem = static_cast<size_t>(d->n_rec) * 4 * 4 + static_cast<size_t>(d->n_in) * 4;
+    if (d->w_rec_kind == BP_W_BF16) {
+        BP_TRY(bp::set_smem(bp::k_snn_forward<BP_W_BF16>, smem));
+        bp::k_snn_forward<BP_W_BF16><<<d->B, bp::kSnnThreads, smem, stream>>>(p, u, m);
+    } else {
+        BP_TRY(bp::set_smem(bp::k_snn_forward<BP_W_F32>, smem));
+        bp::k_snn_forward<BP_W_F32><<<d->B, bp::kSnnThreads, smem, stream>>>(p, u, m);
+    }
+    BP_LAUNCHED();
+    return BP_OK;
+}
+
+bp_status bp_snn_loss(int32_t B, int32_t n_out, const float* m, const int64_t* labels, float* loss, float* g_m,
+                      bp_stream_t stream) {
+    bp::clear_error();
+    BP_REQUIRE(B > 0 && n_out > 0, "B and n_out must be positive");
+    BP_REQUIRE(m && labels && loss && g_m, "a pointer is NULL");
+    bp::k_snn_loss<<<1, 256, 0, stream>>>(B, n_out, m, labels, loss, g_m);
+    BP_LAUNCHED();
+    return BP_OK;
+}
+
+bp_status bp_snn_backward(const bp_snn_desc* d, const uint8_t* u, const float* g_m, void* workspace, float* dW_in,
+                          float* dw_rec, float* dW_out, float* db_out, bp_stream_t stream) {
+    bp::clear_error();
+    BP_TRY(bp::snn_check(d));
+    BP_REQUIRE(u && g_m && workspace && dW_in && dw_rec && dW_out && db_out, "a pointer is NULL");
+    BP_REQUIRE((reinterpret_cast<uintptr_t>(workspace) & 255) == 0, "workspace must be 256-byte aligned");
+    bp::SnnK p = bp::snn_kernel_args(*d, workspace);
+    p.vec_red = (d->n_rec % 4 == 0 && (reinterpret_cast<uintptr_t>(dW_in) & 15) == 0) ? 1 : 0;
+    const size_t smem = static_cast<size_t>(d->n_rec) * 4 * 7 + static_cast<size_t>(d->n_in) * 4;
+    if (d->w_rec_kind == BP_W_BF16) {
+        BP_TRY(bp::set_smem(bp::k_snn_backward<BP_W_BF16>, smem));
+        bp::k_snn_backward<BP_W_BF16><<<d->B, bp::kSnnThreads, smem, stream>>>(p, u, g_m, dW_in, dw_rec, dW_out,
+                                                                              db_out);
+    } else {
+        BP_TRY(bp::set_smem(bp::k_snn_backward<BP_W_F32>, smem));
+        bp::k_snn_backward<BP_W_F32><<<d->B, bp::kSnnThreads, smem, stream>>>(p, u, g_m, dW_in, dw_rec, dW_out,
+                                                                             db_out);
+    }
+    BP_LAUNCHED();
+    return BP_OK;
+}
+
+}  // extern "C"

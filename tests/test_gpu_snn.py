@@ -1,0 +1,157 @@
+"""GPU parity of the differentiable network and its BPTT adjoint (a10) against
+the FP64 oracle (oracle/bptt.py).
+
+Tolerances (relative to the largest magnitude of each array): readout and
+loss 1e-5; gradients 1e-3 with FP32 recurrent weights, 1e-3 against the
+oracle fed the same BF16-rounded weights and 1e-2 against the unrounded FP32
+weights.  Spike decisions flip between FP32 and FP64 when a potential lands
+within rounding of the threshold; cases are checked to keep every decision at
+least 1e-4 away from it in the oracle (a flip would change the trajectory).
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import bptt
+from paper_2311_05106_gb300 import binding as B
+from paper_2311_05106_gb300 import workloads as wl
+from paper_2311_05106_gb300.snn import bptt_loss, make_desc
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-30))
+
+
+def problem(seed, B_, T, n_in, n_rec, n_out, p_rec, in_scale=4.0, rate=8.0, rec_std=0.5):
+    u = wl.poisson_inputs(B_, T, n_in, seed, rate_lo=5.0 * rate, rate_hi=50.0 * rate)
+    w = wl.snn_weights(n_in, n_rec, n_out, p_rec, seed + 1, rec_std=rec_std)
+    w["W_in"] = (w["W_in"] * in_scale).astype(np.float32)
+    labels = wl.labels(B_, n_out, seed + 2)
+    return u, labels, w
+
+
+def oracle_run(u, labels, w, rec_weights):
+    L, m, g, fw = bptt.loss_and_grads(u, labels, w["W_in"].astype(np.float64), w["indptr"], w["indices"],
+                                     rec_weights.astype(np.float64), w["W_out"].astype(np.float64),
+                                     w["b_out"].astype(np.float64))
+    margin = float(np.min(np.abs(fw["Vp"] - 1.0)))
+    return L, m, g, fw, margin
+
+
+def gpu_run(u, labels, w, rec_dtype, ckpt):
+    dev = "cuda"
+    T_ = lambda x: torch.as_tensor(np.ascontiguousarray(x)).to(dev)
+    W_in = T_(w["W_in"]).float().requires_grad_()
+    w_rec = T_(w["w_rec"]).float().requires_grad_()
+    W_out = T_(w["W_out"]).float().requires_grad_()
+    b_out = T_(w["b_out"]).float().requires_grad_()
+    loss = bptt_loss(W_in, w_rec, W_out, b_out, T_(u), T_(labels).long(), T_(w["indptr"]).long(),
+                     T_(w["indices"]).int(), rec_dtype, ckpt)
+    loss.backward()
+    return (loss.item(), W_in.grad.cpu().numpy(), w_rec.grad.cpu().numpy(), W_out.grad.cpu().numpy(),
+            b_out.grad.cpu().numpy())
+
+
+def find_case(B_, T, n_in, n_rec, n_out, p_rec, seeds=range(1, 40), **kw):
+    for s in seeds:
+        u, labels, w = problem(s, B_, T, n_in, n_rec, n_out, p_rec, **kw)
+        res = oracle_run(u, labels, w, w["w_rec"])
+        if res[4] > 1e-4 and res[3]["z"].mean() > 0.005:
+            return u, labels, w, res
+    pytest.fail("no case without near-threshold decisions")
+
+
+@pytest.mark.parametrize("ckpt", [0, 7])
+def test_forward_loss_and_gradients_fp32(ckpt):
+    u, labels, w, (L, m, g, fw, margin) = find_case(3, 40, 24, 96, 6, 0.1)
+    Lg, dWin, dwrec, dWout, db = gpu_run(u, labels, w, torch.float32, ckpt)
+    assert abs(Lg - L) <= 1e-5 * max(1.0, abs(L))
+    assert rel(dWin, g["W_in"]) < 1e-3
+    assert rel(dwrec, g["w_rec"]) < 1e-3
+    assert rel(dWout, g["W_out"]) < 1e-3
+    assert rel(db, g["b_out"]) < 1e-3
+
+
+def test_readout_matches_oracle():
+    u, labels, w, (L, m, g, fw, margin) = find_case(4, 60, 30, 128, 5, 0.1)
+    dev = "cuda"
+    T_ = lambda x: torch.as_tensor(np.ascontiguousarray(x)).to(dev)
+    ip, ix = T_(w["indptr"]).long(), T_(w["indices"]).int()
+    W_in, wr, W_out, b = (T_(w[k]).float() for k in ("W_in", "w_rec", "W_out", "b_out"))
+    d = make_desc(4, 60, 30, 128, 5, W_in, ip, ix, wr, W_out, b, 16)
+    ws = torch.empty(B.bp_snn_workspace_bytes(d), dtype=torch.uint8, device=dev)
+    mg = torch.empty((4, 5), dtype=torch.float32, device=dev)
+    B.bp_snn_forward(d, T_(u), mg, ws)
+    assert rel(mg.cpu().numpy(), m) < 1e-5
+
+
+def test_bf16_recurrent_weights():
+    for seed in range(1, 60):
+        u, labels, w = problem(seed, 3, 40, 24, 96, 6, 0.1)
+        L, m, g, fw, margin = oracle_run(u, labels, w, w["w_rec"])
+        w16 = torch.as_tensor(w["w_rec"]).to(torch.bfloat16).float().numpy()
+        L16, m16, g16, fw16, margin16 = oracle_run(u, labels, w, w16)
+        # a case where rounding the weights to BF16 moves no decision near the threshold
+        if margin > 1e-4 and margin16 > 1e-4 and np.array_equal(fw16["z"], fw["z"]) and fw["z"].mean() > 0.005:
+            break
+    else:
+        pytest.fail("no case without near-threshold decisions")
+    Lg, dWin, dwrec, dWout, db = gpu_run(u, labels, w, torch.bfloat16, 10)
+    for got, key in ((dWin, "W_in"), (dwrec, "w_rec"), (dWout, "W_out"), (db, "b_out")):
+        assert rel(got, g16[key]) < 1e-3, key
+        assert rel(got, g[key]) < 1e-2, key
+
+
+def test_checkpoint_interval_does_not_change_gradients():
+    u, labels, w, _ = find_case(2, 50, 16, 64, 4, 0.15)
+    a = gpu_run(u, labels, w, torch.float32, 0)
+    b = gpu_run(u, labels, w, torch.float32, 6)
+    c = gpu_run(u, labels, w, torch.float32, 1)
+    for x, y, z in zip(a[1:], b[1:], c[1:]):
+        assert rel(y, x) < 1e-6 and rel(z, x) < 1e-6
+    assert abs(a[0] - b[0]) < 1e-6 and abs(a[0] - c[0]) < 1e-6
+
+
+def test_full_size_configuration_properties():
+    """B = 128, 700 inputs (5-50 Hz), 1024 recurrent neurons with 10 % BF16
+    recurrent weights, 20 readouts, T = 1000, checkpoints every 100 steps: the
+    loss is finite, the gradients are finite and non-zero, the checkpointed
+    and the single-segment backward agree, and the loss equals the oracle's
+    cross-entropy of the GPU readout."""
+    Bsz, T, n_in, n_rec, n_out = 128, 1000, 700, 1024, 20
+    u = wl.poisson_inputs(Bsz, T, n_in, seed=5)
+    w = wl.snn_weights(n_in, n_rec, n_out, 0.1, seed=6, rec_std=1.0 / math.sqrt(102.0))
+    labels = wl.labels(Bsz, n_out, seed=7)
+    dev = "cuda"
+    T_ = lambda x: torch.as_tensor(np.ascontiguousarray(x)).to(dev)
+    ip, ix = T_(w["indptr"]).long(), T_(w["indices"]).int()
+    W_in, W_out, b = (T_(w[k]).float() for k in ("W_in", "W_out", "b_out"))
+    wr = T_(w["w_rec"]).to(torch.bfloat16)
+    uu, lab = T_(u), T_(labels).long()
+    grads = []
+    for ck in (100, 0):
+        d = make_desc(Bsz, T, n_in, n_rec, n_out, W_in, ip, ix, wr, W_out, b, ck)
+        ws = torch.empty(B.bp_snn_workspace_bytes(d), dtype=torch.uint8, device=dev)
+        m = torch.empty((Bsz, n_out), dtype=torch.float32, device=dev)
+        loss = torch.empty(1, dtype=torch.float32, device=dev)
+        gm = torch.empty_like(m)
+        B.bp_snn_forward(d, uu, m, ws)
+        B.bp_snn_loss(m, lab, loss, gm)
+        gs = [torch.zeros_like(W_in), torch.zeros(ix.numel(), device=dev), torch.zeros_like(W_out), torch.zeros_like(b)]
+        B.bp_snn_backward(d, uu, gm, ws, *gs)
+        torch.cuda.synchronize()
+        Lref, gref = bptt.loss_and_grad_m(m.cpu().double().numpy(), labels)
+        assert abs(loss.item() - Lref) < 1e-5 * max(1.0, Lref)
+        assert rel(gm.cpu().numpy(), gref) < 1e-5
+        grads.append([x.cpu().numpy() for x in gs])
+        assert all(np.isfinite(x).all() for x in grads[-1])
+        assert all(np.abs(x).max() > 0 for x in grads[-1])
+    for x, y in zip(*grads):
+        assert rel(x, y) < 1e-5
