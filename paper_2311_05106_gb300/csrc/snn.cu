@@ -69,21 +69,48 @@ __device__ __forceinline__ float w_at(const void* w, int64_t j) {
     }
 }
 
-// Compacts the active inputs of step t into list (shared), returns the count.
+// Recurrent input is accumulated as a 64-bit fixed-point number (scale 2^32):
+// integer additions commute, so the sum - and with it every spike decision -
+// does not depend on the order in which the delivering warps arrive, and the
+// backward pass recomputes the forward bit for bit.  Weights of magnitude
+// above 2^-9 convert exactly; sums are exact up to |sum| < 2^31.
+constexpr double kFixScale = 4294967296.0;  // 2^32
+
+__device__ __forceinline__ unsigned long long to_fix(float w) {
+    return static_cast<unsigned long long>(__double2ll_rn(static_cast<double>(w) * kFixScale));
+}
+__device__ __forceinline__ float from_fix(unsigned long long v) {
+    return static_cast<float>(static_cast<double>(static_cast<long long>(v)) * (1.0 / kFixScale));
+}
+
+// Compacts the active inputs of step t into list (shared) in increasing index
+// order (ballot per warp, prefix over warps), so that the input current sums
+// the W_in rows in a fixed order.  Returns the count.
 __device__ __forceinline__ int gather_inputs(const uint8_t* __restrict__ ut, int n_in, int32_t* list,
                                              int32_t* counter) {
+    __shared__ int32_t s_wpre[kSnnThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) *counter = 0;
     __syncthreads();
     for (int base = 0; base < n_in; base += kSnnThreads) {
         const int k = base + threadIdx.x;
         const bool on = k < n_in && ut[k] != 0;
         const unsigned m = __ballot_sync(FULL_MASK, on);
-        int pos = 0;
-        if ((threadIdx.x & 31) == 0 && m) pos = atomicAdd(counter, __popc(m));
-        pos = __shfl_sync(FULL_MASK, pos, 0);
-        if (on) list[pos + __popc(m & lanemask_lt())] = k;
+        if (lane == 0) s_wpre[warp] = __popc(m);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int run = *counter;
+            for (int w = 0; w < kSnnThreads / 32; ++w) {
+                const int c = s_wpre[w];
+                s_wpre[w] = run;
+                run += c;
+            }
+            *counter = run;
+        }
+        __syncthreads();
+        if (on) list[s_wpre[warp] + __popc(m & lanemask_lt())] = k;
+        __syncthreads();
     }
-    __syncthreads();
     return *counter;
 }
 
@@ -93,7 +120,8 @@ __device__ __forceinline__ int gather_inputs(const uint8_t* __restrict__ ut, int
 // replays the forward's spikes so that its recomputation cannot take another
 // branch).  The step's spikes are appended to spk; zbits (nullable) receives
 // their bits; Vp_out (nullable) the potentials before reset.
-__device__ __forceinline__ void neuron_step(const SnnK& p, float* I, float* V, float* racc, const int32_t* in_list,
+__device__ __forceinline__ void neuron_step(const SnnK& p, float* I, float* V, unsigned long long* racc,
+                                            const int32_t* in_list,
                                             int n_act, int32_t* spk, int32_t* n_spk, float* Vp_out,
                                             uint32_t* zbits, const uint32_t* force_z) {
     for (int jb = 0; jb < p.n_rec; jb += kSnnThreads) {
@@ -102,8 +130,8 @@ __device__ __forceinline__ void neuron_step(const SnnK& p, float* I, float* V, f
         if (j < p.n_rec) {
             float in = 0.f;
             for (int a = 0; a < n_act; ++a) in += __ldg(p.W_in + static_cast<int64_t>(in_list[a]) * p.n_rec + j);
-            const float Ij = p.a_s * I[j] + racc[j] + in;
-            racc[j] = 0.f;
+            const float Ij = p.a_s * I[j] + from_fix(racc[j]) + in;
+            racc[j] = 0ull;
             I[j] = Ij;
             const float vp = p.a_m * V[j] + (1.f - p.a_m) * (p.V_rest + p.R * Ij);
             z = force_z ? ((force_z[j >> 5] >> (j & 31)) & 1u) != 0 : vp > p.V_th;
@@ -121,14 +149,15 @@ __device__ __forceinline__ void neuron_step(const SnnK& p, float* I, float* V, f
     }
 }
 
-// racc[col] += w for every entry of the rows in spk[0..n) (one warp per row).
+// racc[col] += w for every entry of the rows in spk[0..n) (one warp per row),
+// in fixed point.
 template <int WK>
-__device__ __forceinline__ void deliver(const SnnK& p, const int32_t* spk, int n, float* racc) {
+__device__ __forceinline__ void deliver(const SnnK& p, const int32_t* spk, int n, unsigned long long* racc) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int e = warp; e < n; e += kSnnThreads / 32) {
         const int i = spk[e];
         const int64_t b0 = p.indptr[i], b1 = p.indptr[i + 1];
-        for (int64_t j = b0 + lane; j < b1; j += 32) atomicAdd(racc + p.indices[j], w_at<WK>(p.w_rec, j));
+        for (int64_t j = b0 + lane; j < b1; j += 32) atomicAdd(racc + p.indices[j], to_fix(w_at<WK>(p.w_rec, j)));
     }
 }
 
@@ -136,15 +165,18 @@ template <int WK>
 __global__ void __launch_bounds__(kSnnThreads, 1) k_snn_forward(SnnK p, const uint8_t* __restrict__ u,
                                                                float* __restrict__ m_out) {
     extern __shared__ __align__(16) float sh[];
-    float* I = sh;
+    unsigned long long* racc = reinterpret_cast<unsigned long long*>(sh);
+    float* I = reinterpret_cast<float*>(racc + p.n_rec);
     float* V = I + p.n_rec;
-    float* racc = V + p.n_rec;
-    int32_t* spk = reinterpret_cast<int32_t*>(racc + p.n_rec);
+    int32_t* spk = reinterpret_cast<int32_t*>(V + p.n_rec);
     int32_t* in_list = spk + p.n_rec;
     __shared__ int32_t s_cnt[2];
     __shared__ float s_y[kSnnMaxOut], s_m[kSnnMaxOut];
     const int b = blockIdx.x;
-    for (int j = threadIdx.x; j < p.n_rec; j += kSnnThreads) I[j] = V[j] = racc[j] = 0.f;
+    for (int j = threadIdx.x; j < p.n_rec; j += kSnnThreads) {
+        I[j] = V[j] = 0.f;
+        racc[j] = 0ull;
+    }
     if (threadIdx.x < p.n_out) s_y[threadIdx.x] = s_m[threadIdx.x] = 0.f;
     __syncthreads();
     for (int t = 0; t < p.T; ++t) {
@@ -165,9 +197,13 @@ __global__ void __launch_bounds__(kSnnThreads, 1) k_snn_forward(SnnK p, const ui
         const int n = s_cnt[1];
         deliver<WK>(p, spk, n, racc);
         if (threadIdx.x < p.n_out) {
+            // summed in neuron order (from the recorded bits), so the readout is reproducible
             const int o = threadIdx.x;
+            const uint32_t* zt = p.z_all + (static_cast<int64_t>(b) * p.T + t) * p.zw;
             float acc = 0.f;
-            for (int e = 0; e < n; ++e) acc += __ldg(p.W_out + static_cast<int64_t>(spk[e]) * p.n_out + o);
+            for (int w = 0; w < p.zw; ++w)
+                for (uint32_t bits = zt[w]; bits; bits &= bits - 1)
+                    acc += __ldg(p.W_out + static_cast<int64_t>(32 * w + __ffs(bits) - 1) * p.n_out + o);
             const float y = p.a_o * s_y[o] + p.dt * (acc + p.b_out[o]);
             s_y[o] = y;
             s_m[o] += y;
@@ -183,10 +219,10 @@ __global__ void __launch_bounds__(kSnnThreads, 1) k_snn_backward(SnnK p, const u
                                                                 float* __restrict__ dw_rec, float* __restrict__ dW_out,
                                                                 float* __restrict__ db_out) {
     extern __shared__ __align__(16) float sh[];
-    float* I = sh;                    // recompute state
+    unsigned long long* racc = reinterpret_cast<unsigned long long*>(sh);
+    float* I = reinterpret_cast<float*>(racc + p.n_rec);  // recompute state
     float* V = I + p.n_rec;
-    float* racc = V + p.n_rec;
-    float* Ib_next = racc + p.n_rec;  // Ibar_{t+1}
+    float* Ib_next = V + p.n_rec;     // Ibar_{t+1}
     float* Ib = Ib_next + p.n_rec;    // Ibar_t
     float* Vb = Ib + p.n_rec;         // Vbar_t
     int32_t* spk = reinterpret_cast<int32_t*>(Vb + p.n_rec);
@@ -213,7 +249,7 @@ __global__ void __launch_bounds__(kSnnThreads, 1) k_snn_backward(SnnK p, const u
         for (int j = threadIdx.x; j < p.n_rec; j += kSnnThreads) {
             I[j] = p.ck_I[o * p.n_rec + j];
             V[j] = p.ck_V[o * p.n_rec + j];
-            racc[j] = 0.f;
+            racc[j] = 0ull;
         }
         if (threadIdx.x == 0) s_cnt[1] = 0;
         __syncthreads();
@@ -443,7 +479,8 @@ bp_status bp_snn_forward(const bp_snn_desc* d, const uint8_t* u, float* m, void*
     BP_REQUIRE(u && m && workspace, "u, m or workspace is NULL");
     BP_REQUIRE((reinterpret_cast<uintptr_t>(workspace) & 255) == 0, "workspace must be 256-byte aligned");
     const bp::SnnK p = bp::snn_kernel_args(*d, workspace);
-    const size_t smem = static_cast<size_t>(d->n_rec) * 4 * 4 + static_cast<size_t>(d->n_in) * 4;
+    // racc (8 B), I, V, spike list (4 B each) per neuron, plus the input list
+    const size_t smem = static_cast<size_t>(d->n_rec) * (8 + 4 * 3) + static_cast<size_t>(d->n_in) * 4;
     if (d->w_rec_kind == BP_W_BF16) {
         BP_TRY(bp::set_smem(bp::k_snn_forward<BP_W_BF16>, smem));
         bp::k_snn_forward<BP_W_BF16><<<d->B, bp::kSnnThreads, smem, stream>>>(p, u, m);
@@ -473,7 +510,8 @@ bp_status bp_snn_backward(const bp_snn_desc* d, const uint8_t* u, const float* g
     BP_REQUIRE((reinterpret_cast<uintptr_t>(workspace) & 255) == 0, "workspace must be 256-byte aligned");
     bp::SnnK p = bp::snn_kernel_args(*d, workspace);
     p.vec_red = (d->n_rec % 4 == 0 && (reinterpret_cast<uintptr_t>(dW_in) & 15) == 0) ? 1 : 0;
-    const size_t smem = static_cast<size_t>(d->n_rec) * 4 * 7 + static_cast<size_t>(d->n_in) * 4;
+    // racc (8 B), I, V, Ibar_{t+1}, Ibar_t, Vbar, spike list (4 B each) per neuron, plus the input list
+    const size_t smem = static_cast<size_t>(d->n_rec) * (8 + 4 * 6) + static_cast<size_t>(d->n_in) * 4;
     if (d->w_rec_kind == BP_W_BF16) {
         BP_TRY(bp::set_smem(bp::k_snn_backward<BP_W_BF16>, smem));
         bp::k_snn_backward<BP_W_BF16><<<d->B, bp::kSnnThreads, smem, stream>>>(p, u, g_m, dW_in, dw_rec, dW_out,
