@@ -60,6 +60,11 @@ def parse():
     ap.add_argument("--sweep-n", default="1e4,1e5,1e6")
     ap.add_argument("--sweep-p", default="0.001,0.01,0.1")
     ap.add_argument("--sweep-rho", default="0.001,0.01,0.1")
+    ap.add_argument("--sweep-weights", default="homo,f32,bf16")
+    ap.add_argument("--sweep-ops", default="csr,csr_t,jit")
+    # the differentiable-network measurement alone (profiling)
+    ap.add_argument("--bptt-only", action="store_true")
+    ap.add_argument("--bptt-T", type=int, default=1000)
     return ap.parse_args()
 
 
@@ -356,7 +361,7 @@ def bench_batched(torch, steps=2000, n_nets=256):
             "speedup_vs_sequential": seq_ms_per_step / (ms / steps)}
 
 
-def bench_bptt(torch, reps=3):
+def bench_bptt(torch, reps=3, T=1000):
     """Differentiable network of Appendix I at the configured size: batch 128,
     700 Poisson inputs (5-50 Hz), 1024 recurrent LIF with 10 % recurrent CSR
     weights N(0, 1/sqrt(102)), 20 leaky readouts, T = 1000, dt = 1 ms,
@@ -368,7 +373,7 @@ def bench_bptt(torch, reps=3):
     from paper_2311_05106_gb300 import binding as B
     from paper_2311_05106_gb300 import workloads as wl
     from paper_2311_05106_gb300.snn import make_desc
-    Bsz, T, n_in, n_rec, n_out = 128, 1000, 700, 1024, 20
+    Bsz, n_in, n_rec, n_out = 128, 700, 1024, 20
     u = torch.from_numpy(wl.poisson_inputs(Bsz, T, n_in, seed=5)).cuda()
     w = wl.snn_weights(n_in, n_rec, n_out, 0.1, seed=6, rec_std=1.0 / math.sqrt(102.0))
     labels = torch.from_numpy(wl.labels(Bsz, n_out, seed=7)).cuda()
@@ -491,6 +496,9 @@ def run_sweep(args):
     sizes = [int(float(x)) for x in args.sweep_n.split(",")]
     probs = [float(x) for x in args.sweep_p.split(",")]
     rhos = [float(x) for x in args.sweep_rho.split(",")]
+    wsel = set(args.sweep_weights.split(","))
+    ops = set(args.sweep_ops.split(","))
+    stored = bool(wsel & {"f32", "bf16"})
     stream = torch.cuda.current_stream()
 
     def timeit(fn, reps):
@@ -517,10 +525,11 @@ def run_sweep(args):
             dh = B.bp_jit_desc_init(seed, p)
             ip = ix = w32 = w16 = tp = None
             tc = 0
+            csr_ok = csr_ok and bool(ops & {"csr", "csr_t"})
             if csr_ok:
-                ip, ix, w32 = B.jit_materialize(dn, n, n, data_dtype=torch.float32)
+                ip, ix, w32 = B.jit_materialize(dn, n, n, data_dtype=torch.float32 if stored else None)
                 nnz = ix.numel()
-                w16 = w32.to(torch.bfloat16)
+                w16 = w32.to(torch.bfloat16) if "bf16" in wsel else None
                 tc = B.bp_tile_cols() if n > B.bp_tile_cols() else 0
                 if tc:
                     tp = torch.empty(B.bp_csr_tile_index_size(n, n, tc), dtype=torch.int32, device="cuda")
@@ -530,6 +539,8 @@ def run_sweep(args):
                 x = torch.ones(n, dtype=torch.float32, device="cuda")
                 yp = torch.zeros(n, dtype=torch.float32, device="cuda")
                 for wname, wt, wb in (("homo", None, 0), ("f32", w32, 4), ("bf16", w16, 2)):
+                    if wname not in wsel or "csr_t" not in ops:
+                        continue
                     ms = timeit(lambda: B.bp_event_csrmv_t(ip, ix, wt, 1.0, x, yp), 5)
                     alg = nnz * (4 + wb) + 8 * (n + 1)
                     emit(op="event_csrmv_t", n=n, p=p, weights=wname, us=ms * 1e3, nnz=nnz,
@@ -547,6 +558,8 @@ def run_sweep(args):
                     lens = ip[1:] - ip[:-1]
                     ev_count = int(lens[sl[:n_spk].long()].sum().item()) if n_spk else 0
                     for wname, wt, wb, y in (("homo", None, 0, yc), ("f32", w32, 4, yf), ("bf16", w16, 2, yf)):
+                        if wname not in wsel or "csr" not in ops:
+                            continue
                         ms = timeit(lambda: B.bp_event_csrmv(ip, ix, wt, 1.0, sl, ns, y, tile_ptr=tp, tile_cols=tc), 7)
                         alg = ev_count * (4 + wb) + 16 * n_spk
                         emit(op="event_csrmv", n=n, p=p, rho=rho, weights=wname, us=ms * 1e3, spikes=n_spk,
@@ -557,6 +570,8 @@ def run_sweep(args):
                 B.bp_jitconn_event_mv(dh, n, sl, ns, yy)
                 ev_jit = int(yy.sum().item())
                 for wname, d, y in (("homo", dh, yc), ("normal", dn, yf)):
+                    if "jit" not in ops:
+                        continue
                     ms = timeit(lambda: B.bp_jitconn_event_mv(d, n, sl, ns, y), 5)
                     emit(op="jitconn_event_mv", n=n, p=p, rho=rho, weights=wname, us=ms * 1e3, spikes=n_spk,
                          events=ev_jit, events_per_s=ev_jit / (ms * 1e-3), bound="alu")
@@ -573,6 +588,11 @@ def main():
         return run_reference(args)
     if args.sweep:
         return run_sweep(args)
+    if args.bptt_only:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps({"bptt": bench_bptt(torch, T=args.bptt_T)}))
+        return 0
     rank, world, local = dist_env()
     import torch
     dist = None

@@ -443,6 +443,7 @@ typedef struct {
     int32_t w_rec_kind;                /* BP_W_F32 or BP_W_BF16 */
     const float* W_out;                /* [n_rec][n_out] */
     const float* b_out;                /* [n_out] */
+    int64_t nnz;                       /* number of stored recurrent weights (= indptr[n_rec]) */
 } bp_snn_desc;
 
 /* dt = 1 ms, tau_m = 20, tau_s = 100, tau_o = 20 ms, V_rest = V_reset = 0,
@@ -451,8 +452,10 @@ typedef struct {
 bp_status bp_snn_desc_default(bp_snn_desc* d);
 
 /* Device workspace (bytes, 256-byte aligned) shared by forward and backward:
- * checkpoints, the recorded spike bits of every step and one segment of
- * potentials per batch element.  0 for an invalid desc. */
+ * checkpoints, the recorded spike bits of every step, one segment of
+ * potentials and the gradient partials of each batch element (summed over the
+ * batch in a fixed order, so gradients are reproducible bit for bit).  0 for
+ * an invalid desc. */
 size_t bp_snn_workspace_bytes(const bp_snn_desc* d);
 
 /* Forward pass over T steps: u uint8 [B][T][n_in] (input spikes), m float

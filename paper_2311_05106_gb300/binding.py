@@ -66,7 +66,7 @@ class SnnDesc(ctypes.Structure):
                 ("V_rest", c_f64), ("V_reset", c_f64), ("V_th", c_f64), ("R", c_f64), ("slope", c_f64),
                 ("ckpt_every", c_i32),
                 ("W_in", VP), ("indptr", VP), ("indices", VP), ("w_rec", VP), ("w_rec_kind", c_i32),
-                ("W_out", VP), ("b_out", VP)]
+                ("W_out", VP), ("b_out", VP), ("nnz", c_i64)]
 
 
 _SIGS = {

@@ -55,8 +55,12 @@ struct SnnK {
     float* ck_y;         // [B][n_ck][n_out]
     uint32_t* z_all;     // [B][T][zw]  spike bits of every step (recorded by the forward)
     float* seg_Vp;       // [B][K][n_rec]
+    float* g_in;         // [B][n_in][n_rec]   per-batch-element gradient partials
+    float* g_rec;        // [B][nnz]
+    float* g_out;        // [B][n_rec][n_out]
+    float* g_b;          // [B][n_out]
+    int64_t nnz;
     int32_t n_ck, zw;
-    int32_t vec_red;     // dW_in rows 16-byte aligned: vector reductions
 };
 
 template <int WK>
@@ -74,13 +78,14 @@ __device__ __forceinline__ float w_at(const void* w, int64_t j) {
 // does not depend on the order in which the delivering warps arrive, and the
 // backward pass recomputes the forward bit for bit.  Weights of magnitude
 // above 2^-9 convert exactly; sums are exact up to |sum| < 2^31.
-constexpr double kFixScale = 4294967296.0;  // 2^32
-
+// Scaling by a power of two is exact in FP32, so the conversions need no FP64
+// arithmetic (whose rate is low on this GPU): one rounding float -> int64 on
+// the way in, one rounding int64 -> float on the way out.
 __device__ __forceinline__ unsigned long long to_fix(float w) {
-    return static_cast<unsigned long long>(__double2ll_rn(static_cast<double>(w) * kFixScale));
+    return static_cast<unsigned long long>(__float2ll_rn(w * 4294967296.0f));
 }
 __device__ __forceinline__ float from_fix(unsigned long long v) {
-    return static_cast<float>(static_cast<double>(static_cast<long long>(v)) * (1.0 / kFixScale));
+    return __ll2float_rn(static_cast<long long>(v)) * (1.0f / 4294967296.0f);
 }
 
 // Compacts the active inputs of step t into list (shared) in increasing index
@@ -129,7 +134,18 @@ __device__ __forceinline__ void neuron_step(const SnnK& p, float* I, float* V, u
         bool z = false;
         if (j < p.n_rec) {
             float in = 0.f;
-            for (int a = 0; a < n_act; ++a) in += __ldg(p.W_in + static_cast<int64_t>(in_list[a]) * p.n_rec + j);
+            int a = 0;
+            for (; a + 4 <= n_act; a += 4) {  // four row loads in flight, summed in list order
+                const float x0 = __ldg(p.W_in + static_cast<int64_t>(in_list[a]) * p.n_rec + j);
+                const float x1 = __ldg(p.W_in + static_cast<int64_t>(in_list[a + 1]) * p.n_rec + j);
+                const float x2 = __ldg(p.W_in + static_cast<int64_t>(in_list[a + 2]) * p.n_rec + j);
+                const float x3 = __ldg(p.W_in + static_cast<int64_t>(in_list[a + 3]) * p.n_rec + j);
+                in += x0;
+                in += x1;
+                in += x2;
+                in += x3;
+            }
+            for (; a < n_act; ++a) in += __ldg(p.W_in + static_cast<int64_t>(in_list[a]) * p.n_rec + j);
             const float Ij = p.a_s * I[j] + from_fix(racc[j]) + in;
             racc[j] = 0ull;
             I[j] = Ij;
@@ -196,17 +212,23 @@ __global__ void __launch_bounds__(kSnnThreads, 1) k_snn_forward(SnnK p, const ui
         __syncthreads();
         const int n = s_cnt[1];
         deliver<WK>(p, spk, n, racc);
-        if (threadIdx.x < p.n_out) {
-            // summed in neuron order (from the recorded bits), so the readout is reproducible
-            const int o = threadIdx.x;
+        {
+            // W_out^T z_t: one warp per output, lanes over the recorded spike words
+            // in a fixed order and a fixed reduction tree, so the readout is reproducible
+            const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
             const uint32_t* zt = p.z_all + (static_cast<int64_t>(b) * p.T + t) * p.zw;
-            float acc = 0.f;
-            for (int w = 0; w < p.zw; ++w)
-                for (uint32_t bits = zt[w]; bits; bits &= bits - 1)
-                    acc += __ldg(p.W_out + static_cast<int64_t>(32 * w + __ffs(bits) - 1) * p.n_out + o);
-            const float y = p.a_o * s_y[o] + p.dt * (acc + p.b_out[o]);
-            s_y[o] = y;
-            s_m[o] += y;
+            for (int o = warp; o < p.n_out; o += kSnnThreads / 32) {
+                float acc = 0.f;
+                for (int w = lane; w < p.zw; w += 32)
+                    for (uint32_t bits = zt[w]; bits; bits &= bits - 1)
+                        acc += __ldg(p.W_out + static_cast<int64_t>(32 * w + __ffs(bits) - 1) * p.n_out + o);
+                acc = group_reduce_sum(acc, 32);
+                if (lane == 0) {
+                    const float y = p.a_o * s_y[o] + p.dt * (acc + p.b_out[o]);
+                    s_y[o] = y;
+                    s_m[o] += y;
+                }
+            }
         }
         __syncthreads();
     }
@@ -215,9 +237,7 @@ __global__ void __launch_bounds__(kSnnThreads, 1) k_snn_forward(SnnK p, const ui
 
 template <int WK>
 __global__ void __launch_bounds__(kSnnThreads, 1) k_snn_backward(SnnK p, const uint8_t* __restrict__ u,
-                                                                const float* __restrict__ g_m, float* __restrict__ dW_in,
-                                                                float* __restrict__ dw_rec, float* __restrict__ dW_out,
-                                                                float* __restrict__ db_out) {
+                                                                const float* __restrict__ g_m) {
     extern __shared__ __align__(16) float sh[];
     unsigned long long* racc = reinterpret_cast<unsigned long long*>(sh);
     float* I = reinterpret_cast<float*>(racc + p.n_rec);  // recompute state
@@ -231,6 +251,14 @@ __global__ void __launch_bounds__(kSnnThreads, 1) k_snn_backward(SnnK p, const u
     __shared__ float s_yb[kSnnMaxOut], s_gm[kSnnMaxOut];
     const int b = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // this batch element's gradient partials (summed over the batch afterwards
+    // in a fixed order, so every gradient is reproducible bit for bit)
+    float* gin = p.g_in + static_cast<int64_t>(b) * p.n_in * p.n_rec;
+    float* grec = p.g_rec + static_cast<int64_t>(b) * p.nnz;
+    float* gout = p.g_out + static_cast<int64_t>(b) * p.n_rec * p.n_out;
+    for (int64_t e = threadIdx.x; e < static_cast<int64_t>(p.n_in) * p.n_rec; e += kSnnThreads) gin[e] = 0.f;
+    for (int64_t e = threadIdx.x; e < p.nnz; e += kSnnThreads) grec[e] = 0.f;
+    for (int64_t e = threadIdx.x; e < static_cast<int64_t>(p.n_rec) * p.n_out; e += kSnnThreads) gout[e] = 0.f;
     for (int j = threadIdx.x; j < p.n_rec; j += kSnnThreads) Ib_next[j] = Vb[j] = 0.f;
     if (threadIdx.x < p.n_out) {
         s_yb[threadIdx.x] = 0.f;
@@ -286,14 +314,23 @@ __global__ void __launch_bounds__(kSnnThreads, 1) k_snn_backward(SnnK p, const u
             __syncthreads();
             const float* Vp = segVp + static_cast<int64_t>(t - t0) * p.n_rec;
             const uint32_t* zb = zall + static_cast<int64_t>(t) * p.zw;
-            // zbar_j: readout part per neuron, recurrent part by one warp per row
-            for (int j = warp; j < p.n_rec; j += kSnnThreads / 32) {
-                const int64_t r0 = p.indptr[j], r1 = p.indptr[j + 1];
-                float acc = 0.f;
-                for (int64_t e = r0 + lane; e < r1; e += 32) acc += w_at<WK>(p.w_rec, e) * Ib_next[p.indices[e]];
-                for (int oo = lane; oo < p.n_out; oo += 32) acc += p.dt * __ldg(p.W_out + static_cast<int64_t>(j) * p.n_out + oo) * s_yb[oo];
-                acc = group_reduce_sum(acc, 32);
-                if (lane == 0) Ib[j] = acc;  // zbar_j for now
+            // zbar_j: recurrent part W_rec Ibar_{t+1} plus the readout part; groups of
+            // 8 lanes per row, so a warp has four rows' loads in flight
+            {
+                constexpr int G = 8;
+                const int gl = lane & (G - 1);
+                for (int jb = 0; jb < p.n_rec; jb += kSnnThreads / G) {
+                    const int j = jb + threadIdx.x / G;
+                    float acc = 0.f;
+                    if (j < p.n_rec) {
+                        const int64_t r0 = p.indptr[j], r1 = p.indptr[j + 1];
+                        for (int64_t e = r0 + gl; e < r1; e += G) acc += w_at<WK>(p.w_rec, e) * Ib_next[p.indices[e]];
+                        for (int oo = gl; oo < p.n_out; oo += G)
+                            acc += p.dt * __ldg(p.W_out + static_cast<int64_t>(j) * p.n_out + oo) * s_yb[oo];
+                    }
+                    acc = group_reduce_sum(acc, G);
+                    if (j < p.n_rec && gl == 0) Ib[j] = acc;  // zbar_j for now
+                }
             }
             __syncthreads();
             for (int j = threadIdx.x; j < p.n_rec; j += kSnnThreads) {
@@ -305,32 +342,38 @@ __global__ void __launch_bounds__(kSnnThreads, 1) k_snn_backward(SnnK p, const u
                 const float ib = (1.f - p.a_m) * p.R * vpb + p.a_s * Ib_next[j];
                 Ib[j] = ib;
                 Vb[j] = p.a_m * vpb;
-                if (z) {
-                    for (int oo = 0; oo < p.n_out; ++oo)
-                        atomicAdd(dW_out + static_cast<int64_t>(j) * p.n_out + oo, p.dt * s_yb[oo]);
+                if (z) {  // dW_out[j, :] += dt ybar_t (row j belongs to this thread)
+                    float* row = gout + static_cast<int64_t>(j) * p.n_out;
+                    for (int oo = 0; oo < p.n_out; ++oo) row[oo] += p.dt * s_yb[oo];
                 }
             }
             __syncthreads();
-            // dW_in += u_t Ibar_t^T (inputs active at t)
+            // dW_in[k, :] += Ibar_t for the inputs active at t (column j belongs to thread j)
             const int n_act = gather_inputs(u + (static_cast<int64_t>(b) * p.T + t) * p.n_in, p.n_in, in_list, &s_cnt[0]);
-            for (int a = 0; a < n_act; ++a) {
-                float* row = dW_in + static_cast<int64_t>(in_list[a]) * p.n_rec;
-                if (p.vec_red) {
-                    for (int j4 = 4 * threadIdx.x; j4 < p.n_rec; j4 += 4 * kSnnThreads)
-                        red_add_v4(row + j4, make_float4(Ib[j4], Ib[j4 + 1], Ib[j4 + 2], Ib[j4 + 3]));
-                } else {
-                    for (int j = threadIdx.x; j < p.n_rec; j += kSnnThreads) atomicAdd(row + j, Ib[j]);
+            for (int j = threadIdx.x; j < p.n_rec; j += kSnnThreads) {
+                const float ib = Ib[j];
+                int a = 0;
+                for (; a + 4 <= n_act; a += 4) {  // four independent read-modify-writes in flight
+                    float* r0 = gin + static_cast<int64_t>(in_list[a]) * p.n_rec + j;
+                    float* r1 = gin + static_cast<int64_t>(in_list[a + 1]) * p.n_rec + j;
+                    float* r2 = gin + static_cast<int64_t>(in_list[a + 2]) * p.n_rec + j;
+                    float* r3 = gin + static_cast<int64_t>(in_list[a + 3]) * p.n_rec + j;
+                    const float v0 = *r0, v1 = *r1, v2 = *r2, v3 = *r3;
+                    *r0 = v0 + ib;
+                    *r1 = v1 + ib;
+                    *r2 = v2 + ib;
+                    *r3 = v3 + ib;
                 }
+                for (; a < n_act; ++a) gin[static_cast<int64_t>(in_list[a]) * p.n_rec + j] += ib;
             }
-            // dw_rec: rows spiking at t - 1
+            // dw_rec[e] += Ibar_t[col e] for the rows spiking at t - 1 (one warp per row)
             if (t > 0) {
                 const uint32_t* zp = zall + static_cast<int64_t>(t - 1) * p.zw;
                 for (int w = warp; w < p.zw; w += kSnnThreads / 32) {
-                    uint32_t bits = zp[w];
-                    for (; bits; bits &= bits - 1) {
+                    for (uint32_t bits = zp[w]; bits; bits &= bits - 1) {
                         const int i = 32 * w + __ffs(bits) - 1;
                         const int64_t r0 = p.indptr[i], r1 = p.indptr[i + 1];
-                        for (int64_t e = r0 + lane; e < r1; e += 32) atomicAdd(dw_rec + e, Ib[p.indices[e]]);
+                        for (int64_t e = r0 + lane; e < r1; e += 32) grec[e] += Ib[p.indices[e]];
                     }
                 }
             }
@@ -339,7 +382,17 @@ __global__ void __launch_bounds__(kSnnThreads, 1) k_snn_backward(SnnK p, const u
             __syncthreads();
         }
     }
-    if (threadIdx.x < p.n_out) atomicAdd(db_out + threadIdx.x, db_acc);
+    if (threadIdx.x < p.n_out) p.g_b[static_cast<int64_t>(b) * p.n_out + threadIdx.x] = db_acc;
+}
+
+// out[e] += sum over the batch of part[b][e], b in order (reproducible).
+__global__ void k_snn_reduce(const float* __restrict__ part, int32_t B, int64_t n, float* __restrict__ out) {
+    for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < n;
+         e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        float acc = 0.f;
+        for (int b = 0; b < B; ++b) acc += part[static_cast<int64_t>(b) * n + e];
+        out[e] += acc;
+    }
 }
 
 // Mean cross-entropy of softmax(m) over the batch and its gradient.
@@ -369,7 +422,7 @@ __global__ void k_snn_loss(int32_t B, int32_t n_out, const float* __restrict__ m
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct SnnLayout {
-    size_t ck_I, ck_V, ck_y, z_all, seg_Vp, total;
+    size_t ck_I, ck_V, ck_y, z_all, seg_Vp, g_in, g_rec, g_out, g_b, total;
     int32_t n_ck, zw;
 };
 
@@ -386,6 +439,10 @@ SnnLayout snn_layout(const bp_snn_desc& d) {
     L.ck_y = o; o = align256(o + B * L.n_ck * d.n_out * 4);
     L.z_all = o; o = align256(o + B * static_cast<size_t>(d.T) * L.zw * 4);
     L.seg_Vp = o; o = align256(o + B * static_cast<size_t>(K) * d.n_rec * 4);
+    L.g_in = o; o = align256(o + B * static_cast<size_t>(d.n_in) * d.n_rec * 4);
+    L.g_rec = o; o = align256(o + B * static_cast<size_t>(d.nnz > 0 ? d.nnz : 0) * 4);
+    L.g_out = o; o = align256(o + B * static_cast<size_t>(d.n_rec) * d.n_out * 4);
+    L.g_b = o; o = align256(o + B * static_cast<size_t>(d.n_out) * 4);
     L.total = o;
     return L;
 }
@@ -399,6 +456,7 @@ bp_status snn_check(const bp_snn_desc* d) {
     BP_REQUIRE(d->ckpt_every >= 0, "ckpt_every < 0");
     BP_REQUIRE(d->w_rec_kind == BP_W_F32 || d->w_rec_kind == BP_W_BF16, "recurrent weights must be F32 or BF16");
     BP_REQUIRE(d->W_in && d->indptr && d->indices && d->w_rec && d->W_out && d->b_out, "a parameter pointer is NULL");
+    BP_REQUIRE(d->nnz >= 0, "nnz < 0");
     BP_REQUIRE(d->tau_m > 0 && d->tau_s > 0 && d->tau_o > 0 && d->dt > 0, "time constants must be positive");
     return BP_OK;
 }
@@ -433,9 +491,13 @@ SnnK snn_kernel_args(const bp_snn_desc& d, void* ws) {
     p.ck_y = reinterpret_cast<float*>(w + L.ck_y);
     p.z_all = reinterpret_cast<uint32_t*>(w + L.z_all);
     p.seg_Vp = reinterpret_cast<float*>(w + L.seg_Vp);
+    p.g_in = reinterpret_cast<float*>(w + L.g_in);
+    p.g_rec = reinterpret_cast<float*>(w + L.g_rec);
+    p.g_out = reinterpret_cast<float*>(w + L.g_out);
+    p.g_b = reinterpret_cast<float*>(w + L.g_b);
+    p.nnz = d.nnz;
     p.n_ck = L.n_ck;
     p.zw = L.zw;
-    p.vec_red = 0;
     return p;
 }
 
@@ -508,19 +570,22 @@ bp_status bp_snn_backward(const bp_snn_desc* d, const uint8_t* u, const float* g
     BP_TRY(bp::snn_check(d));
     BP_REQUIRE(u && g_m && workspace && dW_in && dw_rec && dW_out && db_out, "a pointer is NULL");
     BP_REQUIRE((reinterpret_cast<uintptr_t>(workspace) & 255) == 0, "workspace must be 256-byte aligned");
-    bp::SnnK p = bp::snn_kernel_args(*d, workspace);
-    p.vec_red = (d->n_rec % 4 == 0 && (reinterpret_cast<uintptr_t>(dW_in) & 15) == 0) ? 1 : 0;
+    const bp::SnnK p = bp::snn_kernel_args(*d, workspace);
     // racc (8 B), I, V, Ibar_{t+1}, Ibar_t, Vbar, spike list (4 B each) per neuron, plus the input list
     const size_t smem = static_cast<size_t>(d->n_rec) * (8 + 4 * 6) + static_cast<size_t>(d->n_in) * 4;
     if (d->w_rec_kind == BP_W_BF16) {
         BP_TRY(bp::set_smem(bp::k_snn_backward<BP_W_BF16>, smem));
-        bp::k_snn_backward<BP_W_BF16><<<d->B, bp::kSnnThreads, smem, stream>>>(p, u, g_m, dW_in, dw_rec, dW_out,
-                                                                              db_out);
+        bp::k_snn_backward<BP_W_BF16><<<d->B, bp::kSnnThreads, smem, stream>>>(p, u, g_m);
     } else {
         BP_TRY(bp::set_smem(bp::k_snn_backward<BP_W_F32>, smem));
-        bp::k_snn_backward<BP_W_F32><<<d->B, bp::kSnnThreads, smem, stream>>>(p, u, g_m, dW_in, dw_rec, dW_out,
-                                                                             db_out);
+        bp::k_snn_backward<BP_W_F32><<<d->B, bp::kSnnThreads, smem, stream>>>(p, u, g_m);
     }
+    BP_LAUNCHED();
+    const int grid = bp::sm_count() * 8;
+    bp::k_snn_reduce<<<grid, 256, 0, stream>>>(p.g_in, d->B, static_cast<int64_t>(d->n_in) * d->n_rec, dW_in);
+    bp::k_snn_reduce<<<grid, 256, 0, stream>>>(p.g_rec, d->B, d->nnz, dw_rec);
+    bp::k_snn_reduce<<<grid, 256, 0, stream>>>(p.g_out, d->B, static_cast<int64_t>(d->n_rec) * d->n_out, dW_out);
+    bp::k_snn_reduce<<<1, 64, 0, stream>>>(p.g_b, d->B, d->n_out, db_out);
     BP_LAUNCHED();
     return BP_OK;
 }

@@ -26,6 +26,7 @@ def make_desc(B_, T, n_in, n_rec, n_out, W_in, indptr, indices, w_rec, W_out, b_
     d.w_rec_kind = B.BP_W_BF16 if w_rec.dtype == torch.bfloat16 else B.BP_W_F32
     d.W_out = W_out.data_ptr()
     d.b_out = b_out.data_ptr()
+    d.nnz = int(indices.numel())
     return d
 
 

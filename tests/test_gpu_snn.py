@@ -114,9 +114,11 @@ def test_checkpoint_interval_does_not_change_gradients():
     a = gpu_run(u, labels, w, torch.float32, 0)
     b = gpu_run(u, labels, w, torch.float32, 6)
     c = gpu_run(u, labels, w, torch.float32, 1)
+    # the forward is deterministic and the gradient partials are summed in a
+    # fixed order: recomputing from checkpoints changes nothing, bit for bit
     for x, y, z in zip(a[1:], b[1:], c[1:]):
-        assert rel(y, x) < 1e-6 and rel(z, x) < 1e-6
-    assert abs(a[0] - b[0]) < 1e-6 and abs(a[0] - c[0]) < 1e-6
+        assert np.array_equal(x, y) and np.array_equal(x, z)
+    assert a[0] == b[0] == c[0]
 
 
 def test_full_size_configuration_properties():
@@ -124,8 +126,7 @@ def test_full_size_configuration_properties():
     recurrent weights, 20 readouts, T = 1000, checkpoints every 100 steps: the
     loss equals the oracle's cross-entropy of the GPU readout, the forward is
     reproducible bit for bit, the gradients are finite and non-zero, and the
-    checkpointed and the single-segment backward agree (they differ only in
-    the order of the cross-batch gradient atomics)."""
+    checkpointed and the single-segment backward give identical gradients."""
     Bsz, T, n_in, n_rec, n_out = 128, 1000, 700, 1024, 20
     u = wl.poisson_inputs(Bsz, T, n_in, seed=5)
     w = wl.snn_weights(n_in, n_rec, n_out, 0.1, seed=6, rec_std=1.0 / math.sqrt(102.0))
@@ -157,4 +158,4 @@ def test_full_size_configuration_properties():
         assert all(np.abs(x).max() > 0 for x in grads[-1])
     assert np.array_equal(ms[0], ms[1])
     for x, y in zip(*grads):
-        assert rel(x, y) < 1e-5
+        assert np.array_equal(x, y)
