@@ -204,6 +204,16 @@ def time_simulate(torch, net, steps, warmup, dist=None):
     return ms, int(d[2]), int(d[0] + d[1])
 
 
+def aggregate_ranks(torch, dist, ms, events, device):
+    """Whole-job numbers of replicated runs: the slowest rank's time and the
+    events of all ranks (each rank simulates its own replica)."""
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ev = torch.tensor([float(events)], dtype=torch.float64, device=device)
+    dist.all_reduce(ev)
+    return float(t.item()), int(ev.item())
+
+
 def launches_in_simulate(steps, host_step_before):
     """Kernels bp_simulate enqueues: one fused step kernel per step, one
     chunk-advance per 64-step graph and per leftover group, two record set-ups."""
@@ -315,6 +325,36 @@ def bench_small_net(torch, steps=1000):
     t = bat.totals.cpu().numpy()[0]
     out["persistent_jit"] = {"ms_per_run": ms, "steps_per_s": steps / (ms * 1e-3), "events_per_s": t[2] / (ms * 1e-3)}
     bat.close()
+    return out
+
+
+def bench_fig_s7(torch, n=400_000, steps=500):
+    """Fig. S7 variants of the scaled network (JIT connectivity, N = 4e5):
+    1000 synapses per neuron, and a fixed connection probability 0.001 with the
+    weights rescaled by 80 / (p N) so that the mean input is unchanged."""
+    from paper_2311_05106_gb300 import binding as B
+    from paper_2311_05106_gb300 import workloads as wl
+    from paper_2311_05106_gb300.network import CobaNetwork
+    V0 = wl.coba_v0(n, seed=V0_SEED)
+    out = {}
+    stream = torch.cuda.current_stream()
+    for name, p in (("syn_1000_per_neuron", 1000.0 / n), ("p_0.001_rescaled", 0.001)):
+        scale = 80.0 / (p * n)
+        params = B.bp_coba_params_default(w_e=0.6 * scale, w_i=6.7 * scale)
+        net = CobaNetwork(n, conn="jit", seed=SEED, p=p, V0=V0, params=params)
+        net.simulate(50)
+        net.reset_counters()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        net.simulate(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        t = net.totals.cpu().numpy()
+        out[name] = {"neurons": n, "p": p, "synapses_per_neuron": p * n, "ms_per_step": ms / steps,
+                     "events_per_s": t[2] / (ms * 1e-3), "rate_hz": (t[0] + t[1]) / (n * steps * DT_MS * 1e-3)}
+        net.close()
     return out
 
 
@@ -623,12 +663,7 @@ def main():
     clk = clocks.stop()
     launches = launches_in_simulate(args.steps, host_before + args.warmup)
     if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        ev = torch.tensor([events], dtype=torch.float64, device="cuda")
-        dist.all_reduce(ev)
-        events = int(ev.item())
+        ms, events = aggregate_ranks(torch, dist, ms, events, "cuda")
     value = events / (ms * 1e-3)
     steps_per_s = args.steps / (ms * 1e-3)
 
@@ -681,6 +716,7 @@ def main():
             variants[k]["vs_plain_f32"] = variants[k]["events_per_s"] / value
         variants["coba_4k_1000_steps"] = bench_small_net(torch)
         variants["batched_256_nets"] = bench_batched(torch)
+        variants["fig_s7_jit_N4e5"] = bench_fig_s7(torch)
         variants["bptt_b128_t1000"] = bench_bptt(torch)
 
     cpu = None

@@ -462,6 +462,19 @@ size_t bp_snn_workspace_bytes(const bp_snn_desc* d);
  * [B][n_out] (mean readout).  Fills the workspace for bp_snn_backward. */
 bp_status bp_snn_forward(const bp_snn_desc* d, const uint8_t* u, float* m, void* workspace, bp_stream_t stream);
 
+/* Adjoint of one step of the LIF layer above, neuron by neuron (the update
+ * bp_snn_backward applies inside its time loop): with x = Vp - V_th and the
+ * surrogate slope s(slope x)(1 - s(slope x)),
+ *   Vpbar = Vbar (1 - z) + zbar surrogate(x)
+ *   Ibar = (1 - a_m) R Vpbar + a_s Ibar_next,   Vbar_prev = a_m Vpbar
+ * (reset detached).  Arrays [n]: Vp (potential before reset at step t), z
+ * (uint8 spike flags of step t), Vbar = dL/dV_t, zbar = dL/dz_t, Ibar_next =
+ * dL/dI_{t+1}; outputs Ibar = dL/dI_t, Vbar_prev = dL/dV_{t-1}.  Only the
+ * constants of `d` are used (dt, tau_m, tau_s, V_th, R, slope). */
+bp_status bp_lif_step_bwd(const bp_snn_desc* d, int64_t n, const float* Vp, const uint8_t* z, const float* Vbar,
+                          const float* zbar, const float* Ibar_next, float* Ibar, float* Vbar_prev,
+                          bp_stream_t stream);
+
 /* Mean over the batch of the cross-entropy of softmax(m_b) with label_b
  * (labels int64 [B]), written to loss[0], and its gradient g_m = dL/dm
  * [B][n_out]. */

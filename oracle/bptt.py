@@ -94,6 +94,24 @@ def loss_and_grad_m(m, labels):
     return L, g / B
 
 
+def lif_step_adjoint(Vp, z, Vbar, zbar, Ibar_next, params=None, smooth=False):
+    """Adjoint of one LIF step (reset detached unless smooth): from dL/dV_t,
+    dL/dz_t and dL/dI_{t+1}, returns (dL/dI_t, dL/dV_{t-1})."""
+    p = dict(SNN_DEFAULTS)
+    if params:
+        p.update(params)
+    a_s, a_m, _ = _consts(p)
+    k = p["slope"]
+    s = _sig(k * (Vp - p["V_th"]))
+    dz = k * s * (1.0 - s)
+    if smooth:
+        Vpbar = Vbar * (1.0 - z) + (zbar + Vbar * (p["V_reset"] - Vp)) * dz
+    else:
+        Vpbar = Vbar * (1.0 - z) + zbar * dz
+    Ibar = (1.0 - a_m) * p["R"] * Vpbar + a_s * Ibar_next
+    return Ibar, a_m * Vpbar
+
+
 def backward(fw, u, indptr, indices, W_out, g_m, smooth=False):
     """Hand-written adjoint, t = T..1.  Returns gradients of L with respect to
     W_in [n_in, n_rec], the stored recurrent weights w_rec [nnz], W_out and
@@ -111,20 +129,11 @@ def backward(fw, u, indptr, indices, W_out, g_m, smooth=False):
     ybar = np.zeros((B, W_out.shape[1]))
     Ibar_next = np.zeros((B, n_rec))
     Vbar = np.zeros((B, n_rec))
-    k = p["slope"]
     for t in range(T - 1, -1, -1):
         ybar = a_o * ybar + g_m / T
         zbar = p["dt"] * ybar @ W_out.T + Ibar_next @ W.T
-        x = Vp[:, t] - p["V_th"]
-        s = _sig(k * x)
-        dz = k * s * (1.0 - s)
-        if smooth:
-            # reset path included: V = Vp (1 - z) + V_reset z
-            Vpbar = Vbar * (1.0 - z[:, t]) + (zbar + Vbar * (p["V_reset"] - Vp[:, t])) * dz
-        else:
-            Vpbar = Vbar * (1.0 - z[:, t]) + zbar * dz
-        Ibar = (1.0 - a_m) * p["R"] * Vpbar + a_s * Ibar_next
-        Vbar = a_m * Vpbar
+        # smooth: the reset path V = Vp (1 - z) + V_reset z is included
+        Ibar, Vbar = lif_step_adjoint(Vp[:, t], z[:, t], Vbar, zbar, Ibar_next, p, smooth)
         dW_out += p["dt"] * z[:, t].T @ ybar
         db += p["dt"] * ybar.sum(axis=0)
         dW_in += u[:, t, :].astype(np.float64).T @ Ibar

@@ -112,6 +112,7 @@ _SIGS = {
     "bp_snn_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(SnnDesc)]),
     "bp_snn_forward": (c_i32, [ctypes.POINTER(SnnDesc), VP, VP, VP, VP]),
     "bp_snn_loss": (c_i32, [c_i32, c_i32, VP, VP, VP, VP, VP]),
+    "bp_lif_step_bwd": (c_i32, [ctypes.POINTER(SnnDesc), c_i64, VP, VP, VP, VP, VP, VP, VP, VP]),
     "bp_snn_backward": (c_i32, [ctypes.POINTER(SnnDesc), VP, VP, VP, VP, VP, VP, VP, VP]),
 }
 
@@ -420,3 +421,8 @@ def bp_snn_loss(m, labels, loss, g_m, stream=None):
 def bp_snn_backward(desc, u, g_m, workspace, dW_in, dw_rec, dW_out, db_out, stream=None):
     _check("bp_snn_backward", lib().bp_snn_backward(ctypes.byref(desc), _p(u), _p(g_m), _p(workspace), _p(dW_in),
                                                     _p(dw_rec), _p(dW_out), _p(db_out), _stream(stream)))
+
+
+def bp_lif_step_bwd(desc, Vp, z, Vbar, zbar, Ibar_next, Ibar, Vbar_prev, stream=None):
+    _check("bp_lif_step_bwd", lib().bp_lif_step_bwd(ctypes.byref(desc), Vp.numel(), _p(Vp), _p(z), _p(Vbar), _p(zbar),
+                                                    _p(Ibar_next), _p(Ibar), _p(Vbar_prev), _stream(stream)))

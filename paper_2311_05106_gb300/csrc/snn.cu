@@ -395,6 +395,24 @@ __global__ void k_snn_reduce(const float* __restrict__ part, int32_t B, int64_t 
     }
 }
 
+// Adjoint of one LIF step, elementwise (the update k_snn_backward applies per
+// neuron): Vpbar = Vbar (1 - z) + zbar s'(Vp - V_th), Ibar = (1 - a_m) R Vpbar
+// + a_s Ibar_next, Vbar_prev = a_m Vpbar.
+__global__ void k_lif_step_bwd(int64_t n, float a_m, float a_s, float R, float V_th, float slope,
+                               const float* __restrict__ Vp, const uint8_t* __restrict__ z,
+                               const float* __restrict__ Vbar, const float* __restrict__ zbar,
+                               const float* __restrict__ Ibar_next, float* __restrict__ Ibar,
+                               float* __restrict__ Vbar_prev) {
+    for (int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; j < n;
+         j += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const float x = Vp[j] - V_th;
+        const float s = 1.f / (1.f + expf(-slope * x));
+        const float vpb = Vbar[j] * (z[j] ? 0.f : 1.f) + zbar[j] * (slope * s * (1.f - s));
+        Ibar[j] = (1.f - a_m) * R * vpb + a_s * Ibar_next[j];
+        Vbar_prev[j] = a_m * vpb;
+    }
+}
+
 // Mean cross-entropy of softmax(m) over the batch and its gradient.
 __global__ void k_snn_loss(int32_t B, int32_t n_out, const float* __restrict__ m, const int64_t* __restrict__ labels,
                            float* __restrict__ loss, float* __restrict__ g_m) {
@@ -550,6 +568,25 @@ bp_status bp_snn_forward(const bp_snn_desc* d, const uint8_t* u, float* m, void*
         BP_TRY(bp::set_smem(bp::k_snn_forward<BP_W_F32>, smem));
         bp::k_snn_forward<BP_W_F32><<<d->B, bp::kSnnThreads, smem, stream>>>(p, u, m);
     }
+    BP_LAUNCHED();
+    return BP_OK;
+}
+
+bp_status bp_lif_step_bwd(const bp_snn_desc* d, int64_t n, const float* Vp, const uint8_t* z, const float* Vbar,
+                          const float* zbar, const float* Ibar_next, float* Ibar, float* Vbar_prev, bp_stream_t stream) {
+    bp::clear_error();
+    BP_REQUIRE(d != nullptr, "desc is NULL");
+    BP_REQUIRE(d->dt > 0 && d->tau_m > 0 && d->tau_s > 0, "time constants must be positive");
+    BP_REQUIRE(n >= 0, "n < 0");
+    BP_REQUIRE(n == 0 || (Vp && z && Vbar && zbar && Ibar_next && Ibar && Vbar_prev), "a pointer is NULL");
+    if (n == 0) return BP_OK;
+    const float a_m = static_cast<float>(std::exp(-d->dt / d->tau_m));
+    const float a_s = static_cast<float>(std::exp(-d->dt / d->tau_s));
+    int64_t grid = (n + 255) / 256;
+    if (grid > bp::sm_count() * 16) grid = bp::sm_count() * 16;
+    bp::k_lif_step_bwd<<<static_cast<unsigned>(grid), 256, 0, stream>>>(
+        n, a_m, a_s, static_cast<float>(d->R), static_cast<float>(d->V_th), static_cast<float>(d->slope), Vp, z, Vbar,
+        zbar, Ibar_next, Ibar, Vbar_prev);
     BP_LAUNCHED();
     return BP_OK;
 }

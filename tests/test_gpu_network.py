@@ -170,3 +170,26 @@ def test_full_size_scaled_network_short_horizon():
     gpu = CobaNetwork(n, conn="csr", seed=seed, p=p, V0=V0, keep_spk=True)
     compare_free_run(ref, gpu, 8)
     gpu.close()
+
+
+@pytest.mark.parametrize("conn", ["jit", "csr"])
+def test_long_rows_network_matches_oracle(conn):
+    """Fig. S7 regime: about 1000 synapses per neuron, weights rescaled by 80/1000
+    so that the mean input matches the 80-synapse network."""
+    n, seed, p = 20000, 77, 0.05
+    scale = 80.0 / (p * n)
+    params = B.bp_coba_params_default(w_e=0.6 * scale, w_i=6.7 * scale)
+    V0 = wl.coba_v0(n, seed=8)
+    K = orc.jit_K(p)
+    se, si = orc.projection_seed(seed, 0), orc.projection_seed(seed, 1)
+    if conn == "jit":
+        ref = orc.CobaNet(n, 16000, ("jit", se, si, K), V0.astype(np.float64), w_e=0.6 * scale, w_i=6.7 * scale)
+    else:
+        ipe, ixe, _ = orc.jit_materialize(se, K, 16000, n)
+        ipi, ixi, _ = orc.jit_materialize(si, K, 4000, n)
+        ref = orc.CobaNet(n, 16000, ("csr", np.concatenate([ipe, ipi[1:] + ipe[-1]]), np.concatenate([ixe, ixi]),
+                                     None), V0.astype(np.float64), w_e=0.6 * scale, w_i=6.7 * scale)
+    gpu = CobaNetwork(n, conn=conn, seed=seed, p=p, V0=V0, params=params, keep_spk=True)
+    same = compare_free_run(ref, gpu, 60)
+    assert same >= 5
+    gpu.close()

@@ -159,3 +159,20 @@ def test_full_size_configuration_properties():
     assert np.array_equal(ms[0], ms[1])
     for x, y in zip(*grads):
         assert np.array_equal(x, y)
+
+
+def test_lif_step_adjoint_matches_oracle():
+    rng = np.random.default_rng(3)
+    n = 100003
+    Vp = rng.uniform(-0.5, 2.0, n).astype(np.float32)
+    z = (Vp > 1.0).astype(np.uint8)
+    Vbar, zbar, Inext = (rng.normal(size=n).astype(np.float32) for _ in range(3))
+    Ib_ref, Vb_ref = bptt.lif_step_adjoint(Vp.astype(np.float64), z.astype(np.float64), Vbar.astype(np.float64),
+                                           zbar.astype(np.float64), Inext.astype(np.float64))
+    d = B.bp_snn_desc_default()
+    T_ = lambda x: torch.as_tensor(x).cuda()
+    Ib = torch.empty(n, dtype=torch.float32, device="cuda")
+    Vb = torch.empty(n, dtype=torch.float32, device="cuda")
+    B.bp_lif_step_bwd(d, T_(Vp), T_(z), T_(Vbar), T_(zbar), T_(Inext), Ib, Vb)
+    assert rel(Ib.cpu().numpy(), Ib_ref) < 1e-5
+    assert rel(Vb.cpu().numpy(), Vb_ref) < 1e-5
