@@ -10,7 +10,11 @@ Adjoint (hand-written):
 * equals torch autograd (FP64 CPU) of the same model with a custom surrogate
   spike function and a detached reset;
 * equals central finite differences of a fully smooth variant (logistic spikes,
-  differentiable reset), where the surrogate is the exact derivative.
+  differentiable reset), where the surrogate is the exact derivative;
+* with the ReLU surrogate and the voltage regulariser (Appendix I): equals
+  torch autograd of the same model with that surrogate and the penalty written
+  in torch; the regulariser's gradient equals finite differences of the smooth
+  variant; the surrogate and the penalty match their closed forms.
 """
 import math
 
@@ -98,13 +102,32 @@ def test_cross_entropy():
     np.testing.assert_allclose(g.sum(axis=1), 0.0, atol=1e-15)
 
 
-def test_adjoint_equals_torch_autograd():
-    torch = pytest.importorskip("torch")
-    u, labels, w = small_problem()
-    L, m, g, fw = bptt.loss_and_grads(u, labels, w["W_in"].astype(np.float64), w["indptr"], w["indices"],
-                                     w["w_rec"].astype(np.float64), w["W_out"].astype(np.float64),
-                                     w["b_out"].astype(np.float64))
-    assert fw["z"].mean() > 0.01        # the network spikes, so the surrogate paths are exercised
+def test_relu_surrogate_closed_form():
+    p = dict(bptt.SNN_DEFAULTS, surrogate="relu")
+    x = np.array([0.0, 0.5, -0.5, 0.25, 1.0, -1.0, 1.5, -7.0])
+    np.testing.assert_allclose(bptt.surrogate_grad(x, p), [0.3, 0.15, 0.15, 0.225, 0.0, 0.0, 0.0, 0.0], atol=1e-15)
+    # a triangle of height alpha * width and half-width width: area alpha * width^2
+    q = dict(p, sg_alpha=0.7, sg_width=2.0)
+    xs = np.linspace(-3, 3, 600001)
+    area = np.sum(bptt.surrogate_grad(xs, q)) * (xs[1] - xs[0])
+    assert abs(area - 0.7 * 4.0) < 1e-6
+    # the default remains the logistic surrogate: k/4 at x = 0
+    assert abs(bptt.surrogate_grad(np.array([0.0]), bptt.SNN_DEFAULTS)[0] - 1.0) < 1e-15
+
+
+def test_voltage_penalty_closed_form():
+    p = bptt.SNN_DEFAULTS
+    V = np.array([1.4, 0.4, 0.0, -2.0, -3.0, -1.0, 2.4])
+    np.testing.assert_allclose(bptt.voltage_penalty(V, p), [1.0, 0.0, 0.0, 0.0, 1.0, 0.0, 4.0], atol=1e-15)
+    h = 1e-6
+    Vs = np.array([1.3, -2.5, 0.1, 3.0])
+    fd = (bptt.voltage_penalty(Vs + h, p) - bptt.voltage_penalty(Vs - h, p)) / (2 * h)
+    np.testing.assert_allclose(bptt.voltage_penalty_grad(Vs, p), fd, rtol=1e-7, atol=1e-9)
+
+
+def torch_model_loss(torch, u, labels, w, surrogate, lambda_v):
+    """Loss and parameter leaves of the Appendix I model written in torch
+    (FP64), with its own spike function and penalty."""
     p = bptt.SNN_DEFAULTS
     a_s, a_m, a_o = (math.exp(-1 / p["tau_s"]), math.exp(-1 / p["tau_m"]), math.exp(-1 / p["tau_o"]))
     k = p["slope"]
@@ -118,6 +141,8 @@ def test_adjoint_equals_torch_autograd():
         @staticmethod
         def backward(ctx, go):
             (x,) = ctx.saved_tensors
+            if surrogate == "relu":
+                return go * torch.clamp(0.3 * (1.0 - x.abs()), min=0.0)
             s = torch.sigmoid(k * x)
             return go * k * s * (1 - s)
 
@@ -137,28 +162,46 @@ def test_adjoint_equals_torch_autograd():
     z = torch.zeros_like(I)
     y = torch.zeros((B, W_out.shape[1]), dtype=d)
     msum = torch.zeros_like(y)
+    pen = torch.zeros((), dtype=d)
     for t in range(T):
         I = a_s * I + z @ W + U[:, t] @ W_in
         Vp = a_m * V + (1 - a_m) * I
+        pen = pen + (torch.relu(Vp - 0.4) ** 2 + torch.relu(-Vp - 2.0) ** 2).sum()
         z = Spike.apply(Vp - 1.0)
         V = Vp + z.detach() * (0.0 - Vp)
         y = a_o * y + (z @ W_out + b_out)
         msum = msum + y
     mt = msum / T
-    loss = torch.nn.functional.cross_entropy(mt, torch.tensor(labels))
+    loss = torch.nn.functional.cross_entropy(mt, torch.tensor(labels)) + lambda_v / B * pen
+    return loss, (W_in, w_rec, W_out, b_out)
+
+
+@pytest.mark.parametrize("surrogate,lambda_v", [("sigmoid", 0.0), ("relu", 0.0), ("relu", 0.05), ("sigmoid", 0.02)])
+def test_adjoint_equals_torch_autograd(surrogate, lambda_v):
+    torch = pytest.importorskip("torch")
+    u, labels, w = small_problem()
+    params = dict(surrogate=surrogate, lambda_v=lambda_v)
+    L, m, g, fw = bptt.loss_and_grads(u, labels, w["W_in"].astype(np.float64), w["indptr"], w["indices"],
+                                     w["w_rec"].astype(np.float64), w["W_out"].astype(np.float64),
+                                     w["b_out"].astype(np.float64), params)
+    assert fw["z"].mean() > 0.01        # the network spikes, so the surrogate paths are exercised
+    if lambda_v:
+        assert fw["L_v"] > 1e-3 * L     # and the penalty is active
+    loss, leaves = torch_model_loss(torch, u, labels, w, surrogate, lambda_v)
     loss.backward()
     assert abs(loss.item() - L) < 1e-12
-    np.testing.assert_allclose(W_in.grad.numpy(), g["W_in"], rtol=1e-9, atol=1e-12)
-    np.testing.assert_allclose(w_rec.grad.numpy(), g["w_rec"], rtol=1e-9, atol=1e-12)
-    np.testing.assert_allclose(W_out.grad.numpy(), g["W_out"], rtol=1e-9, atol=1e-12)
-    np.testing.assert_allclose(b_out.grad.numpy(), g["b_out"], rtol=1e-9, atol=1e-12)
+    for leaf, name in zip(leaves, ("W_in", "w_rec", "W_out", "b_out")):
+        np.testing.assert_allclose(leaf.grad.numpy(), g[name], rtol=1e-9, atol=1e-12)
 
 
-def test_adjoint_finite_differences_smooth_variant():
+@pytest.mark.parametrize("lambda_v", [0.0, 0.05])
+def test_adjoint_finite_differences_smooth_variant(lambda_v):
     u, labels, w = small_problem(seed=4, T=20)
     args = [w["W_in"].astype(np.float64), w["indptr"], w["indices"], w["w_rec"].astype(np.float64),
-            w["W_out"].astype(np.float64), w["b_out"].astype(np.float64)]
+            w["W_out"].astype(np.float64), w["b_out"].astype(np.float64), dict(lambda_v=lambda_v)]
     L, m, g, fw = bptt.loss_and_grads(u, labels, *args, smooth=True)
+    if lambda_v:
+        assert fw["L_v"] > 1e-3 * L
     rng = np.random.default_rng(5)
     h = 1e-6
 
