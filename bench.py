@@ -409,7 +409,9 @@ def bench_bptt(torch, reps=3, T=1000):
     700 Poisson inputs (5-50 Hz), 1024 recurrent LIF with 10 % recurrent CSR
     weights N(0, 1/sqrt(102)), 20 leaky readouts, T = 1000, dt = 1 ms,
     checkpoints every 100 steps: forward + loss + backward per iteration, BF16
-    and FP32 recurrent weights."""
+    and FP32 recurrent weights, and BF16 with Appendix I's ReLU surrogate and
+    voltage regulariser (lambda_v = 1e-6: the untrained network's potentials sit far outside
+    the penalty's bounds, and a larger weight would only rescale the loss)."""
     import math
 
     import numpy as np
@@ -426,8 +428,10 @@ def bench_bptt(torch, reps=3, T=1000):
     W_in, W_out, b = (T_(w[k]).float() for k in ("W_in", "W_out", "b_out"))
     stream = torch.cuda.current_stream()
     out = {}
-    for name, wr in (("bf16", T_(w["w_rec"]).to(torch.bfloat16)), ("f32", T_(w["w_rec"]).float())):
-        d = make_desc(Bsz, T, n_in, n_rec, n_out, W_in, ip, ix, wr, W_out, b, 100)
+    w16 = T_(w["w_rec"]).to(torch.bfloat16)
+    for name, wr, extra in (("bf16", w16, {}), ("f32", T_(w["w_rec"]).float(), {}),
+                            ("bf16_relu_vreg", w16, dict(surrogate=B.BP_SG_RELU, lambda_v=1e-6))):
+        d = make_desc(Bsz, T, n_in, n_rec, n_out, W_in, ip, ix, wr, W_out, b, 100, **extra)
         ws = torch.empty(B.bp_snn_workspace_bytes(d), dtype=torch.uint8, device=dev)
         m = torch.empty((Bsz, n_out), dtype=torch.float32, device=dev)
         loss = torch.empty(1, dtype=torch.float32, device=dev)
@@ -438,6 +442,7 @@ def bench_bptt(torch, reps=3, T=1000):
         def it():
             B.bp_snn_forward(d, u, m, ws)
             B.bp_snn_loss(m, labels, loss, gm)
+            B.bp_snn_reg_loss(d, ws, loss)
             B.bp_snn_backward(d, u, gm, ws, *gs)
         it()
         torch.cuda.synchronize()
@@ -447,6 +452,7 @@ def bench_bptt(torch, reps=3, T=1000):
             e0.record(stream)
             B.bp_snn_forward(d, u, m, ws)
             B.bp_snn_loss(m, labels, loss, gm)
+            B.bp_snn_reg_loss(d, ws, loss)
             e1.record(stream)
             B.bp_snn_backward(d, u, gm, ws, *gs)
             e2.record(stream)

@@ -424,8 +424,15 @@ bp_status bp_batch_destroy(bp_batch* b);
  *   Vp_t = a_m V_{t-1} + (1 - a_m)(V_rest + R I_t)        (exponential Euler)
  *   z_t  = [Vp_t > V_th];  V_t = z_t ? V_reset : Vp_t      (reset detached)
  *   y_t  = a_o y_{t-1} + dt (W_out^T z_t + b_out);  m = mean_t y_t
- * Gradients use dz/dVp ~ slope s(slope x)(1 - s(slope x)), x = Vp - V_th,
- * s the logistic function.  W_rec is CSR with presynaptic rows (event-driven
+ * Gradients use the surrogate dz/dVp ~ slope s(slope x)(1 - s(slope x)),
+ * x = Vp - V_th, s the logistic function (BP_SG_SIGMOID), or the ReLU
+ * surrogate of Appendix I, max(0, sg_alpha (sg_width - |x|)) (BP_SG_RELU).
+ * With lambda_v > 0 the loss includes the voltage regulariser of Appendix I
+ * (training methods), on the potential before reset and averaged over the
+ * batch like the cross-entropy:
+ *   L_v = (lambda_v / B) sum_b sum_t sum_i [max(Vp - v_hi, 0)^2 + max(v_lo - Vp, 0)^2]
+ * (bp_snn_forward accumulates it, bp_snn_reg_loss adds it to the loss and
+ * bp_snn_backward includes its gradient).  W_rec is CSR with presynaptic rows (event-driven
  * delivery of z_{t-1}); its stored values are FP32 or BF16, all arithmetic is
  * FP32.  Checkpoints every ckpt_every steps; the backward pass recomputes
  * each segment from its checkpoint, replaying the spikes the forward
@@ -444,11 +451,18 @@ typedef struct {
     const float* W_out;                /* [n_rec][n_out] */
     const float* b_out;                /* [n_out] */
     int64_t nnz;                       /* number of stored recurrent weights (= indptr[n_rec]) */
+    int32_t surrogate;                 /* BP_SG_SIGMOID (uses slope) or BP_SG_RELU */
+    double sg_alpha, sg_width;         /* ReLU surrogate height factor and half-width (> 0) */
+    double lambda_v;                   /* voltage regulariser strength (>= 0; 0 = off) */
+    double v_hi, v_lo;                 /* regulariser bounds, v_lo < v_hi */
 } bp_snn_desc;
 
+enum { BP_SG_SIGMOID = 0, BP_SG_RELU = 1 };
+
 /* dt = 1 ms, tau_m = 20, tau_s = 100, tau_o = 20 ms, V_rest = V_reset = 0,
- * V_th = 1, R = 1, slope = 4, ckpt_every = 100, F32 recurrent weights; sizes
- * and pointers zero. */
+ * V_th = 1, R = 1, slope = 4, ckpt_every = 100, F32 recurrent weights,
+ * logistic surrogate (sg_alpha = 0.3, sg_width = 1 for the ReLU one),
+ * lambda_v = 0, v_hi = 0.4, v_lo = -2; sizes and pointers zero. */
 bp_status bp_snn_desc_default(bp_snn_desc* d);
 
 /* Device workspace (bytes, 256-byte aligned) shared by forward and backward:
@@ -464,13 +478,16 @@ bp_status bp_snn_forward(const bp_snn_desc* d, const uint8_t* u, float* m, void*
 
 /* Adjoint of one step of the LIF layer above, neuron by neuron (the update
  * bp_snn_backward applies inside its time loop): with x = Vp - V_th and the
- * surrogate slope s(slope x)(1 - s(slope x)),
+ * desc's surrogate,
  *   Vpbar = Vbar (1 - z) + zbar surrogate(x)
+ *           + (lambda_v / B) (2 max(Vp - v_hi, 0) - 2 max(v_lo - Vp, 0))
  *   Ibar = (1 - a_m) R Vpbar + a_s Ibar_next,   Vbar_prev = a_m Vpbar
- * (reset detached).  Arrays [n]: Vp (potential before reset at step t), z
- * (uint8 spike flags of step t), Vbar = dL/dV_t, zbar = dL/dz_t, Ibar_next =
- * dL/dI_{t+1}; outputs Ibar = dL/dI_t, Vbar_prev = dL/dV_{t-1}.  Only the
- * constants of `d` are used (dt, tau_m, tau_s, V_th, R, slope). */
+ * (reset detached; the regulariser term only when lambda_v > 0, B taken as 1
+ * when it is not positive).  Arrays [n]: Vp (potential before reset at step
+ * t), z (uint8 spike flags of step t), Vbar = dL/dV_t, zbar = dL/dz_t,
+ * Ibar_next = dL/dI_{t+1}; outputs Ibar = dL/dI_t, Vbar_prev = dL/dV_{t-1}.
+ * Only the constants of `d` are used (dt, tau_m, tau_s, V_th, R, the
+ * surrogate and regulariser fields, B). */
 bp_status bp_lif_step_bwd(const bp_snn_desc* d, int64_t n, const float* Vp, const uint8_t* z, const float* Vbar,
                           const float* zbar, const float* Ibar_next, float* Ibar, float* Vbar_prev,
                           bp_stream_t stream);
@@ -480,6 +497,12 @@ bp_status bp_lif_step_bwd(const bp_snn_desc* d, int64_t n, const float* Vp, cons
  * [B][n_out]. */
 bp_status bp_snn_loss(int32_t B, int32_t n_out, const float* m, const int64_t* labels, float* loss, float* g_m,
                       bp_stream_t stream);
+
+/* Adds the voltage regulariser L_v accumulated by the last bp_snn_forward
+ * with this desc and workspace to loss[0] (the per-batch sums are added in
+ * batch order in FP64, so the result is reproducible).  Does nothing when
+ * lambda_v = 0. */
+bp_status bp_snn_reg_loss(const bp_snn_desc* d, const void* workspace, float* loss, bp_stream_t stream);
 
 /* Backward pass (BPTT with checkpointed recomputation) for an upstream
  * gradient g_m = dL/dm [B][n_out], after bp_snn_forward with the same desc,

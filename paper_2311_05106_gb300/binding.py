@@ -66,7 +66,13 @@ class SnnDesc(ctypes.Structure):
                 ("V_rest", c_f64), ("V_reset", c_f64), ("V_th", c_f64), ("R", c_f64), ("slope", c_f64),
                 ("ckpt_every", c_i32),
                 ("W_in", VP), ("indptr", VP), ("indices", VP), ("w_rec", VP), ("w_rec_kind", c_i32),
-                ("W_out", VP), ("b_out", VP), ("nnz", c_i64)]
+                ("W_out", VP), ("b_out", VP), ("nnz", c_i64),
+                ("surrogate", c_i32), ("sg_alpha", c_f64), ("sg_width", c_f64),
+                ("lambda_v", c_f64), ("v_hi", c_f64), ("v_lo", c_f64)]
+
+
+BP_SG_SIGMOID = 0
+BP_SG_RELU = 1
 
 
 _SIGS = {
@@ -112,6 +118,7 @@ _SIGS = {
     "bp_snn_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(SnnDesc)]),
     "bp_snn_forward": (c_i32, [ctypes.POINTER(SnnDesc), VP, VP, VP, VP]),
     "bp_snn_loss": (c_i32, [c_i32, c_i32, VP, VP, VP, VP, VP]),
+    "bp_snn_reg_loss": (c_i32, [ctypes.POINTER(SnnDesc), VP, VP, VP]),
     "bp_lif_step_bwd": (c_i32, [ctypes.POINTER(SnnDesc), c_i64, VP, VP, VP, VP, VP, VP, VP, VP]),
     "bp_snn_backward": (c_i32, [ctypes.POINTER(SnnDesc), VP, VP, VP, VP, VP, VP, VP, VP]),
 }
@@ -416,6 +423,10 @@ def bp_snn_forward(desc, u, m, workspace, stream=None):
 def bp_snn_loss(m, labels, loss, g_m, stream=None):
     B, n_out = m.shape
     _check("bp_snn_loss", lib().bp_snn_loss(B, n_out, _p(m), _p(labels), _p(loss), _p(g_m), _stream(stream)))
+
+
+def bp_snn_reg_loss(desc, workspace, loss, stream=None):
+    _check("bp_snn_reg_loss", lib().bp_snn_reg_loss(ctypes.byref(desc), _p(workspace), _p(loss), _stream(stream)))
 
 
 def bp_snn_backward(desc, u, g_m, workspace, dW_in, dw_rec, dW_out, db_out, stream=None):

@@ -6,10 +6,14 @@
 //   Vp_t = a_m V_{t-1} + (1 - a_m)(V_rest + R I_t),  z_t = [Vp_t > V_th],
 //   V_t  = z_t ? V_reset : Vp_t (reset detached from the gradient),
 //   y_t  = a_o y_{t-1} + dt (W_out^T z_t + b),  m = mean_t y_t.
-// Adjoint (t = T..1), with surrogate dz/dVp = k s(kx)(1 - s(kx)):
+// Loss: cross-entropy of softmax(m) (mean over the batch) plus, when
+// lambda_v > 0, the voltage regulariser of Appendix I,
+//   L_v = (lambda_v / B) sum_{b,t,i} [max(Vp - v_hi, 0)^2 + max(v_lo - Vp, 0)^2].
+// Adjoint (t = T..1), with surrogate s'(x) = k s(kx)(1 - s(kx)) (logistic) or
+// max(0, alpha (width - |x|)) (ReLU, Appendix I):
 //   ybar_t = a_o ybar_{t+1} + g_m / T
 //   zbar_t = dt W_out ybar_t + W_rec Ibar_{t+1}          (gather over rows)
-//   Vpbar_t = Vbar_t (1 - z_t) + zbar_t s'(Vp_t - V_th)
+//   Vpbar_t = Vbar_t (1 - z_t) + zbar_t s'(Vp_t - V_th) + dL_v/dVp_t
 //   Ibar_t = (1 - a_m) R Vpbar_t + a_s Ibar_{t+1},  Vbar_{t-1} = a_m Vpbar_t
 //   dW_out += dt z_t ybar_t^T, db += dt ybar_t, dW_in += u_t Ibar_t^T,
 //   dw_rec[j] += Ibar_t[col j] for every entry j of rows spiking at t - 1.
@@ -40,9 +44,35 @@ constexpr int kSnnMaxRec = 4096;
 constexpr int kSnnMaxIn = 4096;
 constexpr int kSnnMaxOut = 64;
 
+// Surrogate derivative and voltage-regulariser constants.
+struct SgK {
+    int32_t kind;                        // BP_SG_SIGMOID or BP_SG_RELU
+    int32_t reg_on;                      // lambda_v > 0
+    float slope, alpha, width;
+    float reg_scale, v_hi, v_lo;         // reg_scale = lambda_v / B
+};
+
+__device__ __forceinline__ float surrogate(const SgK& g, float x) {
+    if (g.kind == BP_SG_RELU) return fmaxf(0.f, g.alpha * (g.width - fabsf(x)));
+    const float s = 1.f / (1.f + expf(-g.slope * x));
+    return g.slope * s * (1.f - s);
+}
+
+__device__ __forceinline__ float penalty(const SgK& g, float vp) {
+    const float a = fmaxf(vp - g.v_hi, 0.f), b = fmaxf(g.v_lo - vp, 0.f);
+    return a * a + b * b;
+}
+
+// dL_v/dVp of one element (zero when the regulariser is off).
+__device__ __forceinline__ float penalty_grad(const SgK& g, float vp) {
+    if (!g.reg_on) return 0.f;
+    return g.reg_scale * (2.f * fmaxf(vp - g.v_hi, 0.f) - 2.f * fmaxf(g.v_lo - vp, 0.f));
+}
+
 struct SnnK {
     int32_t B, T, n_in, n_rec, n_out, K;
-    float a_s, a_m, a_o, dt, V_rest, V_reset, V_th, R, slope;
+    float a_s, a_m, a_o, dt, V_rest, V_reset, V_th, R;
+    SgK sg;
     const float* W_in;
     const int64_t* indptr;
     const int32_t* indices;
@@ -59,6 +89,7 @@ struct SnnK {
     float* g_rec;        // [B][nnz]
     float* g_out;        // [B][n_rec][n_out]
     float* g_b;          // [B][n_out]
+    double* vreg;        // [B]  regulariser sums of the forward
     int64_t nnz;
     int32_t n_ck, zw;
 };
@@ -124,11 +155,12 @@ __device__ __forceinline__ int gather_inputs(const uint8_t* __restrict__ ut, int
 // when force_z is given, taken from those recorded bits (the backward pass
 // replays the forward's spikes so that its recomputation cannot take another
 // branch).  The step's spikes are appended to spk; zbits (nullable) receives
-// their bits; Vp_out (nullable) the potentials before reset.
+// their bits; Vp_out (nullable) the potentials before reset; reg (nullable)
+// accumulates this thread's regulariser terms.
 __device__ __forceinline__ void neuron_step(const SnnK& p, float* I, float* V, unsigned long long* racc,
                                             const int32_t* in_list,
                                             int n_act, int32_t* spk, int32_t* n_spk, float* Vp_out,
-                                            uint32_t* zbits, const uint32_t* force_z) {
+                                            uint32_t* zbits, const uint32_t* force_z, double* reg) {
     for (int jb = 0; jb < p.n_rec; jb += kSnnThreads) {
         const int j = jb + threadIdx.x;
         bool z = false;
@@ -153,6 +185,7 @@ __device__ __forceinline__ void neuron_step(const SnnK& p, float* I, float* V, u
             z = force_z ? ((force_z[j >> 5] >> (j & 31)) & 1u) != 0 : vp > p.V_th;
             V[j] = z ? p.V_reset : vp;
             if (Vp_out) Vp_out[j] = vp;
+            if (reg) *reg += static_cast<double>(penalty(p.sg, vp));
         }
         const unsigned m = __ballot_sync(FULL_MASK, z);
         if ((threadIdx.x & 31) == 0) {
@@ -194,6 +227,7 @@ __global__ void __launch_bounds__(kSnnThreads, 1) k_snn_forward(SnnK p, const ui
         racc[j] = 0ull;
     }
     if (threadIdx.x < p.n_out) s_y[threadIdx.x] = s_m[threadIdx.x] = 0.f;
+    double reg = 0.0;
     __syncthreads();
     for (int t = 0; t < p.T; ++t) {
         if (t % p.K == 0) {  // checkpoint of the state before step t
@@ -208,7 +242,7 @@ __global__ void __launch_bounds__(kSnnThreads, 1) k_snn_forward(SnnK p, const ui
         if (threadIdx.x == 0) s_cnt[1] = 0;
         __syncthreads();
         neuron_step(p, I, V, racc, in_list, n_act, spk, &s_cnt[1], nullptr,
-                    p.z_all + (static_cast<int64_t>(b) * p.T + t) * p.zw, nullptr);
+                    p.z_all + (static_cast<int64_t>(b) * p.T + t) * p.zw, nullptr, p.sg.reg_on ? &reg : nullptr);
         __syncthreads();
         const int n = s_cnt[1];
         deliver<WK>(p, spk, n, racc);
@@ -233,6 +267,17 @@ __global__ void __launch_bounds__(kSnnThreads, 1) k_snn_forward(SnnK p, const ui
         __syncthreads();
     }
     if (threadIdx.x < p.n_out) m_out[static_cast<int64_t>(b) * p.n_out + threadIdx.x] = s_m[threadIdx.x] / p.T;
+    if (p.sg.reg_on) {  // fixed reduction order: lanes by a tree, warps in index order
+        __shared__ double s_reg[kSnnThreads / 32];
+        reg = group_reduce_sum(reg, 32);
+        if ((threadIdx.x & 31) == 0) s_reg[threadIdx.x >> 5] = reg;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double acc = 0.0;
+            for (int w = 0; w < kSnnThreads / 32; ++w) acc += s_reg[w];
+            p.vreg[b] = acc;
+        }
+    }
 }
 
 template <int WK>
@@ -299,7 +344,7 @@ __global__ void __launch_bounds__(kSnnThreads, 1) k_snn_backward(SnnK p, const u
             if (threadIdx.x == 0) s_cnt[1] = 0;
             __syncthreads();
             neuron_step(p, I, V, racc, in_list, n_act, spk, &s_cnt[1], segVp + static_cast<int64_t>(t - t0) * p.n_rec,
-                        nullptr, zall + static_cast<int64_t>(t) * p.zw);
+                        nullptr, zall + static_cast<int64_t>(t) * p.zw, nullptr);
             __syncthreads();
             deliver<WK>(p, spk, s_cnt[1], racc);
             __syncthreads();
@@ -336,9 +381,8 @@ __global__ void __launch_bounds__(kSnnThreads, 1) k_snn_backward(SnnK p, const u
             for (int j = threadIdx.x; j < p.n_rec; j += kSnnThreads) {
                 const float zbar = Ib[j];
                 const bool z = (zb[j >> 5] >> (j & 31)) & 1u;
-                const float x = Vp[j] - p.V_th;
-                const float s = 1.f / (1.f + expf(-p.slope * x));
-                const float vpb = Vb[j] * (z ? 0.f : 1.f) + zbar * (p.slope * s * (1.f - s));
+                const float vpb = Vb[j] * (z ? 0.f : 1.f) + zbar * surrogate(p.sg, Vp[j] - p.V_th) +
+                                  penalty_grad(p.sg, Vp[j]);
                 const float ib = (1.f - p.a_m) * p.R * vpb + p.a_s * Ib_next[j];
                 Ib[j] = ib;
                 Vb[j] = p.a_m * vpb;
@@ -396,18 +440,16 @@ __global__ void k_snn_reduce(const float* __restrict__ part, int32_t B, int64_t 
 }
 
 // Adjoint of one LIF step, elementwise (the update k_snn_backward applies per
-// neuron): Vpbar = Vbar (1 - z) + zbar s'(Vp - V_th), Ibar = (1 - a_m) R Vpbar
-// + a_s Ibar_next, Vbar_prev = a_m Vpbar.
-__global__ void k_lif_step_bwd(int64_t n, float a_m, float a_s, float R, float V_th, float slope,
+// neuron): Vpbar = Vbar (1 - z) + zbar s'(Vp - V_th) + dL_v/dVp, Ibar =
+// (1 - a_m) R Vpbar + a_s Ibar_next, Vbar_prev = a_m Vpbar.
+__global__ void k_lif_step_bwd(int64_t n, float a_m, float a_s, float R, float V_th, SgK sg,
                                const float* __restrict__ Vp, const uint8_t* __restrict__ z,
                                const float* __restrict__ Vbar, const float* __restrict__ zbar,
                                const float* __restrict__ Ibar_next, float* __restrict__ Ibar,
                                float* __restrict__ Vbar_prev) {
     for (int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; j < n;
          j += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const float x = Vp[j] - V_th;
-        const float s = 1.f / (1.f + expf(-slope * x));
-        const float vpb = Vbar[j] * (z[j] ? 0.f : 1.f) + zbar[j] * (slope * s * (1.f - s));
+        const float vpb = Vbar[j] * (z[j] ? 0.f : 1.f) + zbar[j] * surrogate(sg, Vp[j] - V_th) + penalty_grad(sg, Vp[j]);
         Ibar[j] = (1.f - a_m) * R * vpb + a_s * Ibar_next[j];
         Vbar_prev[j] = a_m * vpb;
     }
@@ -437,10 +479,18 @@ __global__ void k_snn_loss(int32_t B, int32_t n_out, const float* __restrict__ m
     if (threadIdx.x == 0) *loss = static_cast<float>(s_sum / B);
 }
 
+// loss[0] += scale * sum_b vreg[b], in batch order, in FP64.
+__global__ void k_snn_reg_add(int32_t B, double scale, const double* __restrict__ vreg, float* __restrict__ loss) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double acc = 0.0;
+    for (int b = 0; b < B; ++b) acc += vreg[b];
+    loss[0] = static_cast<float>(static_cast<double>(loss[0]) + scale * acc);
+}
+
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct SnnLayout {
-    size_t ck_I, ck_V, ck_y, z_all, seg_Vp, g_in, g_rec, g_out, g_b, total;
+    size_t ck_I, ck_V, ck_y, z_all, seg_Vp, g_in, g_rec, g_out, g_b, vreg, total;
     int32_t n_ck, zw;
 };
 
@@ -461,8 +511,31 @@ SnnLayout snn_layout(const bp_snn_desc& d) {
     L.g_rec = o; o = align256(o + B * static_cast<size_t>(d.nnz > 0 ? d.nnz : 0) * 4);
     L.g_out = o; o = align256(o + B * static_cast<size_t>(d.n_rec) * d.n_out * 4);
     L.g_b = o; o = align256(o + B * static_cast<size_t>(d.n_out) * 4);
+    L.vreg = o; o = align256(o + B * 8);
     L.total = o;
     return L;
+}
+
+bp_status sg_check(const bp_snn_desc* d) {
+    BP_REQUIRE(d->surrogate == BP_SG_SIGMOID || d->surrogate == BP_SG_RELU, "unknown surrogate %d", d->surrogate);
+    BP_REQUIRE(d->surrogate != BP_SG_RELU || (d->sg_alpha >= 0 && d->sg_width > 0),
+               "ReLU surrogate needs sg_alpha >= 0 and sg_width > 0");
+    BP_REQUIRE(d->lambda_v >= 0, "lambda_v < 0");
+    BP_REQUIRE(d->lambda_v == 0 || d->v_lo < d->v_hi, "regulariser bounds need v_lo < v_hi");
+    return BP_OK;
+}
+
+SgK make_sg(const bp_snn_desc& d) {
+    SgK g;
+    g.kind = d.surrogate;
+    g.reg_on = d.lambda_v > 0 ? 1 : 0;
+    g.slope = static_cast<float>(d.slope);
+    g.alpha = static_cast<float>(d.sg_alpha);
+    g.width = static_cast<float>(d.sg_width);
+    g.reg_scale = static_cast<float>(d.lambda_v / (d.B > 0 ? d.B : 1));
+    g.v_hi = static_cast<float>(d.v_hi);
+    g.v_lo = static_cast<float>(d.v_lo);
+    return g;
 }
 
 bp_status snn_check(const bp_snn_desc* d) {
@@ -476,6 +549,7 @@ bp_status snn_check(const bp_snn_desc* d) {
     BP_REQUIRE(d->W_in && d->indptr && d->indices && d->w_rec && d->W_out && d->b_out, "a parameter pointer is NULL");
     BP_REQUIRE(d->nnz >= 0, "nnz < 0");
     BP_REQUIRE(d->tau_m > 0 && d->tau_s > 0 && d->tau_o > 0 && d->dt > 0, "time constants must be positive");
+    BP_TRY(sg_check(d));
     return BP_OK;
 }
 
@@ -496,7 +570,7 @@ SnnK snn_kernel_args(const bp_snn_desc& d, void* ws) {
     p.V_reset = static_cast<float>(d.V_reset);
     p.V_th = static_cast<float>(d.V_th);
     p.R = static_cast<float>(d.R);
-    p.slope = static_cast<float>(d.slope);
+    p.sg = make_sg(d);
     p.W_in = d.W_in;
     p.indptr = d.indptr;
     p.indices = d.indices;
@@ -513,6 +587,7 @@ SnnK snn_kernel_args(const bp_snn_desc& d, void* ws) {
     p.g_rec = reinterpret_cast<float*>(w + L.g_rec);
     p.g_out = reinterpret_cast<float*>(w + L.g_out);
     p.g_b = reinterpret_cast<float*>(w + L.g_b);
+    p.vreg = reinterpret_cast<double*>(w + L.vreg);
     p.nnz = d.nnz;
     p.n_ck = L.n_ck;
     p.zw = L.zw;
@@ -543,6 +618,12 @@ bp_status bp_snn_desc_default(bp_snn_desc* d) {
     d->V_th = 1.0;
     d->R = 1.0;
     d->slope = 4.0;
+    d->surrogate = BP_SG_SIGMOID;
+    d->sg_alpha = 0.3;
+    d->sg_width = 1.0;
+    d->lambda_v = 0.0;
+    d->v_hi = 0.4;
+    d->v_lo = -2.0;
     d->ckpt_every = 100;
     d->w_rec_kind = BP_W_F32;
     return BP_OK;
@@ -578,6 +659,7 @@ bp_status bp_lif_step_bwd(const bp_snn_desc* d, int64_t n, const float* Vp, cons
     BP_REQUIRE(d != nullptr, "desc is NULL");
     BP_REQUIRE(d->dt > 0 && d->tau_m > 0 && d->tau_s > 0, "time constants must be positive");
     BP_REQUIRE(n >= 0, "n < 0");
+    BP_TRY(bp::sg_check(d));
     BP_REQUIRE(n == 0 || (Vp && z && Vbar && zbar && Ibar_next && Ibar && Vbar_prev), "a pointer is NULL");
     if (n == 0) return BP_OK;
     const float a_m = static_cast<float>(std::exp(-d->dt / d->tau_m));
@@ -585,7 +667,7 @@ bp_status bp_lif_step_bwd(const bp_snn_desc* d, int64_t n, const float* Vp, cons
     int64_t grid = (n + 255) / 256;
     if (grid > bp::sm_count() * 16) grid = bp::sm_count() * 16;
     bp::k_lif_step_bwd<<<static_cast<unsigned>(grid), 256, 0, stream>>>(
-        n, a_m, a_s, static_cast<float>(d->R), static_cast<float>(d->V_th), static_cast<float>(d->slope), Vp, z, Vbar,
+        n, a_m, a_s, static_cast<float>(d->R), static_cast<float>(d->V_th), bp::make_sg(*d), Vp, z, Vbar,
         zbar, Ibar_next, Ibar, Vbar_prev);
     BP_LAUNCHED();
     return BP_OK;
@@ -597,6 +679,19 @@ bp_status bp_snn_loss(int32_t B, int32_t n_out, const float* m, const int64_t* l
     BP_REQUIRE(B > 0 && n_out > 0, "B and n_out must be positive");
     BP_REQUIRE(m && labels && loss && g_m, "a pointer is NULL");
     bp::k_snn_loss<<<1, 256, 0, stream>>>(B, n_out, m, labels, loss, g_m);
+    BP_LAUNCHED();
+    return BP_OK;
+}
+
+bp_status bp_snn_reg_loss(const bp_snn_desc* d, const void* workspace, float* loss, bp_stream_t stream) {
+    bp::clear_error();
+    BP_TRY(bp::snn_check(d));
+    BP_REQUIRE(workspace && loss, "workspace or loss is NULL");
+    BP_REQUIRE((reinterpret_cast<uintptr_t>(workspace) & 255) == 0, "workspace must be 256-byte aligned");
+    if (d->lambda_v == 0) return BP_OK;
+    const bp::SnnLayout L = bp::snn_layout(*d);
+    const double* vreg = reinterpret_cast<const double*>(static_cast<const char*>(workspace) + L.vreg);
+    bp::k_snn_reg_add<<<1, 32, 0, stream>>>(d->B, d->lambda_v / d->B, vreg, loss);
     BP_LAUNCHED();
     return BP_OK;
 }

@@ -45,6 +45,7 @@ class _BPTT(torch.autograd.Function):
         g_m = torch.empty_like(m)
         B.bp_snn_forward(d, u, m, ws)
         B.bp_snn_loss(m, labels, loss, g_m)
+        B.bp_snn_reg_loss(d, ws, loss)
         ctx.keep = (d, ws, u, g_m, w_k, W_in_c, W_out_c, b_c, indptr, indices)
         ctx.shapes = (W_in.shape, w_rec.shape, W_out.shape, b_out.shape)
         ctx.m = m
@@ -66,8 +67,11 @@ class _BPTT(torch.autograd.Function):
 
 def bptt_loss(W_in, w_rec, W_out, b_out, u, labels, indptr, indices, rec_dtype=torch.float32, ckpt_every=100,
               **overrides):
-    """Mean cross-entropy loss of the network on inputs u (uint8 [B, T, n_in]);
-    differentiable with respect to W_in, w_rec, W_out and b_out."""
+    """Mean cross-entropy loss of the network on inputs u (uint8 [B, T, n_in]),
+    plus the voltage regulariser when lambda_v > 0; differentiable with
+    respect to W_in, w_rec, W_out and b_out.  Overrides set bp_snn_desc
+    fields: e.g. surrogate=BP_SG_RELU, sg_alpha, sg_width, lambda_v, v_hi,
+    v_lo, slope."""
     return _BPTT.apply(W_in, w_rec, W_out, b_out, u, labels, indptr, indices, rec_dtype, ckpt_every, overrides)
 
 

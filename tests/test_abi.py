@@ -67,3 +67,35 @@ def test_host_only_helpers(libpath):
     for s in (0, 2024, 2**63 + 5):
         for j in (0, 1):
             assert B.bp_projection_seed(s, j) == orc.projection_seed(s, j)
+
+
+def test_snn_desc_defaults_and_host_checks(libpath):
+    """bp_snn_desc round-trips through the binding's struct layout (defaults of
+    the surrogate and regulariser fields read back), and invalid surrogate or
+    regulariser settings are rejected on the host before any device work."""
+    from paper_2311_05106_gb300 import binding as B
+    d = B.bp_snn_desc_default()
+    assert (d.dt, d.tau_m, d.tau_s, d.tau_o, d.V_th, d.slope, d.ckpt_every) == (1.0, 20.0, 100.0, 20.0, 1.0, 4.0, 100)
+    assert (d.surrogate, d.sg_alpha, d.sg_width, d.lambda_v, d.v_hi, d.v_lo) == (B.BP_SG_SIGMOID, 0.3, 1.0, 0.0, 0.4, -2.0)
+    d.B, d.T, d.n_in, d.n_rec, d.n_out, d.nnz = 2, 10, 8, 16, 3, 0
+    base = B.bp_snn_workspace_bytes(d)
+    assert base > 0 and base % 256 == 0
+    L = B.lib()
+    fake = ctypes.c_void_p(256)  # never dereferenced: the checks fail first
+    d.W_in = d.indptr = d.indices = d.w_rec = d.W_out = d.b_out = fake.value
+
+    def variant(**kw):
+        bad = B.SnnDesc.from_buffer_copy(d)
+        for k, v in kw.items():
+            setattr(bad, k, v)
+        return ctypes.byref(bad)
+
+    assert L.bp_snn_forward(variant(surrogate=7), fake, fake, fake, None) != 0
+    assert b"surrogate" in L.bp_last_error()
+    assert L.bp_snn_forward(variant(lambda_v=-1.0), fake, fake, fake, None) != 0
+    assert b"lambda_v" in L.bp_last_error()
+    assert L.bp_snn_reg_loss(variant(surrogate=B.BP_SG_RELU, sg_width=0.0), fake, fake, None) != 0
+    assert b"sg_width" in L.bp_last_error()
+    assert L.bp_lif_step_bwd(variant(lambda_v=0.1, v_lo=1.0, v_hi=0.5), 4, fake, fake, fake, fake, fake, fake, fake,
+                             None) != 0
+    assert b"v_lo" in L.bp_last_error()

@@ -37,15 +37,15 @@ def problem(seed, B_, T, n_in, n_rec, n_out, p_rec, in_scale=4.0, rate=8.0, rec_
     return u, labels, w
 
 
-def oracle_run(u, labels, w, rec_weights):
+def oracle_run(u, labels, w, rec_weights, params=None):
     L, m, g, fw = bptt.loss_and_grads(u, labels, w["W_in"].astype(np.float64), w["indptr"], w["indices"],
                                      rec_weights.astype(np.float64), w["W_out"].astype(np.float64),
-                                     w["b_out"].astype(np.float64))
+                                     w["b_out"].astype(np.float64), params)
     margin = float(np.min(np.abs(fw["Vp"] - 1.0)))
     return L, m, g, fw, margin
 
 
-def gpu_run(u, labels, w, rec_dtype, ckpt):
+def gpu_run(u, labels, w, rec_dtype, ckpt, **overrides):
     dev = "cuda"
     T_ = lambda x: torch.as_tensor(np.ascontiguousarray(x)).to(dev)
     W_in = T_(w["W_in"]).float().requires_grad_()
@@ -53,16 +53,16 @@ def gpu_run(u, labels, w, rec_dtype, ckpt):
     W_out = T_(w["W_out"]).float().requires_grad_()
     b_out = T_(w["b_out"]).float().requires_grad_()
     loss = bptt_loss(W_in, w_rec, W_out, b_out, T_(u), T_(labels).long(), T_(w["indptr"]).long(),
-                     T_(w["indices"]).int(), rec_dtype, ckpt)
+                     T_(w["indices"]).int(), rec_dtype, ckpt, **overrides)
     loss.backward()
     return (loss.item(), W_in.grad.cpu().numpy(), w_rec.grad.cpu().numpy(), W_out.grad.cpu().numpy(),
             b_out.grad.cpu().numpy())
 
 
-def find_case(B_, T, n_in, n_rec, n_out, p_rec, seeds=range(1, 40), **kw):
+def find_case(B_, T, n_in, n_rec, n_out, p_rec, seeds=range(1, 40), params=None, **kw):
     for s in seeds:
         u, labels, w = problem(s, B_, T, n_in, n_rec, n_out, p_rec, **kw)
-        res = oracle_run(u, labels, w, w["w_rec"])
+        res = oracle_run(u, labels, w, w["w_rec"], params)
         if res[4] > 1e-4 and res[3]["z"].mean() > 0.005:
             return u, labels, w, res
     pytest.fail("no case without near-threshold decisions")
@@ -77,6 +77,35 @@ def test_forward_loss_and_gradients_fp32(ckpt):
     assert rel(dwrec, g["w_rec"]) < 1e-3
     assert rel(dWout, g["W_out"]) < 1e-3
     assert rel(db, g["b_out"]) < 1e-3
+
+
+@pytest.mark.parametrize("ckpt", [0, 9])
+def test_relu_surrogate_and_voltage_regulariser(ckpt):
+    """Appendix I's ReLU surrogate (alpha 0.3, width 1) and voltage penalty
+    (lambda_v = 0.05, bounds 0.4 and -2, both branches active): loss and
+    gradients against the oracle."""
+    params = dict(surrogate="relu", lambda_v=0.05)
+    u, labels, w, (L, m, g, fw, margin) = find_case(3, 40, 24, 96, 6, 0.1, params=params)
+    assert fw["L_v"] > 1e-3 * L
+    assert (fw["Vp"] > 0.4).any() and (fw["Vp"] < -2.0).any()
+    Lg, dWin, dwrec, dWout, db = gpu_run(u, labels, w, torch.float32, ckpt, surrogate=B.BP_SG_RELU, lambda_v=0.05)
+    assert abs(Lg - L) <= 1e-5 * max(1.0, abs(L))
+    for got, key in ((dWin, "W_in"), (dwrec, "w_rec"), (dWout, "W_out"), (db, "b_out")):
+        assert rel(got, g[key]) < 1e-3, key
+
+
+def test_regulariser_alone_changes_only_what_it_should():
+    """With the logistic surrogate, turning the penalty on adds exactly the
+    oracle's L_v to the loss and leaves dW_out and db_out (which do not see the
+    potentials) unchanged."""
+    u, labels, w, (L0, m0, g0, fw0, _) = find_case(2, 30, 16, 64, 4, 0.15)
+    p = dict(lambda_v=0.02)
+    L1, m1, g1, fw1, _ = oracle_run(u, labels, w, w["w_rec"], p)
+    a = gpu_run(u, labels, w, torch.float32, 10)
+    b = gpu_run(u, labels, w, torch.float32, 10, lambda_v=0.02)
+    assert abs((b[0] - a[0]) - fw1["L_v"]) <= 1e-5 * max(1.0, abs(L1))
+    assert np.array_equal(a[3], b[3]) and np.array_equal(a[4], b[4])
+    assert rel(b[1], g1["W_in"]) < 1e-3 and rel(b[2], g1["w_rec"]) < 1e-3
 
 
 def test_readout_matches_oracle():
@@ -161,15 +190,21 @@ def test_full_size_configuration_properties():
         assert np.array_equal(x, y)
 
 
-def test_lif_step_adjoint_matches_oracle():
+@pytest.mark.parametrize("surrogate,lambda_v", [("sigmoid", 0.0), ("relu", 0.0), ("relu", 0.3)])
+def test_lif_step_adjoint_matches_oracle(surrogate, lambda_v):
     rng = np.random.default_rng(3)
     n = 100003
-    Vp = rng.uniform(-0.5, 2.0, n).astype(np.float32)
+    Vp = rng.uniform(-3.0, 2.5, n).astype(np.float32)
     z = (Vp > 1.0).astype(np.uint8)
     Vbar, zbar, Inext = (rng.normal(size=n).astype(np.float32) for _ in range(3))
+    Bsz = 4
     Ib_ref, Vb_ref = bptt.lif_step_adjoint(Vp.astype(np.float64), z.astype(np.float64), Vbar.astype(np.float64),
-                                           zbar.astype(np.float64), Inext.astype(np.float64))
+                                           zbar.astype(np.float64), Inext.astype(np.float64),
+                                           dict(surrogate=surrogate), vreg_scale=lambda_v / Bsz)
     d = B.bp_snn_desc_default()
+    d.B = Bsz
+    d.surrogate = B.BP_SG_RELU if surrogate == "relu" else B.BP_SG_SIGMOID
+    d.lambda_v = lambda_v
     T_ = lambda x: torch.as_tensor(x).cuda()
     Ib = torch.empty(n, dtype=torch.float32, device="cuda")
     Vb = torch.empty(n, dtype=torch.float32, device="cuda")
