@@ -239,9 +239,15 @@ class CobaNet:
 
     ``conn`` is either ("csr", indptr, indices, data_or_None) over all n rows, or
     ("jit", seed_e, seed_i, K).
+
+    ``delay_e`` / ``delay_i``: synaptic delay of the E / I projection in steps
+    (the delayed spike retrieval of Appendix D; 0 = the spikes of step t act at
+    step t + 1).  Each projection keeps d + 1 pending event buffers: step t
+    reads and clears buffer t mod (d + 1), then delivers its spikes into that
+    same buffer, which is read again d + 1 steps later.
     """
 
-    def __init__(self, n, n_e, conn, V0, **params):
+    def __init__(self, n, n_e, conn, V0, delay_e=0, delay_i=0, **params):
         p = dict(COBA_DEFAULTS)
         p.update(params)
         self.n, self.n_e = int(n), int(n_e)
@@ -257,12 +263,24 @@ class CobaNet:
         else:
             self.C = _Conn(kind=1, indptr=None, indices=None, data=None,
                            seed_e=conn[1] & (2**64 - 1), seed_i=conn[2] & (2**64 - 1), K=int(conn[3]))
+        if delay_e < 0 or delay_i < 0:
+            raise ValueError("delays must be >= 0")
         self.V = _c(V0, np.float64).copy()
         self.ge = np.zeros(self.n)
         self.gi = np.zeros(self.n)
         self.ref = np.zeros(self.n, np.int32)
-        self.ye = np.zeros(self.n)
-        self.yi = np.zeros(self.n)
+        self.ring_e = [np.zeros(self.n) for _ in range(int(delay_e) + 1)]
+        self.ring_i = [np.zeros(self.n) for _ in range(int(delay_i) + 1)]
+        self.t = 0
+
+    @property
+    def ye(self):
+        """The E event buffer the next step reads."""
+        return self.ring_e[self.t % len(self.ring_e)]
+
+    @property
+    def yi(self):
+        return self.ring_i[self.t % len(self.ring_i)]
 
     def step(self, return_vdec=False):
         """One step; returns the spike flags (and, if asked, the potential each
@@ -271,16 +289,47 @@ class CobaNet:
         vdec = np.zeros(self.n) if return_vdec else None
         _load().orc_coba_step(ctypes.byref(self.P), ctypes.byref(self.C), _p(self.V), _p(self.ge), _p(self.gi),
                               _p(self.ref), _p(self.ye), _p(self.yi), _p(spk), _p(vdec))
+        self.t += 1
         return (spk, vdec) if return_vdec else spk
 
     def run(self, T, raster=False, events=False):
+        if len(self.ring_e) > 1 or len(self.ring_i) > 1:
+            return self._run_steps(T, raster, events)
         se = np.zeros(T, np.int64)
         si = np.zeros(T, np.int64)
         ev = np.zeros(T, np.int64) if events else None
         ras = np.zeros((T, self.n), np.uint8) if raster else None
         _load().orc_coba_run(ctypes.byref(self.P), ctypes.byref(self.C), T, _p(self.V), _p(self.ge), _p(self.gi),
                              _p(self.ref), _p(self.ye), _p(self.yi), _p(se), _p(si), _p(ev), _p(ras))
+        self.t += T
         return dict(spikes_e=se, spikes_i=si, events=ev, raster=ras)
+
+    def _run_steps(self, T, raster, events):
+        se = np.zeros(T, np.int64)
+        si = np.zeros(T, np.int64)
+        ev = np.zeros(T, np.int64) if events else None
+        ras = np.zeros((T, self.n), np.uint8) if raster else None
+        lens = None
+        if events:
+            lens = row_lengths_of(self)
+        for t in range(T):
+            spk = self.step()
+            se[t] = int(spk[:self.n_e].sum())
+            si[t] = int(spk[self.n_e:].sum())
+            if events:
+                ev[t] = int(lens[spk.astype(bool)].sum())
+            if raster:
+                ras[t] = spk
+        return dict(spikes_e=se, spikes_i=si, events=ev, raster=ras)
+
+
+def row_lengths_of(net):
+    """Out-degree of every row of an oracle network's connectivity."""
+    if net.C.kind == 0:
+        return np.diff(net._keep[0])
+    K = net.C.K
+    return np.concatenate([jit_row_lengths(net.C.seed_e, K, net.n_e, net.n),
+                           jit_row_lengths(net.C.seed_i, K, net.n - net.n_e, net.n)])
 
 
 def rate_hz(total_spikes, n, T, dt_ms):

@@ -12,6 +12,11 @@ What pins what:
                                summed equal the merged per-neuron conductance
                                (Section 3.3: the merging is exact).
 * event delivery            -> events per step = sum of out-degrees of spiking rows.
+* synaptic delay            -> a single presynaptic spike at the closed-form step
+                               t_s = 138 reaches the target's conductance exactly
+                               at step t_s + 1 + d, with one weight, for each
+                               projection and delay (Appendix D: spikes are
+                               retrieved after the projection's delay).
 """
 import math
 
@@ -151,3 +156,32 @@ def test_stored_csr_equals_jit_network():
     a = orc.CobaNet(n, n_e, ("jit", se, si, K), V0).run(300, raster=True)
     b = orc.CobaNet(n, n_e, ("csr", ip, ix, None), V0).run(300, raster=True)
     assert np.array_equal(a["raster"], b["raster"])
+
+
+@pytest.mark.parametrize("d_e,d_i", [(0, 0), (3, 0), (0, 5), (7, 2)])
+def test_delay_shifts_arrival_closed_form(d_e, d_i):
+    """Neuron 0 (E) and neuron 2 (I) start at V_reset and spike first at the
+    closed-form step 138 (0-based: after 139 integrating steps); both project
+    onto neuron 1, which sits far below threshold.  Its g_e must stay 0 until
+    step 138 + 1 + d_e and then equal w_e = 0.6 (decaying afterwards); likewise
+    g_i with w_i = 6.7 and d_i."""
+    indptr = np.array([0, 1, 1, 2], np.int64)
+    indices = np.array([1, 1], np.int32)
+    V0 = np.array([-60.0, -1000.0, -60.0])
+    net = orc.CobaNet(3, 2, ("csr", indptr, indices, None), V0, delay_e=d_e, delay_i=d_i)
+    ge1, gi1 = [], []
+    t_spike = None
+    for t in range(138 + 12):
+        spk = net.step()
+        if spk[0]:
+            assert spk[2] and t_spike is None
+            t_spike = t
+        ge1.append(net.ge[1])
+        gi1.append(net.gi[1])
+    assert t_spike == 138
+    ge1, gi1 = np.array(ge1), np.array(gi1)
+    te, ti = t_spike + 1 + d_e, t_spike + 1 + d_i
+    assert np.all(ge1[:te] == 0.0) and ge1[te] == 0.6
+    assert np.all(gi1[:ti] == 0.0) and gi1[ti] == 6.7
+    # afterwards plain decay (no second spike within the window)
+    assert abs(ge1[te + 1] - 0.6 * math.exp(-0.1 / 5.0)) < 1e-15
