@@ -170,7 +170,7 @@ def step_traffic_record():
 LIF_BYTES_PER_NEURON = 36
 
 
-def build_network(torch, B, conn, weights, n=N_NEURONS):
+def build_network(torch, B, conn, weights, n=N_NEURONS, delay=0):
     import numpy as np
     from paper_2311_05106_gb300 import workloads as wl
     from paper_2311_05106_gb300.network import CobaNetwork, materialize_network_csr
@@ -180,7 +180,7 @@ def build_network(torch, B, conn, weights, n=N_NEURONS):
     csr = None
     if conn == "csr":
         csr = materialize_network_csr(SEED, p, n, n_e, data_dtype=torch.float32 if weights == "f32" else None)
-    net = CobaNetwork(n, n_e, conn=conn, seed=SEED, p=p, V0=V0, csr=csr)
+    net = CobaNetwork(n, n_e, conn=conn, seed=SEED, p=p, V0=V0, csr=csr, delay_e=delay, delay_i=delay)
     return net, np.asarray(V0)
 
 
@@ -707,8 +707,10 @@ def main():
     variants = {}
     headline = args.conn == "csr" and args.weights == "f32" and args.neurons == 4_000_000
     if not args.no_variants and headline:
-        for name, conn, w in (("csr_counts", "csr", None), ("jit_counts", "jit", None)):
-            v, _ = build_network(torch, B, conn, w)
+        # delay_1ms: both projections delayed by 10 steps (Appendix D)
+        for name, conn, w, dl in (("csr_counts", "csr", None, 0), ("jit_counts", "jit", None, 0),
+                                  ("csr_f32_delay_1ms", "csr", "f32", 10)):
+            v, _ = build_network(torch, B, conn, w, delay=dl)
             v.simulate(3)
             v.reset_counters()
             vms, vev, _ = time_simulate(torch, v, args.steps, args.warmup)

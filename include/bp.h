@@ -301,6 +301,15 @@ uint64_t bp_projection_seed(uint64_t net_seed, int32_t projection);
  * accumulators are double-buffered ([2n] each): step t reads and clears
  * elements [(t mod 2) n, (t mod 2 + 1) n) and delivers into the other half,
  * which lets one kernel do both.
+ * Synaptic delay (Appendix D: a projection retrieves the presynaptic spikes
+ * after its delay): with delay_e = d > 0 the E spikes of step t act at step
+ * t + 1 + d instead of t + 1 (likewise delay_i for the I spikes).  The spike
+ * ids of each step are kept in a ring of D + 2 lists, D = max(delay_e,
+ * delay_i), in the caller's delay_buf: int32 [(D + 2) (n + 1)], the D + 2
+ * counts followed by D + 2 lists of n ids.  Step t appends its spikes to
+ * list t mod (D + 2) and, over all CTAs, delivers the rows of the spikes of
+ * step t - d into the accumulator half that step t + 1 reads; a projection
+ * with delay 0 delivers its own spikes as above.
  * ------------------------------------------------------------------------ */
 enum { BP_CONN_CSR = 0, BP_CONN_JIT = 1 };
 
@@ -330,17 +339,21 @@ typedef struct {
     int32_t* n_spikes;              /* [2] with spike_list: the last step t's count is n_spikes[t mod 2] */
     int64_t* totals;                /* [4] cumulative: spikes E, spikes I, synaptic events, steps */
     uint8_t* spk;                   /* [n] nullable: spike flags of the last step */
+    int32_t delay_e, delay_i;       /* synaptic delays in steps, 0 .. 65535 (0 = next step) */
+    int32_t* delay_buf;             /* [(D + 2)(n + 1)] when a delay is > 0 (see above), else NULL */
 } bp_net_desc;
 
 typedef struct bp_net bp_net;
 
 /* Validates `desc`, copies it, derives the decay factors and JIT seeds.
- * Allocates only host memory (the CUDA graph of bp_simulate is built on its
- * first call).  *out receives the handle. */
+ * Allocates the handle and a 32-byte device control block (step counter,
+ * record target); the CUDA graph of bp_simulate is built on its first call.
+ * *out receives the handle. */
 bp_status bp_network_create(const bp_net_desc* desc, bp_net** out);
 
-/* Zeroes the counters (n_spikes, totals) and both halves of the event
- * accumulators, and restarts the step count at 0. */
+/* Zeroes the counters (n_spikes, totals), both halves of the event
+ * accumulators and the delay ring's counts, and restarts the step count at
+ * 0. */
 bp_status bp_network_reset_counters(bp_net* net, bp_stream_t stream);
 
 /* One time step (a1-a5/a6 above). */

@@ -52,7 +52,8 @@ class NetDesc(ctypes.Structure):
                 ("tile_ptr", VP), ("tile_cols", c_i32),
                 ("seed", c_u64), ("p", c_f64),
                 ("V", VP), ("ge", VP), ("gi", VP), ("ref", VP), ("ye", VP), ("yi", VP),
-                ("spike_list", VP), ("n_spikes", VP), ("totals", VP), ("spk", VP)]
+                ("spike_list", VP), ("n_spikes", VP), ("totals", VP), ("spk", VP),
+                ("delay_e", c_i32), ("delay_i", c_i32), ("delay_buf", VP)]
 
 
 class BatchDesc(ctypes.Structure):

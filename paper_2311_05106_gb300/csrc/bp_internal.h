@@ -76,6 +76,10 @@ struct NetStepLaunch {
     CsrArgs csr;
     int32_t group;         // lanes per CSR row in the delivery (4, 8, 16 or 32)
     JitArgs je, ji;
+    // delay ring (a projection with delay > 0): ring_slots = max delay + 2
+    // spike lists of n ids after ring_slots counts; 0 = no delayed projection
+    int32_t* ring;
+    int32_t ring_slots, delay_e, delay_i;
 };
 
 // ---- lif.cu

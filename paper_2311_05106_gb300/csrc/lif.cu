@@ -55,6 +55,9 @@ struct StepArgs {
     CsrArgs csr;
     int32_t group;  // lanes per CSR row in the delivery
     JitArgs je, ji;
+    // delay ring: ring_slots counts, then ring_slots lists of n spike ids
+    int32_t* ring;
+    int32_t ring_slots, delay_e, delay_i;
 };
 
 struct StepSmem {
@@ -62,10 +65,11 @@ struct StepSmem {
     int32_t warp_sum[kStepWarps];
     int32_t total;
     int32_t base;
+    int32_t ring_base;
     long long red[3][kStepWarps];
 };
 
-template <bool COUNTS, int VEC, int CONN, int WK>
+template <bool COUNTS, int VEC, int CONN, int WK, bool RING = false>
 __global__ void __launch_bounds__(kStepThreads, 4) k_step(StepArgs a) {
     __shared__ StepSmem sm;
     using Y = typename std::conditional<COUNTS, int32_t, float>::type;
@@ -73,7 +77,18 @@ __global__ void __launch_bounds__(kStepThreads, 4) k_step(StepArgs a) {
     const LifConst& c = a.c;
     Y* __restrict__ ye = static_cast<Y*>(a.ye_in);
     Y* __restrict__ yi = static_cast<Y*>(a.yi_in);
+    Y* out_e = static_cast<Y*>(a.ye_out);
+    Y* out_i = static_cast<Y*>(a.yi_out);
     if (a.clear_counter && blockIdx.x == 0 && threadIdx.x == 0) *a.clear_counter = 0;
+    // RING (a delayed projection): step t appends its spikes to list
+    // t mod S and delivers the lists of steps t - d; the count of list
+    // (t + 1) mod S, which no one reads or writes in this step, is cleared
+    // for the next step (S = max delay + 2).
+    int64_t tt = 0;
+    if constexpr (RING) {
+        tt = a.ctrl->step + a.t_local;
+        if (blockIdx.x == 0 && threadIdx.x == 0) a.ring[(tt + 1) % a.ring_slots] = 0;
+    }
 
     uint32_t mask = 0;
     int cnt_e = 0, cnt_i = 0;
@@ -188,31 +203,64 @@ __global__ void __launch_bounds__(kStepThreads, 4) k_step(StepArgs a) {
             if (base + k >= 0 && base + k < a.n) a.spike_list[base + k] = sm.ids[k];
     }
 
-    // ---- delivery of this CTA's spikes (network step)
+    // ---- delay ring: append this CTA's spikes to list t mod S (one atomic)
+    if constexpr (RING) {
+        if (total > 0) {
+            const int64_t ws = tt % a.ring_slots;
+            if (threadIdx.x == 0) sm.ring_base = atomicAdd(a.ring + ws, total);
+            __syncthreads();
+            const int64_t base = sm.ring_base;
+            int32_t* list = a.ring + a.ring_slots + ws * a.n;
+            for (int k = threadIdx.x; k < total; k += kStepThreads)
+                if (base + k >= 0 && base + k < a.n) list[base + k] = sm.ids[k];
+        }
+    }
+
+    // ---- delivery (network step): lanes in groups of G walk one row each
     int64_t ev = 0;
-    if constexpr (CONN == CONN_CSR) {
-        const CsrArgs& A = a.csr;
-        const int G = a.group;
+    if constexpr (CONN != CONN_NONE) {
+        const int G = CONN == CONN_CSR ? a.group : 32;  // JIT rows: whole warps
         const int gl = threadIdx.x % G;
         const int ng = kStepThreads / G;
-        Y* out_e = static_cast<Y*>(a.ye_out);
-        Y* out_i = static_cast<Y*>(a.yi_out);
+        // called by the G lanes of a group with the same row i
+        auto deliver = [&](int32_t i) {
+            if constexpr (CONN == CONN_CSR) {
+                const CsrArgs& A = a.csr;
+                const int64_t b0 = A.indptr[i], b1 = A.indptr[i + 1];
+                if (gl == 0) ev += b1 - b0;
+                scatter_segment<Y, WK, true>(A.indices, A.data, A.w_homo, b0, b1, gl, G, i < a.n_e ? out_e : out_i, 0);
+            } else {
+                const bool upper = i >= a.n_e;
+                const JitArgs& d = upper ? a.ji : a.je;
+                Y* out = upper ? out_i : out_e;
+                ev += jit_walk<BP_JIT_HOMO>(d, static_cast<uint32_t>(upper ? i - a.n_e : i), a.n,
+                                            [&](int64_t q, uint64_t, float w) { red_add_keep(out + q, event_value<Y>(w), keep); });
+            }
+        };
+        // this CTA's own spikes (every projection without delay)
         for (int k = threadIdx.x / G; k < total; k += ng) {
             const int32_t i = sm.ids[k];
-            const int64_t b0 = A.indptr[i], b1 = A.indptr[i + 1];
-            if (gl == 0) ev += b1 - b0;
-            scatter_segment<Y, WK, true>(A.indices, A.data, A.w_homo, b0, b1, gl, G, i < a.n_e ? out_e : out_i, 0);
+            if (RING && (i < a.n_e ? a.delay_e : a.delay_i) > 0) continue;
+            deliver(i);
         }
-    } else if constexpr (CONN == CONN_JIT) {
-        Y* out_e = static_cast<Y*>(a.ye_out);
-        Y* out_i = static_cast<Y*>(a.yi_out);
-        for (int k = warp; k < total; k += kStepWarps) {
-            const int32_t i = sm.ids[k];
-            const bool upper = i >= a.n_e;
-            const JitArgs& d = upper ? a.ji : a.je;
-            Y* out = upper ? out_i : out_e;
-            ev += jit_walk<BP_JIT_HOMO>(d, static_cast<uint32_t>(upper ? i - a.n_e : i), a.n,
-                                        [&](int64_t q, uint64_t, float w) { red_add_keep(out + q, event_value<Y>(w), keep); });
+        if constexpr (RING) {
+            // the spikes of step t - d of each delayed projection, rows spread
+            // over all CTAs (the lists were completed by earlier launches)
+            const bool same = a.delay_e == a.delay_i;
+            for (int proj = 0; proj < 2; ++proj) {
+                const int d = proj ? a.delay_i : a.delay_e;
+                if (d == 0 || (proj == 1 && same)) continue;
+                const int64_t rs = (tt + a.ring_slots - d) % a.ring_slots;
+                const int64_t c = min(static_cast<int64_t>(a.ring[rs]), a.n);
+                const int32_t* list = a.ring + a.ring_slots + rs * a.n;
+                for (int64_t k = static_cast<int64_t>(blockIdx.x) * ng + threadIdx.x / G; k < c;
+                     k += static_cast<int64_t>(gridDim.x) * ng) {
+                    const int32_t i = list[k];
+                    if (i < 0 || i >= a.n) continue;
+                    if (!same && ((i < a.n_e) != (proj == 0))) continue;
+                    deliver(i);
+                }
+            }
         }
     }
 
@@ -315,13 +363,19 @@ bp_status launch_k(K kernel, const StepArgs& a, int vec, cudaStream_t s) {
     return BP_OK;
 }
 
+template <bool COUNTS, int VEC, bool RING>
+bp_status launch_step_conn(const StepArgs& a, int conn, int wk, cudaStream_t s) {
+    if (conn == CONN_JIT) return launch_k(k_step<COUNTS, VEC, CONN_JIT, WK_HOMO, RING>, a, VEC, s);
+    if (wk == WK_F32) return launch_k(k_step<COUNTS, VEC, CONN_CSR, WK_F32, RING>, a, VEC, s);
+    if (wk == WK_BF16) return launch_k(k_step<COUNTS, VEC, CONN_CSR, WK_BF16, RING>, a, VEC, s);
+    return launch_k(k_step<COUNTS, VEC, CONN_CSR, WK_HOMO, RING>, a, VEC, s);
+}
+
 template <bool COUNTS, int VEC>
 bp_status launch_step_vec(const StepArgs& a, int conn, int wk, cudaStream_t s) {
     if (conn == CONN_NONE) return launch_k(k_step<COUNTS, VEC, CONN_NONE, WK_HOMO>, a, VEC, s);
-    if (conn == CONN_JIT) return launch_k(k_step<COUNTS, VEC, CONN_JIT, WK_HOMO>, a, VEC, s);
-    if (wk == WK_F32) return launch_k(k_step<COUNTS, VEC, CONN_CSR, WK_F32>, a, VEC, s);
-    if (wk == WK_BF16) return launch_k(k_step<COUNTS, VEC, CONN_CSR, WK_BF16>, a, VEC, s);
-    return launch_k(k_step<COUNTS, VEC, CONN_CSR, WK_HOMO>, a, VEC, s);
+    if (a.ring) return launch_step_conn<COUNTS, VEC, true>(a, conn, wk, s);
+    return launch_step_conn<COUNTS, VEC, false>(a, conn, wk, s);
 }
 
 bp_status launch_step(const StepArgs& a, bool counts, int conn, int wk, cudaStream_t s) {
@@ -376,6 +430,10 @@ bp_status launch_network_step(const NetStepLaunch& L, int parity, int32_t t_loca
     a.yi_in = yi + (parity ? half : 0);
     a.ye_out = ye + (parity ? 0 : half);
     a.yi_out = yi + (parity ? 0 : half);
+    a.ring = L.ring;
+    a.ring_slots = L.ring_slots;
+    a.delay_e = L.delay_e;
+    a.delay_i = L.delay_i;
     a.spk = L.spk;
     a.spike_list = L.spike_list;
     a.n_spikes = L.spike_list ? L.n_spikes + parity : nullptr;

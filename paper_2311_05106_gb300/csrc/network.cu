@@ -7,7 +7,10 @@
 // Section 3.3).  The accumulators are double-buffered: step t reads and
 // clears half t mod 2 and delivers into the other half, which step t + 1
 // reads (zero delay, Appendix N Listing S6), so delivery can run in the same
-// kernel as the neuron pass.  The optional spike-list counter alternates
+// kernel as the neuron pass.  A delayed projection (delay d > 0, Appendix D)
+// takes its spikes from a ring of per-step spike lists instead (the kernel
+// indexes it from the device step counter), so the accumulators keep their
+// two halves whatever the delay.  The optional spike-list counter alternates
 // between two slots the same way.  bp_simulate captures a chunk of steps once
 // in a CUDA graph and replays it; per-step indices that differ between
 // replays (the record row) are read from a small device control block.
@@ -114,6 +117,9 @@ bp_status bp_network_create(const bp_net_desc* desc, bp_net** out) {
     BP_REQUIRE(!d.spike_list || d.n_spikes, "spike_list needs n_spikes");
     BP_REQUIRE(d.conn_kind == BP_CONN_CSR || d.conn_kind == BP_CONN_JIT, "unknown connectivity kind %d",
                d.conn_kind);
+    BP_REQUIRE(d.delay_e >= 0 && d.delay_e <= 65535 && d.delay_i >= 0 && d.delay_i <= 65535,
+               "delays must be in [0, 65535] steps (got %d, %d)", d.delay_e, d.delay_i);
+    BP_REQUIRE((d.delay_e == 0 && d.delay_i == 0) || d.delay_buf, "a delayed projection needs delay_buf");
     bp::NetStepLaunch L{};
     L.c = bp::make_lif_const(d.coba);
     L.n = d.n;
@@ -129,6 +135,12 @@ bp_status bp_network_create(const bp_net_desc* desc, bp_net** out) {
     L.n_spikes = d.n_spikes;
     L.totals = d.totals;
     L.counts = true;
+    if (d.delay_e > 0 || d.delay_i > 0) {
+        L.ring = d.delay_buf;
+        L.ring_slots = (d.delay_e > d.delay_i ? d.delay_e : d.delay_i) + 2;
+        L.delay_e = d.delay_e;
+        L.delay_i = d.delay_i;
+    }
     if (d.conn_kind == BP_CONN_CSR) {
         BP_REQUIRE(d.indptr && d.indices, "CSR indptr or indices is NULL");
         BP_REQUIRE(d.wkind >= BP_W_HOMO && d.wkind <= BP_W_BF16, "unknown weight kind");
@@ -192,6 +204,7 @@ bp_status bp_network_reset_counters(bp_net* net, bp_stream_t stream) {
     BP_CUDA(cudaMemsetAsync(d.totals, 0, 4 * sizeof(int64_t), stream));
     BP_CUDA(cudaMemsetAsync(d.ye, 0, static_cast<size_t>(d.n) * 8, stream));
     BP_CUDA(cudaMemsetAsync(d.yi, 0, static_cast<size_t>(d.n) * 8, stream));
+    if (net->L.ring) BP_CUDA(cudaMemsetAsync(net->L.ring, 0, static_cast<size_t>(net->L.ring_slots) * 4, stream));
     bp::k_reset_ctrl<<<1, 1, 0, stream>>>(net->ctrl);
     BP_LAUNCHED();
     net->host_step = 0;

@@ -36,11 +36,12 @@ class CobaNetwork:
     conn="jit": connectivity regenerated every step from `seed` with
     probability p (default 80/n).  conn="csr": a stored CSR (indptr, indices,
     data) over all n presynaptic rows; data None means homogeneous weights
-    w_e / w_i with exact integer event counts.
+    w_e / w_i with exact integer event counts.  delay_e / delay_i: synaptic
+    delay of the E / I projection in steps (0: spikes act at the next step).
     """
 
     def __init__(self, n, n_e=None, conn="jit", seed=2024, p=None, V0=None, csr=None, tile_cols=0,
-                 params=None, keep_spk=False, keep_spikes=False, device="cuda"):
+                 params=None, keep_spk=False, keep_spikes=False, delay_e=0, delay_i=0, device="cuda"):
         self.n = int(n)
         self.n_e = int(n_e if n_e is not None else (4 * self.n) // 5)
         self.p = float(p if p is not None else 80.0 / self.n)
@@ -89,6 +90,14 @@ class CobaNetwork:
         # two halves: step t reads half t mod 2 and delivers into the other
         self.ye = torch.zeros(2 * self.n, dtype=ydt, device=device)
         self.yi = torch.zeros(2 * self.n, dtype=ydt, device=device)
+        # delayed projections: ring of max(delay) + 2 per-step spike lists
+        self.delay_e, self.delay_i = int(delay_e), int(delay_i)
+        self.delay_buf = None
+        if self.delay_e > 0 or self.delay_i > 0:
+            slots = max(self.delay_e, self.delay_i) + 2
+            self.delay_buf = torch.zeros(slots * (self.n + 1), dtype=i32, device=device)
+        desc.delay_e, desc.delay_i = self.delay_e, self.delay_i
+        desc.delay_buf = None if self.delay_buf is None else self.delay_buf.data_ptr()
         desc.V, desc.ge, desc.gi, desc.ref = (t.data_ptr() for t in (self.V, self.ge, self.gi, self.ref))
         desc.ye, desc.yi = self.ye.data_ptr(), self.yi.data_ptr()
         desc.spike_list = None if self.spike_list is None else self.spike_list.data_ptr()

@@ -22,16 +22,16 @@ from paper_2311_05106_gb300.network import CobaNetwork
 pytestmark = pytest.mark.gpu
 
 
-def oracle_net(n, n_e, seed, p, V0, conn="jit"):
+def oracle_net(n, n_e, seed, p, V0, conn="jit", **kw):
     K = orc.jit_K(p)
     se, si = orc.projection_seed(seed, 0), orc.projection_seed(seed, 1)
     if conn == "jit":
-        return orc.CobaNet(n, n_e, ("jit", se, si, K), V0)
+        return orc.CobaNet(n, n_e, ("jit", se, si, K), V0, **kw)
     ipe, ixe, _ = orc.jit_materialize(se, K, n_e, n)
     ipi, ixi, _ = orc.jit_materialize(si, K, n - n_e, n)
     ip = np.concatenate([ipe, ipi[1:] + ipe[-1]])
     ix = np.concatenate([ixe, ixi])
-    return orc.CobaNet(n, n_e, ("csr", ip, ix, None), V0)
+    return orc.CobaNet(n, n_e, ("csr", ip, ix, None), V0, **kw)
 
 
 def gpu_raster(net, T):
@@ -193,3 +193,66 @@ def test_long_rows_network_matches_oracle(conn):
     same = compare_free_run(ref, gpu, 60)
     assert same >= 5
     gpu.close()
+
+
+@pytest.mark.parametrize("conn,d_e,d_i", [("jit", 15, 7), ("csr", 0, 20), ("csr", 3, 3)])
+def test_delayed_network_free_run_matches_oracle(conn, d_e, d_i):
+    """Synaptic delays (Appendix D) of 0.3-2 ms on the 4 000-neuron network:
+    the raster equals the oracle's until an explained near-threshold flip."""
+    n, seed = 4000, 2024
+    n_e, p = 3200, 0.02
+    V0 = wl.coba_v0(n, seed=7)
+    ref = oracle_net(n, n_e, seed, p, V0.astype(np.float64), conn, delay_e=d_e, delay_i=d_i)
+    gpu = CobaNetwork(n, conn=conn, seed=seed, p=p, V0=V0, keep_spk=True, delay_e=d_e, delay_i=d_i)
+    same = compare_free_run(ref, gpu, 400)
+    assert same >= 40
+    gpu.close()
+
+
+@pytest.mark.parametrize("n", [3, 4])
+@pytest.mark.parametrize("d_e,d_i", [(0, 0), (3, 0), (7, 2)])
+def test_delay_arrival_step_closed_form(n, d_e, d_i):
+    """The closed-form case of the oracle's delay pin on the GPU (n = 3: scalar
+    path, n = 4: 16-byte path): neurons 0 (E) and 2 (I) first spike at step
+    138 and project onto neuron 1; its g_e / g_i stay 0 until step
+    139 + d_e / 139 + d_i and then equal w_e / w_i."""
+    indptr = torch.tensor([0, 1, 1, 2] + ([2] if n == 4 else []), dtype=torch.int64, device="cuda")
+    indices = torch.tensor([1, 1], dtype=torch.int32, device="cuda")
+    V0 = np.array([-60.0, -1000.0, -60.0, -1000.0][:n], np.float32)
+    net = CobaNetwork(n, n_e=2, conn="csr", csr=(indptr, indices, None), V0=V0, keep_spk=True,
+                      delay_e=d_e, delay_i=d_i)
+    ge1, gi1, t_spike = [], [], None
+    for t in range(150):
+        net.step()
+        spk = net.spk.cpu().numpy()
+        if spk[0] and t_spike is None:
+            t_spike = t
+        ge1.append(net.ge[1].item())
+        gi1.append(net.gi[1].item())
+    assert t_spike == 138
+    ge1, gi1 = np.array(ge1), np.array(gi1)
+    te, ti = 139 + d_e, 139 + d_i
+    assert np.all(ge1[:te] == 0.0) and ge1[te] == np.float32(0.6)
+    assert np.all(gi1[:ti] == 0.0) and gi1[ti] == np.float32(6.7)
+    net.close()
+
+
+@pytest.mark.parametrize("conn", ["jit", "csr"])
+def test_delayed_simulate_equals_single_steps(conn):
+    """bp_simulate (captured 64-step graphs, ring slots from the device step
+    counter; ring sizes 7 and 12 do not divide 64) equals stepping one launch
+    at a time, bit for bit (integer event counts)."""
+    n, seed, p, T = 6000, 5, 80.0 / 6000, 300
+    V0 = wl.coba_v0(n, seed=3)
+    a = CobaNetwork(n, conn=conn, seed=seed, p=p, V0=V0, delay_e=5, delay_i=10)
+    b = CobaNetwork(n, conn=conn, seed=seed, p=p, V0=V0, delay_e=5, delay_i=10)
+    a.step()            # odd start: the simulate call begins with one single step
+    a.simulate(T - 1)
+    for _ in range(T):
+        b.step()
+    torch.cuda.synchronize()
+    assert torch.equal(a.V, b.V) and torch.equal(a.ge, b.ge) and torch.equal(a.gi, b.gi)
+    assert torch.equal(a.totals, b.totals) and int(a.totals[0].item()) > 0
+    assert torch.equal(a.ye, b.ye) and torch.equal(a.yi, b.yi)
+    a.close()
+    b.close()
