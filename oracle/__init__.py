@@ -16,6 +16,7 @@ Parity status of each routine (what pins it) is listed in the test files
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 import threading
@@ -245,9 +246,18 @@ class CobaNet:
     step t + 1).  Each projection keeps d + 1 pending event buffers: step t
     reads and clears buffer t mod (d + 1), then delivers its spikes into that
     same buffer, which is read again d + 1 steps later.
+
+    ``align``: "post" (default) keeps one conductance per postsynaptic neuron
+    and adds the delivered events to it (AlignPost, Section 3.3, Appendix E);
+    "pre" keeps one synaptic trace per presynaptic neuron instead, s <- s a + z
+    with the projection's decay a and the previous step's spikes z, and
+    recomputes every step the conductance g = W^T s through the connection
+    matrix (AlignPre, Appendix D).  For exponential synapses the two are the
+    same dynamics (g_t = a g_{t-1} + W^T z_{t-1} follows from g = W^T s by
+    linearity).  "pre" needs no delay.
     """
 
-    def __init__(self, n, n_e, conn, V0, delay_e=0, delay_i=0, **params):
+    def __init__(self, n, n_e, conn, V0, delay_e=0, delay_i=0, align="post", **params):
         p = dict(COBA_DEFAULTS)
         p.update(params)
         self.n, self.n_e = int(n), int(n_e)
@@ -272,6 +282,27 @@ class CobaNet:
         self.ring_e = [np.zeros(self.n) for _ in range(int(delay_e) + 1)]
         self.ring_i = [np.zeros(self.n) for _ in range(int(delay_i) + 1)]
         self.t = 0
+        if align not in ("post", "pre"):
+            raise ValueError("align must be 'post' or 'pre'")
+        self.align = align
+        if align == "pre":
+            if delay_e or delay_i:
+                raise ValueError("the AlignPre form here has no delay")
+            if conn[0] == "csr":
+                ip, ix, w = self._keep
+            else:
+                ipe, ixe, _ = jit_materialize(self.C.seed_e, self.C.K, self.n_e, self.n)
+                ipi, ixi, _ = jit_materialize(self.C.seed_i, self.C.K, self.n - self.n_e, self.n)
+                ip = np.concatenate([ipe, ipi[1:] + ipe[-1]])
+                ix = np.concatenate([ixe, ixi])
+                w = None
+            self._pre_rows = np.repeat(np.arange(self.n), np.diff(ip))
+            self._pre_cols = ix.astype(np.int64)
+            self._pre_w = None if w is None else np.asarray(w, np.float64)
+            self.s = np.zeros(self.n)                  # one trace per presynaptic neuron
+            self._z = np.zeros(self.n)
+            self._a = np.where(np.arange(self.n) < self.n_e, math.exp(-p["dt"] / p["tau_e"]),
+                               math.exp(-p["dt"] / p["tau_i"]))
 
     @property
     def ye(self):
@@ -282,18 +313,35 @@ class CobaNet:
     def yi(self):
         return self.ring_i[self.t % len(self.ring_i)]
 
+    def _align_pre_input(self):
+        """Trace update and W^T s for this step; the step routine then sees
+        g = 0 plus the recomputed conductance as its increment."""
+        self.s = self.s * self._a + self._z
+        contrib = self.s[self._pre_rows]
+        if self._pre_w is not None:
+            contrib = contrib * self._pre_w
+        e_rows = self._pre_rows < self.n_e
+        self.ye[:] = np.bincount(self._pre_cols[e_rows], weights=contrib[e_rows], minlength=self.n)
+        self.yi[:] = np.bincount(self._pre_cols[~e_rows], weights=contrib[~e_rows], minlength=self.n)
+        self.ge[:] = 0.0
+        self.gi[:] = 0.0
+
     def step(self, return_vdec=False):
         """One step; returns the spike flags (and, if asked, the potential each
         threshold test saw, NaN for refractory neurons)."""
         spk = np.zeros(self.n, np.uint8)
         vdec = np.zeros(self.n) if return_vdec else None
+        if self.align == "pre":
+            self._align_pre_input()
         _load().orc_coba_step(ctypes.byref(self.P), ctypes.byref(self.C), _p(self.V), _p(self.ge), _p(self.gi),
                               _p(self.ref), _p(self.ye), _p(self.yi), _p(spk), _p(vdec))
         self.t += 1
+        if self.align == "pre":
+            self._z = spk.astype(np.float64)
         return (spk, vdec) if return_vdec else spk
 
     def run(self, T, raster=False, events=False):
-        if len(self.ring_e) > 1 or len(self.ring_i) > 1:
+        if len(self.ring_e) > 1 or len(self.ring_i) > 1 or self.align == "pre":
             return self._run_steps(T, raster, events)
         se = np.zeros(T, np.int64)
         si = np.zeros(T, np.int64)

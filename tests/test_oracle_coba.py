@@ -17,6 +17,10 @@ What pins what:
                                at step t_s + 1 + d, with one weight, for each
                                projection and delay (Appendix D: spikes are
                                retrieved after the projection's delay).
+* AlignPre                  -> equals AlignPost (Appendix D: the projections are
+                               exact, not approximations; for exponential synapses
+                               g = W^T s by linearity): identical rasters, equal
+                               conductances and potentials up to FP64 rounding.
 """
 import math
 
@@ -185,3 +189,33 @@ def test_delay_shifts_arrival_closed_form(d_e, d_i):
     assert np.all(gi1[:ti] == 0.0) and gi1[ti] == 6.7
     # afterwards plain decay (no second spike within the window)
     assert abs(ge1[te + 1] - 0.6 * math.exp(-0.1 / 5.0)) < 1e-15
+
+
+@pytest.mark.parametrize("form", ["csr_homo", "csr_weights", "jit"])
+def test_align_pre_equals_align_post(form):
+    n, n_e, seed, p = 2000, 1600, 77, 0.04
+    K = orc.jit_K(p)
+    se, si = orc.projection_seed(seed, 0), orc.projection_seed(seed, 1)
+    if form == "jit":
+        conn = ("jit", se, si, K)
+    else:
+        ipe, ixe, _ = orc.jit_materialize(se, K, n_e, n)
+        ipi, ixi, _ = orc.jit_materialize(si, K, n - n_e, n)
+        ip = np.concatenate([ipe, ipi[1:] + ipe[-1]])
+        ix = np.concatenate([ixe, ixi])
+        data = None
+        if form == "csr_weights":
+            data = np.where(np.arange(len(ix)) < len(ixe), 0.6, 6.7)
+        conn = ("csr", ip, ix, data)
+    V0 = wl.coba_v0(n, seed=9).astype(np.float64)
+    post = orc.CobaNet(n, n_e, conn, V0, align="post")
+    pre = orc.CobaNet(n, n_e, conn, V0, align="pre")
+    total = 0
+    for _ in range(300):
+        a, b = post.step(), pre.step()
+        assert np.array_equal(a, b)
+        total += int(a.sum())
+    assert total > 100
+    np.testing.assert_allclose(pre.ge, post.ge, rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(pre.gi, post.gi, rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(pre.V, post.V, rtol=0, atol=1e-9)
