@@ -64,6 +64,7 @@ def parse():
     ap.add_argument("--sweep-ops", default="csr,csr_t,jit")
     # the differentiable-network measurement alone (profiling)
     ap.add_argument("--bptt-only", action="store_true")
+    ap.add_argument("--align-pre-only", action="store_true")
     ap.add_argument("--bptt-T", type=int, default=1000)
     return ap.parse_args()
 
@@ -358,6 +359,34 @@ def bench_fig_s7(torch, n=400_000, steps=500):
     return out
 
 
+def bench_align_pre(torch, steps=100, warmup=5):
+    """The headline network (N = 4e6, stored CSR, FP32 weights) in the
+    AlignPre form of Appendix D: per-presynaptic traces and the full product
+    W^T s every step (about 3.2e8 synapses), against AlignPost which touches
+    only the rows of the step's spikes."""
+    from paper_2311_05106_gb300 import binding as B
+    from paper_2311_05106_gb300 import workloads as wl
+    from paper_2311_05106_gb300.network import CobaNetwork, materialize_network_csr
+    n = N_NEURONS
+    n_e = (4 * n) // 5
+    csr = materialize_network_csr(SEED, 80.0 / n, n, n_e, data_dtype=torch.float32)
+    nnz = int(csr[1].numel())
+    net = CobaNetwork(n, n_e, conn="csr", seed=SEED, p=80.0 / n, V0=wl.coba_v0(n, seed=V0_SEED), csr=csr,
+                      align="pre")
+    net.simulate(warmup)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    net.simulate(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    net.close()
+    return {"neurons": n, "synapses": nnz, "ms_per_step": ms, "synapse_updates_per_s": nnz / (ms * 1e-3),
+            "launches_per_step": 2}
+
+
 def bench_batched(torch, steps=2000, n_nets=256):
     """256 independent COBA E/I networks, N ~ U[1000, 50000] (seed 11), JIT
     connectivity p = 80/N, per-network seeds: the persistent batched kernel
@@ -642,6 +671,11 @@ def main():
         torch.cuda.set_device(0)
         print(json.dumps({"bptt": bench_bptt(torch, T=args.bptt_T)}))
         return 0
+    if args.align_pre_only:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps({"align_pre": bench_align_pre(torch)}))
+        return 0
     rank, world, local = dist_env()
     import torch
     dist = None
@@ -725,6 +759,9 @@ def main():
         variants["coba_4k_1000_steps"] = bench_small_net(torch)
         variants["batched_256_nets"] = bench_batched(torch)
         variants["fig_s7_jit_N4e5"] = bench_fig_s7(torch)
+        variants["align_pre_csr_f32"] = bench_align_pre(torch)
+        variants["align_pre_csr_f32"]["vs_align_post_step_time"] = \
+            variants["align_pre_csr_f32"]["ms_per_step"] / (ms / args.steps)
         variants["bptt_b128_t1000"] = bench_bptt(torch)
 
     cpu = None

@@ -310,6 +310,18 @@ uint64_t bp_projection_seed(uint64_t net_seed, int32_t projection);
  * list t mod (D + 2) and, over all CTAs, delivers the rows of the spikes of
  * step t - d into the accumulator half that step t + 1 reads; a projection
  * with delay 0 delivers its own spikes as above.
+ * AlignPre form (align = BP_ALIGN_PRE, Appendix D): instead of one merged
+ * conductance per postsynaptic neuron, one synaptic trace per presynaptic
+ * neuron, s_i <- s_i a + z_i (a = exp(-dt/tau_e) on E rows, exp(-dt/tau_i) on
+ * I rows, z the previous step's spike flags), and every step the
+ * conductances are recomputed through the connection matrix, g_e = W_E^T s
+ * (times w_e for homogeneous weights), g_i likewise.  For these exponential
+ * synapses it is the same dynamics as AlignPost at the cost of a full
+ * product per step; each step is two launches (trace + product, then the
+ * neurons).  It needs `trace` [n] (initially 0), `spk` (the flags are its
+ * input), float accumulators (ye, yi [2n] float whatever the weights) and no
+ * delay; totals[2] counts each step's synaptic events when the next step
+ * consumes them.
  * ------------------------------------------------------------------------ */
 enum { BP_CONN_CSR = 0, BP_CONN_JIT = 1 };
 
@@ -341,7 +353,11 @@ typedef struct {
     uint8_t* spk;                   /* [n] nullable: spike flags of the last step */
     int32_t delay_e, delay_i;       /* synaptic delays in steps, 0 .. 65535 (0 = next step) */
     int32_t* delay_buf;             /* [(D + 2)(n + 1)] when a delay is > 0 (see above), else NULL */
+    int32_t align;                  /* BP_ALIGN_POST (default) or BP_ALIGN_PRE */
+    float* trace;                   /* [n] presynaptic traces for BP_ALIGN_PRE, else NULL */
 } bp_net_desc;
+
+enum { BP_ALIGN_POST = 0, BP_ALIGN_PRE = 1 };
 
 typedef struct bp_net bp_net;
 

@@ -53,7 +53,12 @@ class NetDesc(ctypes.Structure):
                 ("seed", c_u64), ("p", c_f64),
                 ("V", VP), ("ge", VP), ("gi", VP), ("ref", VP), ("ye", VP), ("yi", VP),
                 ("spike_list", VP), ("n_spikes", VP), ("totals", VP), ("spk", VP),
-                ("delay_e", c_i32), ("delay_i", c_i32), ("delay_buf", VP)]
+                ("delay_e", c_i32), ("delay_i", c_i32), ("delay_buf", VP),
+                ("align", c_i32), ("trace", VP)]
+
+
+BP_ALIGN_POST = 0
+BP_ALIGN_PRE = 1
 
 
 class BatchDesc(ctypes.Structure):

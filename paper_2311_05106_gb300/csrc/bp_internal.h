@@ -80,6 +80,8 @@ struct NetStepLaunch {
     // spike lists of n ids after ring_slots counts; 0 = no delayed projection
     int32_t* ring;
     int32_t ring_slots, delay_e, delay_i;
+    // AlignPre form: presynaptic traces (NULL: AlignPost)
+    float* trace;
 };
 
 // ---- lif.cu

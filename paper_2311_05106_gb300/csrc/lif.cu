@@ -31,7 +31,9 @@ constexpr int kStepThreads = 256;
 constexpr int kStepWarps = kStepThreads / 32;
 constexpr int kMaskBits = 32;
 
-enum { CONN_NONE = 0, CONN_CSR = 1, CONN_JIT = 2 };
+// CONN_PRE: the neuron pass of the AlignPre form (the conductances are
+// recomputed each step, so they are not loaded; no delivery)
+enum { CONN_NONE = 0, CONN_CSR = 1, CONN_JIT = 2, CONN_PRE = 3 };
 
 struct StepArgs {
     LifConst c;
@@ -104,8 +106,11 @@ __global__ void __launch_bounds__(kStepThreads, 4) k_step(StepArgs a) {
             // the state streams through L2 (evict-first); the accumulators
             // are read with the keep policy since the next delivery targets them
             float4 v = __ldcs(reinterpret_cast<const float4*>(a.V + i0));
-            float4 g_e = __ldcs(reinterpret_cast<const float4*>(a.ge + i0));
-            float4 g_i = __ldcs(reinterpret_cast<const float4*>(a.gi + i0));
+            float4 g_e = make_float4(0.f, 0.f, 0.f, 0.f), g_i = g_e;
+            if constexpr (CONN != CONN_PRE) {
+                g_e = __ldcs(reinterpret_cast<const float4*>(a.ge + i0));
+                g_i = __ldcs(reinterpret_cast<const float4*>(a.gi + i0));
+            }
             int4 r = __ldcs(reinterpret_cast<const int4*>(a.ref + i0));
             const Y4 ce = ld_keep(reinterpret_cast<const Y4*>(ye + i0), keep);
             const Y4 ci = ld_keep(reinterpret_cast<const Y4*>(yi + i0), keep);
@@ -134,7 +139,9 @@ __global__ void __launch_bounds__(kStepThreads, 4) k_step(StepArgs a) {
             for (int k = 0; k < VEC; ++k) {
                 const int64_t i = i0 + k;
                 if (i >= a.n) break;
-                float v = a.V[i], g_e = a.ge[i], g_i = a.gi[i];
+                float v = a.V[i];
+                float g_e = CONN == CONN_PRE ? 0.f : a.ge[i];
+                float g_i = CONN == CONN_PRE ? 0.f : a.gi[i];
                 int32_t r = a.ref[i];
                 const int32_t r_old = r;
                 const Y ce = ye[i], ci = yi[i];
@@ -218,7 +225,7 @@ __global__ void __launch_bounds__(kStepThreads, 4) k_step(StepArgs a) {
 
     // ---- delivery (network step): lanes in groups of G walk one row each
     int64_t ev = 0;
-    if constexpr (CONN != CONN_NONE) {
+    if constexpr (CONN == CONN_CSR || CONN == CONN_JIT) {
         const int G = CONN == CONN_CSR ? a.group : 32;  // JIT rows: whole warps
         const int gl = threadIdx.x % G;
         const int ng = kStepThreads / G;
@@ -299,6 +306,75 @@ __global__ void __launch_bounds__(kStepThreads, 4) k_step(StepArgs a) {
     }
 }
 
+struct TraceArgs {
+    int64_t n, n_e;
+    float a_e, a_i, w_e, w_i;
+    float* trace;
+    const uint8_t* spk;
+    float* acc_e;
+    float* acc_i;
+    int64_t* totals;
+    CsrArgs csr;
+    int32_t group;
+    JitArgs je, ji;
+};
+
+// AlignPre (Appendix D): every presynaptic row i updates its trace,
+// s_i <- s_i a + z_i (z_i the previous step's spike flag), and, when s_i is
+// not zero, adds s_i w_ij to the conductance sum of each target j (stored
+// CSR rows walked by G lanes, or JIT rows regenerated by a warp).  Lane 0 of
+// a group owns the trace read-modify-write and broadcasts s_i.  totals[2] +=
+// the out-degree of the rows with z_i = 1.
+template <int CONN, int WK>
+__global__ void __launch_bounds__(kStepThreads) k_trace_scatter(TraceArgs a) {
+    const int G = CONN == CONN_CSR ? a.group : 32;
+    const int lane = threadIdx.x & 31;
+    const int gl = lane % G;
+    const unsigned gmask = G == 32 ? FULL_MASK : ((1u << G) - 1u) << (lane / G * G);
+    const int64_t ngroups = static_cast<int64_t>(gridDim.x) * (kStepThreads / G);
+    const int64_t g0 = (static_cast<int64_t>(blockIdx.x) * kStepThreads + threadIdx.x) / G;
+    const uint64_t keep = l2_keep_policy();
+    int64_t ev = 0;
+    for (int64_t i = g0; i < a.n; i += ngroups) {
+        const bool is_e = i < a.n_e;
+        float s = 0.f;
+        int z = 0;
+        if (gl == 0) {
+            z = a.spk[i] != 0;
+            s = a.trace[i] * (is_e ? a.a_e : a.a_i) + (z ? 1.f : 0.f);
+            a.trace[i] = s;
+        }
+        s = __shfl_sync(gmask, s, 0, G);
+        z = __shfl_sync(gmask, z, 0, G);
+        if (s == 0.f) continue;
+        float* out = is_e ? a.acc_e : a.acc_i;
+        const float wh = is_e ? a.w_e : a.w_i;
+        if constexpr (CONN == CONN_CSR) {
+            const int64_t b0 = a.csr.indptr[i], b1 = a.csr.indptr[i + 1];
+            if (z && gl == 0) ev += b1 - b0;
+            for (int64_t j = b0 + gl; j < b1; j += 4 * G) {
+                int32_t col[4];
+                float w[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int64_t jj = j + u * G;
+                    col[u] = jj < b1 ? ld_stream(a.csr.indices + jj) : -1;
+                    w[u] = jj < b1 ? load_weight<WK>(a.csr.data, jj, wh) : 0.f;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (col[u] >= 0) red_add_keep(out + col[u], s * w[u], keep);
+            }
+        } else {
+            const JitArgs& d = is_e ? a.je : a.ji;
+            const int64_t c = jit_walk<BP_JIT_HOMO>(d, static_cast<uint32_t>(is_e ? i : i - a.n_e), a.n,
+                                                    [&](int64_t q, uint64_t, float) { red_add_keep(out + q, s * wh, keep); });
+            if (z) ev += c;
+        }
+    }
+    if (a.totals) block_add_i64(ev, a.totals + 2);
+}
+
 // Dense event flags -> spike list (Appendix B's `events` to the compact form).
 __global__ void __launch_bounds__(kStepThreads) k_spike_compact(int64_t n, const uint8_t* __restrict__ events,
                                                                int32_t* __restrict__ spike_list,
@@ -374,6 +450,9 @@ bp_status launch_step_conn(const StepArgs& a, int conn, int wk, cudaStream_t s) 
 template <bool COUNTS, int VEC>
 bp_status launch_step_vec(const StepArgs& a, int conn, int wk, cudaStream_t s) {
     if (conn == CONN_NONE) return launch_k(k_step<COUNTS, VEC, CONN_NONE, WK_HOMO>, a, VEC, s);
+    if constexpr (!COUNTS) {
+        if (conn == CONN_PRE) return launch_k(k_step<false, VEC, CONN_PRE, WK_HOMO>, a, VEC, s);
+    }
     if (a.ring) return launch_step_conn<COUNTS, VEC, true>(a, conn, wk, s);
     return launch_step_conn<COUNTS, VEC, false>(a, conn, wk, s);
 }
@@ -445,6 +524,44 @@ bp_status launch_network_step(const NetStepLaunch& L, int parity, int32_t t_loca
     a.group = L.group;
     a.je = L.je;
     a.ji = L.ji;
+    if (L.trace) {
+        // AlignPre: traces and W^T s into the first halves, then the neurons
+        TraceArgs t{};
+        t.n = L.n;
+        t.n_e = L.n_e;
+        t.a_e = L.c.a_e;
+        t.a_i = L.c.a_i;
+        t.w_e = L.c.w_e;
+        t.w_i = L.c.w_i;
+        t.trace = L.trace;
+        t.spk = L.spk;
+        t.acc_e = static_cast<float*>(L.ye2);
+        t.acc_i = static_cast<float*>(L.yi2);
+        t.totals = L.totals;
+        t.csr = L.csr;
+        t.group = L.jit ? 32 : L.group;
+        t.je = L.je;
+        t.ji = L.ji;
+        const int64_t groups_per_cta = kStepThreads / t.group;
+        int64_t grid = (L.n + groups_per_cta - 1) / groups_per_cta;
+        const int64_t cap = static_cast<int64_t>(sm_count()) * 8;
+        if (grid > cap) grid = cap;
+        if (L.jit) {
+            k_trace_scatter<CONN_JIT, WK_HOMO><<<static_cast<unsigned>(grid), kStepThreads, 0, s>>>(t);
+        } else if (L.csr.wkind == WK_F32) {
+            k_trace_scatter<CONN_CSR, WK_F32><<<static_cast<unsigned>(grid), kStepThreads, 0, s>>>(t);
+        } else if (L.csr.wkind == WK_BF16) {
+            k_trace_scatter<CONN_CSR, WK_BF16><<<static_cast<unsigned>(grid), kStepThreads, 0, s>>>(t);
+        } else {
+            k_trace_scatter<CONN_CSR, WK_HOMO><<<static_cast<unsigned>(grid), kStepThreads, 0, s>>>(t);
+        }
+        BP_LAUNCHED();
+        a.ye_in = ye;
+        a.yi_in = yi;
+        a.ye_out = a.yi_out = nullptr;
+        a.ring = nullptr;
+        return launch_step(a, false, CONN_PRE, WK_HOMO, s);
+    }
     const int conn = L.jit ? CONN_JIT : CONN_CSR;
     return launch_step(a, L.counts, conn, L.csr.wkind, s);
 }

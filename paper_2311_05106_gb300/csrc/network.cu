@@ -120,6 +120,9 @@ bp_status bp_network_create(const bp_net_desc* desc, bp_net** out) {
     BP_REQUIRE(d.delay_e >= 0 && d.delay_e <= 65535 && d.delay_i >= 0 && d.delay_i <= 65535,
                "delays must be in [0, 65535] steps (got %d, %d)", d.delay_e, d.delay_i);
     BP_REQUIRE((d.delay_e == 0 && d.delay_i == 0) || d.delay_buf, "a delayed projection needs delay_buf");
+    BP_REQUIRE(d.align == BP_ALIGN_POST || d.align == BP_ALIGN_PRE, "unknown align %d", d.align);
+    BP_REQUIRE(d.align == BP_ALIGN_POST || (d.trace && d.spk && d.delay_e == 0 && d.delay_i == 0),
+               "the AlignPre form needs trace and spk and no delay");
     bp::NetStepLaunch L{};
     L.c = bp::make_lif_const(d.coba);
     L.n = d.n;
@@ -166,6 +169,12 @@ bp_status bp_network_create(const bp_net_desc* desc, bp_net** out) {
         L.jit = true;
         L.je = {de.seed, static_cast<uint32_t>(de.K), BP_JIT_HOMO, 1.0f, 0.0f};
         L.ji = {di.seed, static_cast<uint32_t>(di.K), BP_JIT_HOMO, 1.0f, 0.0f};
+    }
+    if (d.align == BP_ALIGN_PRE) {
+        // the accumulators hold float sums s w (the CSR operand keeps its
+        // weight kind: stored weights, or w_e / w_i for homogeneous rows)
+        L.trace = d.trace;
+        L.counts = false;
     }
     bp_net* net = new (std::nothrow) bp_net();
     if (!net) {

@@ -38,10 +38,14 @@ class CobaNetwork:
     data) over all n presynaptic rows; data None means homogeneous weights
     w_e / w_i with exact integer event counts.  delay_e / delay_i: synaptic
     delay of the E / I projection in steps (0: spikes act at the next step).
+    align="pre": the AlignPre form (one trace per presynaptic neuron, the
+    conductances recomputed through the connection matrix every step) instead
+    of the merged postsynaptic conductances of AlignPost.
     """
 
     def __init__(self, n, n_e=None, conn="jit", seed=2024, p=None, V0=None, csr=None, tile_cols=0,
-                 params=None, keep_spk=False, keep_spikes=False, delay_e=0, delay_i=0, device="cuda"):
+                 params=None, keep_spk=False, keep_spikes=False, delay_e=0, delay_i=0, align="post",
+                 device="cuda"):
         self.n = int(n)
         self.n_e = int(n_e if n_e is not None else (4 * self.n) // 5)
         self.p = float(p if p is not None else 80.0 / self.n)
@@ -58,7 +62,12 @@ class CobaNetwork:
         self.spike_list = torch.zeros(self.n, dtype=i32, device=device) if keep_spikes else None
         self.n_spikes = torch.zeros(2, dtype=i32, device=device)
         self.totals = torch.zeros(4, dtype=torch.int64, device=device)
+        if align not in ("post", "pre"):
+            raise ValueError("align must be 'post' or 'pre'")
+        self.align = align
+        keep_spk = keep_spk or align == "pre"  # the AlignPre trace update reads the flags
         self.spk = torch.zeros(self.n, dtype=torch.uint8, device=device) if keep_spk else None
+        self.trace = torch.zeros(self.n, dtype=f32, device=device) if align == "pre" else None
         self.tile_ptr = None
         desc = B.NetDesc()
         desc.n, desc.n_e = self.n, self.n_e
@@ -86,7 +95,7 @@ class CobaNetwork:
                 desc.tile_cols = tile_cols
         else:
             raise ValueError("conn must be 'jit' or 'csr'")
-        ydt = i32 if counts else f32
+        ydt = i32 if counts and align == "post" else f32
         # two halves: step t reads half t mod 2 and delivers into the other
         self.ye = torch.zeros(2 * self.n, dtype=ydt, device=device)
         self.yi = torch.zeros(2 * self.n, dtype=ydt, device=device)
@@ -98,6 +107,8 @@ class CobaNetwork:
             self.delay_buf = torch.zeros(slots * (self.n + 1), dtype=i32, device=device)
         desc.delay_e, desc.delay_i = self.delay_e, self.delay_i
         desc.delay_buf = None if self.delay_buf is None else self.delay_buf.data_ptr()
+        desc.align = B.BP_ALIGN_PRE if align == "pre" else B.BP_ALIGN_POST
+        desc.trace = None if self.trace is None else self.trace.data_ptr()
         desc.V, desc.ge, desc.gi, desc.ref = (t.data_ptr() for t in (self.V, self.ge, self.gi, self.ref))
         desc.ye, desc.yi = self.ye.data_ptr(), self.yi.data_ptr()
         desc.spike_list = None if self.spike_list is None else self.spike_list.data_ptr()
