@@ -293,3 +293,69 @@ def test_align_pre_rate_equals_align_post():
         net.close()
     assert rates[0] > 1.0
     assert abs(rates[1] - rates[0]) <= 0.02 * rates[0]
+
+
+def test_full_size_delayed_network_event_identity():
+    """N = 4e6, stored CSR with FP32 weights, both projections delayed by 10
+    steps (the delayed configuration the bench times): the synaptic events a
+    step delivers are exactly the out-degrees of the spikes of 10 steps
+    before (none during the first 10 steps), step by step."""
+    n, seed, d = 4_000_000, 2024, 10
+    n_e, p = 3_200_000, 80.0 / 4_000_000
+    V0 = wl.coba_v0(n, seed=7)
+    csr = materialize_network_csr(seed, p, n, n_e, data_dtype=torch.float32)
+    lens = torch.diff(csr[0]).cpu().numpy()
+    gpu = CobaNetwork(n, conn="csr", csr=csr, seed=seed, p=p, V0=V0, keep_spk=True, delay_e=d, delay_i=d)
+    spikes, deltas = [], []
+    prev = 0
+    for _ in range(40):
+        gpu.step()
+        spikes.append(gpu.spk.cpu().numpy().astype(bool))
+        ev = int(gpu.totals[2].item())
+        deltas.append(ev - prev)
+        prev = ev
+    for t in range(40):
+        expect = int(lens[spikes[t - d]].sum()) if t >= d else 0
+        assert deltas[t] == expect, (t, deltas[t], expect)
+    assert sum(deltas) > 0
+    gpu.close()
+
+
+def test_full_size_align_pre_step_sampled():
+    """N = 4e6, stored CSR with FP32 weights, AlignPre form: from random traces
+    and spike flags, one step's conductances at 2 000 sampled neurons equal
+    the FP64 product over all synapses into them, g_e = sum_i w_ij s_i over E
+    rows (likewise g_i), with s_i = a s_i + z_i."""
+    n, seed = 4_000_000, 2024
+    n_e, p = 3_200_000, 80.0 / 4_000_000
+    csr = materialize_network_csr(seed, p, n, n_e, data_dtype=torch.float32)
+    gpu = CobaNetwork(n, conn="csr", csr=csr, seed=seed, p=p, V0=np.full(n, -70.0, np.float32), align="pre")
+    rng = np.random.default_rng(4)
+    s0 = rng.random(n).astype(np.float32) * (rng.random(n) < 0.3)
+    z0 = (rng.random(n) < 0.01).astype(np.uint8)
+    gpu.trace.copy_(torch.from_numpy(s0))
+    gpu.spk.copy_(torch.from_numpy(z0))
+    gpu.step()
+    torch.cuda.synchronize()
+    a_e, a_i = np.exp(-0.1 / 5.0), np.exp(-0.1 / 10.0)
+    a = np.where(np.arange(n) < n_e, a_e, a_i)
+    s1 = s0.astype(np.float64) * a + z0
+    np.testing.assert_allclose(gpu.trace.cpu().numpy(), s1, rtol=1e-6, atol=1e-7)
+    ip, ix, w = (x.cpu().numpy() for x in csr)
+    sample = np.sort(rng.choice(n, 2000, replace=False))
+    in_sample = np.zeros(n, bool)
+    in_sample[sample] = True
+    pos = np.nonzero(in_sample[ix])[0]
+    rows = np.searchsorted(ip, pos, side="right") - 1
+    contrib = s1[rows] * w[pos].astype(np.float64)
+    e_rows = rows < n_e
+    col = np.searchsorted(sample, ix[pos])
+    ge = np.bincount(col[e_rows], weights=contrib[e_rows], minlength=len(sample))
+    gi = np.bincount(col[~e_rows], weights=contrib[~e_rows], minlength=len(sample))
+    got_e = gpu.ge.cpu().numpy()[sample]
+    got_i = gpu.gi.cpu().numpy()[sample]
+    scale_e, scale_i = max(ge.max(), 1e-30), max(gi.max(), 1e-30)
+    assert np.max(np.abs(got_e - ge)) / scale_e < 1e-5
+    assert np.max(np.abs(got_i - gi)) / scale_i < 1e-5
+    assert ge.max() > 0 and gi.max() > 0
+    gpu.close()
