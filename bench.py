@@ -619,10 +619,13 @@ def run_sweep(args):
                 for wname, wt, wb in (("homo", None, 0), ("f32", w32, 4), ("bf16", w16, 2)):
                     if wname not in wsel or "csr_t" not in ops:
                         continue
-                    ms = timeit(lambda: B.bp_event_csrmv_t(ip, ix, wt, 1.0, x, yp), 5)
                     alg = nnz * (4 + wb) + 8 * (n + 1)
-                    emit(op="event_csrmv_t", n=n, p=p, weights=wname, us=ms * 1e3, nnz=nnz,
-                         alg_bytes=alg, gbs=alg / ms / 1e6, frac_hbm=alg / ms / 1e6 / peak, peak_source=peak_kind)
+                    # x staged in shared-memory tiles (the default), and x read through L2
+                    for form, fl in (("tiles", 0), ("l2", B.BP_ACC_GLOBAL)) if tc else (("l2", 0),):
+                        ms = timeit(lambda: B.bp_event_csrmv_t(ip, ix, wt, 1.0, x, yp, flags=fl, tile_ptr=tp,
+                                                               tile_cols=tc), 5)
+                        emit(op="event_csrmv_t", form=form, n=n, p=p, weights=wname, us=ms * 1e3, nnz=nnz,
+                             alg_bytes=alg, gbs=alg / ms / 1e6, frac_hbm=alg / ms / 1e6 / peak, peak_source=peak_kind)
             for rho in rhos:
                 ev_np = wl.bernoulli_spikes(n, rho, seed=seed + int(rho * 1e4))
                 events = torch.from_numpy(ev_np).cuda()

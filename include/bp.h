@@ -219,11 +219,20 @@ bp_status bp_csr_tile_index(int64_t n_pre, int64_t n_post, const int64_t* indptr
 /* Gather ("transpose") form over the same CSR, all rows (Section 3.1: every
  * operator has reverse-mode rules; this is the product with W rather than
  * W^T):  y_pre[i] += sum_{j in row i} w_j x_post[indices[j]].
- * x_post float [n_post], y_pre float [n_pre]. */
+ * x_post float [n_post], y_pre float [n_pre].  With a tile index
+ * (bp_csr_tile_index, sorted rows; NULL / 0 for none) x_post is staged in
+ * shared memory tile by tile and each (row, tile) partial sum is added to
+ * y_pre once (float atomics across tiles, so with several tiles the order of
+ * the additions, and the last bits of y_pre, may vary between calls); it pays
+ * when x_post is larger than the caches and rows hold a few hundred entries
+ * per tile or more.  Otherwise, or with BP_ACC_GLOBAL in flags, x_post is
+ * read through L1/L2 by a gather that keeps more rows in flight.
+ * BP_OVERWRITE replaces y_pre instead of adding to it. */
 bp_status bp_event_csrmv_t(int64_t n_pre, int64_t n_post,
                            const int64_t* indptr, const int32_t* indices,
                            const void* data, int32_t wkind, float w_homo,
                            const float* x_post, float* y_pre,
+                           const int32_t* tile_ptr, int32_t tile_cols,
                            uint32_t flags, bp_stream_t stream);
 
 /* Reverse mode of bp_event_csrmv for a loss L with dy = dL/dy (Section 3.1):

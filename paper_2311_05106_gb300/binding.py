@@ -99,7 +99,7 @@ _SIGS = {
     "bp_event_csrmv_dense_noalloc": (c_i32, [c_i64, c_i64, VP, VP, VP, c_i32, c_f32, VP, VP, c_i32, c_u32, VP]),
     "bp_csr_tile_index_size": (c_i64, [c_i64, c_i64, c_i32]),
     "bp_csr_tile_index": (c_i32, [c_i64, c_i64, VP, VP, c_i32, VP, VP]),
-    "bp_event_csrmv_t": (c_i32, [c_i64, c_i64, VP, VP, VP, c_i32, c_f32, VP, VP, c_u32, VP]),
+    "bp_event_csrmv_t": (c_i32, [c_i64, c_i64, VP, VP, VP, c_i32, c_f32, VP, VP, VP, c_i32, c_u32, VP]),
     "bp_event_csrmv_bwd": (c_i32, [c_i64, c_i64, VP, VP, VP, c_i32, c_f32, VP, VP, c_i64, VP, VP, VP, VP]),
     "bp_jit_desc_init": (c_i32, [ctypes.POINTER(JitDesc), c_u64, c_f64, c_i32, c_f32, c_f32]),
     "bp_jitconn_event_mv": (c_i32, [ctypes.POINTER(JitDesc), c_i64, c_i64, VP, VP, c_i64, VP, c_i32, c_u32, VP]),
@@ -279,10 +279,10 @@ def bp_csr_tile_index(indptr, indices, n_post, tile_cols, tile_ptr, stream=None)
                                                         int(tile_cols), _p(tile_ptr), _stream(stream)))
 
 
-def bp_event_csrmv_t(indptr, indices, data, w_homo, x_post, y_pre, flags=0, stream=None):
+def bp_event_csrmv_t(indptr, indices, data, w_homo, x_post, y_pre, flags=0, stream=None, tile_ptr=None, tile_cols=0):
     _check("bp_event_csrmv_t", lib().bp_event_csrmv_t(indptr.numel() - 1, x_post.numel(), _p(indptr), _p(indices),
                                                       _p(data), _wkind(data), float(w_homo), _p(x_post), _p(y_pre),
-                                                      int(flags), _stream(stream)))
+                                                      _p(tile_ptr), int(tile_cols), int(flags), _stream(stream)))
 
 
 def bp_event_csrmv_bwd(indptr, indices, data, w_homo, spike_list, n_spikes, dy, dw=None, dx_pre=None,

@@ -180,6 +180,70 @@ __global__ void __launch_bounds__(256) k_csr_gather(CsrArgs a, const float* __re
     }
 }
 
+// Gather with x staged in shared memory: CTA (s, r) copies x[s W, (s+1) W)
+// into shared memory and walks rows r, r + R, ... over their segments in
+// post tile s (from the tile index; the whole row when one tile covers
+// n_post), G lanes per row with four index loads in flight per lane.  With
+// one tile each row has a single owner and is written directly; with
+// several, each (row, tile) partial sum is added to y_pre with one atomic
+// (y_pre cleared first when overwriting).  Indices outside the tile (an index
+// that does not match the matrix) contribute nothing.
+template <int WK>
+__global__ void __launch_bounds__(kTileThreads, 1) k_csr_gather_tiled(CsrArgs a, const float* __restrict__ x,
+                                                                      float* __restrict__ y, int overwrite,
+                                                                      int32_t W, int32_t S) {
+    extern __shared__ __align__(16) float xs[];
+    const int s = blockIdx.x % S;
+    const int64_t r = blockIdx.x / S;
+    const int64_t R = gridDim.x / S;
+    const int64_t col0 = static_cast<int64_t>(s) * W;
+    const int64_t rem = a.n_post - col0;
+    const int lim = static_cast<int>(rem < W ? rem : W);
+    for (int t = threadIdx.x; t < W; t += blockDim.x) xs[t] = t < lim ? x[col0 + t] : 0.f;
+    __syncthreads();
+    const int64_t nnz = a.indptr[a.n_pre];
+    const int G = pick_group(nnz, a.n_pre, S);
+    const int lane = threadIdx.x % G;
+    const int64_t gid = threadIdx.x / G;
+    const int64_t ng = blockDim.x / G;
+    for (int64_t i = r + R * gid; i < a.n_pre; i += R * ng) {
+        const int64_t rs = a.indptr[i];
+        int64_t b0, b1;
+        if (S > 1) {
+            const int32_t* tp = a.tile_ptr + i * (S + 1) + s;
+            b0 = rs + tp[0];
+            b1 = rs + tp[1];
+        } else {
+            b0 = rs;
+            b1 = a.indptr[i + 1];
+        }
+        float sum = 0.f;
+        for (int64_t j = b0 + lane; j < b1; j += 4 * G) {
+            int32_t c[4];
+            float w[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t jj = j + u * G;
+                c[u] = jj < b1 ? ld_stream(a.indices + jj) : static_cast<int32_t>(col0);
+                w[u] = jj < b1 ? load_weight<WK>(a.data, jj, a.w_homo) : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint32_t k = static_cast<uint32_t>(static_cast<int64_t>(c[u]) - col0);
+                sum += k < static_cast<uint32_t>(W) ? w[u] * xs[k] : 0.f;
+            }
+        }
+        sum = group_reduce_sum(sum, G);
+        if (lane == 0) {
+            if (S == 1) {
+                y[i] = overwrite ? sum : y[i] + sum;
+            } else if (b1 > b0) {
+                atomicAdd(y + i, sum);
+            }
+        }
+    }
+}
+
 // dw[j] += dy[indices[j]] for the entries of each spiking row.
 __global__ void __launch_bounds__(256) k_csr_dw(CsrArgs a, const int32_t* __restrict__ spike_list,
                                                 const int32_t* __restrict__ n_spikes, int64_t max_spikes,
@@ -423,13 +487,51 @@ bp_status bp_csr_tile_index(int64_t n_pre, int64_t n_post, const int64_t* indptr
 
 bp_status bp_event_csrmv_t(int64_t n_pre, int64_t n_post, const int64_t* indptr, const int32_t* indices,
                            const void* data, int32_t wkind, float w_homo, const float* x_post, float* y_pre,
-                           uint32_t flags, bp_stream_t stream) {
+                           const int32_t* tile_ptr, int32_t tile_cols, uint32_t flags, bp_stream_t stream) {
     bp::clear_error();
-    const bp::CsrArgs a = make_csr(n_pre, n_post, indptr, indices, data, wkind, w_homo, nullptr, 0);
+    const bp::CsrArgs a = make_csr(n_pre, n_post, indptr, indices, data, wkind, w_homo, tile_ptr, tile_cols);
     BP_TRY(bp::check_csr(a));
     BP_REQUIRE(n_pre == 0 || (y_pre && x_post && indices), "x_post, y_pre or indices is NULL");
     if (n_pre == 0) return BP_OK;
     const int ow = (flags & BP_OVERWRITE) ? 1 : 0;
+    // shared-memory tiles of x when the caller gives a tile index (measured:
+    // 2.2x the L2 form at n = 1e6 with ~550 entries per row and tile; the L2
+    // form wins when x stays in L1/L2 or segments are short) and the L2 form
+    // is not forced
+    int32_t W = 0, S = 0;
+    if (tile_ptr && tile_cols > 0) {
+        W = tile_cols;
+        S = static_cast<int32_t>((n_post + W - 1) / W);
+        if (S < 1) S = 1;
+    }
+    if (S > 0 && !(flags & BP_ACC_GLOBAL)) {
+        if (S > 1 && ow) BP_CUDA(cudaMemsetAsync(y_pre, 0, static_cast<size_t>(n_pre) * sizeof(float), stream));
+        const size_t smem = static_cast<size_t>(W) * sizeof(float);
+        int64_t R = static_cast<int64_t>(bp::sm_count()) / S;
+        const int64_t rows_cap = (n_pre + 255) / 256;
+        if (R > rows_cap) R = rows_cap;
+        if (R < 1) R = 1;
+        const unsigned grid = static_cast<unsigned>(S * R);
+        const int ow_tile = S == 1 ? ow : 0;
+#define BP_GATHER_T(WKV)                                                                                          \
+    do {                                                                                                          \
+        static bool attr = false;                                                                                 \
+        if (!attr) {                                                                                              \
+            BP_CUDA(cudaFuncSetAttribute(bp::k_csr_gather_tiled<WKV>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                         static_cast<int>(bp::kTileCols * sizeof(float))));                       \
+            attr = true;                                                                                          \
+        }                                                                                                         \
+        bp::k_csr_gather_tiled<WKV><<<grid, bp::kTileThreads, smem, stream>>>(a, x_post, y_pre, ow_tile, W, S);   \
+    } while (0)
+        switch (wkind) {
+            case BP_W_F32: BP_GATHER_T(bp::WK_F32); break;
+            case BP_W_BF16: BP_GATHER_T(bp::WK_BF16); break;
+            default: BP_GATHER_T(bp::WK_HOMO); break;
+        }
+#undef BP_GATHER_T
+        BP_LAUNCHED();
+        return BP_OK;
+    }
     const int grid = bp::gather_grid(n_pre);
     switch (wkind) {
         case BP_W_F32: bp::k_csr_gather<bp::WK_F32><<<grid, 256, 0, stream>>>(a, x_post, y_pre, ow); break;
@@ -455,7 +557,8 @@ bp_status bp_event_csrmv_bwd(int64_t n_pre, int64_t n_post, const int64_t* indpt
         bp::k_csr_dw<<<grid, 256, 0, stream>>>(a, spike_list, n_spikes, max_spikes, dy, dw);
         BP_LAUNCHED();
     }
-    if (dx_pre) return bp_event_csrmv_t(n_pre, n_post, indptr, indices, data, wkind, w_homo, dy, dx_pre, 0, stream);
+    if (dx_pre)
+        return bp_event_csrmv_t(n_pre, n_post, indptr, indices, data, wkind, w_homo, dy, dx_pre, nullptr, 0, 0, stream);
     return BP_OK;
 }
 

@@ -195,7 +195,10 @@ def test_tile_index_matches_searchsorted():
 
 
 @pytest.mark.parametrize("wdt", [None, torch.float32, torch.bfloat16])
-def test_csrmv_t_gather(wdt):
+@pytest.mark.parametrize("form", ["l2", "one_tile", "one_tile_overwrite"])
+def test_csrmv_t_gather(wdt, form):
+    """Gather through L2, and with a one-tile index (x wholly in shared
+    memory, each row written by one owner)."""
     n_pre, n_post = 6000, 5000
     ip, ix = _csr(n_pre, n_post, 0.01, seed=13)
     w = wl.normal_weights(len(ix), 0.0, 1.0, seed=14)
@@ -203,8 +206,38 @@ def test_csrmv_t_gather(wdt):
     dw = None if wdt is None else cuda(w).to(wdt)
     wref = None if wdt is None else dw.float().cpu().numpy().astype(np.float64)
     y = torch.full((n_pre,), 0.25, dtype=torch.float32, device="cuda")
-    B.bp_event_csrmv_t(cuda(ip), cuda(ix), dw, 0.6, cuda(x), y)
-    ref = 0.25 + orc.csrmv_t(ip, ix, wref, x.astype(np.float64), w_homo=0.6)
+    tp, tc = None, 0
+    if form != "l2":
+        tc = (n_post + 31) // 32 * 32
+        tp = torch.empty(B.bp_csr_tile_index_size(n_pre, n_post, tc), dtype=torch.int32, device="cuda")
+        B.bp_csr_tile_index(cuda(ip), cuda(ix), n_post, tc, tp)
+    flags = B.BP_OVERWRITE if form == "one_tile_overwrite" else 0
+    B.bp_event_csrmv_t(cuda(ip), cuda(ix), dw, 0.6, cuda(x), y, flags=flags, tile_ptr=tp, tile_cols=tc)
+    base = 0.0 if flags else 0.25
+    ref = base + orc.csrmv_t(ip, ix, wref, x.astype(np.float64), w_homo=0.6)
+    assert rel_err(y.cpu().numpy(), ref) < RTOL_F32
+
+
+@pytest.mark.parametrize("wdt", [None, torch.float32, torch.bfloat16])
+@pytest.mark.parametrize("mode", ["tiles", "l2", "tiles_overwrite"])
+def test_csrmv_t_gather_tiles(wdt, mode):
+    """n_post = 130 000 spans three shared-memory tiles of x (57 344 columns,
+    ragged last tile): the tiled gather, the L2 gather and the overwrite form
+    against the oracle's sequential product."""
+    n_pre, n_post = 7001, 130000
+    ip, ix = _csr(n_pre, n_post, 0.002, seed=23)
+    w = wl.normal_weights(len(ix), 0.0, 1.0, seed=24)
+    x = np.random.default_rng(2).normal(size=n_post).astype(np.float32)
+    dw = None if wdt is None else cuda(w).to(wdt)
+    wref = None if wdt is None else dw.float().cpu().numpy().astype(np.float64)
+    tc = B.bp_tile_cols()
+    tp = torch.empty(B.bp_csr_tile_index_size(n_pre, n_post, tc), dtype=torch.int32, device="cuda")
+    B.bp_csr_tile_index(cuda(ip), cuda(ix), n_post, tc, tp)
+    y = torch.full((n_pre,), 0.25, dtype=torch.float32, device="cuda")
+    flags = {"tiles": 0, "l2": B.BP_ACC_GLOBAL, "tiles_overwrite": B.BP_OVERWRITE}[mode]
+    B.bp_event_csrmv_t(cuda(ip), cuda(ix), dw, 0.6, cuda(x), y, flags=flags, tile_ptr=tp, tile_cols=tc)
+    base = 0.0 if mode == "tiles_overwrite" else 0.25
+    ref = base + orc.csrmv_t(ip, ix, wref, x.astype(np.float64), w_homo=0.6)
     assert rel_err(y.cpu().numpy(), ref) < RTOL_F32
 
 
