@@ -239,12 +239,15 @@ bp_status bp_event_csrmv_t(int64_t n_pre, int64_t n_post,
  *   dw[j] += dy[indices[j]] for every entry j of every spiking row (if dw is
  *   non-NULL; float [nnz]; each spiking row must appear once);
  *   dx_pre[i] += sum_j w_j dy[indices[j]] for every row i (if dx_pre is
- *   non-NULL; float [n_pre]: the gradient with respect to the spike vector). */
+ *   non-NULL; float [n_pre]: the gradient with respect to the spike vector),
+ *   computed as bp_event_csrmv_t with the optional tile index (the one the
+ *   forward product uses; NULL / 0 for none). */
 bp_status bp_event_csrmv_bwd(int64_t n_pre, int64_t n_post,
                              const int64_t* indptr, const int32_t* indices,
                              const void* data, int32_t wkind, float w_homo,
                              const int32_t* spike_list, const int32_t* n_spikes, int64_t max_spikes,
                              const float* dy, float* dw, float* dx_pre,
+                             const int32_t* tile_ptr, int32_t tile_cols,
                              bp_stream_t stream);
 
 /* --------------------------------------------------------------------------

@@ -100,7 +100,7 @@ _SIGS = {
     "bp_csr_tile_index_size": (c_i64, [c_i64, c_i64, c_i32]),
     "bp_csr_tile_index": (c_i32, [c_i64, c_i64, VP, VP, c_i32, VP, VP]),
     "bp_event_csrmv_t": (c_i32, [c_i64, c_i64, VP, VP, VP, c_i32, c_f32, VP, VP, VP, c_i32, c_u32, VP]),
-    "bp_event_csrmv_bwd": (c_i32, [c_i64, c_i64, VP, VP, VP, c_i32, c_f32, VP, VP, c_i64, VP, VP, VP, VP]),
+    "bp_event_csrmv_bwd": (c_i32, [c_i64, c_i64, VP, VP, VP, c_i32, c_f32, VP, VP, c_i64, VP, VP, VP, VP, c_i32, VP]),
     "bp_jit_desc_init": (c_i32, [ctypes.POINTER(JitDesc), c_u64, c_f64, c_i32, c_f32, c_f32]),
     "bp_jitconn_event_mv": (c_i32, [ctypes.POINTER(JitDesc), c_i64, c_i64, VP, VP, c_i64, VP, c_i32, c_u32, VP]),
     "bp_jitconn_event_mv_bwd": (c_i32, [ctypes.POINTER(JitDesc), c_i64, c_i64, VP, VP, VP]),
@@ -286,12 +286,13 @@ def bp_event_csrmv_t(indptr, indices, data, w_homo, x_post, y_pre, flags=0, stre
 
 
 def bp_event_csrmv_bwd(indptr, indices, data, w_homo, spike_list, n_spikes, dy, dw=None, dx_pre=None,
-                       max_spikes=None, stream=None):
+                       max_spikes=None, stream=None, tile_ptr=None, tile_cols=0):
     n_pre = indptr.numel() - 1
     ms = n_pre if max_spikes is None else max_spikes
     _check("bp_event_csrmv_bwd", lib().bp_event_csrmv_bwd(n_pre, dy.numel(), _p(indptr), _p(indices), _p(data),
                                                           _wkind(data), float(w_homo), _p(spike_list), _p(n_spikes),
-                                                          ms, _p(dy), _p(dw), _p(dx_pre), _stream(stream)))
+                                                          ms, _p(dy), _p(dw), _p(dx_pre), _p(tile_ptr),
+                                                          int(tile_cols), _stream(stream)))
 
 
 # ------------------------------------------------------------------ a6

@@ -545,9 +545,9 @@ bp_status bp_event_csrmv_t(int64_t n_pre, int64_t n_post, const int64_t* indptr,
 bp_status bp_event_csrmv_bwd(int64_t n_pre, int64_t n_post, const int64_t* indptr, const int32_t* indices,
                              const void* data, int32_t wkind, float w_homo, const int32_t* spike_list,
                              const int32_t* n_spikes, int64_t max_spikes, const float* dy, float* dw, float* dx_pre,
-                             bp_stream_t stream) {
+                             const int32_t* tile_ptr, int32_t tile_cols, bp_stream_t stream) {
     bp::clear_error();
-    const bp::CsrArgs a = make_csr(n_pre, n_post, indptr, indices, data, wkind, w_homo, nullptr, 0);
+    const bp::CsrArgs a = make_csr(n_pre, n_post, indptr, indices, data, wkind, w_homo, tile_ptr, tile_cols);
     BP_TRY(bp::check_csr(a));
     BP_REQUIRE(max_spikes >= 0 && max_spikes <= n_pre, "max_spikes out of range");
     BP_REQUIRE(dy != nullptr || n_post == 0, "dy is NULL");
@@ -558,7 +558,8 @@ bp_status bp_event_csrmv_bwd(int64_t n_pre, int64_t n_post, const int64_t* indpt
         BP_LAUNCHED();
     }
     if (dx_pre)
-        return bp_event_csrmv_t(n_pre, n_post, indptr, indices, data, wkind, w_homo, dy, dx_pre, nullptr, 0, 0, stream);
+        return bp_event_csrmv_t(n_pre, n_post, indptr, indices, data, wkind, w_homo, dy, dx_pre, tile_ptr, tile_cols, 0,
+                                stream);
     return BP_OK;
 }
 
