@@ -65,6 +65,7 @@ def parse():
     # the differentiable-network measurement alone (profiling)
     ap.add_argument("--bptt-only", action="store_true")
     ap.add_argument("--align-pre-only", action="store_true")
+    ap.add_argument("--cpu-table", action="store_true")
     ap.add_argument("--bptt-T", type=int, default=1000)
     return ap.parse_args()
 
@@ -520,6 +521,67 @@ def oracle_sample(budget_s, n_sample=None):
     return dict(value=events / dt, steps=steps, seconds=dt, n=n)
 
 
+def run_cpu_table(args):
+    """The FP64 oracle, as it stands and on one thread, timed on this machine's
+    host cores on bounded samples of each configuration: config 1 (4 000
+    neurons, 1 000 steps, JIT rows), config 2 at N = 4e4 (1 000 steps) and
+    N = 4e5 (50 steps), config 3 operator cells through the oracle's event
+    product over JIT rows (the matrix the stored CSR materialises), config 4 on
+    8 of the 256 networks for 100 steps, config 5 one forward + backward at
+    B = 8, T = 100 (the full size scales as B x T).  Prints one JSON line."""
+    import numpy as np
+    import oracle as orc
+    from oracle import bptt
+    from paper_2311_05106_gb300 import workloads as wl
+    out = {"cores": 1, "threads_env": {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS")}}
+
+    def net_run(n, T, seed=SEED, v0_seed=V0_SEED, p=None):
+        p = 80.0 / n if p is None else p
+        K = orc.jit_K(p)
+        net = orc.CobaNet(n, (4 * n) // 5, ("jit", orc.projection_seed(seed, 0), orc.projection_seed(seed, 1), K),
+                          wl.coba_v0(n, seed=v0_seed).astype(np.float64))
+        t0 = time.perf_counter()
+        r = net.run(T, events=True)
+        dt = time.perf_counter() - t0
+        return dt, int(r["events"].sum())
+
+    dt, ev = net_run(4000, 1000, p=0.02)
+    out["config1_coba_4k"] = {"steps": 1000, "seconds": dt, "steps_per_s": 1000 / dt, "events_per_s": ev / dt}
+    for n, T in ((40_000, 1000), (400_000, 50)):
+        dt, ev = net_run(n, T)
+        out["config2_N%d" % n] = {"steps": T, "seconds": dt, "steps_per_s": T / dt, "events_per_s": ev / dt}
+    cells = []
+    for n, p, rho in ((10_000, 0.01, 0.1), (10_000, 0.1, 0.1), (100_000, 0.001, 0.1), (100_000, 0.01, 0.1),
+                      (1_000_000, 0.001, 0.01), (1_000_000, 0.01, 0.01)):
+        K = orc.jit_K(p)
+        ev_in = wl.bernoulli_spikes(n, rho, seed=1000 + n % 997 + int(rho * 1e4))
+        t0 = time.perf_counter()
+        y = orc.jitconn_event_mv(1000 + n % 997 + int(p * 1e4), K, n, n, ev_in)
+        dt = time.perf_counter() - t0
+        cells.append({"n": n, "p": p, "rho": rho, "seconds": dt, "events_per_s": float(y.sum()) / dt})
+    out["config3_jit_event_mv"] = cells
+    sizes = wl.batched_sizes(256, 1000, 50000, seed=11)[:8]
+    tot_t, tot_ev = 0.0, 0
+    for b, n in enumerate(sizes):
+        dt, ev = net_run(int(n), 100, seed=SEED + 7919 * b, v0_seed=1000 + b)
+        tot_t += dt
+        tot_ev += ev
+    out["config4_8_of_256_nets"] = {"neurons": int(sum(sizes)), "steps": 100, "seconds": tot_t,
+                                    "events_per_s": tot_ev / tot_t,
+                                    "per_step_all_256_s_extrapolated": tot_t / 100 * 256 / 8}
+    Bsz, T, n_in, n_rec, n_out = 8, 100, 700, 1024, 20
+    u = wl.poisson_inputs(Bsz, T, n_in, seed=5)
+    w = wl.snn_weights(n_in, n_rec, n_out, 0.1, seed=6, rec_std=1.0 / np.sqrt(102.0))
+    labels = wl.labels(Bsz, n_out, seed=7)
+    t0 = time.perf_counter()
+    bptt.loss_and_grads(u, labels, w["W_in"].astype(np.float64), w["indptr"], w["indices"],
+                        w["w_rec"].astype(np.float64), w["W_out"].astype(np.float64), w["b_out"].astype(np.float64))
+    dt = time.perf_counter() - t0
+    out["config5_bptt_B8_T100"] = {"seconds": dt, "fwd_bwd_s_at_B128_T1000_extrapolated": dt * (128 / Bsz) * (1000 / T)}
+    print(json.dumps({"cpu_table": out}))
+    return 0
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -590,7 +652,31 @@ def run_sweep(args):
             b.record(stream)
         torch.cuda.synchronize()
         ms = sorted(a.elapsed_time(b) for a, b in evs)
-        return ms[len(ms) // 2]
+        med = ms[len(ms) // 2]
+        if med >= 0.1:
+            return med
+        # a short call on an idle GPU waits for the host to enqueue it: time
+        # 20 calls captured in a CUDA graph instead (device time per call)
+        g = torch.cuda.CUDAGraph()
+        cap = torch.cuda.Stream()
+        cap.wait_stream(stream)
+        with torch.cuda.stream(cap):
+            with torch.cuda.graph(g, stream=cap):
+                for _ in range(20):
+                    fn()
+        stream.wait_stream(cap)
+        g.replay()
+        torch.cuda.synchronize()
+        gms = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            g.replay()
+            b.record(stream)
+            torch.cuda.synchronize()
+            gms.append(a.elapsed_time(b) / 20)
+        gms.sort()
+        return gms[len(gms) // 2]
 
     def emit(**kw):
         print(json.dumps(kw), flush=True)
@@ -669,6 +755,8 @@ def main():
         return run_reference(args)
     if args.sweep:
         return run_sweep(args)
+    if args.cpu_table:
+        return run_cpu_table(args)
     if args.bptt_only:
         import torch
         torch.cuda.set_device(0)

@@ -37,6 +37,15 @@ __device__ __forceinline__ int pick_group_v4(int64_t nnz, int64_t n_pre, int64_t
     return 4;
 }
 
+// Lanes per row group when few rows are to be delivered: the group (which
+// needs no shuffles, so it may span several warps) doubles while there are
+// still lanes for every row, so that a handful of long rows is walked by the
+// whole grid instead of one group each.
+__device__ __forceinline__ int widen_group(int G, int64_t rows, int64_t lanes, int cap) {
+    while (G < cap && rows * 2 * G <= lanes) G *= 2;
+    return G;
+}
+
 template <typename Acc, int WK, bool VECL>
 __device__ __forceinline__ void scatter_any(const int32_t* __restrict__ indices, const void* __restrict__ data,
                                             float w_homo, int64_t b0, int64_t b1, int lane, int G,
@@ -65,7 +74,8 @@ __global__ void __launch_bounds__(kTileThreads, 1)
     }
     int64_t ev = 0;
     if (mode == 1) {
-        const int G = VECL ? pick_group_v4(nnz, a.n_pre, 1) : pick_group(nnz, a.n_pre, 1);
+        const int G = widen_group(VECL ? pick_group_v4(nnz, a.n_pre, 1) : pick_group(nnz, a.n_pre, 1), ns,
+                                  static_cast<int64_t>(gridDim.x) * blockDim.x, blockDim.x);
         const int lane = threadIdx.x % G;
         const int64_t ngroups = static_cast<int64_t>(gridDim.x) * blockDim.x / G;
         for (int64_t u = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) / G; u < ns; u += ngroups) {
@@ -84,27 +94,38 @@ __global__ void __launch_bounds__(kTileThreads, 1)
         const int nacc = SPLIT ? 2 * W : W;
         for (int t = threadIdx.x; t < nacc; t += blockDim.x) acc[t] = Acc(0);
         __syncthreads();
-        const int G = VECL ? pick_group_v4(nnz, a.n_pre, S) : pick_group(nnz, a.n_pre, S);
-        const int lane = threadIdx.x % G;
-        const int64_t gid = threadIdx.x / G;
-        const int64_t ng = blockDim.x / G;
-        for (int64_t u = r + R * gid; u < ns; u += R * ng) {
-            const int32_t i = spike_list[u];
-            if (static_cast<uint32_t>(i) >= static_cast<uint64_t>(a.n_pre)) continue;
-            const int64_t rs = a.indptr[i];
-            int64_t b0, b1;
-            if (a.tile_ptr) {
-                const int32_t* tp = a.tile_ptr + static_cast<int64_t>(i) * (S + 1) + s;
-                b0 = rs + tp[0];
-                b1 = rs + tp[1];
-            } else {
-                b0 = rs;
-                b1 = a.indptr[i + 1];
+        // rows r, r + R, ... of the spike list, G lanes per row
+        auto walk = [&](int G) {
+            const int lane = threadIdx.x % G;
+            const int64_t gid = threadIdx.x / G;
+            const int64_t ng = blockDim.x / G;
+            for (int64_t u = r + R * gid; u < ns; u += R * ng) {
+                const int32_t i = spike_list[u];
+                if (static_cast<uint32_t>(i) >= static_cast<uint64_t>(a.n_pre)) continue;
+                const int64_t rs = a.indptr[i];
+                int64_t b0, b1;
+                if (a.tile_ptr) {
+                    const int32_t* tp = a.tile_ptr + static_cast<int64_t>(i) * (S + 1) + s;
+                    b0 = rs + tp[0];
+                    b1 = rs + tp[1];
+                } else {
+                    b0 = rs;
+                    b1 = a.indptr[i + 1];
+                }
+                if (events_total && s == 0 && lane == 0) ev += a.indptr[i + 1] - rs;
+                Acc* out = acc + ((SPLIT && i >= split) ? W : 0);
+                scatter_any<Acc, WK, VECL>(a.indices, a.data, a.w_homo, b0, b1, lane, G, out, col0);
             }
-            if (events_total && s == 0 && lane == 0) ev += a.indptr[i + 1] - rs;
-            Acc* out = acc + ((SPLIT && i >= split) ? W : 0);
-            scatter_any<Acc, WK, VECL>(a.indices, a.data, a.w_homo, b0, b1, lane, G, out, col0);
-        }
+        };
+        const int G0 = VECL ? pick_group_v4(nnz, a.n_pre, S) : pick_group(nnz, a.n_pre, S);
+        const int64_t rows_here = ns > r ? (ns - r + R - 1) / R : 0;
+        // the widened walk is a separate copy, so the common walk keeps the
+        // code of the small fixed group sizes (measured: one shared copy with
+        // a run-time group size slows the large cells by 9-17 %)
+        if (rows_here * 2 * G0 <= static_cast<int64_t>(blockDim.x))
+            walk(widen_group(G0, rows_here, blockDim.x, blockDim.x));
+        else
+            walk(G0);
         __syncthreads();
         const int64_t rem = a.n_post - col0;
         const int lim = static_cast<int>(rem < W ? rem : W);
@@ -129,7 +150,8 @@ __global__ void __launch_bounds__(kDirectThreads)
     int64_t ns = *n_spikes;
     ns = ns < max_spikes ? ns : max_spikes;
     const int64_t nnz = a.indptr[a.n_pre];
-    const int G = VECL ? pick_group_v4(nnz, a.n_pre, 1) : pick_group(nnz, a.n_pre, 1);
+    const int G = widen_group(VECL ? pick_group_v4(nnz, a.n_pre, 1) : pick_group(nnz, a.n_pre, 1), ns,
+                              static_cast<int64_t>(gridDim.x) * blockDim.x, blockDim.x);
     const int lane = threadIdx.x % G;
     const int64_t ngroups = static_cast<int64_t>(gridDim.x) * blockDim.x / G;
     int64_t ev = 0;
