@@ -20,8 +20,62 @@ namespace {
 constexpr int kJitThreads = 512;
 constexpr int kJitWarps = kJitThreads / 32;
 
+// The whole CTA walks row `row` together (for calls with few, long rows):
+// per round, warp w draws the 32 Philox blocks c + 32 w + lane (128 gaps), a
+// warp scan orders them within the warp, and a prefix over the warps' totals
+// (shared memory) gives each warp its offset, so the positions are exactly
+// those of jit_walk's chunk-by-chunk walk; rounds continue from the last
+// position until it reaches n_post - 1.  Every thread of the CTA must call
+// it with the same row.  Returns this lane's count.
+template <int WK, typename F>
+__device__ __forceinline__ int64_t jit_walk_cta(const JitArgs& d, uint32_t row, int64_t n_post, F&& f) {
+    __shared__ uint64_t s_tot[kJitWarps];
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const uint32_t k0 = static_cast<uint32_t>(d.seed), k1 = static_cast<uint32_t>(d.seed >> 32);
+    int64_t carry = -1;
+    int64_t count = 0;
+    for (uint32_t c = 0;; c += 32u * kJitWarps) {
+        const uint32_t blk = c + 32u * warp + lane;
+        const uint4 x = Philox::block(make_uint4(blk, row, 0u, 0u), k0, k1);
+        const uint32_t g0 = 1u + __umulhi(x.x, d.K);
+        const uint32_t g1 = 1u + __umulhi(x.y, d.K);
+        const uint32_t g2 = 1u + __umulhi(x.z, d.K);
+        const uint32_t g3 = 1u + __umulhi(x.w, d.K);
+        const uint64_t s4 = static_cast<uint64_t>(g0) + g1 + g2 + g3;
+        const uint64_t incl = warp_inclusive_scan(s4);
+        if (lane == 31u) s_tot[warp] = incl;
+        __syncthreads();
+        uint64_t off = 0, tot = 0;
+#pragma unroll
+        for (int v = 0; v < kJitWarps; ++v) {
+            const uint64_t t = s_tot[v];
+            off += v < static_cast<int>(warp) ? t : 0;
+            tot += t;
+        }
+        const int64_t q0 = carry + static_cast<int64_t>(off + incl - s4) + g0;
+        const int64_t q1 = q0 + g1, q2 = q1 + g2, q3 = q2 + g3;
+        if (q0 < n_post) {
+            float w[4];
+            jit_weights<WK>(d, blk, row, w);
+            const uint64_t kb = 4ull * blk;
+            f(q0, kb, w[0]);
+            ++count;
+            if (q1 < n_post) { f(q1, kb + 1, w[1]); ++count; }
+            if (q2 < n_post) { f(q2, kb + 2, w[2]); ++count; }
+            if (q3 < n_post) { f(q3, kb + 3, w[3]); ++count; }
+        }
+        carry += static_cast<int64_t>(tot);
+        __syncthreads();  // s_tot is rewritten next round
+        if (carry >= n_post - 1) break;
+    }
+    return count;
+}
+
 // Event scatter of JIT rows.  SMEM: the CTA accumulates all n_post columns
-// (two vectors with SPLIT) in shared memory of `wpad` entries each.
+// (two vectors with SPLIT) in shared memory of `wpad` entries each.  With
+// few rows compared with the warps and long rows (expected length 2 n_post /
+// (K + 1) of 512 or more) each row is walked by a whole CTA (jit_walk_cta)
+// instead of one warp.
 template <typename Acc, int WK, bool SPLIT, bool SMEM>
 __global__ void __launch_bounds__(kJitThreads) k_jit_scatter(JitArgs lo, JitArgs hi, int64_t split, int64_t n_post,
                                                              const int32_t* __restrict__ spike_list,
@@ -39,14 +93,30 @@ __global__ void __launch_bounds__(kJitThreads) k_jit_scatter(JitArgs lo, JitArgs
     ns = ns < max_spikes ? ns : max_spikes;
     const int64_t nwarps = static_cast<int64_t>(gridDim.x) * kJitWarps;
     int64_t ev = 0;
-    for (int64_t u = static_cast<int64_t>(blockIdx.x) * kJitWarps + (threadIdx.x >> 5); u < ns; u += nwarps) {
-        const int32_t i = spike_list[u];
-        if (i < 0) continue;
-        const bool upper = SPLIT && i >= split;
-        const JitArgs& d = upper ? hi : lo;
-        const uint32_t row = static_cast<uint32_t>(upper ? i - split : i);
-        Acc* out = SMEM ? (acc + (upper ? wpad : 0)) : (upper ? y_hi : y);
-        ev += jit_walk<WK>(d, row, n_post, [&](int64_t q, uint64_t, float w) { acc_add(out + q, event_value<Acc>(w)); });
+    const uint32_t kmin = lo.K < hi.K ? lo.K : hi.K;
+    const int64_t est_len = 2 * n_post / (static_cast<int64_t>(kmin) + 1);
+    if (ns * 4 <= nwarps && est_len >= 512) {
+        for (int64_t u = blockIdx.x; u < ns; u += gridDim.x) {
+            const int32_t i = spike_list[u];
+            if (i < 0) continue;
+            const bool upper = SPLIT && i >= split;
+            const JitArgs& d = upper ? hi : lo;
+            const uint32_t row = static_cast<uint32_t>(upper ? i - split : i);
+            Acc* out = SMEM ? (acc + (upper ? wpad : 0)) : (upper ? y_hi : y);
+            ev += jit_walk_cta<WK>(d, row, n_post,
+                                   [&](int64_t q, uint64_t, float w) { acc_add(out + q, event_value<Acc>(w)); });
+        }
+    } else {
+        for (int64_t u = static_cast<int64_t>(blockIdx.x) * kJitWarps + (threadIdx.x >> 5); u < ns; u += nwarps) {
+            const int32_t i = spike_list[u];
+            if (i < 0) continue;
+            const bool upper = SPLIT && i >= split;
+            const JitArgs& d = upper ? hi : lo;
+            const uint32_t row = static_cast<uint32_t>(upper ? i - split : i);
+            Acc* out = SMEM ? (acc + (upper ? wpad : 0)) : (upper ? y_hi : y);
+            ev += jit_walk<WK>(d, row, n_post,
+                               [&](int64_t q, uint64_t, float w) { acc_add(out + q, event_value<Acc>(w)); });
+        }
     }
     if constexpr (SMEM) {
         __syncthreads();

@@ -279,8 +279,10 @@ def test_jit_materialized_weights(wkind, w0, w1):
     assert rel_err(data.cpu().numpy(), edata) < RTOL_F32
 
 
+# (2000, 100000, 0.01, 0.05) and (500, 50000, 0.05, 0.1): few long rows, walked
+# by whole CTAs (L2 and shared-memory accumulation)
 @pytest.mark.parametrize("n_pre,n_post,p,rho", [(3000, 3000, 0.05, 0.1), (2000, 100000, 0.01, 0.05),
-                                                (50000, 60000, 0.001, 0.01)])
+                                                (50000, 60000, 0.001, 0.01), (500, 50000, 0.05, 0.1)])
 @pytest.mark.parametrize("flags", [0, B.BP_ACC_GLOBAL])
 def test_jitconn_event_mv_counts_bit_exact(n_pre, n_post, p, rho, flags):
     seed = 99 + n_pre
@@ -314,6 +316,20 @@ def test_jitconn_float_products(wkind, w0, w1):
     B.bp_jitconn_event_mv_bwd(d, cuda(dy), dx)
     assert rel_err(dx.cpu().numpy(), orc.jitconn_mv_t(seed, K, n_pre, n_post, dy.astype(np.float64), wkind, w0,
                                                       w1)) < RTOL_F32
+
+
+@pytest.mark.parametrize("wkind,w0,w1", [(B.BP_JIT_UNIFORM, 0.0, 1.0), (B.BP_JIT_NORMAL, 0.5, 0.1)])
+def test_jitconn_float_few_long_rows(wkind, w0, w1):
+    """About 30 spiking rows of ~1 600 targets: the whole-CTA row walk with
+    drawn weights against the oracle."""
+    n_pre, n_post, p, seed = 300, 80000, 0.02, 41
+    K = orc.jit_K(p)
+    d = B.bp_jit_desc_init(seed, p, wkind, w0, w1)
+    ev = wl.bernoulli_spikes(n_pre, 0.1, seed=42)
+    sl, ns = spike_list_of(ev)
+    y = torch.zeros(n_post, dtype=torch.float32, device="cuda")
+    B.bp_jitconn_event_mv(d, n_pre, sl, ns, y)
+    assert rel_err(y.cpu().numpy(), orc.jitconn_event_mv(seed, K, n_pre, n_post, ev, wkind, w0, w1)) < RTOL_F32
 
 
 def test_jit_and_stored_csr_agree_on_gpu():
