@@ -508,9 +508,10 @@ bp_status bp_snn_desc_default(bp_snn_desc* d);
 
 /* Device workspace (bytes, 256-byte aligned) shared by forward and backward:
  * checkpoints, the recorded spike bits of every step, one segment of
- * potentials and the gradient partials of each batch element (summed over the
- * batch in a fixed order, so gradients are reproducible bit for bit).  0 for
- * an invalid desc. */
+ * potentials, the gradient partials of each batch element (summed over the
+ * batch in a fixed order, so gradients are reproducible bit for bit) and the
+ * recurrent weights in the fixed-point form the forward delivers them in.  0
+ * for an invalid desc. */
 size_t bp_snn_workspace_bytes(const bp_snn_desc* d);
 
 /* Forward pass over T steps: u uint8 [B][T][n_in] (input spikes), m float

@@ -28,7 +28,9 @@
 // recomputed from its checkpoint storing Vp_t, with the recorded spikes
 // replayed rather than re-decided (the shared-memory float atomics may round
 // differently from the forward, and a near-threshold neuron must not take
-// the other branch); the adjoint then runs back through the segment.
+// the other branch); the adjoint then runs back through the segment.  The
+// recurrent weights are converted to fixed point once per forward call
+// (k_snn_fix_weights), so delivering an event is one integer atomic.
 // Recurrent weights are FP32 or BF16 (FP32 arithmetic); gradients are FP32,
 // accumulated with atomics across batch elements.
 #include <cmath>
@@ -90,6 +92,7 @@ struct SnnK {
     float* g_out;        // [B][n_rec][n_out]
     float* g_b;          // [B][n_out]
     double* vreg;        // [B]  regulariser sums of the forward
+    unsigned long long* w_fix;  // [nnz] recurrent weights in fixed point (filled by the forward)
     int64_t nnz;
     int32_t n_ck, zw;
 };
@@ -199,15 +202,23 @@ __device__ __forceinline__ void neuron_step(const SnnK& p, float* I, float* V, u
 }
 
 // racc[col] += w for every entry of the rows in spk[0..n) (one warp per row),
-// in fixed point.
-template <int WK>
+// in fixed point (the weights were converted once per call, so a delivered
+// event is one integer shared-memory atomic).
 __device__ __forceinline__ void deliver(const SnnK& p, const int32_t* spk, int n, unsigned long long* racc) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int e = warp; e < n; e += kSnnThreads / 32) {
         const int i = spk[e];
         const int64_t b0 = p.indptr[i], b1 = p.indptr[i + 1];
-        for (int64_t j = b0 + lane; j < b1; j += 32) atomicAdd(racc + p.indices[j], to_fix(w_at<WK>(p.w_rec, j)));
+        for (int64_t j = b0 + lane; j < b1; j += 32) atomicAdd(racc + p.indices[j], p.w_fix[j]);
     }
+}
+
+// w_fix[j] = to_fix(w_rec[j]) for all stored recurrent weights.
+template <int WK>
+__global__ void k_snn_fix_weights(const void* __restrict__ w, int64_t nnz, unsigned long long* __restrict__ w_fix) {
+    for (int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; j < nnz;
+         j += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        w_fix[j] = to_fix(w_at<WK>(w, j));
 }
 
 template <int WK>
@@ -245,7 +256,7 @@ __global__ void __launch_bounds__(kSnnThreads, 1) k_snn_forward(SnnK p, const ui
                     p.z_all + (static_cast<int64_t>(b) * p.T + t) * p.zw, nullptr, p.sg.reg_on ? &reg : nullptr);
         __syncthreads();
         const int n = s_cnt[1];
-        deliver<WK>(p, spk, n, racc);
+        deliver(p, spk, n, racc);
         {
             // W_out^T z_t: one warp per output, lanes over the recorded spike words
             // in a fixed order and a fixed reduction tree, so the readout is reproducible
@@ -337,7 +348,7 @@ __global__ void __launch_bounds__(kSnnThreads, 1) k_snn_backward(SnnK p, const u
             }
         }
         __syncthreads();
-        deliver<WK>(p, spk, s_cnt[1], racc);
+        deliver(p, spk, s_cnt[1], racc);
         __syncthreads();
         for (int t = t0; t < t1; ++t) {
             const int n_act = gather_inputs(u + (static_cast<int64_t>(b) * p.T + t) * p.n_in, p.n_in, in_list, &s_cnt[0]);
@@ -346,7 +357,7 @@ __global__ void __launch_bounds__(kSnnThreads, 1) k_snn_backward(SnnK p, const u
             neuron_step(p, I, V, racc, in_list, n_act, spk, &s_cnt[1], segVp + static_cast<int64_t>(t - t0) * p.n_rec,
                         nullptr, zall + static_cast<int64_t>(t) * p.zw, nullptr);
             __syncthreads();
-            deliver<WK>(p, spk, s_cnt[1], racc);
+            deliver(p, spk, s_cnt[1], racc);
             __syncthreads();
         }
         // ---- adjoint, t = t1-1 .. t0
@@ -490,7 +501,7 @@ __global__ void k_snn_reg_add(int32_t B, double scale, const double* __restrict_
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct SnnLayout {
-    size_t ck_I, ck_V, ck_y, z_all, seg_Vp, g_in, g_rec, g_out, g_b, vreg, total;
+    size_t ck_I, ck_V, ck_y, z_all, seg_Vp, g_in, g_rec, g_out, g_b, vreg, w_fix, total;
     int32_t n_ck, zw;
 };
 
@@ -512,6 +523,7 @@ SnnLayout snn_layout(const bp_snn_desc& d) {
     L.g_out = o; o = align256(o + B * static_cast<size_t>(d.n_rec) * d.n_out * 4);
     L.g_b = o; o = align256(o + B * static_cast<size_t>(d.n_out) * 4);
     L.vreg = o; o = align256(o + B * 8);
+    L.w_fix = o; o = align256(o + static_cast<size_t>(d.nnz > 0 ? d.nnz : 0) * 8);
     L.total = o;
     return L;
 }
@@ -588,6 +600,7 @@ SnnK snn_kernel_args(const bp_snn_desc& d, void* ws) {
     p.g_out = reinterpret_cast<float*>(w + L.g_out);
     p.g_b = reinterpret_cast<float*>(w + L.g_b);
     p.vreg = reinterpret_cast<double*>(w + L.vreg);
+    p.w_fix = reinterpret_cast<unsigned long long*>(w + L.w_fix);
     p.nnz = d.nnz;
     p.n_ck = L.n_ck;
     p.zw = L.zw;
@@ -642,6 +655,17 @@ bp_status bp_snn_forward(const bp_snn_desc* d, const uint8_t* u, float* m, void*
     const bp::SnnK p = bp::snn_kernel_args(*d, workspace);
     // racc (8 B), I, V, spike list (4 B each) per neuron, plus the input list
     const size_t smem = static_cast<size_t>(d->n_rec) * (8 + 4 * 3) + static_cast<size_t>(d->n_in) * 4;
+    // recurrent weights in fixed point, once per call (the backward's
+    // recomputation reads them from the same workspace)
+    if (d->nnz > 0) {
+        int64_t grid = (d->nnz + 255) / 256;
+        if (grid > bp::sm_count() * 8) grid = bp::sm_count() * 8;
+        if (d->w_rec_kind == BP_W_BF16)
+            bp::k_snn_fix_weights<BP_W_BF16><<<static_cast<unsigned>(grid), 256, 0, stream>>>(d->w_rec, d->nnz, p.w_fix);
+        else
+            bp::k_snn_fix_weights<BP_W_F32><<<static_cast<unsigned>(grid), 256, 0, stream>>>(d->w_rec, d->nnz, p.w_fix);
+        BP_LAUNCHED();
+    }
     if (d->w_rec_kind == BP_W_BF16) {
         BP_TRY(bp::set_smem(bp::k_snn_forward<BP_W_BF16>, smem));
         bp::k_snn_forward<BP_W_BF16><<<d->B, bp::kSnnThreads, smem, stream>>>(p, u, m);
