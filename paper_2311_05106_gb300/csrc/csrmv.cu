@@ -3,9 +3,10 @@
 // and the post-column tile index.
 //
 // Work decomposition.  A "group" of G lanes (G in {4, 8, 16, 32}, chosen on
-// the device from the mean segment length) walks one spiking row's segment
-// with coalesced, evict-first loads of indices and weights, four strided
-// loads in flight per lane.  Two accumulation modes:
+// the device from the mean segment length; widened up to the whole CTA when a
+// call delivers too few rows to keep the lanes busy) walks one spiking row's
+// segment with coalesced, evict-first loads of indices and weights, four
+// strided loads in flight per lane.  Two accumulation modes:
 //   direct  -- atomics straight into y in L2; right when the step delivers
 //              few events compared with n_post (the network steps).
 //   tiled   -- CTA (s, r) owns post columns [s W, (s+1) W) in shared memory
@@ -14,7 +15,9 @@
 //              row when one tile covers n_post).  Shared-memory atomics absorb
 //              the scatter; the tile is flushed to y once, skipping zeros.
 // In auto mode each CTA reads the spike count and picks the mode from the
-// expected number of events, so no host synchronisation is needed.
+// expected number of events, so no host synchronisation is needed.  The
+// gather form reads x through L1/L2, or, given a tile index, stages x in
+// shared memory one post tile at a time.
 #include "bp_common.cuh"
 #include "bp_internal.h"
 #include "bp_rows.cuh"

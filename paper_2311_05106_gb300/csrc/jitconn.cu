@@ -9,7 +9,8 @@
 // Weights come from their own counter streams (1: uniform, 2: normal) at the
 // same synapse index, so any synapse can be regenerated independently.
 // Accumulation: the whole postsynaptic vector in shared memory when it fits
-// (flushed once per CTA, skipping zeros), otherwise atomics into L2.
+// (flushed once per CTA, skipping zeros), otherwise atomics into L2.  Calls
+// with few, long rows walk each row with a whole CTA (jit_walk_cta).
 #include "bp_common.cuh"
 #include "bp_internal.h"
 #include "bp_rows.cuh"
