@@ -81,6 +81,11 @@ __global__ void __launch_bounds__(kStepThreads, 4) k_step(StepArgs a) {
     Y* __restrict__ yi = static_cast<Y*>(a.yi_in);
     Y* out_e = static_cast<Y*>(a.ye_out);
     Y* out_i = static_cast<Y*>(a.yi_out);
+    // programmatic dependent launch (network steps on a partial wave): wait
+    // for the previous step's grid and its memory, then let the next step's
+    // grid be scheduled; both return at once for an ordinary launch
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     if (a.clear_counter && blockIdx.x == 0 && threadIdx.x == 0) *a.clear_counter = 0;
     // RING (a delayed projection): step t appends its spikes to list
     // t mod S and delivers the lists of steps t - d; the count of list
@@ -434,6 +439,26 @@ bp_status launch_k(K kernel, const StepArgs& a, int vec, cudaStream_t s) {
     if (grid > need_max) grid = need_max;
     if (grid < need_min) grid = need_min;
     if (grid < 1) grid = 1;
+    // a network step whose grid fills at most half a resident wave is launched
+    // with programmatic stream serialisation, so its CTAs are scheduled while
+    // the previous step finishes (measured: 4-8 % fewer us per step on the
+    // 4 000-neuron network; 5 % more at 64 % of a wave, 3 % more on full
+    // waves, where it is not used)
+    const int64_t wave = static_cast<int64_t>(sm_count()) * resident_per_sm(reinterpret_cast<const void*>(kernel));
+    if (a.ctrl && 2 * grid <= wave) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(static_cast<unsigned>(grid));
+        cfg.blockDim = dim3(kStepThreads);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        BP_CUDA(cudaLaunchKernelEx(&cfg, kernel, a));
+        return BP_OK;
+    }
     kernel<<<static_cast<unsigned>(grid), kStepThreads, 0, s>>>(a);
     BP_LAUNCHED();
     return BP_OK;
