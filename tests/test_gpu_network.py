@@ -359,3 +359,16 @@ def test_full_size_align_pre_step_sampled():
     assert np.max(np.abs(got_i - gi)) / scale_i < 1e-5
     assert ge.max() > 0 and gi.max() > 0
     gpu.close()
+
+
+@pytest.mark.parametrize("n_e", [4000, 0])
+def test_single_population_networks(n_e):
+    """Only excitatory (n_e = n) or only inhibitory (n_e = 0) neurons: the
+    raster equals the oracle's until an explained near-threshold flip."""
+    n, seed, p = 4000, 2024, 0.02
+    V0 = wl.coba_v0(n, seed=7)
+    ref = oracle_net(n, n_e, seed, p, V0.astype(np.float64), "jit")
+    gpu = CobaNetwork(n, n_e=n_e, conn="jit", seed=seed, p=p, V0=V0, keep_spk=True)
+    same = compare_free_run(ref, gpu, 300)
+    assert same >= 20
+    gpu.close()

@@ -360,3 +360,67 @@ def test_invalid_arguments_rejected_on_host():
     with pytest.raises(B.BpError):   # max_spikes beyond n_pre
         B.bp_jitconn_event_mv(d, 10, sl, ns, y, max_spikes=11)
     assert B.bp_sync_status() == 0
+
+
+# ---------------------------------------------------------------------- degenerate cases
+@pytest.mark.parametrize("n_post", [1000, 70000])
+def test_jit_p_one_hits_every_column(n_post):
+    """p = 1 gives K = 1: every gap is 1, so every spiking row targets every
+    column once; counts equal the number of spikes everywhere (and the
+    oracle's), in shared-memory (n_post <= 57 344) and L2 accumulation."""
+    n_pre = 300
+    d = B.bp_jit_desc_init(5, 1.0)
+    assert d.K == 1
+    ev = wl.bernoulli_spikes(n_pre, 0.3, seed=6)
+    sl, ns = spike_list_of(ev)
+    y = torch.zeros(n_post, dtype=torch.int32, device="cuda")
+    B.bp_jitconn_event_mv(d, n_pre, sl, ns, y)
+    got = y.cpu().numpy()
+    assert np.all(got == int(ev.sum()))
+    assert np.array_equal(got, orc.jitconn_event_mv(5, 1, n_pre, n_post, ev).astype(np.int64))
+
+
+@pytest.mark.parametrize("flags", [0, B.BP_ACC_GLOBAL, B.BP_ACC_SHARED])
+def test_scatter_into_one_column(flags):
+    """Every row holds the single column 0: all events collide on one
+    accumulator (integer counts: exactly the number of spikes)."""
+    n_pre = 50000
+    ip = np.arange(n_pre + 1, dtype=np.int64)
+    ix = np.zeros(n_pre, np.int32)
+    ev = wl.bernoulli_spikes(n_pre, 0.5, seed=9)
+    sl, ns = spike_list_of(ev)
+    y = torch.zeros(1, dtype=torch.int32, device="cuda")
+    B.bp_event_csrmv(cuda(ip), cuda(ix), None, 1.0, sl, ns, y, flags=flags)
+    assert int(y.item()) == int(ev.sum())
+
+
+def test_matrix_without_entries():
+    """No stored entries at all: the scatter and both gather forms leave their
+    outputs as they were."""
+    n_pre, n_post = 5000, 100000
+    ip = cuda(np.zeros(n_pre + 1, np.int64))
+    ix = cuda(np.zeros(1, np.int32))
+    ev = wl.bernoulli_spikes(n_pre, 0.2, seed=10)
+    sl, ns = spike_list_of(ev)
+    y = torch.full((n_post,), 3, dtype=torch.int32, device="cuda")
+    B.bp_event_csrmv(ip, ix, None, 1.0, sl, ns, y)
+    assert torch.all(y == 3)
+    x = torch.ones(n_post, dtype=torch.float32, device="cuda")
+    tc = B.bp_tile_cols()
+    tp = torch.empty(B.bp_csr_tile_index_size(n_pre, n_post, tc), dtype=torch.int32, device="cuda")
+    B.bp_csr_tile_index(ip, ix, n_post, tc, tp)
+    for kw in ({}, {"tile_ptr": tp, "tile_cols": tc}):
+        yp = torch.full((n_pre,), 0.5, dtype=torch.float32, device="cuda")
+        B.bp_event_csrmv_t(ip, ix, None, 1.0, x, yp, **kw)
+        assert torch.all(yp == 0.5)
+
+
+def test_lif_step_with_no_neurons():
+    p = B.bp_coba_params_default()
+    z = lambda dt: torch.zeros(0, dtype=dt, device="cuda")
+    sl = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ns = torch.zeros(1, dtype=torch.int32, device="cuda")
+    B.bp_lif_step(p, 0, z(torch.float32), z(torch.float32), z(torch.float32), z(torch.int32), z(torch.int32),
+                  z(torch.int32), sl, ns)
+    torch.cuda.synchronize()
+    assert int(ns.item()) == 0
