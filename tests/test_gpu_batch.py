@@ -88,3 +88,31 @@ def test_autotune_restores_state_and_continues():
 def test_batch_rejects_oversized_network():
     with pytest.raises(B.BpError):
         BatchedNetworks(np.array([70000]), np.array([1], np.uint64))
+
+
+def test_full_size_batch_networks_equal_single_path():
+    """The batched configuration as the bench runs it: 256 networks,
+    N ~ U[1000, 50000] (seed 11), autotuned, 200 steps; four networks
+    (including the largest and the smallest) equal the single-network path
+    bit for bit, and the totals are consistent."""
+    sizes = wl.batched_sizes(256, 1000, 50000, seed=11)
+    seeds = np.arange(256, dtype=np.uint64) * np.uint64(7919) + np.uint64(2024)
+    V0 = [wl.coba_v0(int(n), seed=1000 + b) for b, n in enumerate(sizes)]
+    bat = BatchedNetworks(sizes, seeds, V0=V0)
+    bat.autotune(probe_steps=10)
+    T = 200
+    bat.simulate(T)
+    torch.cuda.synchronize()
+    picks = sorted({int(np.argmax(sizes)), int(np.argmin(sizes)), 17, 200})
+    for b in picks:
+        single = CobaNetwork(int(sizes[b]), conn="jit", seed=int(seeds[b]), V0=V0[b])
+        single.simulate(T)
+        assert torch.equal(bat.view(bat.V, b), single.V), b
+        assert torch.equal(bat.view(bat.ref, b), single.ref), b
+        t = bat.totals[b].cpu().numpy()
+        s = single.totals.cpu().numpy()
+        assert t[0] == s[0] and t[1] == s[1] and t[2] == s[2] and t[3] == T
+        single.close()
+    tot = bat.totals.cpu().numpy()
+    assert np.all(tot[:, 3] == T) and tot[:, 0].sum() > 0
+    bat.close()

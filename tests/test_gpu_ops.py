@@ -424,3 +424,29 @@ def test_lif_step_with_no_neurons():
                   z(torch.int32), sl, ns)
     torch.cuda.synchronize()
     assert int(ns.item()) == 0
+
+
+def test_full_size_operator_cell():
+    """A graded operator cell at full size: n = 1e6, p = 0.001 (1e9 stored
+    entries), rho = 0.1 (about 1e8 events), matrix = the JIT rows
+    materialised.  The scatter's integer counts equal the oracle's over the
+    whole output vector bit for bit (tiled shared-memory path, as timed), and
+    the tiled gather of a random x matches the oracle's sequential sum."""
+    n, p, seed = 1_000_000, 0.001, 1000 + 1_000_000 % 997 + 10
+    d = B.bp_jit_desc_init(seed, p)
+    ip, ix, _ = B.jit_materialize(d, n, n)
+    tc = B.bp_tile_cols()
+    tp = torch.empty(B.bp_csr_tile_index_size(n, n, tc), dtype=torch.int32, device="cuda")
+    B.bp_csr_tile_index(ip, ix, n, tc, tp)
+    ev = wl.bernoulli_spikes(n, 0.1, seed=seed + 1000)
+    sl, ns = spike_list_of(ev)
+    y = torch.zeros(n, dtype=torch.int32, device="cuda")
+    B.bp_event_csrmv(ip, ix, None, 1.0, sl, ns, y, tile_ptr=tp, tile_cols=tc)
+    h_ip, h_ix = ip.cpu().numpy(), ix.cpu().numpy()
+    expect = orc.event_csr_count(h_ip, h_ix, ev, n)
+    assert np.array_equal(y.cpu().numpy(), expect.astype(np.int64))
+    x = np.random.default_rng(11).normal(size=n).astype(np.float32)
+    yp = torch.zeros(n, dtype=torch.float32, device="cuda")
+    B.bp_event_csrmv_t(ip, ix, None, 1.0, cuda(x), yp, tile_ptr=tp, tile_cols=tc)
+    ref = orc.csrmv_t(h_ip, h_ix, None, x.astype(np.float64))
+    assert rel_err(yp.cpu().numpy(), ref) < RTOL_F32
