@@ -387,6 +387,19 @@ bp_status bp_network_reset_counters(bp_net* net, bp_stream_t stream);
 /* One time step (a1-a5/a6 above). */
 bp_status bp_network_step(bp_net* net, bp_stream_t stream);
 
+/* Checkpoint / resume.  The network's state lives in the caller's buffers
+ * named in bp_net_desc (V, ge, gi, ref, both halves of ye and yi, the delay
+ * ring, the AlignPre traces, spk, n_spikes and totals); the library keeps one
+ * more number, the count of steps since the last reset, which selects the
+ * accumulator half, the counter slot and the delay-ring slot of the next
+ * step.  To checkpoint, copy those buffers and read the count; to resume (on
+ * this or a new network with the same desc layout), write the buffers back
+ * and set the count.  bp_network_step_count returns the count of the steps
+ * enqueued so far (-1 for a NULL handle); bp_network_set_step_count enqueues
+ * the new count on `stream` (step >= 0). */
+int64_t bp_network_step_count(const bp_net* net);
+bp_status bp_network_set_step_count(bp_net* net, int64_t step, bp_stream_t stream);
+
 /* T steps.  On its first call builds and caches a CUDA graph of a chunk of
  * steps (captured on a private stream), then launches it on `stream`;
  * record int32 [T][2] (nullable) receives the E and I spike counts of each

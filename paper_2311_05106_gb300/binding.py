@@ -110,6 +110,8 @@ _SIGS = {
     "bp_network_create": (c_i32, [ctypes.POINTER(NetDesc), ctypes.POINTER(VP)]),
     "bp_network_reset_counters": (c_i32, [VP, VP]),
     "bp_network_step": (c_i32, [VP, VP]),
+    "bp_network_step_count": (c_i64, [VP]),
+    "bp_network_set_step_count": (c_i32, [VP, c_i64, VP]),
     "bp_simulate": (c_i32, [VP, c_i64, VP, VP]),
     "bp_network_stats": (c_i32, [VP, VP, VP]),
     "bp_network_destroy": (c_i32, [VP]),
@@ -352,6 +354,14 @@ def bp_network_create(desc: NetDesc):
 
 def bp_network_reset_counters(net, stream=None):
     _check("bp_network_reset_counters", lib().bp_network_reset_counters(net, _stream(stream)))
+
+
+def bp_network_step_count(net) -> int:
+    return int(lib().bp_network_step_count(net))
+
+
+def bp_network_set_step_count(net, step, stream=None):
+    _check("bp_network_set_step_count", lib().bp_network_set_step_count(net, int(step), _stream(stream)))
 
 
 def bp_network_step(net, stream=None):

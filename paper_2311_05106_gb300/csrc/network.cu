@@ -46,6 +46,8 @@ __global__ void k_set_record(NetCtrl* ctrl, int32_t* record, int64_t len) {
     ctrl->record_len = len;
 }
 
+__global__ void k_set_step(NetCtrl* ctrl, int64_t step) { ctrl->step = step; }
+
 __global__ void k_reset_ctrl(NetCtrl* ctrl) {
     ctrl->step = 0;
     ctrl->record = nullptr;
@@ -217,6 +219,18 @@ bp_status bp_network_reset_counters(bp_net* net, bp_stream_t stream) {
     bp::k_reset_ctrl<<<1, 1, 0, stream>>>(net->ctrl);
     BP_LAUNCHED();
     net->host_step = 0;
+    return BP_OK;
+}
+
+int64_t bp_network_step_count(const bp_net* net) { return net ? net->host_step : -1; }
+
+bp_status bp_network_set_step_count(bp_net* net, int64_t step, bp_stream_t stream) {
+    bp::clear_error();
+    BP_REQUIRE(net, "net is NULL");
+    BP_REQUIRE(step >= 0, "step < 0");
+    bp::k_set_step<<<1, 1, 0, stream>>>(net->ctrl, step);
+    BP_LAUNCHED();
+    net->host_step = step;
     return BP_OK;
 }
 

@@ -122,6 +122,23 @@ class CobaNetwork:
     def reset_counters(self):
         B.bp_network_reset_counters(self.handle)
 
+    def state_tensors(self):
+        """The caller-owned buffers that hold the network's state."""
+        names = ("V", "ge", "gi", "ref", "ye", "yi", "n_spikes", "totals", "spk", "spike_list", "delay_buf", "trace")
+        return {k: getattr(self, k) for k in names if getattr(self, k, None) is not None}
+
+    def checkpoint(self):
+        """A copy of the state (device tensors) and the step count."""
+        return {"step": B.bp_network_step_count(self.handle),
+                "state": {k: t.clone() for k, t in self.state_tensors().items()}}
+
+    def restore(self, ckpt):
+        """Writes a checkpoint back (into this network or a new one of the
+        same configuration) so that the simulation resumes where it was taken."""
+        for k, t in self.state_tensors().items():
+            t.copy_(ckpt["state"][k])
+        B.bp_network_set_step_count(self.handle, ckpt["step"])
+
     def step(self):
         B.bp_network_step(self.handle)
 
