@@ -216,6 +216,18 @@ bp_status bp_csr_tile_index(int64_t n_pre, int64_t n_post, const int64_t* indptr
                             const int32_t* indices, int32_t tile_cols, int32_t* tile_ptr,
                             bp_stream_t stream);
 
+/* Validation of a CSR before use (the products trust their operands and do
+ * not check indices on the hot path): one device pass over indices [nnz]
+ * (the buffer's length) writes int64 counts out[4] = {invalid row extents
+ * (indptr[i+1] < indptr[i], an extent outside [0, nnz]; plus one if
+ * indptr[0] != 0 or indptr[n_pre] != nnz), entries whose index is outside
+ * [0, n_post), rows not sorted ascending (bp_csr_tile_index needs sorted
+ * rows), sorted rows with a repeated column}.  Rows with an invalid extent are
+ * not read.  A matrix is safe for every product when the first two counts
+ * are 0.  out is device memory, overwritten. */
+bp_status bp_csr_check(int64_t n_pre, int64_t n_post, int64_t nnz, const int64_t* indptr, const int32_t* indices,
+                       int64_t* out, bp_stream_t stream);
+
 /* Gather ("transpose") form over the same CSR, all rows (Section 3.1: every
  * operator has reverse-mode rules; this is the product with W rather than
  * W^T):  y_pre[i] += sum_{j in row i} w_j x_post[indices[j]].

@@ -99,6 +99,7 @@ _SIGS = {
     "bp_event_csrmv_dense_noalloc": (c_i32, [c_i64, c_i64, VP, VP, VP, c_i32, c_f32, VP, VP, c_i32, c_u32, VP]),
     "bp_csr_tile_index_size": (c_i64, [c_i64, c_i64, c_i32]),
     "bp_csr_tile_index": (c_i32, [c_i64, c_i64, VP, VP, c_i32, VP, VP]),
+    "bp_csr_check": (c_i32, [c_i64, c_i64, c_i64, VP, VP, VP, VP]),
     "bp_event_csrmv_t": (c_i32, [c_i64, c_i64, VP, VP, VP, c_i32, c_f32, VP, VP, VP, c_i32, c_u32, VP]),
     "bp_event_csrmv_bwd": (c_i32, [c_i64, c_i64, VP, VP, VP, c_i32, c_f32, VP, VP, c_i64, VP, VP, VP, VP, c_i32, VP]),
     "bp_jit_desc_init": (c_i32, [ctypes.POINTER(JitDesc), c_u64, c_f64, c_i32, c_f32, c_f32]),
@@ -279,6 +280,13 @@ def bp_csr_tile_index_size(n_pre, n_post, tile_cols) -> int:
 def bp_csr_tile_index(indptr, indices, n_post, tile_cols, tile_ptr, stream=None):
     _check("bp_csr_tile_index", lib().bp_csr_tile_index(indptr.numel() - 1, n_post, _p(indptr), _p(indices),
                                                         int(tile_cols), _p(tile_ptr), _stream(stream)))
+
+
+def bp_csr_check(indptr, indices, n_post, out, stream=None):
+    """out int64 [4]: bad row extents, out-of-range indices, unsorted rows,
+    rows with repeated columns."""
+    _check("bp_csr_check", lib().bp_csr_check(indptr.numel() - 1, int(n_post), indices.numel(), _p(indptr),
+                                              _p(indices), _p(out), _stream(stream)))
 
 
 def bp_event_csrmv_t(indptr, indices, data, w_homo, x_post, y_pre, flags=0, stream=None, tile_ptr=None, tile_cols=0):

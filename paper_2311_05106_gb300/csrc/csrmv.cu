@@ -345,6 +345,46 @@ __global__ void __launch_bounds__(256) k_csr_dw(CsrArgs a, const int32_t* __rest
     }
 }
 
+// CSR validation: a warp per row counts a bad extent, out-of-range indices,
+// descending neighbours and repeated neighbours (the last two only make sense
+// for a valid extent); counts are summed with one atomic per warp and kind.
+__global__ void __launch_bounds__(256) k_csr_check(int64_t n_pre, int64_t n_post, int64_t nnz,
+                                                   const int64_t* __restrict__ indptr,
+                                                   const int32_t* __restrict__ indices,
+                                                   unsigned long long* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = static_cast<int64_t>(gridDim.x) * (blockDim.x / 32);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (indptr[0] != 0) atomicAdd(out + 0, 1ull);
+        if (indptr[n_pre] != nnz) atomicAdd(out + 0, 1ull);
+    }
+    for (int64_t i = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) / 32; i < n_pre; i += nwarps) {
+        const int64_t b0 = indptr[i], b1 = indptr[i + 1];
+        if (b1 < b0 || b0 < 0 || b1 > nnz) {
+            if (lane == 0) atomicAdd(out + 0, 1ull);
+            continue;
+        }
+        unsigned long long bad = 0, desc = 0, dup = 0;
+        for (int64_t j = b0 + lane; j < b1; j += 32) {
+            const int32_t c = indices[j];
+            if (c < 0 || c >= n_post) ++bad;
+            if (j > b0) {
+                const int32_t prev = indices[j - 1];
+                if (prev > c) ++desc;
+                if (prev == c) ++dup;
+            }
+        }
+        bad = group_reduce_sum(bad, 32);
+        desc = group_reduce_sum(desc, 32);
+        dup = group_reduce_sum(dup, 32);
+        if (lane == 0) {
+            if (bad) atomicAdd(out + 1, bad);
+            if (desc) atomicAdd(out + 2, 1ull);
+            if (dup && !desc) atomicAdd(out + 3, 1ull);
+        }
+    }
+}
+
 // tile_ptr[i (S+1) + s] = lower_bound(row i, s W) - indptr[i].
 __global__ void k_tile_index(int64_t n_pre, const int64_t* __restrict__ indptr, const int32_t* __restrict__ indices,
                              int32_t W, int32_t S, int32_t* __restrict__ tile_ptr) {
@@ -567,6 +607,22 @@ bp_status bp_csr_tile_index(int64_t n_pre, int64_t n_post, const int64_t* indptr
     if (grid > bp::sm_count() * 32) grid = bp::sm_count() * 32;
     bp::k_tile_index<<<static_cast<unsigned>(grid), 256, 0, stream>>>(n_pre, indptr, indices, tile_cols, S,
                                                                        tile_ptr);
+    BP_LAUNCHED();
+    return BP_OK;
+}
+
+bp_status bp_csr_check(int64_t n_pre, int64_t n_post, int64_t nnz, const int64_t* indptr, const int32_t* indices,
+                       int64_t* out, bp_stream_t stream) {
+    bp::clear_error();
+    BP_REQUIRE(n_pre >= 0 && n_post >= 0 && nnz >= 0, "negative size");
+    BP_REQUIRE(indptr && out, "indptr or out is NULL");
+    BP_REQUIRE(nnz == 0 || indices, "indices is NULL");
+    BP_CUDA(cudaMemsetAsync(out, 0, 4 * sizeof(int64_t), stream));
+    int64_t grid = (n_pre * 32 + 255) / 256;
+    if (grid > bp::sm_count() * 16) grid = bp::sm_count() * 16;
+    if (grid < 1) grid = 1;
+    bp::k_csr_check<<<static_cast<unsigned>(grid), 256, 0, stream>>>(n_pre, n_post, nnz, indptr, indices,
+                                                                      reinterpret_cast<unsigned long long*>(out));
     BP_LAUNCHED();
     return BP_OK;
 }

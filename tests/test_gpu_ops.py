@@ -450,3 +450,28 @@ def test_full_size_operator_cell():
     B.bp_event_csrmv_t(ip, ix, None, 1.0, cuda(x), yp, tile_ptr=tp, tile_cols=tc)
     ref = orc.csrmv_t(h_ip, h_ix, None, x.astype(np.float64))
     assert rel_err(yp.cpu().numpy(), ref) < RTOL_F32
+
+
+def test_csr_check_counts_defects():
+    """bp_csr_check on a valid matrix reports nothing; planted defects (an
+    index past n_post, a negative index, a descending row, a repeated column,
+    an extent that runs past the buffer) are each counted, and rows with a bad
+    extent are not read."""
+    n_pre, n_post = 3000, 2000
+    ip, ix = _csr(n_pre, n_post, 0.01, seed=51)
+    out = torch.zeros(4, dtype=torch.int64, device="cuda")
+    B.bp_csr_check(cuda(ip), cuda(ix), n_post, out)
+    assert out.cpu().tolist() == [0, 0, 0, 0]
+    lens = np.diff(ip)
+    rows = [int(r) for r in np.nonzero(lens >= 3)[0][:4]]
+    bad = ix.copy()
+    bad[ip[rows[0] + 1] - 1] = n_post                                # out of range (last entry: still ascending)
+    bad[ip[rows[1]] + 1] = -1                                        # negative (and descending)
+    bad[ip[rows[2]]], bad[ip[rows[2]] + 1] = bad[ip[rows[2]] + 1], bad[ip[rows[2]]]   # descending
+    bad[ip[rows[3]] + 1] = bad[ip[rows[3]]]                          # repeated column
+    B.bp_csr_check(cuda(ip), cuda(bad), n_post, out)
+    assert out.cpu().tolist() == [0, 2, 2, 1]
+    bip = ip.copy()
+    bip[n_pre] = len(ix) + 100                                       # last row runs past the buffer
+    B.bp_csr_check(cuda(bip), cuda(ix), n_post, out)
+    assert out.cpu().tolist()[0] == 2                                # its extent, and indptr[n_pre] != nnz
