@@ -444,6 +444,7 @@ bp_status bp_batch_reset_counters(bp_batch* b, bp_stream_t stream) {
 
 bp_status bp_batch_simulate(bp_batch* b, int64_t T, bp_stream_t stream) {
     bp::clear_error();
+    const bp::NvtxRange nvtx("bp_batch_simulate");
     BP_REQUIRE(b, "batch is NULL");
     BP_REQUIRE(T >= 0, "T < 0");
     if (T == 0) return BP_OK;

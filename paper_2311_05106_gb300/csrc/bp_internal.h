@@ -7,7 +7,19 @@
 
 #include "bp.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace bp {
+
+// Host-side NVTX range around an entry point (a no-op unless a tool such as
+// a profiler is attached; ncu --nvtx can filter kernels by these ranges).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 
 // Post neurons per shared-memory tile: 56 Ki 4-byte accumulators (224 KiB)
 // fit one CTA per SM under the 227 KiB opt-in limit with room for the

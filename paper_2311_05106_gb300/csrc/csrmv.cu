@@ -551,6 +551,7 @@ bp_status bp_event_csrmv(int64_t n_pre, int64_t n_post, const int64_t* indptr, c
                          const int32_t* n_spikes, int64_t max_spikes, void* y, int32_t y_is_count,
                          const int32_t* tile_ptr, int32_t tile_cols, uint32_t flags, bp_stream_t stream) {
     bp::clear_error();
+    const bp::NvtxRange nvtx("bp_event_csrmv");
     const bp::CsrArgs a = make_csr(n_pre, n_post, indptr, indices, data, wkind, w_homo, tile_ptr, tile_cols);
     BP_TRY(bp::check_csr(a));
     BP_REQUIRE(!y_is_count || wkind == BP_W_HOMO, "integer counts need homogeneous weights");
@@ -631,6 +632,7 @@ bp_status bp_event_csrmv_t(int64_t n_pre, int64_t n_post, const int64_t* indptr,
                            const void* data, int32_t wkind, float w_homo, const float* x_post, float* y_pre,
                            const int32_t* tile_ptr, int32_t tile_cols, uint32_t flags, bp_stream_t stream) {
     bp::clear_error();
+    const bp::NvtxRange nvtx("bp_event_csrmv_t");
     const bp::CsrArgs a = make_csr(n_pre, n_post, indptr, indices, data, wkind, w_homo, tile_ptr, tile_cols);
     BP_TRY(bp::check_csr(a));
     BP_REQUIRE(n_pre == 0 || (y_pre && x_post && indices), "x_post, y_pre or indices is NULL");

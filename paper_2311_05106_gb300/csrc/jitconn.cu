@@ -332,6 +332,7 @@ bp_status bp_jitconn_event_mv(const bp_jit_desc* d, int64_t n_pre, int64_t n_pos
                               const int32_t* n_spikes, int64_t max_spikes, void* y, int32_t y_is_count, uint32_t flags,
                               bp_stream_t stream) {
     bp::clear_error();
+    const bp::NvtxRange nvtx("bp_jitconn_event_mv");
     BP_TRY(bp::check_desc(d, n_pre, n_post));
     BP_REQUIRE(!y_is_count || d->wkind == BP_JIT_HOMO, "integer counts need homogeneous weights");
     BP_REQUIRE(max_spikes >= 0 && max_spikes <= n_pre, "max_spikes out of range");

@@ -245,6 +245,7 @@ bp_status bp_network_step(bp_net* net, bp_stream_t stream) {
 
 bp_status bp_simulate(bp_net* net, int64_t T, int32_t* record, bp_stream_t stream) {
     bp::clear_error();
+    const bp::NvtxRange nvtx("bp_simulate");
     BP_REQUIRE(net, "net is NULL");
     BP_REQUIRE(T >= 0, "T < 0");
     if (T == 0) return BP_OK;

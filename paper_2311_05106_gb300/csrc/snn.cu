@@ -649,6 +649,7 @@ size_t bp_snn_workspace_bytes(const bp_snn_desc* d) {
 
 bp_status bp_snn_forward(const bp_snn_desc* d, const uint8_t* u, float* m, void* workspace, bp_stream_t stream) {
     bp::clear_error();
+    const bp::NvtxRange nvtx("bp_snn_forward");
     BP_TRY(bp::snn_check(d));
     BP_REQUIRE(u && m && workspace, "u, m or workspace is NULL");
     BP_REQUIRE((reinterpret_cast<uintptr_t>(workspace) & 255) == 0, "workspace must be 256-byte aligned");
@@ -723,6 +724,7 @@ bp_status bp_snn_reg_loss(const bp_snn_desc* d, const void* workspace, float* lo
 bp_status bp_snn_backward(const bp_snn_desc* d, const uint8_t* u, const float* g_m, void* workspace, float* dW_in,
                           float* dw_rec, float* dW_out, float* db_out, bp_stream_t stream) {
     bp::clear_error();
+    const bp::NvtxRange nvtx("bp_snn_backward");
     BP_TRY(bp::snn_check(d));
     BP_REQUIRE(u && g_m && workspace && dW_in && dw_rec && dW_out && db_out, "a pointer is NULL");
     BP_REQUIRE((reinterpret_cast<uintptr_t>(workspace) & 255) == 0, "workspace must be 256-byte aligned");
