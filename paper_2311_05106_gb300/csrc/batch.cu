@@ -207,12 +207,7 @@ const int kThreadChoices[] = {256, 512, 1024};
 
 template <int THREADS>
 bp_status launch_batch_t(const BinArgs& a, int bins, size_t smem, cudaStream_t s) {
-    static bool attr = false;
-    if (!attr) {
-        BP_CUDA(cudaFuncSetAttribute(k_batch<THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     kBatchCapacity * 4));
-        attr = true;
-    }
+    BP_TRY(ensure_smem_attr(reinterpret_cast<const void*>(k_batch<THREADS>), kBatchCapacity * 4));
     k_batch<THREADS><<<bins, THREADS, smem, s>>>(a);
     BP_LAUNCHED();
     return BP_OK;

@@ -13,6 +13,10 @@ namespace bp {
 
 // Host-side NVTX range around an entry point (a no-op unless a tool such as
 // a profiler is attached; ncu --nvtx can filter kernels by these ranges).
+// Raises a kernel's dynamic shared-memory limit to `bytes` (once per kernel,
+// device and size; defined in lib.cu).
+bp_status ensure_smem_attr(const void* kernel, int bytes);
+
 struct NvtxRange {
     explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
     ~NvtxRange() { nvtxRangePop(); }

@@ -437,12 +437,8 @@ bp_status launch_scatter_t(const CsrArgs& a, const int32_t* spike_list, const in
         return BP_OK;
     }
     const size_t smem = static_cast<size_t>(SPLIT ? 2 * W : W) * sizeof(Acc);
-    static bool attr_set = false;  // per instantiation
-    if (!attr_set) {
-        BP_CUDA(cudaFuncSetAttribute(k_csr_scatter<Acc, WK, SPLIT, VECL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     static_cast<int>(SPLIT ? 2 * cap * sizeof(Acc) : cap * sizeof(Acc))));
-        attr_set = true;
-    }
+    BP_TRY(ensure_smem_attr(reinterpret_cast<const void*>(k_csr_scatter<Acc, WK, SPLIT, VECL>),
+                            static_cast<int>(SPLIT ? 2 * cap * sizeof(Acc) : cap * sizeof(Acc))));
     // one 1024-thread CTA per SM: R row groups per tile so that S x R covers the SMs
     int64_t R = static_cast<int64_t>(sm_count()) / S;
     if (R < 1) R = 1;
@@ -659,12 +655,8 @@ bp_status bp_event_csrmv_t(int64_t n_pre, int64_t n_post, const int64_t* indptr,
         const int ow_tile = S == 1 ? ow : 0;
 #define BP_GATHER_T(WKV)                                                                                          \
     do {                                                                                                          \
-        static bool attr = false;                                                                                 \
-        if (!attr) {                                                                                              \
-            BP_CUDA(cudaFuncSetAttribute(bp::k_csr_gather_tiled<WKV>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                         static_cast<int>(bp::kTileCols * sizeof(float))));                       \
-            attr = true;                                                                                          \
-        }                                                                                                         \
+        BP_TRY(bp::ensure_smem_attr(reinterpret_cast<const void*>(bp::k_csr_gather_tiled<WKV>),                  \
+                                    static_cast<int>(bp::kTileCols * sizeof(float))));                            \
         bp::k_csr_gather_tiled<WKV><<<grid, bp::kTileThreads, smem, stream>>>(a, x_post, y_pre, ow_tile, W, S);   \
     } while (0)
         switch (wkind) {

@@ -252,13 +252,8 @@ bp_status launch_jit_scatter_t(const JitArgs& lo, const JitArgs& hi, int64_t spl
     if (fits && mode != 1) {
         const int32_t wpad = static_cast<int32_t>((n_post + 31) & ~int64_t(31));
         const size_t smem = static_cast<size_t>(SPLIT ? 2 * wpad : wpad) * sizeof(Acc);
-        static bool attr_set = false;
-        if (!attr_set) {
-            BP_CUDA(cudaFuncSetAttribute(k_jit_scatter<Acc, WK, SPLIT, true>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(SPLIT ? 2 * cap * sizeof(Acc) : cap * sizeof(Acc))));
-            attr_set = true;
-        }
+        BP_TRY(ensure_smem_attr(reinterpret_cast<const void*>(k_jit_scatter<Acc, WK, SPLIT, true>),
+                                static_cast<int>(SPLIT ? 2 * cap * sizeof(Acc) : cap * sizeof(Acc))));
         // one shared copy of y per CTA: use one CTA per SM
         k_jit_scatter<Acc, WK, SPLIT, true><<<sm_count(), kJitThreads, smem, s>>>(
             lo, hi, split, n_post, sl, ns, mx, static_cast<Acc*>(y), static_cast<Acc*>(y_hi), wpad, ev);
@@ -377,12 +372,7 @@ bp_status bp_jitconn_mv(const bp_jit_desc* d, int64_t n_pre, int64_t n_post, con
 #define BP_JIT_MV_LAUNCH(WKV)                                                                                     \
     do {                                                                                                        \
         if (smem) {                                                                                             \
-            static bool set_ = false;                                                                           \
-            if (!set_) {                                                                                        \
-                BP_CUDA(cudaFuncSetAttribute(bp::k_jit_mv<WKV, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                             bp::kTileCols * 4));                                               \
-                set_ = true;                                                                                    \
-            }                                                                                                   \
+            BP_TRY(bp::ensure_smem_attr(reinterpret_cast<const void*>(bp::k_jit_mv<WKV, true>), bp::kTileCols * 4)); \
             bp::k_jit_mv<WKV, true><<<grid, bp::kJitThreads, bytes, stream>>>(a, n_pre, n_post, x_pre, y_post);  \
         } else {                                                                                                \
             bp::k_jit_mv<WKV, false><<<grid, bp::kJitThreads, 0, stream>>>(a, n_pre, n_post, x_pre, y_post);    \

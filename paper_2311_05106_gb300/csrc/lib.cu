@@ -2,6 +2,7 @@
 // device status word, parameter defaults and small host-side helpers.
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <mutex>
 
 #include "bp_common.cuh"
@@ -56,6 +57,21 @@ int sm_count() {
         g_sm_count[d] = v > 0 ? v : 1;
     }
     return g_sm_count[d];
+}
+
+bp_status ensure_smem_attr(const void* kernel, int bytes) {
+    // the limit is a property of the function on each device: record it per
+    // (kernel, device) so that a process driving several GPUs sets it on each
+    static std::mutex mu;
+    static std::map<std::pair<const void*, int>, int> done;
+    const int d = current_device();
+    std::lock_guard<std::mutex> lk(mu);
+    const auto key = std::make_pair(kernel, d);
+    const auto it = done.find(key);
+    if (it != done.end() && it->second >= bytes) return BP_OK;
+    BP_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    done[key] = bytes;
+    return BP_OK;
 }
 
 int max_smem_optin() {

@@ -609,8 +609,7 @@ SnnK snn_kernel_args(const bp_snn_desc& d, void* ws) {
 
 template <typename Kern>
 bp_status set_smem(Kern k, size_t bytes) {
-    BP_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes)));
-    return BP_OK;
+    return ensure_smem_attr(reinterpret_cast<const void*>(k), static_cast<int>(bytes));
 }
 
 }  // namespace
