@@ -439,7 +439,8 @@ def bench_bptt(torch, reps=3, T=1000):
     700 Poisson inputs (5-50 Hz), 1024 recurrent LIF with 10 % recurrent CSR
     weights N(0, 1/sqrt(102)), 20 leaky readouts, T = 1000, dt = 1 ms,
     checkpoints every 100 steps: forward + loss + backward per iteration, BF16
-    and FP32 recurrent weights, and BF16 with Appendix I's ReLU surrogate and
+    and FP32 recurrent weights, BF16 with every step's potentials stored (no
+    recomputation in the backward), and BF16 with Appendix I's ReLU surrogate and
     voltage regulariser (lambda_v = 1e-6: the untrained network's potentials sit far outside
     the penalty's bounds, and a larger weight would only rescale the loss)."""
     import math
@@ -459,9 +460,12 @@ def bench_bptt(torch, reps=3, T=1000):
     stream = torch.cuda.current_stream()
     out = {}
     w16 = T_(w["w_rec"]).to(torch.bfloat16)
-    for name, wr, extra in (("bf16", w16, {}), ("f32", T_(w["w_rec"]).float(), {}),
-                            ("bf16_relu_vreg", w16, dict(surrogate=B.BP_SG_RELU, lambda_v=1e-6))):
-        d = make_desc(Bsz, T, n_in, n_rec, n_out, W_in, ip, ix, wr, W_out, b, 100, **extra)
+    # bf16_store_all: one checkpoint segment, every step's potentials kept by
+    # the forward, so the backward recomputes nothing (more workspace)
+    for name, wr, ck, extra in (("bf16", w16, 100, {}), ("f32", T_(w["w_rec"]).float(), 100, {}),
+                                ("bf16_relu_vreg", w16, 100, dict(surrogate=B.BP_SG_RELU, lambda_v=1e-6)),
+                                ("bf16_store_all", w16, 0, {})):
+        d = make_desc(Bsz, T, n_in, n_rec, n_out, W_in, ip, ix, wr, W_out, b, ck, **extra)
         ws = torch.empty(B.bp_snn_workspace_bytes(d), dtype=torch.uint8, device=dev)
         m = torch.empty((Bsz, n_out), dtype=torch.float32, device=dev)
         loss = torch.empty(1, dtype=torch.float32, device=dev)

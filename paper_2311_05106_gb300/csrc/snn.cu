@@ -29,6 +29,8 @@
 // replayed rather than re-decided (the shared-memory float atomics may round
 // differently from the forward, and a near-threshold neuron must not take
 // the other branch); the adjoint then runs back through the segment.  The
+// forward stores the last segment's potentials itself, so that segment (and,
+// with a single segment, the whole run) is not recomputed.  The
 // recurrent weights are converted to fixed point once per forward call
 // (k_snn_fix_weights), so delivering an event is one integer atomic.
 // Recurrent weights are FP32 or BF16 (FP32 arithmetic); gradients are FP32,
@@ -239,6 +241,7 @@ __global__ void __launch_bounds__(kSnnThreads, 1) k_snn_forward(SnnK p, const ui
     }
     if (threadIdx.x < p.n_out) s_y[threadIdx.x] = s_m[threadIdx.x] = 0.f;
     double reg = 0.0;
+    const int t_last0 = ((p.T - 1) / p.K) * p.K;  // first step of the last checkpoint segment
     __syncthreads();
     for (int t = 0; t < p.T; ++t) {
         if (t % p.K == 0) {  // checkpoint of the state before step t
@@ -252,7 +255,10 @@ __global__ void __launch_bounds__(kSnnThreads, 1) k_snn_forward(SnnK p, const ui
         const int n_act = gather_inputs(u + (static_cast<int64_t>(b) * p.T + t) * p.n_in, p.n_in, in_list, &s_cnt[0]);
         if (threadIdx.x == 0) s_cnt[1] = 0;
         __syncthreads();
-        neuron_step(p, I, V, racc, in_list, n_act, spk, &s_cnt[1], nullptr,
+        // the potentials of the last checkpoint segment go straight to the
+        // segment buffer, so the backward need not recompute that segment
+        float* vp_out = t >= t_last0 ? p.seg_Vp + (static_cast<int64_t>(b) * p.K + (t - t_last0)) * p.n_rec : nullptr;
+        neuron_step(p, I, V, racc, in_list, n_act, spk, &s_cnt[1], vp_out,
                     p.z_all + (static_cast<int64_t>(b) * p.T + t) * p.zw, nullptr, p.sg.reg_on ? &reg : nullptr);
         __syncthreads();
         const int n = s_cnt[1];
@@ -328,37 +334,41 @@ __global__ void __launch_bounds__(kSnnThreads, 1) k_snn_backward(SnnK p, const u
         const int t0 = seg * p.K;
         const int t1 = min(p.T, t0 + p.K);
         const int64_t o = static_cast<int64_t>(b) * p.n_ck + seg;
-        // ---- recompute the segment from its checkpoint
+        // ---- recompute the segment from its checkpoint (the last segment's
+        // potentials were stored by the forward; with a single segment nothing
+        // is recomputed)
         __syncthreads();
-        for (int j = threadIdx.x; j < p.n_rec; j += kSnnThreads) {
-            I[j] = p.ck_I[o * p.n_rec + j];
-            V[j] = p.ck_V[o * p.n_rec + j];
-            racc[j] = 0ull;
-        }
-        if (threadIdx.x == 0) s_cnt[1] = 0;
-        __syncthreads();
-        if (t0 > 0) {  // pending input of the spikes of step t0 - 1
-            const uint32_t* zp = zall + static_cast<int64_t>(t0 - 1) * p.zw;
-            for (int w = threadIdx.x; w < p.zw; w += kSnnThreads) {
-                uint32_t bits = zp[w];
-                if (bits) {
-                    int q = atomicAdd(&s_cnt[1], __popc(bits));
-                    for (; bits; bits &= bits - 1) spk[q++] = 32 * w + __ffs(bits) - 1;
-                }
+        if (seg < nseg - 1) {
+            for (int j = threadIdx.x; j < p.n_rec; j += kSnnThreads) {
+                I[j] = p.ck_I[o * p.n_rec + j];
+                V[j] = p.ck_V[o * p.n_rec + j];
+                racc[j] = 0ull;
             }
-        }
-        __syncthreads();
-        deliver(p, spk, s_cnt[1], racc);
-        __syncthreads();
-        for (int t = t0; t < t1; ++t) {
-            const int n_act = gather_inputs(u + (static_cast<int64_t>(b) * p.T + t) * p.n_in, p.n_in, in_list, &s_cnt[0]);
             if (threadIdx.x == 0) s_cnt[1] = 0;
             __syncthreads();
-            neuron_step(p, I, V, racc, in_list, n_act, spk, &s_cnt[1], segVp + static_cast<int64_t>(t - t0) * p.n_rec,
-                        nullptr, zall + static_cast<int64_t>(t) * p.zw, nullptr);
+            if (t0 > 0) {  // pending input of the spikes of step t0 - 1
+                const uint32_t* zp = zall + static_cast<int64_t>(t0 - 1) * p.zw;
+                for (int w = threadIdx.x; w < p.zw; w += kSnnThreads) {
+                    uint32_t bits = zp[w];
+                    if (bits) {
+                        int q = atomicAdd(&s_cnt[1], __popc(bits));
+                        for (; bits; bits &= bits - 1) spk[q++] = 32 * w + __ffs(bits) - 1;
+                    }
+                }
+            }
             __syncthreads();
             deliver(p, spk, s_cnt[1], racc);
             __syncthreads();
+            for (int t = t0; t < t1; ++t) {
+                const int n_act = gather_inputs(u + (static_cast<int64_t>(b) * p.T + t) * p.n_in, p.n_in, in_list, &s_cnt[0]);
+                if (threadIdx.x == 0) s_cnt[1] = 0;
+                __syncthreads();
+                neuron_step(p, I, V, racc, in_list, n_act, spk, &s_cnt[1], segVp + static_cast<int64_t>(t - t0) * p.n_rec,
+                            nullptr, zall + static_cast<int64_t>(t) * p.zw, nullptr);
+                __syncthreads();
+                deliver(p, spk, s_cnt[1], racc);
+                __syncthreads();
+            }
         }
         // ---- adjoint, t = t1-1 .. t0
         for (int t = t1 - 1; t >= t0; --t) {
