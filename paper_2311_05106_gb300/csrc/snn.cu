@@ -431,14 +431,31 @@ __global__ void __launch_bounds__(kSnnThreads, 1) k_snn_backward(SnnK p, const u
                 }
                 for (; a < n_act; ++a) gin[static_cast<int64_t>(in_list[a]) * p.n_rec + j] += ib;
             }
-            // dw_rec[e] += Ibar_t[col e] for the rows spiking at t - 1 (one warp per row)
+            // dw_rec[e] += Ibar_t[col e] for the rows spiking at t - 1 (one warp per row;
+            // each lane issues the index and partial loads of four entries before
+            // their shared-memory lookups and stores, so a row of up to 128
+            // entries costs one memory latency)
             if (t > 0) {
                 const uint32_t* zp = zall + static_cast<int64_t>(t - 1) * p.zw;
                 for (int w = warp; w < p.zw; w += kSnnThreads / 32) {
                     for (uint32_t bits = zp[w]; bits; bits &= bits - 1) {
                         const int i = 32 * w + __ffs(bits) - 1;
                         const int64_t r0 = p.indptr[i], r1 = p.indptr[i + 1];
-                        for (int64_t e = r0 + lane; e < r1; e += 32) grec[e] += Ib[p.indices[e]];
+                        for (int64_t e = r0 + lane; e < r1; e += 4 * 32) {
+                            int32_t c[4];
+                            float g[4];
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) {
+                                const int64_t ee = e + 32 * u;
+                                c[u] = ee < r1 ? p.indices[ee] : 0;
+                                g[u] = ee < r1 ? grec[ee] : 0.f;
+                            }
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) {
+                                const int64_t ee = e + 32 * u;
+                                if (ee < r1) grec[ee] = g[u] + Ib[c[u]];
+                            }
+                        }
                     }
                 }
             }
