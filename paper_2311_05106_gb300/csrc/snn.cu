@@ -211,7 +211,21 @@ __device__ __forceinline__ void deliver(const SnnK& p, const int32_t* spk, int n
     for (int e = warp; e < n; e += kSnnThreads / 32) {
         const int i = spk[e];
         const int64_t b0 = p.indptr[i], b1 = p.indptr[i + 1];
-        for (int64_t j = b0 + lane; j < b1; j += 32) atomicAdd(racc + p.indices[j], p.w_fix[j]);
+        // four index / weight loads in flight per lane before the atomics: a
+        // row of up to 128 entries costs one memory latency
+        for (int64_t j = b0 + lane; j < b1; j += 4 * 32) {
+            int32_t c[4];
+            unsigned long long w[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t jj = j + 32 * u;
+                c[u] = jj < b1 ? p.indices[jj] : -1;
+                w[u] = jj < b1 ? p.w_fix[jj] : 0ull;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (c[u] >= 0) atomicAdd(racc + c[u], w[u]);
+        }
     }
 }
 
