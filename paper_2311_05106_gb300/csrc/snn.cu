@@ -94,6 +94,7 @@ struct SnnK {
     float* g_out;        // [B][n_rec][n_out]
     float* g_b;          // [B][n_out]
     double* vreg;        // [B]  regulariser sums of the forward
+    int32_t stage_wout;  // the forward copies W_out into shared memory (it fits)
     unsigned long long* w_fix;  // [nnz] recurrent weights in fixed point (filled by the forward)
     int64_t nnz;
     int32_t n_ck, zw;
@@ -246,6 +247,7 @@ __global__ void __launch_bounds__(kSnnThreads, 1) k_snn_forward(SnnK p, const ui
     float* V = I + p.n_rec;
     int32_t* spk = reinterpret_cast<int32_t*>(V + p.n_rec);
     int32_t* in_list = spk + p.n_rec;
+    float* s_wout = reinterpret_cast<float*>(in_list + p.n_in);  // [n_rec][n_out] when staged
     __shared__ int32_t s_cnt[2];
     __shared__ float s_y[kSnnMaxOut], s_m[kSnnMaxOut];
     const int b = blockIdx.x;
@@ -253,6 +255,9 @@ __global__ void __launch_bounds__(kSnnThreads, 1) k_snn_forward(SnnK p, const ui
         I[j] = V[j] = 0.f;
         racc[j] = 0ull;
     }
+    if (p.stage_wout)
+        for (int e = threadIdx.x; e < p.n_rec * p.n_out; e += kSnnThreads) s_wout[e] = __ldg(p.W_out + e);
+    const float* Wo = p.stage_wout ? s_wout : p.W_out;  // readout weights, shared or global
     if (threadIdx.x < p.n_out) s_y[threadIdx.x] = s_m[threadIdx.x] = 0.f;
     double reg = 0.0;
     const int t_last0 = ((p.T - 1) / p.K) * p.K;  // first step of the last checkpoint segment
@@ -286,7 +291,7 @@ __global__ void __launch_bounds__(kSnnThreads, 1) k_snn_forward(SnnK p, const ui
                 float acc = 0.f;
                 for (int w = lane; w < p.zw; w += 32)
                     for (uint32_t bits = zt[w]; bits; bits &= bits - 1)
-                        acc += __ldg(p.W_out + static_cast<int64_t>(32 * w + __ffs(bits) - 1) * p.n_out + o);
+                        acc += Wo[static_cast<int64_t>(32 * w + __ffs(bits) - 1) * p.n_out + o];
                 acc = group_reduce_sum(acc, 32);
                 if (lane == 0) {
                     const float y = p.a_o * s_y[o] + p.dt * (acc + p.b_out[o]);
@@ -609,6 +614,7 @@ bp_status snn_check(const bp_snn_desc* d) {
 SnnK snn_kernel_args(const bp_snn_desc& d, void* ws) {
     const SnnLayout L = snn_layout(d);
     SnnK p;
+    p.stage_wout = 0;
     p.B = d.B;
     p.T = d.T;
     p.n_in = d.n_in;
@@ -693,9 +699,13 @@ bp_status bp_snn_forward(const bp_snn_desc* d, const uint8_t* u, float* m, void*
     BP_TRY(bp::snn_check(d));
     BP_REQUIRE(u && m && workspace, "u, m or workspace is NULL");
     BP_REQUIRE((reinterpret_cast<uintptr_t>(workspace) & 255) == 0, "workspace must be 256-byte aligned");
-    const bp::SnnK p = bp::snn_kernel_args(*d, workspace);
-    // racc (8 B), I, V, spike list (4 B each) per neuron, plus the input list
-    const size_t smem = static_cast<size_t>(d->n_rec) * (8 + 4 * 3) + static_cast<size_t>(d->n_in) * 4;
+    bp::SnnK p = bp::snn_kernel_args(*d, workspace);
+    // racc (8 B), I, V, spike list (4 B each) per neuron, plus the input list,
+    // plus the readout weights when they fit
+    size_t smem = static_cast<size_t>(d->n_rec) * (8 + 4 * 3) + static_cast<size_t>(d->n_in) * 4;
+    const size_t wout_bytes = static_cast<size_t>(d->n_rec) * d->n_out * 4;
+    p.stage_wout = smem + wout_bytes <= static_cast<size_t>(bp::max_smem_optin()) ? 1 : 0;
+    if (p.stage_wout) smem += wout_bytes;
     // recurrent weights in fixed point, once per call (the backward's
     // recomputation reads them from the same workspace)
     if (d->nnz > 0) {
