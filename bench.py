@@ -167,9 +167,10 @@ def step_traffic_record():
         return None
 
 
-# bytes the neuron pass must move per neuron: read V, g_e, g_i, ref, and the
-# two event accumulators (6 x 4 B); write V, g_e, g_i (3 x 4 B)
-LIF_BYTES_PER_NEURON = 36
+# bytes the neuron pass must move per neuron: read V, g_e, g_i and the two
+# event accumulators (5 x 4 B) and the one-byte refractory counter; write V,
+# g_e, g_i (3 x 4 B)
+LIF_BYTES_PER_NEURON = 33
 
 
 def build_network(torch, B, conn, weights, n=N_NEURONS, delay=0):
@@ -234,23 +235,21 @@ def launches_in_simulate(steps, host_step_before):
 
 def lif_kernel_time(torch, B, net, reps=50):
     """Average duration of the neuron pass alone (bp_lif_step on the network's
-    state: the fused step kernel without delivery), CUDA events around each
-    launch on the launching stream."""
+    state: the fused step kernel without delivery), `reps` back-to-back
+    launches between two CUDA events on the launching stream (as the network
+    steps run), after 5 untimed ones."""
     stream = torch.cuda.current_stream()
-    sl = torch.zeros(N_NEURONS, dtype=torch.int32, device="cuda")
-    ns = torch.zeros(1, dtype=torch.int32, device="cuda")
-    times = []
-    for _ in range(reps):
-        ns.zero_()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        B.bp_lif_step(net.params, N_EXC, net.V, net.ge, net.gi, net.ref, net.ye, net.yi, sl, ns)
-        b.record(stream)
-        times.append((a, b))
+    for _ in range(5):
+        B.bp_lif_step(net.params, N_EXC, net.V, net.ge, net.gi, net.ref, net.ye, net.yi, None, None)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
-    ms = [a.elapsed_time(b) for a, b in times]
-    return statistics.mean(ms[5:]) if len(ms) > 5 else statistics.mean(ms)
+    a.record(stream)
+    for _ in range(reps):
+        B.bp_lif_step(net.params, N_EXC, net.V, net.ge, net.gi, net.ref, net.ye, net.yi, None, None)
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
 
 
 def e2e_run(torch, net, V0, steps):
@@ -261,7 +260,7 @@ def e2e_run(torch, net, V0, steps):
     f32 = torch.float32
     hV = torch.from_numpy(np.ascontiguousarray(V0, np.float32)).pin_memory()
     hz = torch.zeros(N_NEURONS, dtype=f32).pin_memory()
-    hr = torch.zeros(N_NEURONS, dtype=torch.int32).pin_memory()
+    hr = torch.zeros(N_NEURONS, dtype=torch.uint8).pin_memory()
     rec = torch.zeros((steps, 2), dtype=torch.int32, device="cuda")
     hrec = torch.zeros((steps, 2), dtype=torch.int32).pin_memory()
     hVout = torch.zeros(N_NEURONS, dtype=f32).pin_memory()
@@ -282,7 +281,7 @@ def e2e_run(torch, net, V0, steps):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     events = int(net.totals[2].item())
-    h2d = 4 * 4 * N_NEURONS
+    h2d = (3 * 4 + 1) * N_NEURONS  # V, ge, gi (FP32) and the one-byte refractory counters
     d2h = 8 * steps + 4 * N_NEURONS
     return ms, events, h2d, d2h
 

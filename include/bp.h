@@ -94,9 +94,13 @@ int32_t bp_tile_cols(void);
  * Listing S6 (E/I COBA network: tau = 20 ms, tau_ref = 5 ms, E_e = 0 mV with
  * tau_e = 5 ms, E_i = -80 mV with tau_i = 10 ms, input 20 per step).
  * ------------------------------------------------------------------------ */
+/* Largest refractory period, in steps, that the uint8 refractory counters
+ * hold; every entry point taking bp_coba_params rejects a longer one. */
+#define BP_MAX_REF_STEPS 255
+
 typedef struct {
     double dt;              /* ms */
-    double tau_m, tau_e, tau_i, tau_ref;    /* ms */
+    double tau_m, tau_e, tau_i, tau_ref;    /* ms; round(tau_ref / dt) <= BP_MAX_REF_STEPS */
     double V_rest, V_th, V_reset, E_e, E_i; /* mV */
     double R;               /* membrane resistance */
     double I_ext;           /* constant input added every step */
@@ -122,16 +126,23 @@ bp_status bp_coba_params_default(bp_coba_params* p);
  *     V <- V_reset, ref[i] <- round(tau_ref / dt).
  * The decay factors are evaluated in FP64 on the host and rounded to FP32;
  * the state arithmetic is FP32.
- * Arrays: V, ge, gi float [n]; ref int32 [n]; ye, yi int32 or float [n].
+ * Arrays: V, ge, gi float [n]; ref uint8 [n] (refractory steps left: one
+ *   byte per neuron, since this counter is read every step and the state
+ *   pass is bound by memory traffic); ye, yi int32 or float [n].
+ *   16-byte aligned V, ge, gi, ye, yi (I_vec, spk 16 / 4 bytes) and a
+ *   4-byte aligned ref take the four-neurons-per-thread path; any alignment
+ *   is accepted.
  * Outputs: spk uint8 [n] (nullable) = 1 where the neuron spiked this step;
  *   spike ids are APPENDED to spike_list int32 [n] (nullable together with
  *   n_spikes) at positions reserved by an atomic add on *n_spikes (the caller
  *   zeroes *n_spikes beforehand; the order of ids in the list is unspecified);
  *   spike_totals int64 [2] (nullable) += number of spikes among neurons
  *   [0, n_e) and [n_e, n).
- * Errors: BP_ERR_INVALID for n < 0, n_e outside [0, n] or a required NULL. */
+ * Errors: BP_ERR_INVALID for n < 0, n_e outside [0, n], a required NULL or
+ *   a refractory period round(tau_ref / dt) above 255 steps (BP_MAX_REF_STEPS,
+ *   the range of the uint8 counter: 25.5 ms at dt = 0.1 ms). */
 bp_status bp_lif_step(const bp_coba_params* p, int64_t n, int64_t n_e,
-                      float* V, float* ge, float* gi, int32_t* ref,
+                      float* V, float* ge, float* gi, uint8_t* ref,
                       void* ye, void* yi, int32_t y_is_count,
                       const float* I_vec,
                       uint8_t* spk, int32_t* spike_list, int32_t* n_spikes,
@@ -368,7 +379,7 @@ typedef struct {
     float* V;                       /* [n] */
     float* ge;                      /* [n] */
     float* gi;                      /* [n] */
-    int32_t* ref;                   /* [n] */
+    uint8_t* ref;                   /* [n] refractory steps left (see bp_lif_step) */
     void* ye;                       /* [2n] int32 counts (homogeneous) or float sums, two halves */
     void* yi;                       /* [2n] */
     int32_t* spike_list;            /* [n] nullable: spike ids of the last step (order unspecified) */
@@ -447,7 +458,7 @@ typedef struct {
     float* V;
     float* ge;
     float* gi;
-    int32_t* ref;
+    uint8_t* ref;           /* refractory steps left (see bp_lif_step) */
     int64_t* totals;        /* device [n_nets][4]: spikes E, spikes I, events, steps (accumulated) */
 } bp_batch_desc;
 

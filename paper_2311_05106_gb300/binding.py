@@ -223,6 +223,8 @@ def bp_coba_params_default(**overrides) -> CobaParams:
 def bp_lif_step(p, n_e, V, ge, gi, ref, ye, yi, spike_list, n_spikes, I_vec=None, spk=None, spike_totals=None,
                 stream=None):
     counts = 1 if ye.dtype == torch.int32 else 0
+    if ref.dtype != torch.uint8:
+        raise TypeError("ref holds one-byte refractory counters (torch.uint8), got %s" % ref.dtype)
     _check("bp_lif_step", lib().bp_lif_step(ctypes.byref(p), V.numel(), n_e, _p(V), _p(ge), _p(gi), _p(ref), _p(ye),
                                             _p(yi), counts, _p(I_vec), _p(spk), _p(spike_list), _p(n_spikes),
                                             _p(spike_totals), _stream(stream)))

@@ -55,7 +55,7 @@ struct BinArgs {
     float* V;
     float* ge;
     float* gi;
-    int32_t* ref;
+    uint8_t* ref;
     int32_t* spill;            // packed counts between launches, concatenated layout
     int32_t* spk_list;
     int64_t* totals;           // [n_nets][4]
@@ -116,7 +116,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_batch(BinArgs a) {
                     float4 v = ld_keep(reinterpret_cast<const float4*>(a.V + g), pol);
                     float4 ge = ld_keep(reinterpret_cast<const float4*>(a.ge + g), pol);
                     float4 gi = ld_keep(reinterpret_cast<const float4*>(a.gi + g), pol);
-                    int4 r = ld_keep(reinterpret_cast<const int4*>(a.ref + g), pol);
+                    // four one-byte refractory counters in one word
+                    const uint32_t r4 = ld_keep(reinterpret_cast<const uint32_t*>(a.ref + g), pol);
+                    int4 r = make_int4(r4 & 0xFFu, (r4 >> 8) & 0xFFu, (r4 >> 16) & 0xFFu, r4 >> 24);
                     int4 y = *reinterpret_cast<int4*>(cnt + 4 * q);
                     *reinterpret_cast<int4*>(cnt + 4 * q) = make_int4(0, 0, 0, 0);
                     float* vv = &v.x;
@@ -137,7 +139,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_batch(BinArgs a) {
                     st_keep(reinterpret_cast<float4*>(a.V + g), v, pol);
                     st_keep(reinterpret_cast<float4*>(a.ge + g), ge, pol);
                     st_keep(reinterpret_cast<float4*>(a.gi + g), gi, pol);
-                    st_keep(reinterpret_cast<int4*>(a.ref + g), r, pol);
+                    st_keep(reinterpret_cast<uint32_t*>(a.ref + g),
+                            static_cast<uint32_t>(r.x) | (static_cast<uint32_t>(r.y) << 8) |
+                                (static_cast<uint32_t>(r.z) << 16) | (static_cast<uint32_t>(r.w) << 24),
+                            pol);
                 }
                 // warp-aggregated append of (net slot << 20 | neuron) entries
                 const int mine = __popc(bits);
@@ -300,6 +305,10 @@ bp_status bp_batch_create(const bp_batch_desc* desc, bp_batch** out) {
     BP_REQUIRE(d.n_nets > 0 && d.n && d.seed, "n_nets, n or seed missing");
     BP_TRY(bp::check_coba(&d.coba));
     BP_REQUIRE(d.V && d.ge && d.gi && d.ref && d.totals, "a required state pointer is NULL");
+    // the kernel moves four neurons per 16-byte (FP32) and 4-byte (counter) access
+    const auto al = [](const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; };
+    BP_REQUIRE(al(d.V, 16) && al(d.ge, 16) && al(d.gi, 16) && al(d.ref, 4),
+               "V, ge, gi must be 16-byte and ref 4-byte aligned");
     const int32_t N = d.n_nets;
     std::vector<int64_t> off(N + 1);
     const int64_t total = bp_batch_layout(N, d.n, off.data());
@@ -377,8 +386,8 @@ bp_status bp_batch_create(const bp_batch_desc* desc, bp_batch** out) {
     b->smem = static_cast<size_t>(std::max<int64_t>(max_load, 4)) * 4;
     b->total = total;
     b->graphs = new (std::nothrow) std::map<int64_t, cudaGraphExec_t>();
-    const size_t state_bytes = static_cast<size_t>(total) * 16 + static_cast<size_t>(total) * 4 +
-                               static_cast<size_t>(N) * 32;
+    // V, ge, gi (4 B), ref (1 B), the spilled counts (4 B) and the totals
+    const size_t state_bytes = static_cast<size_t>(total) * (3 * 4 + 1 + 4) + static_cast<size_t>(N) * 32;
     cudaError_t e = cudaSuccess;
     e = e ? e : cudaMalloc(&b->d_nets, sizeof(bp::NetInfo) * N);
     e = e ? e : cudaMalloc(&b->d_bin_nets, sizeof(int32_t) * bin_nets.size());
@@ -478,7 +487,7 @@ bp_status bp_batch_autotune(bp_batch* b, int32_t probe_steps, int32_t* chosen_th
     const size_t f = static_cast<size_t>(b->total) * 4;
     char* snap = static_cast<char*>(b->d_snapshot);
     void* src[] = {b->d.V, b->d.ge, b->d.gi, b->d.ref, b->d_spill, b->d.totals};
-    const size_t sz[] = {f, f, f, f, f, static_cast<size_t>(b->n_nets) * 32};
+    const size_t sz[] = {f, f, f, static_cast<size_t>(b->total), f, static_cast<size_t>(b->n_nets) * 32};
     size_t offs[6];
     size_t o = 0;
     for (int k = 0; k < 6; ++k) {

@@ -166,6 +166,14 @@ __device__ __forceinline__ float4 ld_keep(const float4* p, uint64_t pol) {
                  : "l"(p), "l"(pol));
     return v;
 }
+__device__ __forceinline__ uint32_t ld_keep(const uint32_t* p, uint64_t pol) {
+    uint32_t v;
+    asm volatile("ld.global.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ void st_keep(uint32_t* p, uint32_t v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.u32 [%0], %1, %2;" ::"l"(p), "r"(v), "l"(pol) : "memory");
+}
 __device__ __forceinline__ void st_keep(int4* p, int4 v, uint64_t pol) {
     asm volatile("st.global.L2::cache_hint.v4.s32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "r"(v.x), "r"(v.y), "r"(v.z),
                  "r"(v.w), "l"(pol)

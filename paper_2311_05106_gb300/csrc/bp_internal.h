@@ -79,7 +79,7 @@ struct NetStepLaunch {
     float* V;
     float* ge;
     float* gi;
-    int32_t* ref;
+    uint8_t* ref;
     void* ye2;
     void* yi2;
     uint8_t* spk;
@@ -102,7 +102,7 @@ struct NetStepLaunch {
 
 // ---- lif.cu
 bp_status launch_lif_step(const LifConst& c, int64_t n, int64_t n_e, float* V, float* ge, float* gi,
-                          int32_t* ref, void* ye, void* yi, bool counts, const float* I_vec, uint8_t* spk,
+                          uint8_t* ref, void* ye, void* yi, bool counts, const float* I_vec, uint8_t* spk,
                           int32_t* spike_list, int32_t* n_spikes, int32_t* clear_counter,
                           int64_t* totals, const NetCtrl* ctrl, int32_t t_local, cudaStream_t s);
 bp_status launch_network_step(const NetStepLaunch& L, int parity, int32_t t_local, cudaStream_t s);

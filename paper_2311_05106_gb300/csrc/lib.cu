@@ -106,6 +106,10 @@ bp_status check_coba(const bp_coba_params* p) {
     BP_REQUIRE(p != nullptr, "coba params are NULL");
     BP_REQUIRE(p->dt > 0 && p->tau_m > 0 && p->tau_e > 0 && p->tau_i > 0 && p->tau_ref >= 0,
                "coba params: dt and time constants must be positive");
+    const double steps = p->tau_ref / p->dt;
+    BP_REQUIRE(steps < BP_MAX_REF_STEPS + 0.5,
+               "coba params: refractory period of %.1f steps exceeds the %d steps of the uint8 counter",
+               steps, BP_MAX_REF_STEPS);
     return BP_OK;
 }
 

@@ -41,7 +41,7 @@ struct StepArgs {
     float* V;
     float* ge;
     float* gi;
-    int32_t* ref;
+    uint8_t* ref;  // refractory steps left, one byte per neuron
     void* ye_in;   // read and zeroed this step
     void* yi_in;
     void* ye_out;  // receive this step's deliveries
@@ -116,7 +116,8 @@ __global__ void __launch_bounds__(kStepThreads, 4) k_step(StepArgs a) {
                 g_e = __ldcs(reinterpret_cast<const float4*>(a.ge + i0));
                 g_i = __ldcs(reinterpret_cast<const float4*>(a.gi + i0));
             }
-            int4 r = __ldcs(reinterpret_cast<const int4*>(a.ref + i0));
+            const uchar4 r8 = __ldcs(reinterpret_cast<const uchar4*>(a.ref + i0));
+            int4 r = make_int4(r8.x, r8.y, r8.z, r8.w);
             const Y4 ce = ld_keep(reinterpret_cast<const Y4*>(ye + i0), keep);
             const Y4 ci = ld_keep(reinterpret_cast<const Y4*>(yi + i0), keep);
             float4 Iv = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -130,7 +131,9 @@ __global__ void __launch_bounds__(kStepThreads, 4) k_step(StepArgs a) {
             __stcs(reinterpret_cast<float4*>(a.ge + i0), g_e);
             __stcs(reinterpret_cast<float4*>(a.gi + i0), g_i);
             if (r.x != r_old.x || r.y != r_old.y || r.z != r_old.z || r.w != r_old.w)
-                __stcs(reinterpret_cast<int4*>(a.ref + i0), r);
+                __stcs(reinterpret_cast<uchar4*>(a.ref + i0),
+                       make_uchar4(static_cast<unsigned char>(r.x), static_cast<unsigned char>(r.y),
+                                   static_cast<unsigned char>(r.z), static_cast<unsigned char>(r.w)));
             if (ce.x != Y(0) || ce.y != Y(0) || ce.z != Y(0) || ce.w != Y(0))
                 st_keep(reinterpret_cast<Y4*>(ye + i0), Y4{}, keep);
             if (ci.x != Y(0) || ci.y != Y(0) || ci.z != Y(0) || ci.w != Y(0))
@@ -156,7 +159,7 @@ __global__ void __launch_bounds__(kStepThreads, 4) k_step(StepArgs a) {
                 a.V[i] = v;
                 a.ge[i] = g_e;
                 a.gi[i] = g_i;
-                if (r != r_old) a.ref[i] = r;
+                if (r != r_old) a.ref[i] = static_cast<uint8_t>(r);
                 if (ce != Y(0)) ye[i] = Y(0);
                 if (ci != Y(0)) yi[i] = Y(0);
                 if (a.spk) a.spk[i] = s ? 1 : 0;
@@ -487,13 +490,13 @@ bp_status launch_step(const StepArgs& a, bool counts, int conn, int wk, cudaStre
         if (a.clear_counter) BP_CUDA(cudaMemsetAsync(a.clear_counter, 0, sizeof(int32_t), s));
         return BP_OK;
     }
-    const bool vec = aligned(a.V, 16) && aligned(a.ge, 16) && aligned(a.gi, 16) && aligned(a.ref, 16) &&
+    const bool vec = aligned(a.V, 16) && aligned(a.ge, 16) && aligned(a.gi, 16) && aligned(a.ref, 4) &&
                      aligned(a.ye_in, 16) && aligned(a.yi_in, 16) && aligned(a.I_vec, 16) && aligned(a.spk, 4);
     if (counts) return vec ? launch_step_vec<true, 4>(a, conn, wk, s) : launch_step_vec<true, 1>(a, conn, wk, s);
     return vec ? launch_step_vec<false, 4>(a, conn, wk, s) : launch_step_vec<false, 1>(a, conn, wk, s);
 }
 
-StepArgs base_args(const LifConst& c, int64_t n, int64_t n_e, float* V, float* ge, float* gi, int32_t* ref) {
+StepArgs base_args(const LifConst& c, int64_t n, int64_t n_e, float* V, float* ge, float* gi, uint8_t* ref) {
     StepArgs a{};
     a.c = c;
     a.n = n;
@@ -508,7 +511,7 @@ StepArgs base_args(const LifConst& c, int64_t n, int64_t n_e, float* V, float* g
 }  // namespace
 
 bp_status launch_lif_step(const LifConst& c, int64_t n, int64_t n_e, float* V, float* ge, float* gi,
-                          int32_t* ref, void* ye, void* yi, bool counts, const float* I_vec, uint8_t* spk,
+                          uint8_t* ref, void* ye, void* yi, bool counts, const float* I_vec, uint8_t* spk,
                           int32_t* spike_list, int32_t* n_spikes, int32_t* clear_counter, int64_t* totals,
                           const NetCtrl* ctrl, int32_t t_local, cudaStream_t s) {
     StepArgs a = base_args(c, n, n_e, V, ge, gi, ref);
@@ -607,7 +610,7 @@ bp_status launch_spike_compact(int64_t n, const uint8_t* events, int32_t* spike_
 extern "C" {
 
 bp_status bp_lif_step(const bp_coba_params* p, int64_t n, int64_t n_e, float* V, float* ge, float* gi,
-                      int32_t* ref, void* ye, void* yi, int32_t y_is_count, const float* I_vec, uint8_t* spk,
+                      uint8_t* ref, void* ye, void* yi, int32_t y_is_count, const float* I_vec, uint8_t* spk,
                       int32_t* spike_list, int32_t* n_spikes, int64_t* spike_totals, bp_stream_t stream) {
     bp::clear_error();
     BP_TRY(bp::check_coba(p));

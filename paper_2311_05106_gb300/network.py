@@ -58,7 +58,7 @@ class CobaNetwork:
         self.V = torch.as_tensor(np.asarray(V0, np.float32), device=device).contiguous()
         self.ge = torch.zeros(self.n, dtype=f32, device=device)
         self.gi = torch.zeros(self.n, dtype=f32, device=device)
-        self.ref = torch.zeros(self.n, dtype=i32, device=device)
+        self.ref = torch.zeros(self.n, dtype=torch.uint8, device=device)
         self.spike_list = torch.zeros(self.n, dtype=i32, device=device) if keep_spikes else None
         self.n_spikes = torch.zeros(2, dtype=i32, device=device)
         self.totals = torch.zeros(4, dtype=torch.int64, device=device)
@@ -185,7 +185,7 @@ class BatchedNetworks:
         self.V = torch.as_tensor(V, device=device)
         self.ge = torch.zeros(total, dtype=f32, device=device)
         self.gi = torch.zeros(total, dtype=f32, device=device)
-        self.ref = torch.zeros(total, dtype=torch.int32, device=device)
+        self.ref = torch.zeros(total, dtype=torch.uint8, device=device)
         self.totals = torch.zeros((self.n_nets, 4), dtype=torch.int64, device=device)
         self._p = None if p is None else np.ascontiguousarray(p, dtype=np.float64)
         d = B.BatchDesc()

@@ -99,3 +99,23 @@ def test_snn_desc_defaults_and_host_checks(libpath):
     assert L.bp_lif_step_bwd(variant(lambda_v=0.1, v_lo=1.0, v_hi=0.5), 4, fake, fake, fake, fake, fake, fake, fake,
                              None) != 0
     assert b"v_lo" in L.bp_last_error()
+
+
+def test_refractory_counter_range_host_check(libpath):
+    """The refractory counters are one byte per neuron: a period of 255 steps
+    is accepted and one of 256 is rejected on the host, with a message, by
+    every entry point that takes COBA parameters (n = 0 makes no device call)."""
+    from paper_2311_05106_gb300 import binding as B
+    L = B.lib()
+    p = B.bp_coba_params_default()
+    p.tau_ref = 25.5                     # 255 steps at dt = 0.1 ms
+    args = (0, 0, None, None, None, None, None, None, 1, None, None, None, None, None, None)
+    assert L.bp_lif_step(ctypes.byref(p), *args) == 0
+    p.tau_ref = 25.6                     # 256 steps
+    assert L.bp_lif_step(ctypes.byref(p), *args) != 0
+    assert b"refractory" in L.bp_last_error()
+    d = B.NetDesc()
+    d.n, d.n_e, d.coba = 10, 8, p
+    h = ctypes.c_void_p()
+    assert L.bp_network_create(ctypes.byref(d), ctypes.byref(h)) != 0
+    assert b"refractory" in L.bp_last_error()

@@ -46,12 +46,16 @@ def spike_list_of(events):
 
 
 # ---------------------------------------------------------------------- a1-a4
-@pytest.mark.parametrize("n,counts", [(1, True), (255, True), (70001, True), (70001, False), (300000, True)])
-def test_lif_step_matches_oracle(n, counts):
-    st = wl.lif_state(n, seed=n)
+@pytest.mark.parametrize("n,counts,tau_ref", [(1, True, 5.0), (255, True, 5.0), (70001, True, 5.0),
+                                               (70001, False, 5.0), (300000, True, 5.0), (70001, True, 25.5)])
+def test_lif_step_matches_oracle(n, counts, tau_ref):
+    """One step from a random state against the oracle; tau_ref = 25.5 ms is
+    the longest refractory period the one-byte counters hold (255 steps)."""
+    ref_steps = int(round(tau_ref / 0.1))
+    st = wl.lif_state(n, seed=n, ref_steps=ref_steps)
     n_e = (4 * n) // 5
     empty = ("csr", np.zeros(n + 1, np.int64), np.zeros(1, np.int32), None if counts else np.zeros(1))
-    net = orc.CobaNet(n, n_e, empty, st["V"].astype(np.float64))
+    net = orc.CobaNet(n, n_e, empty, st["V"].astype(np.float64), tau_ref=tau_ref)
     net.ge[:] = st["ge"]
     net.gi[:] = st["gi"]
     net.ref[:] = st["ref"]
@@ -61,8 +65,8 @@ def test_lif_step_matches_oracle(n, counts):
     net.yi[:] = yi_in
     spk_ref, vdec = net.step(return_vdec=True)
 
-    p = B.bp_coba_params_default()
-    V, ge, gi, ref = cuda(st["V"]), cuda(st["ge"]), cuda(st["gi"]), cuda(st["ref"])
+    p = B.bp_coba_params_default(tau_ref=tau_ref)
+    V, ge, gi, ref = cuda(st["V"]), cuda(st["ge"]), cuda(st["gi"]), cuda(st["ref"].astype(np.uint8))
     ye, yi = cuda(ye_in), cuda(yi_in)
     spk = torch.zeros(n, dtype=torch.uint8, device="cuda")
     sl = torch.zeros(n, dtype=torch.int32, device="cuda")
@@ -79,6 +83,8 @@ def test_lif_step_matches_oracle(n, counts):
     ok = ~near
     assert rel_err(V.cpu().numpy()[ok], net.V[ok]) < RTOL_F32
     assert np.array_equal(ref.cpu().numpy()[ok], net.ref[ok])
+    if n >= 70001:  # counters set by this step's spikes and counters counting down from the top
+        assert (net.ref[ok] == ref_steps).any() and (net.ref[ok] == ref_steps - 1).any()
     assert not ye.any().item() and not yi.any().item()
     k = int(ns.item())
     ids = np.sort(sl[:k].cpu().numpy())
@@ -420,7 +426,7 @@ def test_lif_step_with_no_neurons():
     z = lambda dt: torch.zeros(0, dtype=dt, device="cuda")
     sl = torch.zeros(1, dtype=torch.int32, device="cuda")
     ns = torch.zeros(1, dtype=torch.int32, device="cuda")
-    B.bp_lif_step(p, 0, z(torch.float32), z(torch.float32), z(torch.float32), z(torch.int32), z(torch.int32),
+    B.bp_lif_step(p, 0, z(torch.float32), z(torch.float32), z(torch.float32), z(torch.uint8), z(torch.int32),
                   z(torch.int32), sl, ns)
     torch.cuda.synchronize()
     assert int(ns.item()) == 0
