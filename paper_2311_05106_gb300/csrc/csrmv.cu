@@ -178,15 +178,62 @@ __global__ void __launch_bounds__(kTileThreads, 1)
                 scatter_any<Acc, WK, VECL>(a.indices, a.data, a.w_homo, b0, b1, lane, G, out, col0);
             }
         };
+        // rows in batches of one per thread: every thread first fetches the
+        // segment bounds of its row (spike id -> row start -> tile offsets,
+        // three dependent loads, all of the CTA's in flight together), then
+        // each group of G lanes walks the G segments its lanes hold, one
+        // after another, taking the bounds by shuffle; the dependent chain is
+        // paid once per batch instead of once per segment.  Row k of a batch
+        // is held by lane k / ng of group k mod ng, so that a partial last
+        // batch still spreads over all groups.
+        auto walk_batched = [&](int G) {
+            const int lane = threadIdx.x % G;
+            const int64_t ng = blockDim.x / G;
+            const int64_t k = static_cast<int64_t>(lane) * ng + threadIdx.x / G;
+            const int64_t step = R * static_cast<int64_t>(blockDim.x);
+            for (int64_t base = r; base < ns; base += step) {
+                const int64_t u = base + R * k;
+                int64_t b0 = 0, b1 = 0;
+                int hi = 0;
+                if (u < ns) {
+                    const int32_t i = spike_list[u];
+                    if (static_cast<uint32_t>(i) < static_cast<uint64_t>(a.n_pre)) {
+                        const int64_t rs = a.indptr[i];
+                        if (a.tile_ptr) {
+                            const int32_t* tp = a.tile_ptr + static_cast<int64_t>(i) * (S + 1) + s;
+                            b0 = rs + tp[0];
+                            b1 = rs + tp[1];
+                        } else {
+                            b0 = rs;
+                            b1 = a.indptr[i + 1];
+                        }
+                        if (events_total && s == 0) ev += a.indptr[i + 1] - rs;
+                        hi = SPLIT && i >= split;
+                    }
+                }
+                for (int l = 0; l < G; ++l) {
+                    const int64_t c0 = __shfl_sync(FULL_MASK, b0, l, G);
+                    const int64_t c1 = __shfl_sync(FULL_MASK, b1, l, G);
+                    const int h = __shfl_sync(FULL_MASK, hi, l, G);
+                    if (c1 > c0) scatter_any<Acc, WK, VECL>(a.indices, a.data, a.w_homo, c0, c1, lane, G,
+                                                            acc + (h ? W : 0), col0);
+                }
+            }
+        };
         const int G0 = VECL ? pick_group_v4(nnz, a.n_pre, S) : pick_group(nnz, a.n_pre, S);
         const int64_t rows_here = ns > r ? (ns - r + R - 1) / R : 0;
         // the widened walk is a separate copy, so the common walk keeps the
         // code of the small fixed group sizes (measured: one shared copy with
         // a run-time group size slows the large cells by 9-17 %)
+        // (batched bounds measured on the n = 1e6 cells: FP32 / BF16 weights
+        // 1-18 % faster, integer counts with 16-byte index loads 2-15 % slower,
+        // so the homogeneous form keeps the per-row chain)
         if (rows_here * 2 * G0 <= static_cast<int64_t>(blockDim.x))
             walk(widen_group(G0, rows_here, blockDim.x, blockDim.x));
-        else
+        else if constexpr (WK == WK_HOMO)
             walk(G0);
+        else
+            walk_batched(G0);
         __syncthreads();
         const int64_t rem = a.n_post - col0;
         const int lim = static_cast<int>(rem < W ? rem : W);
