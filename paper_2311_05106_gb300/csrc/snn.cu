@@ -47,6 +47,11 @@ constexpr int kSnnThreads = 1024;
 constexpr int kSnnMaxRec = 4096;
 constexpr int kSnnMaxIn = 4096;
 constexpr int kSnnMaxOut = 64;
+// The recurrent-weight gradient is summed over blocks of kDwBlock steps
+// (aligned to absolute time, so the grouping does not depend on the
+// checkpoint interval): Ibar of the block's steps is kept, and when the block
+// is complete every entry adds its block sum once.
+constexpr int kDwBlock = 32;
 
 // Surrogate derivative and voltage-regulariser constants.
 struct SgK {
@@ -91,6 +96,7 @@ struct SnnK {
     float* seg_Vp;       // [B][K][n_rec]
     float* g_in;         // [B][n_in][n_rec]   per-batch-element gradient partials
     float* g_rec;        // [B][nnz]
+    float* ib_blk;       // [B][kDwBlock][n_rec]  Ibar of the steps of the current gradient block
     float* g_out;        // [B][n_rec][n_out]
     float* g_b;          // [B][n_out]
     double* vreg;        // [B]  regulariser sums of the forward
@@ -336,6 +342,7 @@ __global__ void __launch_bounds__(kSnnThreads, 1) k_snn_backward(SnnK p, const u
     // in a fixed order, so every gradient is reproducible bit for bit)
     float* gin = p.g_in + static_cast<int64_t>(b) * p.n_in * p.n_rec;
     float* grec = p.g_rec + static_cast<int64_t>(b) * p.nnz;
+    float* ib_keep = p.ib_blk + static_cast<int64_t>(b) * kDwBlock * p.n_rec;
     float* gout = p.g_out + static_cast<int64_t>(b) * p.n_rec * p.n_out;
     for (int64_t e = threadIdx.x; e < static_cast<int64_t>(p.n_in) * p.n_rec; e += kSnnThreads) gin[e] = 0.f;
     for (int64_t e = threadIdx.x; e < p.nnz; e += kSnnThreads) grec[e] = 0.f;
@@ -450,30 +457,41 @@ __global__ void __launch_bounds__(kSnnThreads, 1) k_snn_backward(SnnK p, const u
                 }
                 for (; a < n_act; ++a) gin[static_cast<int64_t>(in_list[a]) * p.n_rec + j] += ib;
             }
-            // dw_rec[e] += Ibar_t[col e] for the rows spiking at t - 1 (one warp per row;
-            // each lane issues the index and partial loads of four entries before
-            // their shared-memory lookups and stores, so a row of up to 128
-            // entries costs one memory latency)
-            if (t > 0) {
-                const uint32_t* zp = zall + static_cast<int64_t>(t - 1) * p.zw;
-                for (int w = warp; w < p.zw; w += kSnnThreads / 32) {
-                    for (uint32_t bits = zp[w]; bits; bits &= bits - 1) {
-                        const int i = 32 * w + __ffs(bits) - 1;
-                        const int64_t r0 = p.indptr[i], r1 = p.indptr[i + 1];
-                        for (int64_t e = r0 + lane; e < r1; e += 4 * 32) {
-                            int32_t c[4];
-                            float g[4];
+            // dw_rec[e] += Ibar_t[col e] for the rows spiking at t - 1: Ibar_t is
+            // kept for the step's gradient block, and when the block's lowest
+            // step is done each row that spiked in the block adds, entry by
+            // entry, the block's sum in one read-modify-write (instead of one
+            // per step and spike)
+            float* ibt = ib_keep + static_cast<int64_t>(t % kDwBlock) * p.n_rec;
+            for (int j = threadIdx.x; j < p.n_rec; j += kSnnThreads) ibt[j] = Ib[j];
+            if (t % kDwBlock == 0) {
+                __syncthreads();
+                const int hi = min(p.T, t + kDwBlock);
+                for (int i = warp; i < p.n_rec; i += kSnnThreads / 32) {
+                    // steps s of the block with row i spiking at s - 1 (bit s - t)
+                    uint32_t when = 0;
+                    for (int s = max(t, 1); s < hi; ++s)
+                        when |= ((zall[static_cast<int64_t>(s - 1) * p.zw + (i >> 5)] >> (i & 31)) & 1u) << (s - t);
+                    if (!when) continue;
+                    const int64_t r0 = p.indptr[i], r1 = p.indptr[i + 1];
+                    for (int64_t e = r0 + lane; e < r1; e += 4 * 32) {
+                        int32_t c[4];
+                        float acc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-                            for (int u = 0; u < 4; ++u) {
-                                const int64_t ee = e + 32 * u;
-                                c[u] = ee < r1 ? p.indices[ee] : 0;
-                                g[u] = ee < r1 ? grec[ee] : 0.f;
-                            }
+                        for (int u = 0; u < 4; ++u) {
+                            const int64_t ee = e + 32 * u;
+                            c[u] = ee < r1 ? p.indices[ee] : 0;
+                        }
+                        // steps in increasing order: a fixed summation order
+                        for (uint32_t m = when; m; m &= m - 1) {
+                            const float* row = ib_keep + static_cast<int64_t>(__ffs(m) - 1) * p.n_rec;
 #pragma unroll
-                            for (int u = 0; u < 4; ++u) {
-                                const int64_t ee = e + 32 * u;
-                                if (ee < r1) grec[ee] = g[u] + Ib[c[u]];
-                            }
+                            for (int u = 0; u < 4; ++u) acc[u] += row[c[u]];
+                        }
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int64_t ee = e + 32 * u;
+                            if (ee < r1) grec[ee] += acc[u];
                         }
                     }
                 }
@@ -547,7 +565,7 @@ __global__ void k_snn_reg_add(int32_t B, double scale, const double* __restrict_
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct SnnLayout {
-    size_t ck_I, ck_V, ck_y, z_all, seg_Vp, g_in, g_rec, g_out, g_b, vreg, w_fix, total;
+    size_t ck_I, ck_V, ck_y, z_all, seg_Vp, g_in, g_rec, ib_blk, g_out, g_b, vreg, w_fix, total;
     int32_t n_ck, zw;
 };
 
@@ -566,6 +584,7 @@ SnnLayout snn_layout(const bp_snn_desc& d) {
     L.seg_Vp = o; o = align256(o + B * static_cast<size_t>(K) * d.n_rec * 4);
     L.g_in = o; o = align256(o + B * static_cast<size_t>(d.n_in) * d.n_rec * 4);
     L.g_rec = o; o = align256(o + B * static_cast<size_t>(d.nnz > 0 ? d.nnz : 0) * 4);
+    L.ib_blk = o; o = align256(o + B * static_cast<size_t>(kDwBlock) * d.n_rec * 4);
     L.g_out = o; o = align256(o + B * static_cast<size_t>(d.n_rec) * d.n_out * 4);
     L.g_b = o; o = align256(o + B * static_cast<size_t>(d.n_out) * 4);
     L.vreg = o; o = align256(o + B * 8);
@@ -644,6 +663,7 @@ SnnK snn_kernel_args(const bp_snn_desc& d, void* ws) {
     p.seg_Vp = reinterpret_cast<float*>(w + L.seg_Vp);
     p.g_in = reinterpret_cast<float*>(w + L.g_in);
     p.g_rec = reinterpret_cast<float*>(w + L.g_rec);
+    p.ib_blk = reinterpret_cast<float*>(w + L.ib_blk);
     p.g_out = reinterpret_cast<float*>(w + L.g_out);
     p.g_b = reinterpret_cast<float*>(w + L.g_b);
     p.vreg = reinterpret_cast<double*>(w + L.vreg);
