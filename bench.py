@@ -813,12 +813,15 @@ def main():
     achieved = alg_bytes / (step_ms * 1e-3) / 1e9
     peak, peak_kind = peaks()
     lif_ms = lif_kernel_time(torch, B, net)
-    lif_bytes = LIF_BYTES_PER_NEURON * N_NEURONS
+    # without deliveries the event accumulators stay zero and in L2 (they are
+    # read with the evict-last policy), so the pass alone moves only the state
+    # through DRAM: V, g_e, g_i read and written, the refractory byte read
+    lif_bytes = (3 * 4 * 2 + 1) * N_NEURONS
     roofline = {"bound": "hbm", "kernel": "k_step (fused neuron pass + CSR delivery)", "achieved": achieved,
                 "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": step_traffic_record() if args.conn == "csr" and args.neurons == 4_000_000 else None,
                 "peak_source": peak_kind, "alg_bytes_per_launch": alg_bytes, "us_per_launch": step_ms * 1e3,
-                "neuron_pass_only": {"us_per_launch": lif_ms * 1e3, "alg_bytes": lif_bytes,
+                "neuron_pass_only": {"us_per_launch": lif_ms * 1e3, "state_bytes": lif_bytes,
                                      "achieved_gbs": lif_bytes / (lif_ms * 1e-3) / 1e9,
                                      "frac": lif_bytes / (lif_ms * 1e-3) / 1e9 / peak}}
 
