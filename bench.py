@@ -876,7 +876,8 @@ def main():
                    "connectivity": {"csr": "stored CSR, int32 indices, ", "jit": "JIT rows, "}[args.conn]
                    + {"f32": "FP32 weights", "counts": "homogeneous weights, int32 event counts"}[args.weights],
                    "neurons": N_NEURONS, "sim_steps": args.steps,
-                   "l2": "connectivity 2.6 GB + state 96 MB exceed L2; no flush between steps (state re-read each step)",
+                   "l2": "connectivity 2.6 GB + state 52 MB + event accumulators 64 MB; no flush between steps "
+                         "(state re-read every step, streamed evict-first)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "sim_steps_per_s": steps_per_s, "spikes_in_timed_region": spikes, "events_in_timed_region": events,
         "firing_rate_hz": spikes / (N_NEURONS * args.steps * DT_MS * 1e-3),
