@@ -110,19 +110,17 @@ bp_status launch_spike_compact(int64_t n, const uint8_t* events, int32_t* spike_
                                cudaStream_t s);
 
 // ---- csrmv.cu
-// Scatter of the spiking rows' entries.  Rows >= split go to y_hi (if
-// non-NULL), others to y.  events_total (nullable) += sum of spiking rows'
-// lengths.  mode: 0 auto, 1 direct (global atomics), 2 shared tiles.
+// Scatter of the spiking rows' entries into y.  events_total (nullable) +=
+// sum of spiking rows' lengths.  mode: 0 auto, 1 direct (global atomics),
+// 2 shared tiles.
 bp_status launch_event_csrmv(const CsrArgs& a, const int32_t* spike_list, const int32_t* n_spikes,
-                             int64_t max_spikes, void* y, void* y_hi, int64_t split, bool counts,
-                             int64_t* events_total, int mode, cudaStream_t s);
+                             int64_t max_spikes, void* y, bool counts, int64_t* events_total, int mode,
+                             cudaStream_t s);
 
 // ---- jitconn.cu
-// Scatter of JIT rows: spike ids < split use `lo` (row id = spike id) into y;
-// ids >= split use `hi` (row id = spike id - split) into y_hi.
-bp_status launch_jit_event_mv(const JitArgs& lo, const JitArgs& hi, int64_t split, int64_t n_post,
-                              const int32_t* spike_list, const int32_t* n_spikes, int64_t max_spikes,
-                              void* y, void* y_hi, bool counts, int64_t* events_total, int mode,
+// Scatter of JIT rows (row id = spike id) into y.
+bp_status launch_jit_event_mv(const JitArgs& d, int64_t n_post, const int32_t* spike_list, const int32_t* n_spikes,
+                              int64_t max_spikes, void* y, bool counts, int64_t* events_total, int mode,
                               cudaStream_t s);
 
 }  // namespace bp

@@ -28,8 +28,7 @@ namespace {
 constexpr int kDirectThreads = 256;
 
 // mode: 0 auto, 1 direct, 2 tiled.  W = tile width (post columns per tile),
-// S = number of tiles (the grid is S x R CTAs).  With SPLIT, rows >= split
-// go to y_hi and each CTA keeps two W-wide accumulators.
+// S = number of tiles (the grid is S x R CTAs).
 // Lanes per (row, tile) segment with vector loads: about 16 entries per lane.
 __device__ __forceinline__ int pick_group_v4(int64_t nnz, int64_t n_pre, int64_t tiles) {
     const int64_t denom = (n_pre > 0 ? n_pre : 1) * (tiles > 0 ? tiles : 1);
@@ -117,11 +116,11 @@ __device__ __forceinline__ void scatter_any(const int32_t* __restrict__ indices,
         scatter_segment<Acc, WK>(indices, data, w_homo, b0, b1, lane, G, out, col0);
 }
 
-template <typename Acc, int WK, bool SPLIT, bool VECL>
+template <typename Acc, int WK, bool VECL>
 __global__ void __launch_bounds__(kTileThreads, 1)
     k_csr_scatter(CsrArgs a, const int32_t* __restrict__ spike_list, const int32_t* __restrict__ n_spikes,
-                  int64_t max_spikes, Acc* __restrict__ y, Acc* __restrict__ y_hi, int64_t split, int mode,
-                  int32_t W, int32_t S, int64_t* __restrict__ events_total) {
+                  int64_t max_spikes, Acc* __restrict__ y, int mode, int32_t W, int32_t S,
+                  int64_t* __restrict__ events_total) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Acc* acc = reinterpret_cast<Acc*>(smem_raw);
     int64_t ns = *n_spikes;
@@ -143,17 +142,15 @@ __global__ void __launch_bounds__(kTileThreads, 1)
             const int32_t i = spike_list[u];
             if (static_cast<uint32_t>(i) >= static_cast<uint64_t>(a.n_pre)) continue;
             const int64_t b0 = a.indptr[i], b1 = a.indptr[i + 1];
-            Acc* out = (SPLIT && i >= split) ? y_hi : y;
             if (lane == 0) ev += b1 - b0;
-            scatter_any<Acc, WK, VECL>(a.indices, a.data, a.w_homo, b0, b1, lane, G, out, 0);
+            scatter_any<Acc, WK, VECL>(a.indices, a.data, a.w_homo, b0, b1, lane, G, y, 0);
         }
     } else {
         const int s = blockIdx.x % S;
         const int64_t r = blockIdx.x / S;
         const int64_t R = gridDim.x / S;
         const int64_t col0 = static_cast<int64_t>(s) * W;
-        const int nacc = SPLIT ? 2 * W : W;
-        for (int t = threadIdx.x; t < nacc; t += blockDim.x) acc[t] = Acc(0);
+        for (int t = threadIdx.x; t < W; t += blockDim.x) acc[t] = Acc(0);
         __syncthreads();
         // rows r, r + R, ... of the spike list, G lanes per row
         auto walk = [&](int G) {
@@ -174,8 +171,7 @@ __global__ void __launch_bounds__(kTileThreads, 1)
                     b1 = a.indptr[i + 1];
                 }
                 if (events_total && s == 0 && lane == 0) ev += a.indptr[i + 1] - rs;
-                Acc* out = acc + ((SPLIT && i >= split) ? W : 0);
-                scatter_any<Acc, WK, VECL>(a.indices, a.data, a.w_homo, b0, b1, lane, G, out, col0);
+                scatter_any<Acc, WK, VECL>(a.indices, a.data, a.w_homo, b0, b1, lane, G, acc, col0);
             }
         };
         // rows in batches of one per thread: every thread first fetches the
@@ -194,7 +190,6 @@ __global__ void __launch_bounds__(kTileThreads, 1)
             for (int64_t base = r; base < ns; base += step) {
                 const int64_t u = base + R * k;
                 int64_t b0 = 0, b1 = 0;
-                int hi = 0;
                 if (u < ns) {
                     const int32_t i = spike_list[u];
                     if (static_cast<uint32_t>(i) < static_cast<uint64_t>(a.n_pre)) {
@@ -208,15 +203,12 @@ __global__ void __launch_bounds__(kTileThreads, 1)
                             b1 = a.indptr[i + 1];
                         }
                         if (events_total && s == 0) ev += a.indptr[i + 1] - rs;
-                        hi = SPLIT && i >= split;
                     }
                 }
                 for (int l = 0; l < G; ++l) {
                     const int64_t c0 = __shfl_sync(FULL_MASK, b0, l, G);
                     const int64_t c1 = __shfl_sync(FULL_MASK, b1, l, G);
-                    const int h = __shfl_sync(FULL_MASK, hi, l, G);
-                    if (c1 > c0) scatter_any<Acc, WK, VECL>(a.indices, a.data, a.w_homo, c0, c1, lane, G,
-                                                            acc + (h ? W : 0), col0);
+                    if (c1 > c0) scatter_any<Acc, WK, VECL>(a.indices, a.data, a.w_homo, c0, c1, lane, G, acc, col0);
                 }
             }
         };
@@ -240,21 +232,16 @@ __global__ void __launch_bounds__(kTileThreads, 1)
         for (int t = threadIdx.x; t < lim; t += blockDim.x) {
             const Acc v = acc[t];
             if (v != Acc(0)) acc_add(y + col0 + t, v);
-            if constexpr (SPLIT) {
-                const Acc v2 = acc[W + t];
-                if (v2 != Acc(0)) acc_add(y_hi + col0 + t, v2);
-            }
         }
     }
     if (events_total) block_add_i64(ev, events_total);
 }
 
 // Direct-only variant without dynamic shared memory (more CTAs per SM).
-template <typename Acc, int WK, bool SPLIT, bool VECL>
+template <typename Acc, int WK, bool VECL>
 __global__ void __launch_bounds__(kDirectThreads)
     k_csr_scatter_direct(CsrArgs a, const int32_t* __restrict__ spike_list, const int32_t* __restrict__ n_spikes,
-                         int64_t max_spikes, Acc* __restrict__ y, Acc* __restrict__ y_hi, int64_t split,
-                         int64_t* __restrict__ events_total) {
+                         int64_t max_spikes, Acc* __restrict__ y, int64_t* __restrict__ events_total) {
     int64_t ns = *n_spikes;
     ns = ns < max_spikes ? ns : max_spikes;
     const int64_t nnz = a.indptr[a.n_pre];
@@ -267,9 +254,8 @@ __global__ void __launch_bounds__(kDirectThreads)
         const int32_t i = spike_list[u];
         if (static_cast<uint32_t>(i) >= static_cast<uint64_t>(a.n_pre)) continue;
         const int64_t b0 = a.indptr[i], b1 = a.indptr[i + 1];
-        Acc* out = (SPLIT && i >= split) ? y_hi : y;
         if (lane == 0) ev += b1 - b0;
-        scatter_any<Acc, WK, VECL>(a.indices, a.data, a.w_homo, b0, b1, lane, G, out, 0);
+        scatter_any<Acc, WK, VECL>(a.indices, a.data, a.w_homo, b0, b1, lane, G, y, 0);
     }
     if (events_total) block_add_i64(ev, events_total);
 }
@@ -455,13 +441,12 @@ __global__ void k_tile_index(int64_t n_pre, const int64_t* __restrict__ indptr, 
     }
 }
 
-template <typename Acc, int WK, bool SPLIT, bool VECL>
+template <typename Acc, int WK, bool VECL>
 bp_status launch_scatter_t(const CsrArgs& a, const int32_t* spike_list, const int32_t* n_spikes, int64_t max_spikes,
-                           void* y, void* y_hi, int64_t split, int64_t* events_total, int mode, cudaStream_t s) {
+                           void* y, int64_t* events_total, int mode, cudaStream_t s) {
     Acc* yy = static_cast<Acc*>(y);
-    Acc* yh = static_cast<Acc*>(y_hi);
     // tile geometry: one tile covers n_post if it fits, otherwise the tile index's width
-    const int32_t cap = SPLIT ? kTileCols / 2 : kTileCols;
+    const int32_t cap = kTileCols;
     int32_t W = 0, S = 0;
     if (a.n_post <= cap) {
         W = static_cast<int32_t>(a.n_post > 0 ? a.n_post : 1);
@@ -477,30 +462,29 @@ bp_status launch_scatter_t(const CsrArgs& a, const int32_t* spike_list, const in
     if (S == 1) at.tile_ptr = nullptr;  // one tile covers every column: whole rows
     if (mode == 1) {
         const int grid = sm_count() * 8;
-        k_csr_scatter_direct<Acc, WK, SPLIT, VECL><<<grid, kDirectThreads, 0, s>>>(a, spike_list, n_spikes,
-                                                                                   max_spikes, yy, yh, split,
-                                                                                   events_total);
+        k_csr_scatter_direct<Acc, WK, VECL><<<grid, kDirectThreads, 0, s>>>(a, spike_list, n_spikes, max_spikes, yy,
+                                                                            events_total);
         BP_LAUNCHED();
         return BP_OK;
     }
-    const size_t smem = static_cast<size_t>(SPLIT ? 2 * W : W) * sizeof(Acc);
-    BP_TRY(ensure_smem_attr(reinterpret_cast<const void*>(k_csr_scatter<Acc, WK, SPLIT, VECL>),
-                            static_cast<int>(SPLIT ? 2 * cap * sizeof(Acc) : cap * sizeof(Acc))));
+    const size_t smem = static_cast<size_t>(W) * sizeof(Acc);
+    BP_TRY(ensure_smem_attr(reinterpret_cast<const void*>(k_csr_scatter<Acc, WK, VECL>),
+                            static_cast<int>(cap * sizeof(Acc))));
     // one 1024-thread CTA per SM: R row groups per tile so that S x R covers the SMs
     int64_t R = static_cast<int64_t>(sm_count()) / S;
     if (R < 1) R = 1;
     const int64_t grid = R * S;
-    k_csr_scatter<Acc, WK, SPLIT, VECL><<<static_cast<unsigned>(grid), kTileThreads, smem, s>>>(
-        at, spike_list, n_spikes, max_spikes, yy, yh, split, mode, W, S, events_total);
+    k_csr_scatter<Acc, WK, VECL><<<static_cast<unsigned>(grid), kTileThreads, smem, s>>>(
+        at, spike_list, n_spikes, max_spikes, yy, mode, W, S, events_total);
     BP_LAUNCHED();
     return BP_OK;
 }
 
 bool aligned_to(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
 
-template <typename Acc, int WK, bool SPLIT>
-bp_status launch_scatter_a(const CsrArgs& a, const int32_t* sl, const int32_t* ns, int64_t mx, void* y, void* yh,
-                           int64_t split, int64_t* ev, int mode, cudaStream_t s) {
+template <typename Acc, int WK>
+bp_status launch_scatter_a(const CsrArgs& a, const int32_t* sl, const int32_t* ns, int64_t mx, void* y, int64_t* ev,
+                           int mode, cudaStream_t s) {
     // 16-byte index loads (aligned indices) pay off for homogeneous weights,
     // whose events cost only the 4-byte index: with 4-byte loads too few bytes
     // are in flight per SM.  BF16 weights take pairs (8-byte index and 4-byte
@@ -509,17 +493,17 @@ bp_status launch_scatter_a(const CsrArgs& a, const int32_t* sl, const int32_t* n
     // vector forms measured slower or mixed).
     const bool vec = (WK == WK_HOMO && aligned_to(a.indices, 16)) ||
                      (WK == WK_BF16 && aligned_to(a.indices, 8) && aligned_to(a.data, 4));
-    if (vec) return launch_scatter_t<Acc, WK, SPLIT, true>(a, sl, ns, mx, y, yh, split, ev, mode, s);
-    return launch_scatter_t<Acc, WK, SPLIT, false>(a, sl, ns, mx, y, yh, split, ev, mode, s);
+    if (vec) return launch_scatter_t<Acc, WK, true>(a, sl, ns, mx, y, ev, mode, s);
+    return launch_scatter_t<Acc, WK, false>(a, sl, ns, mx, y, ev, mode, s);
 }
 
-template <typename Acc, bool SPLIT>
-bp_status launch_scatter_wk(const CsrArgs& a, const int32_t* sl, const int32_t* ns, int64_t mx, void* y, void* yh,
-                            int64_t split, int64_t* ev, int mode, cudaStream_t s) {
+template <typename Acc>
+bp_status launch_scatter_wk(const CsrArgs& a, const int32_t* sl, const int32_t* ns, int64_t mx, void* y, int64_t* ev,
+                            int mode, cudaStream_t s) {
     switch (a.wkind) {
-        case BP_W_F32: return launch_scatter_a<Acc, WK_F32, SPLIT>(a, sl, ns, mx, y, yh, split, ev, mode, s);
-        case BP_W_BF16: return launch_scatter_a<Acc, WK_BF16, SPLIT>(a, sl, ns, mx, y, yh, split, ev, mode, s);
-        default: return launch_scatter_a<Acc, WK_HOMO, SPLIT>(a, sl, ns, mx, y, yh, split, ev, mode, s);
+        case BP_W_F32: return launch_scatter_a<Acc, WK_F32>(a, sl, ns, mx, y, ev, mode, s);
+        case BP_W_BF16: return launch_scatter_a<Acc, WK_BF16>(a, sl, ns, mx, y, ev, mode, s);
+        default: return launch_scatter_a<Acc, WK_HOMO>(a, sl, ns, mx, y, ev, mode, s);
     }
 }
 
@@ -544,20 +528,10 @@ int gather_grid(int64_t n_pre) {
 }  // namespace
 
 bp_status launch_event_csrmv(const CsrArgs& a, const int32_t* spike_list, const int32_t* n_spikes, int64_t max_spikes,
-                             void* y, void* y_hi, int64_t split, bool counts, int64_t* events_total, int mode,
-                             cudaStream_t s) {
+                             void* y, bool counts, int64_t* events_total, int mode, cudaStream_t s) {
     if (max_spikes <= 0 || a.n_post == 0) return BP_OK;
-    const bool sp = y_hi != nullptr;
-    if (counts) {
-        return sp ? launch_scatter_wk<int32_t, true>(a, spike_list, n_spikes, max_spikes, y, y_hi, split,
-                                                     events_total, mode, s)
-                  : launch_scatter_wk<int32_t, false>(a, spike_list, n_spikes, max_spikes, y, y_hi, split,
-                                                      events_total, mode, s);
-    }
-    return sp ? launch_scatter_wk<float, true>(a, spike_list, n_spikes, max_spikes, y, y_hi, split, events_total,
-                                               mode, s)
-              : launch_scatter_wk<float, false>(a, spike_list, n_spikes, max_spikes, y, y_hi, split, events_total,
-                                                mode, s);
+    if (counts) return launch_scatter_wk<int32_t>(a, spike_list, n_spikes, max_spikes, y, events_total, mode, s);
+    return launch_scatter_wk<float>(a, spike_list, n_spikes, max_spikes, y, events_total, mode, s);
 }
 
 }  // namespace bp
@@ -602,7 +576,7 @@ bp_status bp_event_csrmv(int64_t n_pre, int64_t n_post, const int64_t* indptr, c
     BP_REQUIRE(n_post == 0 || y != nullptr, "y is NULL");
     BP_REQUIRE(max_spikes == 0 || (spike_list && n_spikes && indices), "spike list, count or indices is NULL");
     if (flags & BP_OVERWRITE) BP_CUDA(cudaMemsetAsync(y, 0, static_cast<size_t>(n_post) * 4, stream));
-    return bp::launch_event_csrmv(a, spike_list, n_spikes, max_spikes, y, nullptr, n_pre, y_is_count != 0, nullptr,
+    return bp::launch_event_csrmv(a, spike_list, n_spikes, max_spikes, y, y_is_count != 0, nullptr,
                                   mode_from_flags(flags), stream);
 }
 
@@ -627,8 +601,8 @@ bp_status bp_event_csrmv_dense(int64_t n_pre, int64_t n_post, const int64_t* ind
     int32_t* list = reinterpret_cast<int32_t*>(static_cast<char*>(workspace) + 16);
     BP_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t), stream));
     BP_TRY(bp::launch_spike_compact(n_pre, events, list, cnt, stream));
-    return bp::launch_event_csrmv(a, list, cnt, n_pre, y, nullptr, n_pre, y_is_count != 0, nullptr,
-                                  mode_from_flags(flags), stream);
+    return bp::launch_event_csrmv(a, list, cnt, n_pre, y, y_is_count != 0, nullptr, mode_from_flags(flags),
+                                  stream);
 }
 
 int64_t bp_csr_tile_index_size(int64_t n_pre, int64_t n_post, int32_t tile_cols) {

@@ -73,49 +73,39 @@ __device__ __forceinline__ int64_t jit_walk_cta(const JitArgs& d, uint32_t row, 
 }
 
 // Event scatter of JIT rows.  SMEM: the CTA accumulates all n_post columns
-// (two vectors with SPLIT) in shared memory of `wpad` entries each.  With
-// few rows compared with the warps and long rows (expected length 2 n_post /
-// (K + 1) of 512 or more) each row is walked by a whole CTA (jit_walk_cta)
-// instead of one warp.
-template <typename Acc, int WK, bool SPLIT, bool SMEM>
-__global__ void __launch_bounds__(kJitThreads) k_jit_scatter(JitArgs lo, JitArgs hi, int64_t split, int64_t n_post,
+// in shared memory of `wpad` entries.  With few rows compared with the warps
+// and long rows (expected length 2 n_post / (K + 1) of 512 or more) each row
+// is walked by a whole CTA (jit_walk_cta) instead of one warp.
+template <typename Acc, int WK, bool SMEM>
+__global__ void __launch_bounds__(kJitThreads) k_jit_scatter(JitArgs d, int64_t n_post,
                                                              const int32_t* __restrict__ spike_list,
                                                              const int32_t* __restrict__ n_spikes, int64_t max_spikes,
-                                                             Acc* __restrict__ y, Acc* __restrict__ y_hi, int32_t wpad,
+                                                             Acc* __restrict__ y, int32_t wpad,
                                                              int64_t* __restrict__ events_total) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Acc* acc = reinterpret_cast<Acc*>(smem_raw);
     if constexpr (SMEM) {
-        const int nacc = SPLIT ? 2 * wpad : wpad;
-        for (int t = threadIdx.x; t < nacc; t += blockDim.x) acc[t] = Acc(0);
+        for (int t = threadIdx.x; t < wpad; t += blockDim.x) acc[t] = Acc(0);
         __syncthreads();
     }
+    Acc* out = SMEM ? acc : y;
     int64_t ns = *n_spikes;
     ns = ns < max_spikes ? ns : max_spikes;
     const int64_t nwarps = static_cast<int64_t>(gridDim.x) * kJitWarps;
     int64_t ev = 0;
-    const uint32_t kmin = lo.K < hi.K ? lo.K : hi.K;
-    const int64_t est_len = 2 * n_post / (static_cast<int64_t>(kmin) + 1);
+    const int64_t est_len = 2 * n_post / (static_cast<int64_t>(d.K) + 1);
     if (ns * 4 <= nwarps && est_len >= 512) {
         for (int64_t u = blockIdx.x; u < ns; u += gridDim.x) {
             const int32_t i = spike_list[u];
             if (i < 0) continue;
-            const bool upper = SPLIT && i >= split;
-            const JitArgs& d = upper ? hi : lo;
-            const uint32_t row = static_cast<uint32_t>(upper ? i - split : i);
-            Acc* out = SMEM ? (acc + (upper ? wpad : 0)) : (upper ? y_hi : y);
-            ev += jit_walk_cta<WK>(d, row, n_post,
+            ev += jit_walk_cta<WK>(d, static_cast<uint32_t>(i), n_post,
                                    [&](int64_t q, uint64_t, float w) { acc_add(out + q, event_value<Acc>(w)); });
         }
     } else {
         for (int64_t u = static_cast<int64_t>(blockIdx.x) * kJitWarps + (threadIdx.x >> 5); u < ns; u += nwarps) {
             const int32_t i = spike_list[u];
             if (i < 0) continue;
-            const bool upper = SPLIT && i >= split;
-            const JitArgs& d = upper ? hi : lo;
-            const uint32_t row = static_cast<uint32_t>(upper ? i - split : i);
-            Acc* out = SMEM ? (acc + (upper ? wpad : 0)) : (upper ? y_hi : y);
-            ev += jit_walk<WK>(d, row, n_post,
+            ev += jit_walk<WK>(d, static_cast<uint32_t>(i), n_post,
                                [&](int64_t q, uint64_t, float w) { acc_add(out + q, event_value<Acc>(w)); });
         }
     }
@@ -124,10 +114,6 @@ __global__ void __launch_bounds__(kJitThreads) k_jit_scatter(JitArgs lo, JitArgs
         for (int t = threadIdx.x; t < n_post; t += blockDim.x) {
             const Acc v = acc[t];
             if (v != Acc(0)) acc_add(y + t, v);
-            if constexpr (SPLIT) {
-                const Acc v2 = acc[wpad + t];
-                if (v2 != Acc(0)) acc_add(y_hi + t, v2);
-            }
         }
     }
     if (events_total) block_add_i64(ev, events_total);
@@ -242,43 +228,35 @@ int jit_grid(int64_t rows) {
     return static_cast<int>(g > 0 ? g : 1);
 }
 
-template <typename Acc, int WK, bool SPLIT>
-bp_status launch_jit_scatter_t(const JitArgs& lo, const JitArgs& hi, int64_t split, int64_t n_post,
-                               const int32_t* sl, const int32_t* ns, int64_t mx, void* y, void* y_hi, int64_t* ev,
-                               int mode, cudaStream_t s) {
-    const int32_t cap = SPLIT ? kTileCols / 2 : kTileCols;
+template <typename Acc, int WK>
+bp_status launch_jit_scatter_t(const JitArgs& d, int64_t n_post, const int32_t* sl, const int32_t* ns, int64_t mx,
+                               void* y, int64_t* ev, int mode, cudaStream_t s) {
+    const int32_t cap = kTileCols;
     const bool fits = n_post <= cap;
     const int grid_direct = sm_count() * 4;
     if (fits && mode != 1) {
         const int32_t wpad = static_cast<int32_t>((n_post + 31) & ~int64_t(31));
-        const size_t smem = static_cast<size_t>(SPLIT ? 2 * wpad : wpad) * sizeof(Acc);
-        BP_TRY(ensure_smem_attr(reinterpret_cast<const void*>(k_jit_scatter<Acc, WK, SPLIT, true>),
-                                static_cast<int>(SPLIT ? 2 * cap * sizeof(Acc) : cap * sizeof(Acc))));
+        const size_t smem = static_cast<size_t>(wpad) * sizeof(Acc);
+        BP_TRY(ensure_smem_attr(reinterpret_cast<const void*>(k_jit_scatter<Acc, WK, true>),
+                                static_cast<int>(cap * sizeof(Acc))));
         // one shared copy of y per CTA: use one CTA per SM
-        k_jit_scatter<Acc, WK, SPLIT, true><<<sm_count(), kJitThreads, smem, s>>>(
-            lo, hi, split, n_post, sl, ns, mx, static_cast<Acc*>(y), static_cast<Acc*>(y_hi), wpad, ev);
+        k_jit_scatter<Acc, WK, true><<<sm_count(), kJitThreads, smem, s>>>(d, n_post, sl, ns, mx,
+                                                                           static_cast<Acc*>(y), wpad, ev);
     } else {
-        k_jit_scatter<Acc, WK, SPLIT, false><<<grid_direct, kJitThreads, 0, s>>>(
-            lo, hi, split, n_post, sl, ns, mx, static_cast<Acc*>(y), static_cast<Acc*>(y_hi), 0, ev);
+        k_jit_scatter<Acc, WK, false><<<grid_direct, kJitThreads, 0, s>>>(d, n_post, sl, ns, mx,
+                                                                          static_cast<Acc*>(y), 0, ev);
     }
     BP_LAUNCHED();
     return BP_OK;
 }
 
-template <typename Acc, bool SPLIT>
-bp_status launch_jit_scatter_wk(const JitArgs& lo, const JitArgs& hi, int64_t split, int64_t n_post,
-                                const int32_t* sl, const int32_t* ns, int64_t mx, void* y, void* y_hi, int64_t* ev,
-                                int mode, cudaStream_t s) {
-    switch (lo.wkind) {
-        case BP_JIT_UNIFORM:
-            return launch_jit_scatter_t<Acc, BP_JIT_UNIFORM, SPLIT>(lo, hi, split, n_post, sl, ns, mx, y, y_hi, ev,
-                                                                     mode, s);
-        case BP_JIT_NORMAL:
-            return launch_jit_scatter_t<Acc, BP_JIT_NORMAL, SPLIT>(lo, hi, split, n_post, sl, ns, mx, y, y_hi, ev,
-                                                                    mode, s);
-        default:
-            return launch_jit_scatter_t<Acc, BP_JIT_HOMO, SPLIT>(lo, hi, split, n_post, sl, ns, mx, y, y_hi, ev,
-                                                                  mode, s);
+template <typename Acc>
+bp_status launch_jit_scatter_wk(const JitArgs& d, int64_t n_post, const int32_t* sl, const int32_t* ns, int64_t mx,
+                                void* y, int64_t* ev, int mode, cudaStream_t s) {
+    switch (d.wkind) {
+        case BP_JIT_UNIFORM: return launch_jit_scatter_t<Acc, BP_JIT_UNIFORM>(d, n_post, sl, ns, mx, y, ev, mode, s);
+        case BP_JIT_NORMAL: return launch_jit_scatter_t<Acc, BP_JIT_NORMAL>(d, n_post, sl, ns, mx, y, ev, mode, s);
+        default: return launch_jit_scatter_t<Acc, BP_JIT_HOMO>(d, n_post, sl, ns, mx, y, ev, mode, s);
     }
 }
 
@@ -303,20 +281,13 @@ bp_status check_desc(const bp_jit_desc* d, int64_t n_pre, int64_t n_post) {
 
 }  // namespace
 
-bp_status launch_jit_event_mv(const JitArgs& lo, const JitArgs& hi, int64_t split, int64_t n_post,
-                              const int32_t* spike_list, const int32_t* n_spikes, int64_t max_spikes, void* y,
-                              void* y_hi, bool counts, int64_t* events_total, int mode, cudaStream_t s) {
+bp_status launch_jit_event_mv(const JitArgs& d, int64_t n_post, const int32_t* spike_list, const int32_t* n_spikes,
+                              int64_t max_spikes, void* y, bool counts, int64_t* events_total, int mode,
+                              cudaStream_t s) {
     if (max_spikes <= 0 || n_post == 0) return BP_OK;
-    const bool sp = y_hi != nullptr;
     if (counts)
-        return sp ? launch_jit_scatter_wk<int32_t, true>(lo, hi, split, n_post, spike_list, n_spikes, max_spikes, y,
-                                                         y_hi, events_total, mode, s)
-                  : launch_jit_scatter_wk<int32_t, false>(lo, hi, split, n_post, spike_list, n_spikes, max_spikes, y,
-                                                          y_hi, events_total, mode, s);
-    return sp ? launch_jit_scatter_wk<float, true>(lo, hi, split, n_post, spike_list, n_spikes, max_spikes, y, y_hi,
-                                                   events_total, mode, s)
-              : launch_jit_scatter_wk<float, false>(lo, hi, split, n_post, spike_list, n_spikes, max_spikes, y, y_hi,
-                                                    events_total, mode, s);
+        return launch_jit_scatter_wk<int32_t>(d, n_post, spike_list, n_spikes, max_spikes, y, events_total, mode, s);
+    return launch_jit_scatter_wk<float>(d, n_post, spike_list, n_spikes, max_spikes, y, events_total, mode, s);
 }
 
 }  // namespace bp
@@ -336,8 +307,8 @@ bp_status bp_jitconn_event_mv(const bp_jit_desc* d, int64_t n_pre, int64_t n_pos
     if (flags & BP_OVERWRITE) BP_CUDA(cudaMemsetAsync(y, 0, static_cast<size_t>(n_post) * 4, stream));
     const bp::JitArgs a = bp::to_args(*d);
     const int mode = (flags & BP_ACC_GLOBAL) ? 1 : ((flags & BP_ACC_SHARED) ? 2 : 0);
-    return bp::launch_jit_event_mv(a, a, n_pre, n_post, spike_list, n_spikes, max_spikes, y, nullptr,
-                                   y_is_count != 0, nullptr, mode, stream);
+    return bp::launch_jit_event_mv(a, n_post, spike_list, n_spikes, max_spikes, y, y_is_count != 0, nullptr, mode,
+                                   stream);
 }
 
 bp_status bp_jitconn_event_mv_bwd(const bp_jit_desc* d, int64_t n_pre, int64_t n_post, const float* dy, float* dx_pre,

@@ -88,7 +88,7 @@ bp_status bp_event_csrmv_dense_noalloc(int64_t n_pre, int64_t n_post, const int6
     BP_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t), stream));
     BP_TRY(bp::launch_spike_compact(n_pre, events, list, cnt, stream));
     const int mode = (flags & BP_ACC_GLOBAL) ? 1 : ((flags & BP_ACC_SHARED) ? 2 : 0);
-    return bp::launch_event_csrmv(a, list, cnt, n_pre, y, nullptr, n_pre, y_is_count != 0, nullptr, mode, stream);
+    return bp::launch_event_csrmv(a, list, cnt, n_pre, y, y_is_count != 0, nullptr, mode, stream);
 }
 
 }  // extern "C"

@@ -176,6 +176,30 @@ def test_event_csrmv_float_weights(case, flags):
     assert rel_err(yh.cpu().numpy(), orc.event_csrmv(ip, ix, None, ev, n_post, w_homo=0.6)) < RTOL_F32
 
 
+def test_event_csrmv_float_weights_many_rows_per_cta():
+    """FP32 and BF16 weights with enough spiking rows per post tile that each
+    CTA fetches the segment bounds of its rows in batches of one per thread
+    (two batches, the second partial): the sums match the oracle's."""
+    n_pre, n_post, p = 120_000, 150_001, 0.002
+    ip, ix = _csr(n_pre, n_post, p, seed=5)
+    w = wl.normal_weights(len(ix), 0.5, 0.1, seed=6)
+    ev = wl.bernoulli_spikes(n_pre, 0.5, seed=7)
+    dip, dix = cuda(ip), cuda(ix)
+    tcols = B.bp_tile_cols()
+    tp = torch.empty(B.bp_csr_tile_index_size(n_pre, n_post, tcols), dtype=torch.int32, device="cuda")
+    B.bp_csr_tile_index(dip, dix, n_post, tcols, tp)
+    sl, ns = spike_list_of(ev)
+    ref = orc.event_csrmv(ip, ix, w.astype(np.float64), ev, n_post)
+    y = torch.zeros(n_post, dtype=torch.float32, device="cuda")
+    B.bp_event_csrmv(dip, dix, cuda(w), 0.0, sl, ns, y, tile_ptr=tp, tile_cols=tcols, flags=B.BP_ACC_SHARED)
+    assert rel_err(y.cpu().numpy(), ref) < RTOL_F32
+    wb = cuda(w).to(torch.bfloat16)
+    yb = torch.zeros(n_post, dtype=torch.float32, device="cuda")
+    B.bp_event_csrmv(dip, dix, wb, 0.0, sl, ns, yb, tile_ptr=tp, tile_cols=tcols, flags=B.BP_ACC_SHARED)
+    ref_b = orc.event_csrmv(ip, ix, wb.float().cpu().numpy().astype(np.float64), ev, n_post)
+    assert rel_err(yb.cpu().numpy(), ref_b) < RTOL_F32
+
+
 def test_event_csrmv_dense_events():
     n_pre, n_post = 7000, 9000
     ip, ix = _csr(n_pre, n_post, 0.01, seed=5)
