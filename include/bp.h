@@ -454,7 +454,8 @@ typedef struct {
     bp_coba_params coba;    /* shared by every network */
     /* device state, caller-owned, concatenated: network b occupies
      * [off_b, off_b + n_b) with off_b from bp_batch_layout; padding entries
-     * are never simulated. */
+     * are never simulated.  V, ge, gi must be 16-byte and ref 4-byte aligned
+     * (four neurons per access; BP_ERR_INVALID otherwise). */
     float* V;
     float* ge;
     float* gi;
