@@ -34,7 +34,8 @@
 // recurrent weights are converted to fixed point once per forward call
 // (k_snn_fix_weights), so delivering an event is one integer atomic.
 // Recurrent weights are FP32 or BF16 (FP32 arithmetic); gradients are FP32,
-// accumulated with atomics across batch elements.
+// accumulated per batch element and then summed over the batch in a fixed
+// order (k_snn_reduce), so they are reproducible bit for bit.
 #include <cmath>
 
 #include "bp_common.cuh"
