@@ -1,9 +1,10 @@
 // lif.cu -- the fused neuron step (a1-a4) and, for the network, the delivery
 // of the step's spikes in the same kernel (a5/a6).
 //
-// Neuron pass.  Structure-of-arrays FP32 state; each thread updates VEC = 4
-// consecutive neurons per grid-stride iteration with 16-byte loads and
-// stores: decay and event add of both conductances (Appendix E), COBA
+// Neuron pass.  Structure-of-arrays FP32 state and one-byte refractory
+// counters; each thread updates VEC = 4 consecutive neurons per grid-stride
+// iteration with 16-byte loads and stores (one 4-byte word for the four
+// counters): decay and event add of both conductances (Appendix E), COBA
 // current with the pre-update potential (Appendix F), exponential-Euler
 // membrane update with refractory clamp, threshold and reset.  Spike flags
 // stay in a 32-bit register mask (bit = iteration * VEC + element), so the
