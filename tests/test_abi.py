@@ -119,3 +119,45 @@ def test_refractory_counter_range_host_check(libpath):
     h = ctypes.c_void_p()
     assert L.bp_network_create(ctypes.byref(d), ctypes.byref(h)) != 0
     assert b"refractory" in L.bp_last_error()
+
+
+def test_operator_and_constructor_host_checks(libpath):
+    """Invalid arguments to the event products, the JIT product, the spike
+    compaction and the network / batch constructors are rejected on the host,
+    with a message naming the problem, before any device work (this machine
+    has no GPU; the pointers below are never dereferenced)."""
+    from paper_2311_05106_gb300 import binding as B
+    L = B.lib()
+    fake = ctypes.c_void_p(256)
+
+    def rejected(status, word):
+        assert status != 0
+        assert word in L.bp_last_error(), L.bp_last_error()
+
+    H, F32 = B.BP_W_HOMO, B.BP_W_F32
+    rejected(L.bp_event_csrmv(-1, 10, fake, fake, None, H, 1.0, fake, fake, 0, fake, 1, None, 0, 0, None),
+             b"negative")
+    rejected(L.bp_event_csrmv(10, 10, fake, fake, fake, F32, 1.0, fake, fake, 5, fake, 1, None, 0, 0, None),
+             b"homogeneous")
+    rejected(L.bp_event_csrmv(10, 10, fake, fake, None, H, 1.0, fake, fake, 11, fake, 1, None, 0, 0, None),
+             b"max_spikes")
+    rejected(L.bp_event_csrmv(10, 10, fake, fake, fake, 7, 1.0, fake, fake, 5, fake, 0, None, 0, 0, None),
+             b"weight kind")
+    rejected(L.bp_event_csrmv(10, 10, fake, fake, None, F32, 1.0, fake, fake, 5, fake, 0, None, 0, 0, None),
+             b"weights are NULL")
+    rejected(L.bp_event_csrmv(10, 10, fake, fake, None, H, 1.0, fake, fake, 5, fake, 1, fake, 100, 0, None),
+             b"tile_cols")
+    rejected(L.bp_event_csrmv_t(10, 10, None, fake, None, H, 1.0, fake, fake, None, 0, 0, None), b"indptr")
+    rejected(L.bp_event_csrmv_t(10, 10, fake, fake, None, H, 1.0, None, fake, None, 0, 0, None), b"x_post")
+    d = B.JitDesc()                      # K = 0: not initialised
+    rejected(L.bp_jitconn_event_mv(ctypes.byref(d), 10, 10, fake, fake, 5, fake, 0, 0, None), b"K =")
+    d = B.bp_jit_desc_init(1, 0.1, B.BP_JIT_NORMAL, 0.5, 0.1)
+    rejected(L.bp_jitconn_event_mv(ctypes.byref(d), 10, 10, fake, fake, 5, fake, 1, 0, None), b"homogeneous")
+    rejected(L.bp_spike_compact(-1, fake, fake, fake, None), b"out of range")
+    rejected(L.bp_spike_compact(10, None, fake, fake, None), b"NULL")
+    nd = B.NetDesc()
+    h = ctypes.c_void_p()
+    rejected(L.bp_network_create(ctypes.byref(nd), ctypes.byref(h)), b"out of range")
+    bd = B.BatchDesc()
+    rejected(L.bp_batch_create(ctypes.byref(bd), ctypes.byref(h)), b"missing")
+    assert not h.value
