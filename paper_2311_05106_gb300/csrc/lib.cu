@@ -1,5 +1,6 @@
 // lib.cu -- library-wide entry points: version, error reporting, the sticky
 // device status word, parameter defaults and small host-side helpers.
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -16,8 +17,10 @@ __device__ int g_device_status = 0;
 
 constexpr int kMaxDevices = 64;
 int* g_status_addr[kMaxDevices] = {nullptr};
-int g_sm_count[kMaxDevices] = {0};
-int g_smem_optin[kMaxDevices] = {0};
+// per-device attributes, queried once; any thread may fill them (the value
+// written is the same), so relaxed atomics suffice
+std::atomic<int> g_sm_count[kMaxDevices];
+std::atomic<int> g_smem_optin[kMaxDevices];
 std::mutex g_mu;
 
 int current_device() {
@@ -51,12 +54,14 @@ int* device_status_ptr() {
 
 int sm_count() {
     const int d = current_device();
-    if (!g_sm_count[d]) {
+    int c = g_sm_count[d].load(std::memory_order_relaxed);
+    if (!c) {
         int v = 0;
         cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, d);
-        g_sm_count[d] = v > 0 ? v : 1;
+        c = v > 0 ? v : 1;
+        g_sm_count[d].store(c, std::memory_order_relaxed);
     }
-    return g_sm_count[d];
+    return c;
 }
 
 bp_status ensure_smem_attr(const void* kernel, int bytes) {
@@ -76,12 +81,14 @@ bp_status ensure_smem_attr(const void* kernel, int bytes) {
 
 int max_smem_optin() {
     const int d = current_device();
-    if (!g_smem_optin[d]) {
+    int c = g_smem_optin[d].load(std::memory_order_relaxed);
+    if (!c) {
         int v = 0;
         cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, d);
-        g_smem_optin[d] = v > 0 ? v : 48 * 1024;
+        c = v > 0 ? v : 48 * 1024;
+        g_smem_optin[d].store(c, std::memory_order_relaxed);
     }
-    return g_smem_optin[d];
+    return c;
 }
 
 LifConst make_lif_const(const bp_coba_params& p) {
