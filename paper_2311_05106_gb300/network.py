@@ -11,6 +11,30 @@ import torch
 from . import binding as B
 
 
+def _require_cuda(device):
+    """The library reads every state and matrix pointer as device memory."""
+    if torch.device(device).type != "cuda":
+        raise ValueError("the network state must live on a CUDA device, got %r" % (device,))
+
+
+def _check_csr(csr, n):
+    """A stored matrix passed to CobaNetwork: CUDA tensors of the types and
+    lengths the library reads (a host pointer or a short buffer would be read
+    out of bounds on the device)."""
+    indptr, indices, data = csr
+    for name, t, dt in (("indptr", indptr, torch.int64), ("indices", indices, torch.int32)):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or not t.is_contiguous() or t.dtype != dt:
+            raise ValueError("csr %s must be a contiguous CUDA %s tensor" % (name, dt))
+    if indptr.numel() != n + 1:
+        raise ValueError("csr indptr has %d entries, expected n + 1 = %d" % (indptr.numel(), n + 1))
+    if data is not None:
+        if (not isinstance(data, torch.Tensor) or not data.is_cuda or not data.is_contiguous()
+                or data.dtype not in (torch.float32, torch.bfloat16)):
+            raise ValueError("csr data must be None or a contiguous CUDA float32 / bfloat16 tensor")
+        if data.numel() != indices.numel():
+            raise ValueError("csr data and indices differ in length (%d, %d)" % (data.numel(), indices.numel()))
+
+
 def materialize_network_csr(seed, p, n, n_e, data_dtype=None, device="cuda"):
     """Stored-CSR form of the network's JIT connectivity: rows [0, n_e) are the
     excitatory projection's rows, rows [n_e, n) the inhibitory ones (row
@@ -46,7 +70,12 @@ class CobaNetwork:
     def __init__(self, n, n_e=None, conn="jit", seed=2024, p=None, V0=None, csr=None, tile_cols=0,
                  params=None, keep_spk=False, keep_spikes=False, delay_e=0, delay_i=0, align="post",
                  device="cuda"):
+        _require_cuda(device)
         self.n = int(n)
+        if conn == "csr" and csr is not None:
+            _check_csr(csr, self.n)
+        if V0 is not None and np.asarray(V0).shape != (self.n,):
+            raise ValueError("V0 must hold n = %d potentials" % self.n)
         self.n_e = int(n_e if n_e is not None else (4 * self.n) // 5)
         self.p = float(p if p is not None else 80.0 / self.n)
         self.seed = int(seed)
@@ -169,7 +198,10 @@ class BatchedNetworks:
     slice of a state array."""
 
     def __init__(self, sizes, seeds, V0=None, p=None, params=None, device="cuda"):
+        _require_cuda(device)
         sizes = np.ascontiguousarray(sizes, dtype=np.int64)
+        if len(seeds) != len(sizes) or (p is not None and len(p) != len(sizes)):
+            raise ValueError("sizes, seeds and p must have one entry per network")
         self.sizes = sizes
         self.n_nets = len(sizes)
         self.seeds = np.ascontiguousarray(seeds, dtype=np.uint64)

@@ -161,3 +161,25 @@ def test_operator_and_constructor_host_checks(libpath):
     bd = B.BatchDesc()
     rejected(L.bp_batch_create(ctypes.byref(bd), ctypes.byref(h)), b"missing")
     assert not h.value
+
+
+def test_python_objects_reject_host_memory_and_bad_shapes():
+    """The network objects hand raw pointers to the library, which reads them
+    as device memory: host tensors, a CPU device, a short row-pointer array or
+    mismatched per-network arrays are rejected in Python before any
+    allocation or library call."""
+    torch = pytest.importorskip("torch")
+    import numpy as np
+    from paper_2311_05106_gb300.network import BatchedNetworks, CobaNetwork
+    with pytest.raises(ValueError, match="CUDA device"):
+        CobaNetwork(100, device="cpu")
+    with pytest.raises(ValueError, match="CUDA device"):
+        BatchedNetworks(np.array([100]), np.array([1], np.uint64), device="cpu")
+    ip = torch.zeros(101, dtype=torch.int64)
+    ix = torch.zeros(0, dtype=torch.int32)
+    with pytest.raises(ValueError, match="indptr"):
+        CobaNetwork(100, conn="csr", csr=(ip, ix, None))        # host tensors
+    with pytest.raises(ValueError, match="seeds"):
+        BatchedNetworks(np.array([100, 200]), np.array([1], np.uint64))
+    with pytest.raises(ValueError, match="V0"):
+        CobaNetwork(100, V0=np.zeros(99, np.float32))
