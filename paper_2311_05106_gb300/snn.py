@@ -13,7 +13,25 @@ import torch
 from . import binding as B
 
 
+def _device_tensor(t, name, dtypes, shape=None):
+    """The library reads the parameter pointers as device memory of these
+    types and sizes: anything else is rejected here."""
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or not t.is_contiguous():
+        raise ValueError("%s must be a contiguous CUDA tensor" % name)
+    if t.dtype not in dtypes:
+        raise ValueError("%s has dtype %s, expected one of %s" % (name, t.dtype, dtypes))
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError("%s has shape %s, expected %s" % (name, tuple(t.shape), tuple(shape)))
+
+
 def make_desc(B_, T, n_in, n_rec, n_out, W_in, indptr, indices, w_rec, W_out, b_out, ckpt_every=100, **overrides):
+    f32 = (torch.float32,)
+    _device_tensor(W_in, "W_in", f32, (n_in, n_rec))
+    _device_tensor(indptr, "indptr", (torch.int64,), (n_rec + 1,))
+    _device_tensor(indices, "indices", (torch.int32,))
+    _device_tensor(w_rec, "w_rec", (torch.float32, torch.bfloat16), (indices.numel(),))
+    _device_tensor(W_out, "W_out", f32, (n_rec, n_out))
+    _device_tensor(b_out, "b_out", f32, (n_out,))
     d = B.bp_snn_desc_default()
     d.B, d.T, d.n_in, d.n_rec, d.n_out = int(B_), int(T), int(n_in), int(n_rec), int(n_out)
     d.ckpt_every = int(ckpt_every)
@@ -35,6 +53,8 @@ class _BPTT(torch.autograd.Function):
     def forward(ctx, W_in, w_rec, W_out, b_out, u, labels, indptr, indices, rec_dtype, ckpt_every, overrides):
         Bsz, T, n_in = u.shape
         n_rec, n_out = W_out.shape
+        _device_tensor(u, "u", (torch.uint8,))
+        _device_tensor(labels, "labels", (torch.int64,), (Bsz,))
         w_k = w_rec.detach().to(rec_dtype).contiguous()
         W_in_c, W_out_c, b_c = W_in.detach().contiguous(), W_out.detach().contiguous(), b_out.detach().contiguous()
         d = make_desc(Bsz, T, n_in, n_rec, n_out, W_in_c, indptr, indices, w_k, W_out_c, b_c, ckpt_every,

@@ -183,3 +183,16 @@ def test_python_objects_reject_host_memory_and_bad_shapes():
         BatchedNetworks(np.array([100, 200]), np.array([1], np.uint64))
     with pytest.raises(ValueError, match="V0"):
         CobaNetwork(100, V0=np.zeros(99, np.float32))
+
+
+def test_bptt_descriptor_rejects_host_or_misshapen_parameters():
+    """snn.make_desc hands the parameter pointers to the library as device
+    memory: host tensors, wrong dtypes and wrong shapes are rejected first."""
+    torch = pytest.importorskip("torch")
+    from paper_2311_05106_gb300.snn import make_desc
+    n_in, n_rec, n_out = 3, 4, 2
+    W_in = torch.zeros(n_in, n_rec)
+    ip = torch.zeros(n_rec + 1, dtype=torch.int64)
+    ix = torch.zeros(0, dtype=torch.int32)
+    with pytest.raises(ValueError, match="W_in must be a contiguous CUDA tensor"):
+        make_desc(1, 5, n_in, n_rec, n_out, W_in, ip, ix, torch.zeros(0), torch.zeros(n_rec, n_out), torch.zeros(n_out))
