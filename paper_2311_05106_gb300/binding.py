@@ -194,6 +194,20 @@ def _wkind(data):
     raise ValueError("weights must be float32 or bfloat16, got %s" % data.dtype)
 
 
+def _csr_sizes(indices, data, n_pre, n_post, tile_ptr, tile_cols, spike_list=None, max_spikes=0):
+    """Lengths the kernels rely on but cannot see through a raw pointer: one
+    weight per stored entry, a tile index of the size bp_csr_tile_index
+    writes, a spike list of at least max_spikes entries."""
+    if data is not None and indices is not None and data.numel() < indices.numel():
+        raise ValueError("data holds %d weights for %d stored entries" % (data.numel(), indices.numel()))
+    if tile_ptr is not None and tile_cols > 0 and n_post > tile_cols:
+        need = int(lib().bp_csr_tile_index_size(n_pre, n_post, int(tile_cols)))
+        if tile_ptr.dtype != torch.int32 or tile_ptr.numel() < need:
+            raise ValueError("tile_ptr must be int32 with at least %d entries" % need)
+    if spike_list is not None and spike_list.numel() < min(max_spikes, n_pre):
+        raise ValueError("spike_list holds %d entries, max_spikes is %d" % (spike_list.numel(), max_spikes))
+
+
 # ------------------------------------------------------------------ library
 def bp_version() -> str:
     return lib().bp_version().decode()
@@ -242,6 +256,7 @@ def bp_event_csrmv(indptr, indices, data, w_homo, spike_list, n_spikes, y, n_pos
     n_post = y.numel() if n_post is None else n_post
     counts = 1 if y.dtype == torch.int32 else 0
     ms = n_pre if max_spikes is None else max_spikes
+    _csr_sizes(indices, data, n_pre, n_post, tile_ptr, tile_cols, spike_list, ms)
     _check("bp_event_csrmv", lib().bp_event_csrmv(n_pre, n_post, _p(indptr), _p(indices), _p(data), _wkind(data),
                                                   float(w_homo), _p(spike_list), _p(n_spikes), ms, _p(y), counts,
                                                   _p(tile_ptr), int(tile_cols), int(flags), _stream(stream)))
@@ -255,6 +270,7 @@ def bp_event_csrmv_dense(indptr, indices, data, w_homo, events, workspace, y, ti
                          stream=None):
     n_pre = indptr.numel() - 1
     counts = 1 if y.dtype == torch.int32 else 0
+    _csr_sizes(indices, data, n_pre, y.numel(), tile_ptr, tile_cols)
     _check("bp_event_csrmv_dense", lib().bp_event_csrmv_dense(n_pre, y.numel(), _p(indptr), _p(indices), _p(data),
                                                               _wkind(data), float(w_homo), _p(events), _p(workspace),
                                                               _p(y), counts, _p(tile_ptr), int(tile_cols), int(flags),
@@ -280,6 +296,7 @@ def bp_csr_tile_index_size(n_pre, n_post, tile_cols) -> int:
 
 
 def bp_csr_tile_index(indptr, indices, n_post, tile_cols, tile_ptr, stream=None):
+    _csr_sizes(indices, None, indptr.numel() - 1, n_post, tile_ptr, tile_cols)
     _check("bp_csr_tile_index", lib().bp_csr_tile_index(indptr.numel() - 1, n_post, _p(indptr), _p(indices),
                                                         int(tile_cols), _p(tile_ptr), _stream(stream)))
 
@@ -292,6 +309,7 @@ def bp_csr_check(indptr, indices, n_post, out, stream=None):
 
 
 def bp_event_csrmv_t(indptr, indices, data, w_homo, x_post, y_pre, flags=0, stream=None, tile_ptr=None, tile_cols=0):
+    _csr_sizes(indices, data, indptr.numel() - 1, x_post.numel(), tile_ptr, tile_cols)
     _check("bp_event_csrmv_t", lib().bp_event_csrmv_t(indptr.numel() - 1, x_post.numel(), _p(indptr), _p(indices),
                                                       _p(data), _wkind(data), float(w_homo), _p(x_post), _p(y_pre),
                                                       _p(tile_ptr), int(tile_cols), int(flags), _stream(stream)))
@@ -301,6 +319,7 @@ def bp_event_csrmv_bwd(indptr, indices, data, w_homo, spike_list, n_spikes, dy, 
                        max_spikes=None, stream=None, tile_ptr=None, tile_cols=0):
     n_pre = indptr.numel() - 1
     ms = n_pre if max_spikes is None else max_spikes
+    _csr_sizes(indices, data, n_pre, dy.numel(), tile_ptr, tile_cols, spike_list, ms)
     _check("bp_event_csrmv_bwd", lib().bp_event_csrmv_bwd(n_pre, dy.numel(), _p(indptr), _p(indices), _p(data),
                                                           _wkind(data), float(w_homo), _p(spike_list), _p(n_spikes),
                                                           ms, _p(dy), _p(dw), _p(dx_pre), _p(tile_ptr),
@@ -318,6 +337,7 @@ def bp_jit_desc_init(seed, p, wkind=BP_JIT_HOMO, w0=1.0, w1=0.0) -> JitDesc:
 def bp_jitconn_event_mv(desc, n_pre, spike_list, n_spikes, y, flags=0, max_spikes=None, stream=None):
     counts = 1 if y.dtype == torch.int32 else 0
     ms = n_pre if max_spikes is None else max_spikes
+    _csr_sizes(None, None, n_pre, y.numel(), None, 0, spike_list, ms)
     _check("bp_jitconn_event_mv", lib().bp_jitconn_event_mv(ctypes.byref(desc), n_pre, y.numel(), _p(spike_list),
                                                             _p(n_spikes), ms, _p(y), counts, int(flags),
                                                             _stream(stream)))

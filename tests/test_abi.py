@@ -16,7 +16,8 @@ HEADERS = [os.path.join(ROOT, "include", f) for f in sorted(os.listdir(os.path.j
 def declared_functions():
     names = []
     for h in HEADERS:
-        text = open(h).read()
+        with open(h) as f:
+            text = f.read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
         names += re.findall(r"^\s*[a-zA-Z_][\w\s\*]*?\b(bp_\w+)\s*\(", text, flags=re.M)
     return sorted(set(names))
@@ -196,3 +197,28 @@ def test_bptt_descriptor_rejects_host_or_misshapen_parameters():
     ix = torch.zeros(0, dtype=torch.int32)
     with pytest.raises(ValueError, match="W_in must be a contiguous CUDA tensor"):
         make_desc(1, 5, n_in, n_rec, n_out, W_in, ip, ix, torch.zeros(0), torch.zeros(n_rec, n_out), torch.zeros(n_out))
+
+
+def test_binding_checks_lengths_behind_raw_pointers():
+    """Lengths the kernels cannot see through a pointer are checked by the
+    binding first: weights shorter than the stored entries, a tile index
+    shorter than bp_csr_tile_index writes, a spike list shorter than
+    max_spikes (the tensors here are host tensors: the length checks come
+    before any pointer is taken)."""
+    torch = pytest.importorskip("torch")
+    from paper_2311_05106_gb300 import binding as B
+    n_pre, n_post = 10, 200000
+    ip = torch.zeros(n_pre + 1, dtype=torch.int64)
+    ix = torch.zeros(8, dtype=torch.int32)
+    sl, ns = torch.zeros(n_pre, dtype=torch.int32), torch.zeros(1, dtype=torch.int32)
+    y = torch.zeros(n_post, dtype=torch.float32)
+    with pytest.raises(ValueError, match="weights for 8 stored entries"):
+        B.bp_event_csrmv(ip, ix, torch.zeros(7), 0.0, sl, ns, y)
+    tc = B.bp_tile_cols()
+    short = torch.zeros(B.bp_csr_tile_index_size(n_pre, n_post, tc) - 1, dtype=torch.int32)
+    with pytest.raises(ValueError, match="tile_ptr"):
+        B.bp_event_csrmv(ip, ix, None, 1.0, sl, ns, y, tile_ptr=short, tile_cols=tc)
+    with pytest.raises(ValueError, match="tile_ptr"):
+        B.bp_csr_tile_index(ip, ix, n_post, tc, short)
+    with pytest.raises(ValueError, match="spike_list"):
+        B.bp_event_csrmv(ip, ix, None, 1.0, sl[:5], ns, y)

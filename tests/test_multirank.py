@@ -34,7 +34,7 @@ def _worker(rank, world, port, out):
 
 def test_two_rank_aggregation_gloo():
     port = _free_port()
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()   # no fork of this (threaded) process
     out = mgr.dict()
     mp.spawn(_worker, args=(2, port, out), nprocs=2, join=True)
     assert out[0] == out[1] == (15.0, 3000)
