@@ -11,11 +11,23 @@ headline `value` uses stored CSR (int64 indptr, int32 indices, FP32 weights
 w_e = 0.6 / w_i = 6.7 stored per synapse, FP32 accumulation); the JIT form and
 the integer-count stored form are reported under `variants`.
 
+Regime: the workload is the network's steady state.  From V0 ~ N(-55, 5) mV
+about 16 % of the neurons start above threshold, and the population rate takes
+a few hundred steps to settle (about 1600 Hz at the first step, 10-18 Hz over
+steps 10-200, then 21-22 Hz); a simulation of the configured 10 000 steps
+spends nearly all its time at the settled rate.  The network is therefore run
+for SETTLE_STEPS = 1000 untimed steps (100 ms of simulated time) before the
+warm-up, and the timed steps are steps 1000 + W .. 1000 + W + K - 1.
+
 Timing: W warm-up steps, then exactly K steps run by bp_simulate (a captured
 CUDA graph), bracketed by a barrier and cuda.synchronize(), timed with CUDA
-events on the launching stream; max over ranks.  The connectivity (2.6 GB) and
-state (96 MB) exceed L2 together; the state is re-read every step, as in any
-time-stepped simulation, and L2 is not flushed between steps.
+events on the launching stream; max over ranks.  The connectivity (2.6 GB)
+and state (52 MB of neuron state, 64 MB of event accumulators) exceed L2
+together; the state is re-read every step, as in any time-stepped simulation,
+and L2 is not flushed between steps.  `e2e` replays the same K steps through
+the public API from the state saved (in pinned host memory) after the
+warm-up: the state upload, the K steps and the download of the per-step
+record and final potentials are all inside its timed region.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -39,7 +51,8 @@ N_EXC = 3_200_000
 SEED = 2024
 V0_SEED = 7
 DT_MS = 0.1
-WORKLOAD = "scaled COBA E/I network, N=4e6 (80/20), p=80/N, dt=0.1 ms"
+SETTLE_STEPS = 1000
+WORKLOAD = "scaled COBA E/I network, N=4e6 (80/20), p=80/N, dt=0.1 ms, steady state"
 
 
 def parse():
@@ -52,7 +65,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     # profiling cases (ncu): headline path only, with another connectivity / size
     ap.add_argument("--conn", default="csr", choices=["csr", "jit"])
-    ap.add_argument("--weights", default="f32", choices=["f32", "counts"])
+    ap.add_argument("--weights", default="f32", choices=["f32", "bf16", "counts"])
+    ap.add_argument("--settle", type=int, default=SETTLE_STEPS)
     ap.add_argument("--neurons", type=int, default=N_NEURONS)
     ap.add_argument("--no-e2e", action="store_true")
     # operator sweep (one JSON line per cell instead of the bench line)
@@ -169,8 +183,10 @@ def step_traffic_record():
 
 # bytes the neuron pass must move per neuron: read V, g_e, g_i and the two
 # event accumulators (5 x 4 B) and the one-byte refractory counter; write V,
-# g_e, g_i (3 x 4 B)
+# g_e, g_i (3 x 4 B).  (33 B: the counter is one byte; a two-byte counter, as
+# first estimated for this pass, would make it 34 B.)
 LIF_BYTES_PER_NEURON = 33
+WEIGHT_BYTES = {"f32": 4, "bf16": 2, "counts": 0}
 
 
 def build_network(torch, B, conn, weights, n=N_NEURONS, delay=0):
@@ -182,14 +198,20 @@ def build_network(torch, B, conn, weights, n=N_NEURONS, delay=0):
     p = 80.0 / n
     csr = None
     if conn == "csr":
-        csr = materialize_network_csr(SEED, p, n, n_e, data_dtype=torch.float32 if weights == "f32" else None)
+        dt = {"f32": torch.float32, "bf16": torch.bfloat16}.get(weights)
+        csr = materialize_network_csr(SEED, p, n, n_e, data_dtype=dt)
     net = CobaNetwork(n, n_e, conn=conn, seed=SEED, p=p, V0=V0, csr=csr, delay_e=delay, delay_i=delay)
     return net, np.asarray(V0)
 
 
-def time_simulate(torch, net, steps, warmup, dist=None):
+def time_simulate(torch, net, steps, warmup, dist=None, keep_host_ckpt=None):
+    """W warm-up steps, then K timed steps; returns (ms, events, spikes) of the
+    timed steps.  keep_host_ckpt (a dict) receives the pinned host checkpoint
+    of the state the timed steps start from."""
     stream = torch.cuda.current_stream()
     net.simulate(warmup)
+    if keep_host_ckpt is not None:
+        keep_host_ckpt.update(net.checkpoint_to_host())
     before = net.totals.clone()
     if dist is not None:
         dist.barrier()
@@ -252,38 +274,35 @@ def lif_kernel_time(torch, B, net, reps=50):
     return a.elapsed_time(b) / reps
 
 
-def e2e_run(torch, net, V0, steps):
-    """End to end through the public API: upload the initial state from pinned
-    host memory, simulate `steps`, download the per-step spike record and the
-    final potentials; all inside the timed region."""
-    import numpy as np
+def e2e_run(torch, net, host_ckpt, steps):
+    """End to end through the public API: the K timed steps replayed from the
+    state they started from, held in pinned host memory (the state after the
+    settle period and the warm-up).  Inside the timed region: the upload of
+    that state (CobaNetwork.restore, non-blocking copies), bp_simulate over the
+    K steps with a per-step spike record, and the download of the record and
+    of the final potentials."""
     f32 = torch.float32
-    hV = torch.from_numpy(np.ascontiguousarray(V0, np.float32)).pin_memory()
-    hz = torch.zeros(N_NEURONS, dtype=f32).pin_memory()
-    hr = torch.zeros(N_NEURONS, dtype=torch.uint8).pin_memory()
+    n = net.n
     rec = torch.zeros((steps, 2), dtype=torch.int32, device="cuda")
     hrec = torch.zeros((steps, 2), dtype=torch.int32).pin_memory()
-    hVout = torch.zeros(N_NEURONS, dtype=f32).pin_memory()
+    hVout = torch.zeros(n, dtype=f32).pin_memory()
     stream = torch.cuda.current_stream()
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    net.V.copy_(hV, non_blocking=True)
-    net.ge.copy_(hz, non_blocking=True)
-    net.gi.copy_(hz, non_blocking=True)
-    net.ref.copy_(hr, non_blocking=True)
-    net.reset_counters()
+    net.restore(host_ckpt, non_blocking=True)
+    before = net.totals.clone()
     net.simulate(steps, rec)
+    events = net.totals[2] - before[2]
     hrec.copy_(rec, non_blocking=True)
     hVout.copy_(net.V, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
-    events = int(net.totals[2].item())
-    h2d = (3 * 4 + 1) * N_NEURONS  # V, ge, gi (FP32) and the one-byte refractory counters
-    d2h = 8 * steps + 4 * N_NEURONS
-    return ms, events, h2d, d2h
+    h2d = sum(t.numel() * t.element_size() for t in host_ckpt["state"].values())
+    d2h = 8 * steps + 4 * n
+    return ms, int(events.item()), h2d, d2h
 
 
 # ----------------------------------------------------------------- other configurations
@@ -596,14 +615,15 @@ def run_reference(args):
     from paper_2311_05106_gb300 import workloads as wl
     budget = 120.0
     per_neuron_step_s = 1.5e-7          # oracle cost per neuron-step incl. its events
-    n = int(budget / max(args.steps + args.warmup, 1) / per_neuron_step_s)
+    settle = SETTLE_STEPS
+    n = int(budget / max(settle + args.steps + args.warmup, 1) / per_neuron_step_s)
     n = max(2000, min(N_NEURONS, n - n % 5))
     n_e = (4 * n) // 5
     p = 80.0 / n
     K = orc.jit_K(p)
     net = orc.CobaNet(n, n_e, ("jit", orc.projection_seed(SEED, 0), orc.projection_seed(SEED, 1), K),
                       wl.coba_v0(n, seed=V0_SEED).astype("float64"))
-    net.run(args.warmup)
+    net.run(settle + args.warmup)
     t0 = time.perf_counter()
     out = net.run(args.steps, events=True)
     dt = time.perf_counter() - t0
@@ -613,10 +633,11 @@ def run_reference(args):
         "impl": "reference", "metric": "synaptic_events_per_s", "value": value, "unit": "events/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample_neurons": n},
+        "config": {"workload": WORKLOAD, "sample_neurons": n, "settle_steps": settle},
         "cpu_baseline": {"value": value, "unit": "events/s", "cores": 1, "kind": "oracle",
                          "sample": "FP64 oracle, one thread: the same E/I network family (in-degree 80, JIT rows) "
-                                   "at n=%d neurons, %d steps after %d warm-up steps" % (n, args.steps, args.warmup)},
+                                   "at n=%d neurons, %d steps after the %d-step settle period and %d warm-up steps"
+                                   % (n, args.steps, settle, args.warmup)},
         "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -624,98 +645,95 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------- operator sweep
-def run_sweep(args):
-    """Standalone operators of the paper's operator benchmark (Section 4.1,
+GRADED_CELLS = ((0.01, 0.01), (0.01, 0.1), (0.001, 0.1))
+
+
+def device_timer(torch, fn, reps):
+    """Median device time (ms) of fn() over `reps` calls, each between two CUDA
+    events on the current stream after two untimed calls; calls shorter than
+    0.1 ms are timed as 20 calls captured in a CUDA graph (device time per
+    call, without the host's enqueue gaps)."""
+    stream = torch.cuda.current_stream()
+    fn()
+    fn()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for a, b in evs:
+        a.record(stream)
+        fn()
+        b.record(stream)
+    torch.cuda.synchronize()
+    ms = sorted(a.elapsed_time(b) for a, b in evs)
+    med = ms[len(ms) // 2]
+    if med >= 0.1:
+        return med
+    g = torch.cuda.CUDAGraph()
+    cap = torch.cuda.Stream()
+    cap.wait_stream(stream)
+    with torch.cuda.stream(cap):
+        with torch.cuda.graph(g, stream=cap):
+            for _ in range(20):
+                fn()
+    stream.wait_stream(cap)
+    g.replay()
+    torch.cuda.synchronize()
+    gms = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        g.replay()
+        b.record(stream)
+        torch.cuda.synchronize()
+        gms.append(a.elapsed_time(b) / 20)
+    gms.sort()
+    return gms[len(gms) // 2]
+
+
+def sweep_cells(torch, sizes, probs, rhos, wsel, ops, cells=None, tile_cols=None):
+    """Standalone operators of the paper's operator benchmark (Section 5.1,
     Appendix B / C) on synthetic inputs: n_pre = n_post = n, connection
     probability p, Bernoulli(rho) spikes, homogeneous (integer counts) or
-    heterogeneous N(0.5, 0.1) weights stored FP32 / BF16.  Prints one JSON line
-    per cell.  Stored matrices come from the JIT materialiser (sorted rows);
-    cells whose CSR would exceed 200 GB run the JIT operator only."""
-    import torch
+    heterogeneous N(0.5, 0.1) weights stored FP32 / BF16.  Yields one dict per
+    cell.  Stored matrices come from the JIT materialiser (sorted rows); cells
+    whose CSR would exceed 200 GB run the JIT operator only.  `cells`
+    (optional) restricts the (p, rho) pairs."""
     from paper_2311_05106_gb300 import binding as B
     from paper_2311_05106_gb300 import workloads as wl
-    torch.cuda.set_device(0)
     peak, peak_kind = peaks()
-    sizes = [int(float(x)) for x in args.sweep_n.split(",")]
-    probs = [float(x) for x in args.sweep_p.split(",")]
-    rhos = [float(x) for x in args.sweep_rho.split(",")]
-    wsel = set(args.sweep_weights.split(","))
-    ops = set(args.sweep_ops.split(","))
-    stored = bool(wsel & {"f32", "bf16"})
-    stream = torch.cuda.current_stream()
-
-    def timeit(fn, reps):
-        fn()
-        fn()
-        torch.cuda.synchronize()
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
-        for a, b in evs:
-            a.record(stream)
-            fn()
-            b.record(stream)
-        torch.cuda.synchronize()
-        ms = sorted(a.elapsed_time(b) for a, b in evs)
-        med = ms[len(ms) // 2]
-        if med >= 0.1:
-            return med
-        # a short call on an idle GPU waits for the host to enqueue it: time
-        # 20 calls captured in a CUDA graph instead (device time per call)
-        g = torch.cuda.CUDAGraph()
-        cap = torch.cuda.Stream()
-        cap.wait_stream(stream)
-        with torch.cuda.stream(cap):
-            with torch.cuda.graph(g, stream=cap):
-                for _ in range(20):
-                    fn()
-        stream.wait_stream(cap)
-        g.replay()
-        torch.cuda.synchronize()
-        gms = []
-        for _ in range(reps):
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            g.replay()
-            b.record(stream)
-            torch.cuda.synchronize()
-            gms.append(a.elapsed_time(b) / 20)
-        gms.sort()
-        return gms[len(gms) // 2]
-
-    def emit(**kw):
-        print(json.dumps(kw), flush=True)
-
+    stored = bool(set(wsel) & {"f32", "bf16"})
     for n in sizes:
         for p in probs:
+            rho_here = [r for r in rhos if cells is None or (p, r) in cells]
+            if not rho_here:
+                continue
             seed = 1000 + n % 997 + int(p * 1e4)
-            csr_ok = p * n * n * 8 <= 200e9
+            csr_ok = p * n * n * 8 <= 200e9 and bool(set(ops) & {"csr", "csr_t"})
             dn = B.bp_jit_desc_init(seed, p, B.BP_JIT_NORMAL, 0.5, 0.1)
             dh = B.bp_jit_desc_init(seed, p)
             ip = ix = w32 = w16 = tp = None
             tc = 0
-            csr_ok = csr_ok and bool(ops & {"csr", "csr_t"})
             if csr_ok:
                 ip, ix, w32 = B.jit_materialize(dn, n, n, data_dtype=torch.float32 if stored else None)
                 nnz = ix.numel()
                 w16 = w32.to(torch.bfloat16) if "bf16" in wsel else None
-                tc = B.bp_tile_cols() if n > B.bp_tile_cols() else 0
+                tc = (tile_cols or B.bp_tile_cols()) if n > B.bp_tile_cols() else 0
                 if tc:
                     tp = torch.empty(B.bp_csr_tile_index_size(n, n, tc), dtype=torch.int32, device="cuda")
                     B.bp_csr_tile_index(ip, ix, n, tc, tp)
                 torch.cuda.synchronize()
-                # gather form over all rows (independent of rho)
                 x = torch.ones(n, dtype=torch.float32, device="cuda")
                 yp = torch.zeros(n, dtype=torch.float32, device="cuda")
                 for wname, wt, wb in (("homo", None, 0), ("f32", w32, 4), ("bf16", w16, 2)):
                     if wname not in wsel or "csr_t" not in ops:
                         continue
                     alg = nnz * (4 + wb) + 8 * (n + 1)
-                    # x staged in shared-memory tiles (the default), and x read through L2
                     for form, fl in (("tiles", 0), ("l2", B.BP_ACC_GLOBAL)) if tc else (("l2", 0),):
-                        ms = timeit(lambda: B.bp_event_csrmv_t(ip, ix, wt, 1.0, x, yp, flags=fl, tile_ptr=tp,
-                                                               tile_cols=tc), 5)
-                        emit(op="event_csrmv_t", form=form, n=n, p=p, weights=wname, us=ms * 1e3, nnz=nnz,
-                             alg_bytes=alg, gbs=alg / ms / 1e6, frac_hbm=alg / ms / 1e6 / peak, peak_source=peak_kind)
-            for rho in rhos:
+                        ms = device_timer(torch, lambda: B.bp_event_csrmv_t(ip, ix, wt, 1.0, x, yp, flags=fl,
+                                                                            tile_ptr=tp, tile_cols=tc), 5)
+                        yield dict(op="event_csrmv_t", form=form, n=n, p=p, weights=wname, us=ms * 1e3, nnz=nnz,
+                                   alg_bytes=alg, gbs=alg / ms / 1e6, frac_hbm=alg / ms / 1e6 / peak,
+                                   peak_source=peak_kind)
+            for rho in rho_here:
                 ev_np = wl.bernoulli_spikes(n, rho, seed=seed + int(rho * 1e4))
                 events = torch.from_numpy(ev_np).cuda()
                 sl = torch.zeros(n, dtype=torch.int32, device="cuda")
@@ -730,25 +748,105 @@ def run_sweep(args):
                     for wname, wt, wb, y in (("homo", None, 0, yc), ("f32", w32, 4, yf), ("bf16", w16, 2, yf)):
                         if wname not in wsel or "csr" not in ops:
                             continue
-                        ms = timeit(lambda: B.bp_event_csrmv(ip, ix, wt, 1.0, sl, ns, y, tile_ptr=tp, tile_cols=tc), 7)
+                        ms = device_timer(torch, lambda: B.bp_event_csrmv(ip, ix, wt, 1.0, sl, ns, y, tile_ptr=tp,
+                                                                          tile_cols=tc), 7)
                         alg = ev_count * (4 + wb) + 16 * n_spk
-                        emit(op="event_csrmv", n=n, p=p, rho=rho, weights=wname, us=ms * 1e3, spikes=n_spk,
-                             events=ev_count, events_per_s=ev_count / (ms * 1e-3), alg_bytes=alg,
-                             gbs=alg / ms / 1e6, frac_hbm=alg / ms / 1e6 / peak, peak_source=peak_kind,
-                             graded=(n == 1_000_000 and (p, rho) in ((0.01, 0.01), (0.01, 0.1), (0.001, 0.1))))
+                        yield dict(op="event_csrmv", n=n, p=p, rho=rho, weights=wname, us=ms * 1e3, spikes=n_spk,
+                                   events=ev_count, events_per_s=ev_count / (ms * 1e-3), alg_bytes=alg,
+                                   gbs=alg / ms / 1e6, frac_hbm=alg / ms / 1e6 / peak, peak_source=peak_kind,
+                                   tile_cols=tc, graded=(n == 1_000_000 and (p, rho) in GRADED_CELLS))
                 yy = torch.zeros(n, dtype=torch.int32, device="cuda")
                 B.bp_jitconn_event_mv(dh, n, sl, ns, yy)
                 ev_jit = int(yy.sum().item())
                 for wname, d, y in (("homo", dh, yc), ("normal", dn, yf)):
                     if "jit" not in ops:
                         continue
-                    ms = timeit(lambda: B.bp_jitconn_event_mv(d, n, sl, ns, y), 5)
-                    emit(op="jitconn_event_mv", n=n, p=p, rho=rho, weights=wname, us=ms * 1e3, spikes=n_spk,
-                         events=ev_jit, events_per_s=ev_jit / (ms * 1e-3), bound="alu")
+                    ms = device_timer(torch, lambda: B.bp_jitconn_event_mv(d, n, sl, ns, y), 5)
+                    yield dict(op="jitconn_event_mv", n=n, p=p, rho=rho, weights=wname, us=ms * 1e3,
+                               spikes=n_spk, events=ev_jit, events_per_s=ev_jit / (ms * 1e-3), bound="alu")
                 del events, sl, ns, yc, yf, yy
             del ip, ix, w32, w16, tp
             torch.cuda.empty_cache()
+
+
+def run_sweep(args):
+    """Prints one JSON line per operator cell (see sweep_cells)."""
+    import torch
+    torch.cuda.set_device(0)
+    sizes = [int(float(x)) for x in args.sweep_n.split(",")]
+    probs = [float(x) for x in args.sweep_p.split(",")]
+    rhos = [float(x) for x in args.sweep_rho.split(",")]
+    for cell in sweep_cells(torch, sizes, probs, rhos, args.sweep_weights.split(","), args.sweep_ops.split(",")):
+        print(json.dumps(cell), flush=True)
     return 0
+
+
+def measure_roofs(torch):
+    """Roofline denominators measured here (CUDA events, median of 5): the
+    Philox-only draw rate (JIT rows' integer-ALU roof), the rate of scattered
+    4-byte L2 reductions into a 4 MB accumulator (1e6 int32, the n_post = 1e6
+    cells), the L2-resident copy bandwidth (two 16 MiB buffers) and, as a
+    cross-check of the driver's figure, the HBM copy bandwidth (two 2 GiB
+    buffers)."""
+    from paper_2311_05106_gb300 import binding as B
+    out = {}
+    th = B.bp_roof_philox_threads()
+    sink = torch.zeros(th, dtype=torch.int32, device="cuda")
+    blocks = 256
+    ms = device_timer(torch, lambda: B.bp_roof_philox(blocks, sink), 5)
+    out["philox_words_per_s"] = 4.0 * th * blocks / (ms * 1e-3)
+    y = torch.zeros(1_000_000, dtype=torch.int32, device="cuda")
+    per = 256
+    ms = device_timer(torch, lambda: B.bp_roof_l2_red(y, per), 5)
+    out["l2_red_per_s_1e6_targets"] = float(B.bp_roof_l2_red_threads() * per) / (ms * 1e-3)
+    for name, nbytes, reps in (("l2_copy_gbs", 16 << 20, 20), ("hbm_copy_gbs", 2 << 30, 1)):
+        src = torch.ones(nbytes // 4, dtype=torch.float32, device="cuda")
+        dst = torch.empty_like(src)
+        ms = device_timer(torch, lambda: B.bp_roof_copy(src, dst, reps), 5)
+        out[name] = 2.0 * nbytes * reps / (ms * 1e-3) / 1e9
+        del src, dst
+    torch.cuda.empty_cache()
+    return out
+
+
+def bench_operator_cells(torch, roofs):
+    """The three graded n = 1e6 cells of the event CSR product (homogeneous
+    counts, FP32 and BF16 weights) with their fraction of HBM, and the JIT
+    event product on the same cells against its roofs (Philox-only draw rate
+    and scattered L2 reductions)."""
+    out = []
+    for c in sweep_cells(torch, [1_000_000], [0.001, 0.01], [0.01, 0.1], ["homo", "f32", "bf16"], ["csr", "jit"],
+                         cells=GRADED_CELLS):
+        if c["op"] == "jitconn_event_mv":
+            roof = min(roofs["philox_words_per_s"], roofs["l2_red_per_s_1e6_targets"])
+            c["roof_events_per_s"] = roof
+            c["roof"] = "philox" if roofs["philox_words_per_s"] <= roofs["l2_red_per_s_1e6_targets"] else "l2_red"
+            c["frac_roof"] = c["events_per_s"] / roof
+        out.append(c)
+    return out
+
+
+def bench_l2_resident(torch, roofs, steps=2000):
+    """The scaled network at N = 4e4 and 4e5 (stored CSR, FP32 weights), whose
+    neuron state and accumulators stay in L2: algorithmic bytes per step over
+    the step time, as a fraction of the L2-resident copy bandwidth measured
+    here (and of HBM, for reference)."""
+    peak, _ = peaks()
+    out = {}
+    for n in (40_000, 400_000):
+        net, _ = build_network(torch, None, "csr", "f32", n)
+        net.simulate(SETTLE_STEPS)
+        ms, events, spikes = time_simulate(torch, net, steps, 50)
+        step_s = ms * 1e-3 / steps
+        alg = LIF_BYTES_PER_NEURON * n + events / steps * 8 + spikes / steps * 16
+        out["N%d" % n] = {"us_per_step": step_s * 1e6, "events_per_s": events / (ms * 1e-3),
+                          "alg_bytes_per_step": alg, "gbs": alg / step_s / 1e9,
+                          "frac_l2": alg / step_s / 1e9 / roofs["l2_copy_gbs"],
+                          "frac_hbm": alg / step_s / 1e9 / peak}
+        net.close()
+        del net
+        torch.cuda.empty_cache()
+    return out
 
 
 # ----------------------------------------------------------------- main
@@ -788,12 +886,14 @@ def main():
     if args.neurons != N_NEURONS:
         N_NEURONS, N_EXC = args.neurons, (4 * args.neurons) // 5
     net, V0 = build_network(torch, B, args.conn, args.weights, N_NEURONS)
-    net.simulate(3)  # builds and caches the CUDA graph outside the timed region
-    net.reset_counters()
-    host_before = 3
+    # the settle period (untimed; also builds and caches the CUDA graph)
+    net.simulate(args.settle)
+    host_before = args.settle
     clocks = ClockSampler(local)
     clocks.start()
-    ms, events, spikes = time_simulate(torch, net, args.steps, args.warmup, dist)
+    host_ckpt = {}
+    ms, events, spikes = time_simulate(torch, net, args.steps, args.warmup, dist,
+                                       keep_host_ckpt=None if args.no_e2e else host_ckpt)
     clk = clocks.stop()
     launches = launches_in_simulate(args.steps, host_before + args.warmup)
     if dist is not None:
@@ -807,7 +907,7 @@ def main():
     step_ms = ms / args.steps
     ev_per_step = events / args.steps
     spk_per_step = spikes / args.steps
-    wbytes = 4 if args.conn == "csr" and args.weights == "f32" else 0
+    wbytes = WEIGHT_BYTES[args.weights] if args.conn == "csr" else 0
     ibytes = 4 if args.conn == "csr" else 0
     alg_bytes = LIF_BYTES_PER_NEURON * N_NEURONS + ev_per_step * (ibytes + wbytes) + spk_per_step * 16
     achieved = alg_bytes / (step_ms * 1e-3) / 1e9
@@ -817,42 +917,57 @@ def main():
     # read with the evict-last policy), so the pass alone moves only the state
     # through DRAM: V, g_e, g_i read and written, the refractory byte read
     lif_bytes = (3 * 4 * 2 + 1) * N_NEURONS
+    headline = args.conn == "csr" and args.weights == "f32" and args.neurons == 4_000_000
     roofline = {"bound": "hbm", "kernel": "k_step (fused neuron pass + CSR delivery)", "achieved": achieved,
                 "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": step_traffic_record() if args.conn == "csr" and args.neurons == 4_000_000 else None,
+                "traffic": step_traffic_record() if headline else None,
                 "peak_source": peak_kind, "alg_bytes_per_launch": alg_bytes, "us_per_launch": step_ms * 1e3,
+                "alg_bytes_rule": "33 B per neuron (V, g_e, g_i and both event accumulators read, the one-byte "
+                                  "refractory counter read, V, g_e, g_i written) + (4 B index + weight bytes) per "
+                                  "delivered event + 16 B per spiking row",
                 "neuron_pass_only": {"us_per_launch": lif_ms * 1e3, "state_bytes": lif_bytes,
                                      "achieved_gbs": lif_bytes / (lif_ms * 1e-3) / 1e9,
                                      "frac": lif_bytes / (lif_ms * 1e-3) / 1e9 / peak}}
 
-    # ---- end to end through the public API (host buffers)
+    # ---- end to end through the public API: the same K steps from host buffers
     e2e = None
     if not args.no_e2e:
-        e2e_ms, e2e_events, h2d, d2h = e2e_run(torch, net, V0, args.steps)
+        e2e_ms, e2e_events, h2d, d2h = e2e_run(torch, net, host_ckpt, args.steps)
         e2e = {"value": e2e_events / (e2e_ms * 1e-3), "unit": "events/s",
-               "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps}
+               "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+               "ms": e2e_ms, "events": e2e_events,
+               "note": "the timed K steps replayed from the post-warm-up state uploaded from pinned host memory"}
     net.close()
     del net
     torch.cuda.empty_cache()
 
     variants = {}
-    headline = args.conn == "csr" and args.weights == "f32" and args.neurons == 4_000_000
     if not args.no_variants and headline:
         # delay_1ms: both projections delayed by 10 steps (Appendix D)
-        for name, conn, w, dl in (("csr_counts", "csr", None, 0), ("jit_counts", "jit", None, 0),
-                                  ("csr_f32_delay_1ms", "csr", "f32", 10)):
+        for name, conn, w, dl in (("csr_bf16", "csr", "bf16", 0), ("csr_counts", "csr", "counts", 0),
+                                  ("jit_counts", "jit", "counts", 0), ("csr_f32_delay_1ms", "csr", "f32", 10)):
             v, _ = build_network(torch, B, conn, w, delay=dl)
-            v.simulate(3)
-            v.reset_counters()
-            vms, vev, _ = time_simulate(torch, v, args.steps, args.warmup)
+            v.simulate(args.settle)
+            vms, vev, vspk = time_simulate(torch, v, args.steps, args.warmup)
             variants[name] = {"events_per_s": vev / (vms * 1e-3), "steps_per_s": args.steps / (vms * 1e-3),
-                              "ms_per_step": vms / args.steps}
+                              "ms_per_step": vms / args.steps,
+                              "rate_hz": vspk / (N_NEURONS * args.steps * DT_MS * 1e-3)}
             v.close()
             del v
             torch.cuda.empty_cache()
-        variants["csr_f32"] = {"events_per_s": value, "steps_per_s": steps_per_s, "ms_per_step": ms / args.steps}
+        variants["csr_f32"] = {"events_per_s": value, "steps_per_s": steps_per_s, "ms_per_step": ms / args.steps,
+                               "rate_hz": spikes / (N_NEURONS * args.steps * DT_MS * 1e-3)}
         for k in variants:
             variants[k]["vs_plain_f32"] = variants[k]["events_per_s"] / value
+            variants[k]["step_time_vs_plain_f32"] = variants[k]["ms_per_step"] / (ms / args.steps)
+        variants["csr_bf16"]["accuracy"] = (
+            "weights stored BF16 (w_e 0.6 -> 0.6015625, w_i 6.7 -> 6.6875), FP32 accumulation and state: per step "
+            "the delivered sums are within 1e-5 of the FP64 oracle fed the same BF16 weights and within 1e-2 of the "
+            "unrounded weights (teacher-forced tests)")
+        roofs = measure_roofs(torch)
+        variants["roofs"] = roofs
+        variants["operator_cells_n1e6"] = bench_operator_cells(torch, roofs)
+        variants["l2_resident_networks"] = bench_l2_resident(torch, roofs)
         variants["coba_4k_1000_steps"] = bench_small_net(torch)
         variants["batched_256_nets"] = bench_batched(torch)
         variants["fig_s7_jit_N4e5"] = bench_fig_s7(torch)
@@ -865,19 +980,25 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline and headline:
         s = oracle_sample(15.0)
         cpu = {"value": s["value"], "unit": "events/s", "cores": 1, "kind": "oracle",
-               "sample": "FP64 oracle, one thread, the same N=4e6 network (JIT rows = the stored matrix) from the "
-                         "same V0, first %d steps (%.1f s)" % (s["steps"], s["seconds"])}
+               "sample": "FP64 oracle, one thread, the same N=4e6 network (JIT rows = the stored matrix) from V0, "
+                         "its first %d steps (%.1f s; the onset, whose steps carry more events than the settled "
+                         "ones: the oracle's cost is per neuron plus per event)" % (s["steps"], s["seconds"])}
 
+    conn_txt = {"csr": "stored CSR, int32 indices, ", "jit": "JIT rows, "}[args.conn]
+    w_txt = {"f32": "FP32 weights", "bf16": "BF16 weights", "counts": "homogeneous weights, int32 event counts"}
     line = {
         "metric": "synaptic_events_per_s", "value": value, "unit": "events/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD if headline else "profiling case (not the headline workload)",
-                   "connectivity": {"csr": "stored CSR, int32 indices, ", "jit": "JIT rows, "}[args.conn]
-                   + {"f32": "FP32 weights", "counts": "homogeneous weights, int32 event counts"}[args.weights],
-                   "neurons": N_NEURONS, "sim_steps": args.steps,
-                   "l2": "connectivity 2.6 GB + state 52 MB + event accumulators 64 MB; no flush between steps "
-                         "(state re-read every step, streamed evict-first)",
+                   "connectivity": conn_txt + w_txt[args.weights],
+                   "neurons": N_NEURONS, "sim_steps": args.steps, "settle_steps": args.settle,
+                   "regime": "steady state: timed steps %d..%d of a run from V0 ~ N(-55, 5) mV (the first %d "
+                             "steps settle the onset burst)" % (args.settle + args.warmup,
+                                                                 args.settle + args.warmup + args.steps - 1,
+                                                                 args.settle),
+                   "l2": "connectivity 2.6 GB + neuron state 52 MB + event accumulators 64 MB; no flush between "
+                         "steps (the state is re-read every step, streamed evict-first)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "sim_steps_per_s": steps_per_s, "spikes_in_timed_region": spikes, "events_in_timed_region": events,
         "firing_rate_hz": spikes / (N_NEURONS * args.steps * DT_MS * 1e-3),

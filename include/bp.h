@@ -31,6 +31,11 @@
  *            failure.
  * Threads.   Calls on different streams may run concurrently if they write
  *            disjoint memory.
+ * Devices.   The library keeps per-device facts for the life of the process
+ *            (device addresses of its own __device__ arrays, SM count, shared
+ *            memory limits).  A cudaDeviceReset (or any other teardown of a
+ *            device's primary context) invalidates them: do not use the
+ *            library on a device after resetting it.
  */
 #ifndef BP_H
 #define BP_H
@@ -56,7 +61,7 @@ typedef enum {
 
 typedef enum { BP_W_HOMO = 0, BP_W_F32 = 1, BP_W_BF16 = 2 } bp_wkind;
 
-/* Weight law of a just-in-time (JIT) connectivity descriptor (Section 3.2,
+/* Weight law of a just-in-time (JIT) connectivity descriptor (Section 4.2,
  * Appendix C): homogeneous w0; uniform in [w0, w1); normal with mean w0 and
  * standard deviation w1. */
 typedef enum { BP_JIT_HOMO = 0, BP_JIT_UNIFORM = 1, BP_JIT_NORMAL = 2 } bp_jit_wkind;
@@ -156,7 +161,7 @@ bp_status bp_spike_compact(int64_t n, const uint8_t* events, int32_t* spike_list
                            int32_t* n_spikes, bp_stream_t stream);
 
 /* --------------------------------------------------------------------------
- * a5. Event-driven CSR product (Appendix B; Section 4.1 operator benchmark).
+ * a5. Event-driven CSR product (Appendix B; Section 5.1 operator benchmark).
  * For every spiking presynaptic row i in spike_list[0 .. *n_spikes):
  *   for j in [indptr[i], indptr[i+1]): y[indices[j]] += w_j
  * i.e. y = W^T s with W stored presynaptic-row-major (Appendix B's listing,
@@ -205,7 +210,8 @@ bp_status bp_event_csrmv_dense(int64_t n_pre, int64_t n_post,
  * inputs return BP_ERR_INVALID with a message and enqueue nothing.  The
  * scratch (about 4 MiB) exists on every GPU that loads the library until the
  * process exits.  The first call on each device looks up the scratch
- * array's device address; make that first call before any stream capture.
+ * array's device address and keeps it (see Devices above: not valid across a
+ * cudaDeviceReset); make that first call before any stream capture.
  * All calls on a device share the scratch, so calls that may overlap on the
  * GPU (other streams or host threads) race and must be serialised by the
  * caller. */
@@ -239,7 +245,7 @@ bp_status bp_csr_tile_index(int64_t n_pre, int64_t n_post, const int64_t* indptr
 bp_status bp_csr_check(int64_t n_pre, int64_t n_post, int64_t nnz, const int64_t* indptr, const int32_t* indices,
                        int64_t* out, bp_stream_t stream);
 
-/* Gather ("transpose") form over the same CSR, all rows (Section 3.1: every
+/* Gather ("transpose") form over the same CSR, all rows (Section 4.1: every
  * operator has reverse-mode rules; this is the product with W rather than
  * W^T):  y_pre[i] += sum_{j in row i} w_j x_post[indices[j]].
  * x_post float [n_post], y_pre float [n_pre].  With a tile index
@@ -258,7 +264,7 @@ bp_status bp_event_csrmv_t(int64_t n_pre, int64_t n_post,
                            const int32_t* tile_ptr, int32_t tile_cols,
                            uint32_t flags, bp_stream_t stream);
 
-/* Reverse mode of bp_event_csrmv for a loss L with dy = dL/dy (Section 3.1):
+/* Reverse mode of bp_event_csrmv for a loss L with dy = dL/dy (Section 4.1):
  *   dw[j] += dy[indices[j]] for every entry j of every spiking row (if dw is
  *   non-NULL; float [nnz]; each spiking row must appear once);
  *   dx_pre[i] += sum_j w_j dy[indices[j]] for every row i (if dx_pre is
@@ -274,7 +280,7 @@ bp_status bp_event_csrmv_bwd(int64_t n_pre, int64_t n_post,
                              bp_stream_t stream);
 
 /* --------------------------------------------------------------------------
- * a6. Just-in-time connectivity (Section 3.2, Appendix C).
+ * a6. Just-in-time connectivity (Section 4.2, Appendix C).
  * Row i's targets are q_0 = U_0 - 1, q_{k+1} = q_k + U_{k+1} while
  * q < n_post, with U_k = 1 + floor(x_k K / 2^32) uniform on [1, K],
  * K = ceil(2/p - 1) (at least 1), and x_k word (k mod 4) of
@@ -305,12 +311,12 @@ bp_status bp_jitconn_event_mv(const bp_jit_desc* d, int64_t n_pre, int64_t n_pos
                               void* y, int32_t y_is_count, uint32_t flags, bp_stream_t stream);
 
 /* Reverse mode with respect to the spike vector (weights are static, so
- * there is no weight gradient, Section 3.2): dx_pre[i] += sum over row i's
+ * there is no weight gradient, Section 4.2): dx_pre[i] += sum over row i's
  * targets q of w dy[q], for all rows i. */
 bp_status bp_jitconn_event_mv_bwd(const bp_jit_desc* d, int64_t n_pre, int64_t n_post,
                                   const float* dy, float* dx_pre, bp_stream_t stream);
 
-/* Non-event JIT product with a dense vector (Section 4.2, mv_prob_uniform /
+/* Non-event JIT product with a dense vector (Section 5.2, mv_prob_uniform /
  * mv_prob_normal): y_post[q] += w x_pre[i] for every target q of every row i. */
 bp_status bp_jitconn_mv(const bp_jit_desc* d, int64_t n_pre, int64_t n_post,
                         const float* x_pre, float* y_post, uint32_t flags, bp_stream_t stream);
@@ -332,7 +338,7 @@ uint64_t bp_projection_seed(uint64_t net_seed, int32_t projection);
  * Neurons [0, n_e) are excitatory, [n_e, n) inhibitory.  Each step is the
  * bp_lif_step update followed by the delivery of this step's spikes: E rows
  * into ye, I rows into yi (one merged conductance per neuron and synapse
- * type, Section 3.3 AlignPost), consumed by the next step.  The event
+ * type, Section 4.3 AlignPost), consumed by the next step.  The event
  * accumulators are double-buffered ([2n] each): step t reads and clears
  * elements [(t mod 2) n, (t mod 2 + 1) n) and delivers into the other half,
  * which lets one kernel do both.
@@ -438,7 +444,7 @@ bp_status bp_network_destroy(bp_net* net);
 
 /* --------------------------------------------------------------------------
  * a9. Batched networks: many independent COBA E/I networks of uneven sizes
- * (the "parameter explorations" of Section 2), each with its own seed and
+ * (the "parameter explorations" of Section 3), each with its own seed and
  * JIT connectivity (probability p, default 80/n, homogeneous w_e / w_i),
  * advanced together by one persistent kernel in which a CTA owns whole
  * networks (no inter-CTA synchronisation), its time loop captured in a CUDA
@@ -496,7 +502,7 @@ bp_status bp_batch_destroy(bp_batch* b);
  * a10. Differentiable recurrent spiking network and its BPTT adjoint
  * (Appendix I: LIF recurrent layer with exponential synaptic current, leaky
  * readout, cross-entropy on the readout, surrogate-gradient training;
- * Section 3.1: every operator has a reverse-mode rule).  Per batch element,
+ * Section 4.1: every operator has a reverse-mode rule).  Per batch element,
  * t = 1..T, starting from I = V = y = 0 and no spikes:
  *   I_t  = a_s I_{t-1} + W_rec^T z_{t-1} + W_in^T u_t     (a_s = exp(-dt/tau_s))
  *   Vp_t = a_m V_{t-1} + (1 - a_m)(V_rest + R I_t)        (exponential Euler)
@@ -590,6 +596,36 @@ bp_status bp_snn_reg_loss(const bp_snn_desc* d, const void* workspace, float* lo
  * db_out [n_out]. */
 bp_status bp_snn_backward(const bp_snn_desc* d, const uint8_t* u, const float* g_m, void* workspace, float* dW_in,
                           float* dw_rec, float* dW_out, float* db_out, bp_stream_t stream);
+
+/* --------------------------------------------------------------------------
+ * Measurement kernels (roofline denominators).  The paper has no counterpart:
+ * these give the roofs that bound this library's kernels where HBM bandwidth
+ * does not (the JIT rows' integer arithmetic, scattered L2 reductions, and the
+ * state pass of networks whose state stays in L2).  Each call enqueues one
+ * kernel on `stream`; the caller times it (CUDA events) and divides the work
+ * stated below by the time.
+ * ------------------------------------------------------------------------ */
+
+/* Philox-only draw rate: bp_roof_philox_threads() threads each compute
+ * blocks_per_thread Philox4x32-10 blocks (key `seed`, counters distinct per
+ * thread and block; 4 32-bit words per block, the draws of Section 4.2's
+ * JIT rows) and write one word each to sink uint32 [bp_roof_philox_threads()]
+ * (device).  Work: 4 x threads x blocks_per_thread words. */
+int64_t bp_roof_philox_threads(void);
+bp_status bp_roof_philox(int64_t blocks_per_thread, uint64_t seed, uint32_t* sink, bp_stream_t stream);
+
+/* Scattered-reduction rate: bp_roof_l2_red_threads() threads each add 1 to
+ * per_thread pseudo-random elements of y int32 [n] (device, n in [1, 2^31))
+ * with the keep-in-L2 hint of the event delivery.  Work: threads x per_thread
+ * reductions (y receives that many counts in total). */
+int64_t bp_roof_l2_red_threads(void);
+bp_status bp_roof_l2_red(int32_t* y, int64_t n, int64_t per_thread, bp_stream_t stream);
+
+/* Copy bandwidth: `reps` passes of dst[0, bytes) = src[0, bytes) (device,
+ * 16-byte aligned, bytes a multiple of 16).  With 2 x bytes well below the
+ * L2 size the buffers stay in L2 and the rate (2 x bytes x reps / time) is
+ * the L2-resident copy bandwidth; above it, the HBM copy bandwidth. */
+bp_status bp_roof_copy(const void* src, void* dst, int64_t bytes, int32_t reps, bp_stream_t stream);
 
 #ifdef __cplusplus
 }

@@ -248,7 +248,7 @@ class CobaNet:
     same buffer, which is read again d + 1 steps later.
 
     ``align``: "post" (default) keeps one conductance per postsynaptic neuron
-    and adds the delivered events to it (AlignPost, Section 3.3, Appendix E);
+    and adds the delivered events to it (AlignPost, Section 4.3, Appendix E);
     "pre" keeps one synaptic trace per presynaptic neuron instead, s <- s a + z
     with the projection's decay a and the previous step's spikes z, and
     recomputes every step the conductance g = W^T s through the connection

@@ -123,6 +123,11 @@ _SIGS = {
     "bp_batch_simulate": (c_i32, [VP, c_i64, VP]),
     "bp_batch_autotune": (c_i32, [VP, c_i32, VP, VP]),
     "bp_batch_destroy": (c_i32, [VP]),
+    "bp_roof_philox_threads": (c_i64, []),
+    "bp_roof_philox": (c_i32, [c_i64, c_u64, VP, VP]),
+    "bp_roof_l2_red_threads": (c_i64, []),
+    "bp_roof_l2_red": (c_i32, [VP, c_i64, c_i64, VP]),
+    "bp_roof_copy": (c_i32, [VP, VP, c_i64, c_i32, VP]),
     "bp_snn_desc_default": (c_i32, [ctypes.POINTER(SnnDesc)]),
     "bp_snn_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(SnnDesc)]),
     "bp_snn_forward": (c_i32, [ctypes.POINTER(SnnDesc), VP, VP, VP, VP]),
@@ -266,11 +271,25 @@ def bp_event_csrmv_dense_workspace_bytes(n_pre) -> int:
     return int(lib().bp_event_csrmv_dense_workspace_bytes(n_pre))
 
 
+def _dense_events(events, n_pre):
+    """The dense event vector the compaction reads: one byte per presynaptic row."""
+    if events is None or events.numel() < n_pre:
+        raise ValueError("events holds %d flags for %d presynaptic rows"
+                         % (0 if events is None else events.numel(), n_pre))
+    if events.dtype != torch.uint8:
+        raise ValueError("events must be uint8")
+
+
 def bp_event_csrmv_dense(indptr, indices, data, w_homo, events, workspace, y, tile_ptr=None, tile_cols=0, flags=0,
                          stream=None):
     n_pre = indptr.numel() - 1
     counts = 1 if y.dtype == torch.int32 else 0
     _csr_sizes(indices, data, n_pre, y.numel(), tile_ptr, tile_cols)
+    _dense_events(events, n_pre)
+    need = bp_event_csrmv_dense_workspace_bytes(n_pre)
+    if workspace is None or workspace.numel() * workspace.element_size() < need:
+        raise ValueError("workspace holds %d bytes, bp_event_csrmv_dense_workspace_bytes(%d) = %d"
+                         % (0 if workspace is None else workspace.numel() * workspace.element_size(), n_pre, need))
     _check("bp_event_csrmv_dense", lib().bp_event_csrmv_dense(n_pre, y.numel(), _p(indptr), _p(indices), _p(data),
                                                               _wkind(data), float(w_homo), _p(events), _p(workspace),
                                                               _p(y), counts, _p(tile_ptr), int(tile_cols), int(flags),
@@ -286,6 +305,8 @@ def bp_event_csrmv_dense_noalloc(indptr, indices, data, w_homo, events, y, flags
     scratch holds the spike list (for callers that cannot allocate)."""
     n_pre = indptr.numel() - 1
     counts = 1 if y.dtype == torch.int32 else 0
+    _csr_sizes(indices, data, n_pre, y.numel(), None, 0)
+    _dense_events(events, n_pre)
     _check("bp_event_csrmv_dense_noalloc",
            lib().bp_event_csrmv_dense_noalloc(n_pre, y.numel(), _p(indptr), _p(indices), _p(data), _wkind(data),
                                               float(w_homo), _p(events), _p(y), counts, int(flags), _stream(stream)))
@@ -484,3 +505,34 @@ def bp_snn_backward(desc, u, g_m, workspace, dW_in, dw_rec, dW_out, db_out, stre
 def bp_lif_step_bwd(desc, Vp, z, Vbar, zbar, Ibar_next, Ibar, Vbar_prev, stream=None):
     _check("bp_lif_step_bwd", lib().bp_lif_step_bwd(ctypes.byref(desc), Vp.numel(), _p(Vp), _p(z), _p(Vbar), _p(zbar),
                                                     _p(Ibar_next), _p(Ibar), _p(Vbar_prev), _stream(stream)))
+
+
+# ------------------------------------------------------------------ measurement kernels
+def bp_roof_philox_threads() -> int:
+    return int(lib().bp_roof_philox_threads())
+
+
+def bp_roof_philox(blocks_per_thread, sink, seed=1, stream=None):
+    """Philox-only draws: 4 words per block per thread; sink uint32 [threads]."""
+    if sink.dtype != torch.int32 or sink.numel() < bp_roof_philox_threads():
+        raise ValueError("sink must be int32 with bp_roof_philox_threads() entries")
+    _check("bp_roof_philox", lib().bp_roof_philox(int(blocks_per_thread), int(seed) & (2**64 - 1), _p(sink),
+                                                  _stream(stream)))
+
+
+def bp_roof_l2_red_threads() -> int:
+    return int(lib().bp_roof_l2_red_threads())
+
+
+def bp_roof_l2_red(y, per_thread, stream=None):
+    """threads x per_thread scattered +1 reductions into y int32."""
+    if y.dtype != torch.int32:
+        raise ValueError("y must be int32")
+    _check("bp_roof_l2_red", lib().bp_roof_l2_red(_p(y), y.numel(), int(per_thread), _stream(stream)))
+
+
+def bp_roof_copy(src, dst, reps, stream=None):
+    nbytes = src.numel() * src.element_size()
+    if dst.numel() * dst.element_size() < nbytes:
+        raise ValueError("dst is shorter than src")
+    _check("bp_roof_copy", lib().bp_roof_copy(_p(src), _p(dst), nbytes, int(reps), _stream(stream)))

@@ -1,4 +1,4 @@
-// jitconn.cu -- just-in-time connectivity (a6, Section 3.2, Appendix C).
+// jitconn.cu -- just-in-time connectivity (a6, Section 4.2, Appendix C).
 //
 // A warp regenerates one presynaptic row in chunks of 128 gaps: lane l draws
 // the Philox block with counter (c + l, row, 0, 0), i.e. gaps 4(c+l) ..

@@ -23,11 +23,16 @@ std::atomic<int> g_sm_count[kMaxDevices];
 std::atomic<int> g_smem_optin[kMaxDevices];
 std::mutex g_mu;
 
+// The calling thread's current device ordinal (0 if it cannot be read).
+// Ordinals of kMaxDevices or more are valid devices too: they are served
+// without the per-device caches below, never folded onto another device.
 int current_device() {
     int d = 0;
-    if (cudaGetDevice(&d) != cudaSuccess) return 0;
-    return d < kMaxDevices ? d : 0;
+    if (cudaGetDevice(&d) != cudaSuccess || d < 0) return 0;
+    return d;
 }
+
+bool cached(int d) { return d < kMaxDevices; }
 }  // namespace
 
 namespace bp {
@@ -41,8 +46,15 @@ void set_error(const char* fmt, ...) {
 
 void clear_error() { g_msg[0] = 0; }
 
+// Device address of the status word on the current device, looked up once
+// per device and kept for the life of the process (the library is not meant
+// to be used across a cudaDeviceReset, which would invalidate it).
 int* device_status_ptr() {
     const int d = current_device();
+    if (!cached(d)) {
+        void* p = nullptr;
+        return cudaGetSymbolAddress(&p, g_device_status) == cudaSuccess ? static_cast<int*>(p) : nullptr;
+    }
     std::lock_guard<std::mutex> lk(g_mu);
     if (!g_status_addr[d]) {
         void* p = nullptr;
@@ -54,12 +66,12 @@ int* device_status_ptr() {
 
 int sm_count() {
     const int d = current_device();
-    int c = g_sm_count[d].load(std::memory_order_relaxed);
+    int c = cached(d) ? g_sm_count[d].load(std::memory_order_relaxed) : 0;
     if (!c) {
         int v = 0;
         cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, d);
         c = v > 0 ? v : 1;
-        g_sm_count[d].store(c, std::memory_order_relaxed);
+        if (cached(d)) g_sm_count[d].store(c, std::memory_order_relaxed);
     }
     return c;
 }
@@ -81,12 +93,12 @@ bp_status ensure_smem_attr(const void* kernel, int bytes) {
 
 int max_smem_optin() {
     const int d = current_device();
-    int c = g_smem_optin[d].load(std::memory_order_relaxed);
+    int c = cached(d) ? g_smem_optin[d].load(std::memory_order_relaxed) : 0;
     if (!c) {
         int v = 0;
         cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, d);
         c = v > 0 ? v : 48 * 1024;
-        g_smem_optin[d].store(c, std::memory_order_relaxed);
+        if (cached(d)) g_smem_optin[d].store(c, std::memory_order_relaxed);
     }
     return c;
 }

@@ -4,7 +4,7 @@
 // A step is one launch (lif.cu, k_step): the neuron pass, the CTA-local
 // compaction of the step's spikes and their delivery through the stored CSR
 // or the JIT rows into the merged E and I event accumulators (AlignPost,
-// Section 3.3).  The accumulators are double-buffered: step t reads and
+// Section 4.3).  The accumulators are double-buffered: step t reads and
 // clears half t mod 2 and delivers into the other half, which step t + 1
 // reads (zero delay, Appendix N Listing S6), so delivery can run in the same
 // kernel as the neuron pass.  A delayed projection (delay d > 0, Appendix D)

@@ -1,5 +1,5 @@
 // snn.cu -- the differentiable recurrent spiking network and its BPTT
-// adjoint (a10; Appendix I, Section 3.1: operators with reverse-mode rules).
+// adjoint (a10; Appendix I, Section 4.1: operators with reverse-mode rules).
 //
 // Model (per batch element; t = 1..T):
 //   I_t  = a_s I_{t-1} + W_rec^T z_{t-1} + W_in^T u_t

@@ -161,12 +161,25 @@ class CobaNetwork:
         return {"step": B.bp_network_step_count(self.handle),
                 "state": {k: t.clone() for k, t in self.state_tensors().items()}}
 
-    def restore(self, ckpt):
+    def checkpoint_to_host(self):
+        """A checkpoint in pinned host memory (for restoring from the host
+        later, e.g. to resume a run in another process)."""
+        torch.cuda.synchronize()
+        return {"step": B.bp_network_step_count(self.handle),
+                "state": {k: t.to("cpu").pin_memory() for k, t in self.state_tensors().items()}}
+
+    def restore(self, ckpt, non_blocking=False):
         """Writes a checkpoint back (into this network or a new one of the
-        same configuration) so that the simulation resumes where it was taken."""
+        same configuration) so that the simulation resumes where it was taken.
+        With non_blocking and a pinned host checkpoint the copies are enqueued
+        on the current stream without waiting for them."""
         for k, t in self.state_tensors().items():
-            t.copy_(ckpt["state"][k])
+            t.copy_(ckpt["state"][k], non_blocking=non_blocking)
         B.bp_network_set_step_count(self.handle, ckpt["step"])
+
+    def state_bytes(self):
+        """Bytes of the caller-owned state buffers (what a restore copies)."""
+        return sum(t.numel() * t.element_size() for t in self.state_tensors().values())
 
     def step(self):
         B.bp_network_step(self.handle)

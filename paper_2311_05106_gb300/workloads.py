@@ -6,7 +6,7 @@ sizes, Poisson input trains, labels) from numpy's seeded generators, with the
 shapes and distributions of the paper's workloads:
 
 * COBA E/I network (Appendix N, Listing S6): 80 % excitatory, V0 ~ N(-55, 5) mV.
-* Operator sweep (Section 4.1 / Appendix B): Bernoulli spike vectors of density
+* Operator sweep (Section 5.1 / Appendix B): Bernoulli spike vectors of density
   rho, connection probability p, weights N(0.5, 0.1) or homogeneous.
 * Batched networks: sizes uniform in [1000, 50000].
 * Differentiable network (Appendix I): Poisson input trains with rates uniform

@@ -222,3 +222,29 @@ def test_binding_checks_lengths_behind_raw_pointers():
         B.bp_csr_tile_index(ip, ix, n_post, tc, short)
     with pytest.raises(ValueError, match="spike_list"):
         B.bp_event_csrmv(ip, ix, None, 1.0, sl[:5], ns, y)
+
+
+def test_dense_event_wrappers_check_lengths():
+    """Both dense-event products check, before any library call, that the
+    weights cover the stored entries, that the event vector holds one flag
+    per presynaptic row, and (workspace form) that the workspace has the
+    size bp_event_csrmv_dense_workspace_bytes reports (host tensors: the
+    checks come before any pointer is taken)."""
+    torch = pytest.importorskip("torch")
+    from paper_2311_05106_gb300 import binding as B
+    n_pre, n_post = 10, 64
+    ip = torch.zeros(n_pre + 1, dtype=torch.int64)
+    ix = torch.zeros(8, dtype=torch.int32)
+    ev = torch.zeros(n_pre, dtype=torch.uint8)
+    y = torch.zeros(n_post, dtype=torch.float32)
+    ws = torch.zeros(B.bp_event_csrmv_dense_workspace_bytes(n_pre), dtype=torch.uint8)
+    with pytest.raises(ValueError, match="weights for 8 stored entries"):
+        B.bp_event_csrmv_dense_noalloc(ip, ix, torch.zeros(7), 0.0, ev, y)
+    with pytest.raises(ValueError, match="weights for 8 stored entries"):
+        B.bp_event_csrmv_dense(ip, ix, torch.zeros(7), 0.0, ev, ws, y)
+    with pytest.raises(ValueError, match="events holds 9 flags"):
+        B.bp_event_csrmv_dense_noalloc(ip, ix, None, 1.0, ev[:9], y)
+    with pytest.raises(ValueError, match="events holds 9 flags"):
+        B.bp_event_csrmv_dense(ip, ix, None, 1.0, ev[:9], ws, y)
+    with pytest.raises(ValueError, match="workspace holds"):
+        B.bp_event_csrmv_dense(ip, ix, None, 1.0, ev, ws[:-1], y)

@@ -10,7 +10,7 @@ What pins what:
                                then every 189 steps; no spike within 51 steps.
 * AlignPost merging         -> per-synapse conductances simulated one by one and
                                summed equal the merged per-neuron conductance
-                               (Section 3.3: the merging is exact).
+                               (Section 4.3: the merging is exact).
 * event delivery            -> events per step = sum of out-degrees of spiking rows.
 * synaptic delay            -> a single presynaptic spike at the closed-form step
                                t_s = 138 reaches the target's conductance exactly

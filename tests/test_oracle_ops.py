@@ -1,4 +1,4 @@
-"""Pins of the oracle's event-driven operators (Appendix B, Appendix C, Section 3.1).
+"""Pins of the oracle's event-driven operators (Appendix B, Appendix C, Section 4.1).
 
 What pins what:
 * event CSR product         -> dense brute force W^T s (float), exact int counts,
