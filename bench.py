@@ -24,10 +24,11 @@ CUDA graph), bracketed by a barrier and cuda.synchronize(), timed with CUDA
 events on the launching stream; max over ranks.  The connectivity (2.6 GB)
 and state (52 MB of neuron state, 64 MB of event accumulators) exceed L2
 together; the state is re-read every step, as in any time-stepped simulation,
-and L2 is not flushed between steps.  `e2e` replays the same K steps through
-the public API from the state saved (in pinned host memory) after the
-warm-up: the state upload, the K steps and the download of the per-step
-record and final potentials are all inside its timed region.
+and L2 is not flushed between steps.  `e2e` replays the warm-up and timed
+steps (W + K) through the public API from the state saved in pinned host
+memory after the settle period: the state upload, the W + K steps and the
+download of the per-step record and final potentials are all inside its timed
+region.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -207,11 +208,16 @@ def build_network(torch, B, conn, weights, n=N_NEURONS, delay=0):
 def time_simulate(torch, net, steps, warmup, dist=None, keep_host_ckpt=None):
     """W warm-up steps, then K timed steps; returns (ms, events, spikes) of the
     timed steps.  keep_host_ckpt (a dict) receives the pinned host checkpoint
-    of the state the timed steps start from."""
+    of the state the warm-up starts from (taken, like the graph capture,
+    before the warm-up, so that the GPU runs the warm-up and the timed steps
+    back to back)."""
     stream = torch.cuda.current_stream()
-    net.simulate(warmup)
     if keep_host_ckpt is not None:
         keep_host_ckpt.update(net.checkpoint_to_host())
+    # the graphs of the warm-up and of a K-step call are captured and uploaded first
+    net.prepare(warmup)
+    net.prepare(steps)
+    net.simulate(warmup)
     before = net.totals.clone()
     if dist is not None:
         dist.barrier()
@@ -275,17 +281,18 @@ def lif_kernel_time(torch, B, net, reps=50):
 
 
 def e2e_run(torch, net, host_ckpt, steps):
-    """End to end through the public API: the K timed steps replayed from the
-    state they started from, held in pinned host memory (the state after the
-    settle period and the warm-up).  Inside the timed region: the upload of
-    that state (CobaNetwork.restore, non-blocking copies), bp_simulate over the
-    K steps with a per-step spike record, and the download of the record and
-    of the final potentials."""
+    """End to end through the public API: the warm-up and timed steps replayed
+    from the state they started from, held in pinned host memory (the state
+    after the settle period).  Inside the timed region: the upload of that
+    state (CobaNetwork.restore, non-blocking copies), bp_simulate over the
+    steps with a per-step spike record, and the download of the record and of
+    the final potentials.  `steps` = W + K."""
     f32 = torch.float32
     n = net.n
     rec = torch.zeros((steps, 2), dtype=torch.int32, device="cuda")
     hrec = torch.zeros((steps, 2), dtype=torch.int32).pin_memory()
     hVout = torch.zeros(n, dtype=f32).pin_memory()
+    net.prepare(steps)
     stream = torch.cuda.current_stream()
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -321,6 +328,7 @@ def bench_small_net(torch, steps=1000):
         net = CobaNetwork(n, conn=conn, seed=SEED, p=0.02, V0=V0)
         net.simulate(64)
         net.reset_counters()
+        net.prepare(steps)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record(stream)
@@ -335,6 +343,7 @@ def bench_small_net(torch, steps=1000):
     bat = BatchedNetworks(np.array([n]), np.array([SEED], np.uint64), V0=[V0])
     bat.simulate(64)
     bat.reset_counters()
+    bat.prepare(steps)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)
@@ -364,6 +373,7 @@ def bench_fig_s7(torch, n=400_000, steps=500):
         net = CobaNetwork(n, conn="jit", seed=SEED, p=p, V0=V0, params=params)
         net.simulate(50)
         net.reset_counters()
+        net.prepare(steps)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record(stream)
@@ -393,6 +403,7 @@ def bench_align_pre(torch, steps=100, warmup=5):
     net = CobaNetwork(n, n_e, conn="csr", seed=SEED, p=80.0 / n, V0=wl.coba_v0(n, seed=V0_SEED), csr=csr,
                       align="pre")
     net.simulate(warmup)
+    net.prepare(steps)
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -407,49 +418,68 @@ def bench_align_pre(torch, steps=100, warmup=5):
 
 
 def bench_batched(torch, steps=2000, n_nets=256):
-    """256 independent COBA E/I networks, N ~ U[1000, 50000] (seed 11), JIT
-    connectivity p = 80/N, per-network seeds: the persistent batched kernel
-    (autotuned CTA size) against the single-network path run network after
-    network (the plain FP32 path, one CUDA graph per network)."""
+    """256 independent COBA E/I networks, N ~ U[1000, 50000] (seed 11),
+    p = 80/N, per-network seeds, with JIT rows and with the same rows stored:
+    the persistent batched kernel (autotuned: CTA size, lanes per delivered
+    row, CTAs per SM) against the single-network path run network after
+    network (the plain path, one CUDA graph per network; sampled: 100 steps
+    each)."""
     import numpy as np
     from paper_2311_05106_gb300 import workloads as wl
-    from paper_2311_05106_gb300.network import BatchedNetworks, CobaNetwork
+    from paper_2311_05106_gb300.network import BatchedNetworks, CobaNetwork, batch_csr
     sizes = wl.batched_sizes(n_nets, 1000, 50000, seed=11)
     seeds = (np.arange(n_nets, dtype=np.uint64) * np.uint64(7919) + np.uint64(SEED))
     V0 = [wl.coba_v0(int(n), seed=1000 + b) for b, n in enumerate(sizes)]
     stream = torch.cuda.current_stream()
-    bat = BatchedNetworks(sizes, seeds, V0=V0)
-    threads = bat.autotune(probe_steps=20)
-    bat.simulate(steps)  # graph build + warm-up
-    bat.reset_counters()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    bat.simulate(steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    tot = bat.totals.cpu().numpy()
-    bins = bat.info()[0]
-    bat.close()
-    # the plain single-network path, one network after the other (sampled: 100 steps each)
-    seq_steps = 100
-    seq_ms = 0.0
-    for b in range(n_nets):
-        net = CobaNetwork(int(sizes[b]), conn="jit", seed=int(seeds[b]), V0=V0[b])
-        net.simulate(64)
-        a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        net.simulate(seq_steps)
-        c.record(stream)
+    out = {}
+    for conn in ("jit", "csr"):
+        csr = batch_csr(sizes, seeds, BatchedNetworks.layout(sizes)) if conn == "csr" else None
+        bat = BatchedNetworks(sizes, seeds, V0=V0, conn=conn, csr=csr)
+        bat.simulate(SETTLE_STEPS)
+        bat.autotune(probe_steps=20)
+        th, g, ps, _ = bat.tuning()
+        bat.prepare(steps)
+        before = bat.totals.clone()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
-        seq_ms += a.elapsed_time(c)
-        net.close()
-    seq_ms_per_step = seq_ms / seq_steps
-    return {"networks": n_nets, "neurons": int(sizes.sum()), "steps": steps, "bins": bins, "cta_threads": threads,
-            "ms_per_step": ms / steps, "events_per_s": float(tot[:, 2].sum()) / (ms * 1e-3),
-            "sequential_single_net_ms_per_step": seq_ms_per_step,
-            "speedup_vs_sequential": seq_ms_per_step / (ms / steps)}
+        e0.record(stream)
+        bat.simulate(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        tot = (bat.totals - before).cpu().numpy()
+        bins = bat.info()[0]
+        bat.close()
+        del bat
+        # the plain single-network path, one network after the other
+        seq_steps = 100
+        seq_ms = 0.0
+        for b in range(n_nets):
+            cb = None
+            if conn == "csr":
+                o0, o1 = int(BatchedNetworks.layout(sizes)[b]), int(sizes[b])
+                lo = int(csr[0][o0].item())
+                ip = csr[0][o0:o0 + o1 + 1] - lo
+                cb = (ip.contiguous(), csr[1][lo:lo + int(ip[-1].item())].contiguous(), None)
+            net = CobaNetwork(int(sizes[b]), conn=conn, seed=int(seeds[b]), V0=V0[b], csr=cb)
+            net.simulate(64)
+            net.prepare(seq_steps)
+            a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            net.simulate(seq_steps)
+            c.record(stream)
+            torch.cuda.synchronize()
+            seq_ms += a.elapsed_time(c)
+            net.close()
+        del csr
+        torch.cuda.empty_cache()
+        seq_ms_per_step = seq_ms / seq_steps
+        out[conn] = {"networks": n_nets, "neurons": int(sizes.sum()), "steps": steps, "bins": bins,
+                     "tuning": {"cta_threads": th, "lanes_per_row": g, "ctas_per_sm": ps},
+                     "ms_per_step": ms / steps, "events_per_s": float(tot[:, 2].sum()) / (ms * 1e-3),
+                     "sequential_single_net_ms_per_step": seq_ms_per_step,
+                     "speedup_vs_sequential": seq_ms_per_step / (ms / steps)}
+    return out
 
 
 def bench_bptt(torch, reps=3, T=1000):
@@ -823,6 +853,13 @@ def bench_operator_cells(torch, roofs):
             c["roof"] = "philox" if roofs["philox_words_per_s"] <= roofs["l2_red_per_s_1e6_targets"] else "l2_red"
             c["frac_roof"] = c["events_per_s"] / roof
         out.append(c)
+    # JIT rows into n_post = 1e4 accumulators (shared memory): no L2
+    # reductions, so the Philox-only draw rate is the roof (one draw per event)
+    for c in sweep_cells(torch, [10_000], [0.1], [0.1], ["homo"], ["jit"]):
+        c["roof_events_per_s"] = roofs["philox_words_per_s"]
+        c["roof"] = "philox"
+        c["frac_roof"] = c["events_per_s"] / roofs["philox_words_per_s"]
+        out.append(c)
     return out
 
 
@@ -932,11 +969,13 @@ def main():
     # ---- end to end through the public API: the same K steps from host buffers
     e2e = None
     if not args.no_e2e:
-        e2e_ms, e2e_events, h2d, d2h = e2e_run(torch, net, host_ckpt, args.steps)
+        n_e2e = args.warmup + args.steps
+        e2e_ms, e2e_events, h2d, d2h = e2e_run(torch, net, host_ckpt, n_e2e)
         e2e = {"value": e2e_events / (e2e_ms * 1e-3), "unit": "events/s",
-               "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
-               "ms": e2e_ms, "events": e2e_events,
-               "note": "the timed K steps replayed from the post-warm-up state uploaded from pinned host memory"}
+               "h2d_bytes_per_step": h2d / n_e2e, "d2h_bytes_per_step": d2h / n_e2e,
+               "ms": e2e_ms, "events": e2e_events, "steps": n_e2e,
+               "note": "the W warm-up and K timed steps replayed through the public API from the post-settle "
+                       "state uploaded from pinned host memory; upload, steps and downloads inside the timed region"}
     net.close()
     del net
     torch.cuda.empty_cache()

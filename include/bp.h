@@ -429,11 +429,18 @@ bp_status bp_network_step(bp_net* net, bp_stream_t stream);
 int64_t bp_network_step_count(const bp_net* net);
 bp_status bp_network_set_step_count(bp_net* net, int64_t step, bp_stream_t stream);
 
-/* T steps.  On its first call builds and caches a CUDA graph of a chunk of
- * steps (captured on a private stream), then launches it on `stream`;
- * record int32 [T][2] (nullable) receives the E and I spike counts of each
- * step. */
+/* T steps, launched as CUDA graphs on `stream`: T is split into 64-step
+ * chunks and a shorter remainder (plus one single step first when the step
+ * count is odd); the graph of each length is captured once, on a private
+ * stream, on first use and cached with the network.  record int32 [T][2]
+ * (nullable) receives the E and I spike counts of each step. */
 bp_status bp_simulate(bp_net* net, int64_t T, int32_t* record, bp_stream_t stream);
+
+/* Captures (if not cached yet) and uploads to the device, on `stream`, the
+ * graphs that bp_simulate(net, T, ...) launches, without running any step:
+ * a later bp_simulate of T steps then spends no host time on capture or
+ * instantiation and its first launch no time on the upload. */
+bp_status bp_simulate_prepare(bp_net* net, int64_t T, bp_stream_t stream);
 
 /* Population statistics in FP64 on the device (a8): out double [4] =
  * {rate of all neurons, E rate, I rate (Hz), synaptic events per step}, from
@@ -445,11 +452,12 @@ bp_status bp_network_destroy(bp_net* net);
 /* --------------------------------------------------------------------------
  * a9. Batched networks: many independent COBA E/I networks of uneven sizes
  * (the "parameter explorations" of Section 3), each with its own seed and
- * JIT connectivity (probability p, default 80/n, homogeneous w_e / w_i),
- * advanced together by one persistent kernel in which a CTA owns whole
- * networks (no inter-CTA synchronisation), its time loop captured in a CUDA
- * graph.  The per-step arithmetic is the one of bp_network_step; a network of
- * the batch follows the trajectory the single-network path computes for it.
+ * either JIT connectivity (probability p, default 80/n) or stored CSR rows,
+ * homogeneous w_e / w_i, advanced together by one persistent kernel in which
+ * a CTA owns whole networks (no inter-CTA synchronisation), its time loop
+ * captured in a CUDA graph.  The per-step arithmetic is the one of
+ * bp_network_step; a network of the batch follows the trajectory the
+ * single-network path computes for it.
  * ------------------------------------------------------------------------ */
 typedef struct {
     int32_t n_nets;
@@ -467,6 +475,14 @@ typedef struct {
     float* gi;
     uint8_t* ref;           /* refractory steps left (see bp_lif_step) */
     int64_t* totals;        /* device [n_nets][4]: spikes E, spikes I, events, steps (accumulated) */
+    /* Stored connectivity (both NULL: JIT rows from the seeds): one CSR over
+     * the padded concatenated layout, device memory.  Row off_b + i holds the
+     * targets of neuron i of network b (E rows i < n_e_b, I rows after) as
+     * indices local to network b, strictly increasing, in [0, n_b); padding
+     * rows are empty.  Validated by bp_batch_create (BP_ERR_INVALID
+     * otherwise); must stay valid and unchanged while the batch exists. */
+    const int64_t* indptr;  /* [padded_total + 1] */
+    const int32_t* indices; /* [indptr[padded_total]] */
 } bp_batch_desc;
 
 typedef struct bp_batch bp_batch;
@@ -476,13 +492,27 @@ typedef struct bp_batch bp_batch;
  * padded to a multiple of 4 neurons).  Returns -1 on bad arguments. */
 int64_t bp_batch_layout(int32_t n_nets, const int64_t* n, int64_t* offsets);
 
-/* Validates, packs the networks into one bin per SM (longest first, bounded
- * by shared memory) and allocates the device tables, the event-count spill
- * buffer and the autotuner's snapshot.  Pending event counts start at zero. */
+/* Validates (for stored rows: one synchronous device pass over them), packs
+ * the networks into one bin per SM (longest first, bounded by shared memory)
+ * and allocates the device tables, the event-count spill buffer and the
+ * autotuner's snapshot.  Pending event counts start at zero.  Initial
+ * tuning: 1024 threads, 8 lanes per stored row / 32 per JIT row, one CTA per
+ * SM. */
 bp_status bp_batch_create(const bp_batch_desc* desc, bp_batch** out);
 
 /* Bins (CTAs), CTA size in use and padded length of the layout. */
 bp_status bp_batch_info(const bp_batch* b, int32_t* bins, int32_t* threads, int64_t* padded_neurons);
+
+/* The tuning in use: CTA size, lanes that walk one delivered row (stored
+ * rows 4, 8, 16 or 32; JIT rows 16 or 32), CTAs (bins) per SM of the packing
+ * (1, 2 or 4; a bin holds at most 56 320, 27 648 or 13 312 neurons), and 1 if
+ * the rows are stored (0: JIT).  Any pointer may be NULL. */
+bp_status bp_batch_tuning(const bp_batch* b, int32_t* threads, int32_t* lanes_per_row, int32_t* ctas_per_sm,
+                          int32_t* stored_rows);
+
+/* Sets the tuning (values as above; re-packs when ctas_per_sm changes;
+ * BP_ERR_INVALID if a network does not fit the bins).  Synchronous. */
+bp_status bp_batch_set_tuning(bp_batch* b, int32_t threads, int32_t lanes_per_row, int32_t ctas_per_sm);
 
 /* Zeroes the pending event counts and the totals. */
 bp_status bp_batch_reset_counters(bp_batch* b, bp_stream_t stream);
@@ -490,10 +520,18 @@ bp_status bp_batch_reset_counters(bp_batch* b, bp_stream_t stream);
 /* T steps of every network (a CUDA graph per distinct T, cached). */
 bp_status bp_batch_simulate(bp_batch* b, int64_t T, bp_stream_t stream);
 
-/* Times probe_steps steps with each candidate CTA size (256, 512, 1024
- * threads) from a snapshot of the current state, restores the state, keeps
- * the fastest and returns it in *chosen_threads (nullable).  Synchronises
- * `stream`. */
+/* Captures (if not cached yet) and uploads, on `stream`, the graph of a
+ * T-step bp_batch_simulate without running it.  A change of tuning drops the
+ * cached graphs. */
+bp_status bp_batch_prepare(bp_batch* b, int64_t T, bp_stream_t stream);
+
+/* Autotuner: from a snapshot of the current state, times probe_steps steps
+ * of every feasible tuning -- CTA size (256, 512, 1024 threads) x lanes per
+ * delivered row x CTAs per SM (packings into 1, 2 or 4 bins per SM where
+ * every network fits and the CTAs can share an SM) -- then restores the
+ * state, keeps the fastest (see bp_batch_tuning) and returns its CTA size in
+ * *chosen_threads (nullable).  Every tuning computes the same trajectories.
+ * Synchronises `stream`. */
 bp_status bp_batch_autotune(bp_batch* b, int32_t probe_steps, int32_t* chosen_threads, bp_stream_t stream);
 
 bp_status bp_batch_destroy(bp_batch* b);
@@ -579,14 +617,15 @@ bp_status bp_lif_step_bwd(const bp_snn_desc* d, int64_t n, const float* Vp, cons
 
 /* Mean over the batch of the cross-entropy of softmax(m_b) with label_b
  * (labels int64 [B]), written to loss[0], and its gradient g_m = dL/dm
- * [B][n_out]. */
+ * [B][n_out].  FP32 (max-subtracted log-sum-exp; the batch mean a
+ * compensated sum in batch order). */
 bp_status bp_snn_loss(int32_t B, int32_t n_out, const float* m, const int64_t* labels, float* loss, float* g_m,
                       bp_stream_t stream);
 
 /* Adds the voltage regulariser L_v accumulated by the last bp_snn_forward
- * with this desc and workspace to loss[0] (the per-batch sums are added in
- * batch order in FP64, so the result is reproducible).  Does nothing when
- * lambda_v = 0. */
+ * with this desc and workspace to loss[0] (FP32 compensated sums: per thread,
+ * then a fixed tree over the CTA, then the batch elements in order, so the
+ * result is reproducible).  Does nothing when lambda_v = 0. */
 bp_status bp_snn_reg_loss(const bp_snn_desc* d, const void* workspace, float* loss, bp_stream_t stream);
 
 /* Backward pass (BPTT with checkpointed recomputation) for an upstream

@@ -63,7 +63,8 @@ BP_ALIGN_PRE = 1
 
 class BatchDesc(ctypes.Structure):
     _fields_ = [("n_nets", c_i32), ("n", VP), ("n_e", VP), ("seed", VP), ("p", VP), ("coba", CobaParams),
-                ("V", VP), ("ge", VP), ("gi", VP), ("ref", VP), ("totals", VP)]
+                ("V", VP), ("ge", VP), ("gi", VP), ("ref", VP), ("totals", VP),
+                ("indptr", VP), ("indices", VP)]
 
 
 class SnnDesc(ctypes.Structure):
@@ -114,14 +115,18 @@ _SIGS = {
     "bp_network_step_count": (c_i64, [VP]),
     "bp_network_set_step_count": (c_i32, [VP, c_i64, VP]),
     "bp_simulate": (c_i32, [VP, c_i64, VP, VP]),
+    "bp_simulate_prepare": (c_i32, [VP, c_i64, VP]),
     "bp_network_stats": (c_i32, [VP, VP, VP]),
     "bp_network_destroy": (c_i32, [VP]),
     "bp_batch_layout": (c_i64, [c_i32, VP, VP]),
     "bp_batch_create": (c_i32, [ctypes.POINTER(BatchDesc), ctypes.POINTER(VP)]),
     "bp_batch_info": (c_i32, [VP, VP, VP, VP]),
+    "bp_batch_tuning": (c_i32, [VP, VP, VP, VP, VP]),
+    "bp_batch_set_tuning": (c_i32, [VP, c_i32, c_i32, c_i32]),
     "bp_batch_reset_counters": (c_i32, [VP, VP]),
     "bp_batch_simulate": (c_i32, [VP, c_i64, VP]),
     "bp_batch_autotune": (c_i32, [VP, c_i32, VP, VP]),
+    "bp_batch_prepare": (c_i32, [VP, c_i64, VP]),
     "bp_batch_destroy": (c_i32, [VP]),
     "bp_roof_philox_threads": (c_i64, []),
     "bp_roof_philox": (c_i32, [c_i64, c_u64, VP, VP]),
@@ -423,6 +428,10 @@ def bp_simulate(net, T, record=None, stream=None):
     _check("bp_simulate", lib().bp_simulate(net, int(T), _p(record), _stream(stream)))
 
 
+def bp_simulate_prepare(net, T, stream=None):
+    _check("bp_simulate_prepare", lib().bp_simulate_prepare(net, int(T), _stream(stream)))
+
+
 def bp_network_stats(net, out, stream=None):
     _check("bp_network_stats", lib().bp_network_stats(net, _p(out), _stream(stream)))
 
@@ -455,12 +464,28 @@ def bp_batch_info(b):
     return bins.value, threads.value, total.value
 
 
+def bp_batch_tuning(b):
+    """(threads, lanes_per_row, ctas_per_sm, stored_rows) of the batch."""
+    th, g, ps, st = c_i32(), c_i32(), c_i32(), c_i32()
+    _check("bp_batch_tuning", lib().bp_batch_tuning(b, ctypes.byref(th), ctypes.byref(g), ctypes.byref(ps),
+                                                    ctypes.byref(st)))
+    return th.value, g.value, ps.value, st.value
+
+
+def bp_batch_set_tuning(b, threads, lanes_per_row, ctas_per_sm):
+    _check("bp_batch_set_tuning", lib().bp_batch_set_tuning(b, int(threads), int(lanes_per_row), int(ctas_per_sm)))
+
+
 def bp_batch_reset_counters(b, stream=None):
     _check("bp_batch_reset_counters", lib().bp_batch_reset_counters(b, _stream(stream)))
 
 
 def bp_batch_simulate(b, T, stream=None):
     _check("bp_batch_simulate", lib().bp_batch_simulate(b, int(T), _stream(stream)))
+
+
+def bp_batch_prepare(b, T, stream=None):
+    _check("bp_batch_prepare", lib().bp_batch_prepare(b, int(T), _stream(stream)))
 
 
 def bp_batch_autotune(b, probe_steps=20, stream=None):

@@ -25,10 +25,12 @@ struct NvtxRange {
 };
 
 
-// Post neurons per shared-memory tile: 56 Ki 4-byte accumulators (224 KiB)
-// fit one CTA per SM under the 227 KiB opt-in limit with room for the
-// kernel's own bookkeeping.
-constexpr int32_t kTileCols = 57344;
+// Post neurons per shared-memory tile: 54 944 4-byte accumulators (214.6 KiB)
+// fit one CTA per SM under the 227 KiB opt-in limit together with the event
+// product's per-warp segment tables (12.3 KiB: 32 row segments per warp of a
+// 1024-thread CTA).
+constexpr int32_t kTileCols = 54944;
+constexpr int kMaxSmemPerCta = 232448;  // 227 KiB opt-in limit of sm_100-class GPUs
 constexpr int kTileThreads = 1024;
 
 // FP32 constants of one COBA/LIF step; decay factors from FP64 exp().

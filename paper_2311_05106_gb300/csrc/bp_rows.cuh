@@ -150,18 +150,24 @@ __device__ __forceinline__ void jit_weights(const JitArgs& d, uint32_t blk, uint
     }
 }
 
-// Walks JIT row `row` with the calling (full) warp in chunks of 128 gaps:
-// lane l draws the Philox block (c + l, row, 0, 0), maps its four words to
-// U[1, K] with a multiply-high, and a warp inclusive scan of the lanes' sums
-// gives the positions q_0 = U_0 - 1, q_{k+1} = q_k + U_{k+1}.  f(q, k, w) runs
-// for every target q < n_post (k = synapse index).  Returns this lane's count.
-template <int WK, typename F>
-__device__ __forceinline__ int64_t jit_walk(const JitArgs& d, uint32_t row, int64_t n_post, F&& f) {
-    const uint32_t lane = threadIdx.x & 31u;
+// Walks JIT row `row` with a group of G lanes (G = 32: the calling full warp;
+// G = 16: the calling half warp, the other half walking another row) in
+// chunks of 4 G gaps: lane l draws the Philox block (c + l, row, 0, 0), maps
+// its four words to U[1, K] with a multiply-high, and a group inclusive scan
+// of the lanes' sums gives the positions q_0 = U_0 - 1,
+// q_{k+1} = q_k + U_{k+1}.  The blocks are drawn in the same order whatever G,
+// so the targets do not depend on it.  f(q, k, w) runs for every target
+// q < n_post (k = synapse index).  Every lane of the group must call it with
+// the same row.  Returns this lane's count.
+template <int WK, int G, typename F>
+__device__ __forceinline__ int64_t jit_walk_g(const JitArgs& d, uint32_t row, int64_t n_post, F&& f) {
+    static_assert(G == 16 || G == 32, "JIT rows are walked by 16 or 32 lanes");
+    const uint32_t lane = threadIdx.x & (G - 1u);
+    const unsigned mask = G == 32 ? FULL_MASK : (0xFFFFu << (threadIdx.x & 16u));
     const uint32_t k0 = static_cast<uint32_t>(d.seed), k1 = static_cast<uint32_t>(d.seed >> 32);
     int64_t carry = -1;
     int64_t count = 0;
-    for (uint32_t c = 0;; c += 32u) {
+    for (uint32_t c = 0;; c += G) {
         const uint32_t blk = c + lane;
         const uint4 x = Philox::block(make_uint4(blk, row, 0u, 0u), k0, k1);
         const uint32_t g0 = 1u + __umulhi(x.x, d.K);
@@ -169,7 +175,12 @@ __device__ __forceinline__ int64_t jit_walk(const JitArgs& d, uint32_t row, int6
         const uint32_t g2 = 1u + __umulhi(x.z, d.K);
         const uint32_t g3 = 1u + __umulhi(x.w, d.K);
         const uint64_t s4 = static_cast<uint64_t>(g0) + g1 + g2 + g3;
-        const uint64_t incl = warp_inclusive_scan(s4);
+        uint64_t incl = s4;
+#pragma unroll
+        for (int dd = 1; dd < G; dd <<= 1) {
+            const uint64_t o = __shfl_up_sync(mask, incl, dd, G);
+            if (lane >= static_cast<uint32_t>(dd)) incl += o;
+        }
         const int64_t q0 = carry + static_cast<int64_t>(incl - s4) + g0;
         const int64_t q1 = q0 + g1, q2 = q1 + g2, q3 = q2 + g3;
         if (q0 < n_post) {
@@ -182,10 +193,16 @@ __device__ __forceinline__ int64_t jit_walk(const JitArgs& d, uint32_t row, int6
             if (q2 < n_post) { f(q2, kb + 2, w[2]); ++count; }
             if (q3 < n_post) { f(q3, kb + 3, w[3]); ++count; }
         }
-        carry += static_cast<int64_t>(__shfl_sync(FULL_MASK, incl, 31));
+        carry += static_cast<int64_t>(__shfl_sync(mask, incl, G - 1, G));
         if (carry >= n_post - 1) break;
     }
     return count;
+}
+
+// The full-warp walk (G = 32).
+template <int WK, typename F>
+__device__ __forceinline__ int64_t jit_walk(const JitArgs& d, uint32_t row, int64_t n_post, F&& f) {
+    return jit_walk_g<WK, 32>(d, row, n_post, static_cast<F&&>(f));
 }
 
 // Adds v (one value per thread) into *dst with one atomic per CTA.  Every

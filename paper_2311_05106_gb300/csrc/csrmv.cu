@@ -116,6 +116,111 @@ __device__ __forceinline__ void scatter_any(const int32_t* __restrict__ indices,
         scatter_segment<Acc, WK>(indices, data, w_homo, b0, b1, lane, G, out, col0);
 }
 
+// Flattened walk of the tile segments of spiking rows, one warp at a time.
+//
+// Each warp of the CTA takes 32 spiking rows at a time (one per lane).  Every
+// lane fetches its row's segment in post tile s, [b0, b0 + len); a warp
+// prefix sum of the lengths lays the 32 segments end to end as one flat list
+// of T units (start[k] = flat position of segment k), and the 32 lanes stream
+// flat positions l, l + 32, ...: consecutive lanes read consecutive units of
+// a segment (coalesced), and the warp's lanes stay busy whatever the segment
+// lengths, so short segments cost neither idle lanes nor a memory latency
+// each.  A lane finds its first segment by binary search over the 33 starts
+// and then follows the segment boundaries as its position advances.  The
+// next 32 rows' bounds are loaded while the current ones are walked (spike
+// ids one round ahead of the row extents and tile offsets).  Warps share
+// nothing but the tile, so they proceed without block-wide barriers.
+//
+// Units are entries, or, with 16-byte aligned operands, 16-byte chunks of 4
+// entries aligned in memory (each lane then moves 16 bytes of indices per
+// load): segment k covers chunks [b0 / 4, (b1 + 3) / 4), and the entries of
+// its first chunk before b0 and of its last chunk from b1 on are masked off.
+struct WarpList {
+    // (global unit index of flat position 0 of segment k) << 8 | edge, with
+    // edge = (entries skipped in the first chunk) | (entries kept in the last
+    // chunk) << 2 for chunked units (0 for entries)
+    int64_t base[32];
+    int32_t start[33];  // exclusive prefix of the 32 segments' unit counts; start[32] = T
+};
+struct FlatSmem {
+    WarpList w[kTileThreads / 32];
+};
+
+// A warp whose 32 segments hold more than this many units (far more than 32
+// segments of a tile without repeated columns: a tile spans at most 54 944
+// columns) is walked segment by segment instead; flat positions stay far from
+// the 32-bit range.
+constexpr int64_t kFlatMaxEntries = int64_t(1) << 24;
+
+template <typename Acc, int WK, bool CHUNKS, int U>
+__device__ __forceinline__ void warp_flat_walk(const CsrArgs& a, const WarpList& L, int32_t T,
+                                               Acc* __restrict__ acc, int64_t col0, int32_t W) {
+    const int lane = threadIdx.x & 31;
+    int32_t e = lane;
+    if (e >= T) return;
+    int k_lo = 0, k_hi = 32;  // start[k_lo] <= e < start[k_hi]
+    while (k_hi - k_lo > 1) {
+        const int mid = (k_lo + k_hi) >> 1;
+        if (L.start[mid] <= e) k_lo = mid; else k_hi = mid;
+    }
+    int seg = k_lo;
+    int32_t cur = L.start[seg];
+    int32_t nxt = L.start[seg + 1];
+    int64_t pk = L.base[seg];
+    constexpr int EPU = CHUNKS ? 4 : 1;  // entries per unit
+    for (; e < T; e += 32 * U) {
+        int32_t col[U][EPU];
+        float w[U][EPU];
+        uint32_t msk[U];
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            const int32_t eq = e + 32 * q;
+            msk[q] = 0;
+#pragma unroll
+            for (int m = 0; m < EPU; ++m) {
+                col[q][m] = 0;
+                w[q][m] = 0.f;
+            }
+            if (eq < T) {
+                if (eq >= nxt) {
+                    do {
+                        ++seg;
+                        cur = nxt;
+                        nxt = L.start[seg + 1];
+                    } while (eq >= nxt);
+                    pk = L.base[seg];
+                }
+                const int64_t g = static_cast<int64_t>(eq - cur) + (pk >> 8);
+                if constexpr (CHUNKS) {
+                    const int4 c4 = ld_stream4(a.indices + 4 * g);
+                    const float4 w4 = load_weight4<WK>(a.data, 4 * g, a.w_homo);
+                    col[q][0] = c4.x, col[q][1] = c4.y, col[q][2] = c4.z, col[q][3] = c4.w;
+                    w[q][0] = w4.x, w[q][1] = w4.y, w[q][2] = w4.z, w[q][3] = w4.w;
+                    const uint32_t edge = static_cast<uint32_t>(pk & 0xFF);
+                    uint32_t mm = 0xFu;
+                    if (eq == cur) mm &= 0xFu << (edge & 3u);
+                    if (eq == nxt - 1) mm &= (1u << (edge >> 2)) - 1u;
+                    msk[q] = mm;
+                } else {
+                    col[q][0] = ld_stream(a.indices + g);
+                    w[q][0] = load_weight<WK>(a.data, g, a.w_homo);
+                    msk[q] = 1u;
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+#pragma unroll
+            for (int m = 0; m < EPU; ++m) {
+                // an index outside this tile (an operand that does not match
+                // its tile index) is skipped rather than written out of the tile
+                const uint32_t c = static_cast<uint32_t>(static_cast<int64_t>(col[q][m]) - col0);
+                if (((msk[q] >> m) & 1u) && c < static_cast<uint32_t>(W)) acc_add(acc + c, event_value<Acc>(w[q][m]));
+            }
+        }
+    }
+}
+
 template <typename Acc, int WK, bool VECL>
 __global__ void __launch_bounds__(kTileThreads, 1)
     k_csr_scatter(CsrArgs a, const int32_t* __restrict__ spike_list, const int32_t* __restrict__ n_spikes,
@@ -123,6 +228,7 @@ __global__ void __launch_bounds__(kTileThreads, 1)
                   int64_t* __restrict__ events_total) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Acc* acc = reinterpret_cast<Acc*>(smem_raw);
+    FlatSmem& fs = *reinterpret_cast<FlatSmem*>(smem_raw + static_cast<size_t>(W) * sizeof(Acc));
     int64_t ns = *n_spikes;
     ns = ns < max_spikes ? ns : max_spikes;
     const int64_t nnz = a.indptr[a.n_pre];
@@ -134,7 +240,7 @@ __global__ void __launch_bounds__(kTileThreads, 1)
     }
     int64_t ev = 0;
     if (mode == 1) {
-        const int G = widen_group(VECL ? pick_group_v4(nnz, a.n_pre, 1) : pick_group(nnz, a.n_pre, 1), ns,
+        const int G = widen_group(VECL && WK != WK_F32 ? pick_group_v4(nnz, a.n_pre, 1) : pick_group(nnz, a.n_pre, 1), ns,
                                   static_cast<int64_t>(gridDim.x) * blockDim.x, blockDim.x);
         const int lane = threadIdx.x % G;
         const int64_t ngroups = static_cast<int64_t>(gridDim.x) * blockDim.x / G;
@@ -143,95 +249,142 @@ __global__ void __launch_bounds__(kTileThreads, 1)
             if (static_cast<uint32_t>(i) >= static_cast<uint64_t>(a.n_pre)) continue;
             const int64_t b0 = a.indptr[i], b1 = a.indptr[i + 1];
             if (lane == 0) ev += b1 - b0;
-            scatter_any<Acc, WK, VECL>(a.indices, a.data, a.w_homo, b0, b1, lane, G, y, 0);
+            scatter_any<Acc, WK, VECL && WK != WK_F32>(a.indices, a.data, a.w_homo, b0, b1, lane, G, y, 0);
         }
     } else {
         const int s = blockIdx.x % S;
         const int64_t r = blockIdx.x / S;
         const int64_t R = gridDim.x / S;
         const int64_t col0 = static_cast<int64_t>(s) * W;
-        for (int t = threadIdx.x; t < W; t += blockDim.x) acc[t] = Acc(0);
+        const int t = threadIdx.x;
+        const int warp = t >> 5, lane = t & 31;
+        WarpList& L = fs.w[warp];
+        for (int k = t; k < W; k += kTileThreads) acc[k] = Acc(0);
         __syncthreads();
-        // rows r, r + R, ... of the spike list, G lanes per row
-        auto walk = [&](int G) {
-            const int lane = threadIdx.x % G;
-            const int64_t gid = threadIdx.x / G;
-            const int64_t ng = blockDim.x / G;
-            for (int64_t u = r + R * gid; u < ns; u += R * ng) {
-                const int32_t i = spike_list[u];
-                if (static_cast<uint32_t>(i) >= static_cast<uint64_t>(a.n_pre)) continue;
-                const int64_t rs = a.indptr[i];
-                int64_t b0, b1;
+        // the CTA's rows are spike-list positions r + R m, m in [0, M); warp w
+        // takes an equal contiguous share [m_lo, m_hi) of them, 32 per round
+        const int32_t M = static_cast<int32_t>(ns > r ? (ns - r + R - 1) / R : 0);  // ns <= n_pre < 2^31
+        const int32_t m_lo = static_cast<int32_t>(static_cast<int64_t>(M) * warp / (kTileThreads / 32));
+        const int32_t m_hi = static_cast<int32_t>(static_cast<int64_t>(M) * (warp + 1) / (kTileThreads / 32));
+        auto row_id = [&](int32_t k) -> int32_t {
+            const int32_t m = m_lo + 32 * k + lane;
+            return m < m_hi ? spike_list[r + R * m] : -1;
+        };
+        // the loads that give a row's segment in tile s; the arithmetic on
+        // them is left to seg_of so that the loads stay in flight
+        struct Raw { int64_t rs, re; int32_t t0, t1; bool ok; };
+        auto row_raw = [&](int32_t i) -> Raw {
+            Raw x{0, 0, 0, 0, false};
+            if (static_cast<uint32_t>(i) < static_cast<uint64_t>(a.n_pre)) {
+                x.ok = true;
+                x.rs = a.indptr[i];
                 if (a.tile_ptr) {
                     const int32_t* tp = a.tile_ptr + static_cast<int64_t>(i) * (S + 1) + s;
-                    b0 = rs + tp[0];
-                    b1 = rs + tp[1];
+                    x.t0 = tp[0];
+                    x.t1 = tp[1];
+                    if (events_total && s == 0) x.re = a.indptr[i + 1];
                 } else {
-                    b0 = rs;
-                    b1 = a.indptr[i + 1];
+                    x.re = a.indptr[i + 1];
                 }
-                if (events_total && s == 0 && lane == 0) ev += a.indptr[i + 1] - rs;
-                scatter_any<Acc, WK, VECL>(a.indices, a.data, a.w_homo, b0, b1, lane, G, acc, col0);
             }
+            return x;
         };
-        // rows in batches of one per thread: every thread first fetches the
-        // segment bounds of its row (spike id -> row start -> tile offsets,
-        // three dependent loads, all of the CTA's in flight together), then
-        // each group of G lanes walks the G segments its lanes hold, one
-        // after another, taking the bounds by shuffle; the dependent chain is
-        // paid once per batch instead of once per segment.  Row k of a batch
-        // is held by lane k / ng of group k mod ng, so that a partial last
-        // batch still spreads over all groups.
-        auto walk_batched = [&](int G) {
-            const int lane = threadIdx.x % G;
-            const int64_t ng = blockDim.x / G;
-            const int64_t k = static_cast<int64_t>(lane) * ng + threadIdx.x / G;
-            const int64_t step = R * static_cast<int64_t>(blockDim.x);
-            for (int64_t base = r; base < ns; base += step) {
-                const int64_t u = base + R * k;
-                int64_t b0 = 0, b1 = 0;
-                if (u < ns) {
-                    const int32_t i = spike_list[u];
-                    if (static_cast<uint32_t>(i) < static_cast<uint64_t>(a.n_pre)) {
-                        const int64_t rs = a.indptr[i];
-                        if (a.tile_ptr) {
-                            const int32_t* tp = a.tile_ptr + static_cast<int64_t>(i) * (S + 1) + s;
-                            b0 = rs + tp[0];
-                            b1 = rs + tp[1];
-                        } else {
-                            b0 = rs;
-                            b1 = a.indptr[i + 1];
+        auto seg_of = [&](const Raw& x, int64_t& b0, int64_t& len) {
+            b0 = 0;
+            len = 0;
+            if (!x.ok) return;
+            if (a.tile_ptr) {
+                b0 = x.rs + x.t0;
+                len = static_cast<int64_t>(x.t1) - x.t0;
+                if (events_total && s == 0) ev += x.re - x.rs;
+            } else {
+                b0 = x.rs;
+                len = x.re - x.rs;
+                if (events_total && s == 0) ev += len;
+            }
+            if (len < 0) len = 0;
+        };
+        Raw cur = row_raw(row_id(0));
+        int32_t id_next = row_id(1);
+        for (int32_t k = 0; m_lo + 32 * k < m_hi; ++k) {
+            int64_t b0, len;
+            seg_of(cur, b0, len);
+            // the segment's units: entries, or aligned 4-entry chunks
+            int64_t u0 = b0, units = len;
+            int64_t edge = 0;
+            if constexpr (VECL) {
+                u0 = b0 >> 2;
+                const int64_t u1 = (b0 + len + 3) >> 2;
+                units = len > 0 ? u1 - u0 : 0;
+                edge = (b0 & 3) | ((b0 + len - 4 * (u1 - 1)) << 2);
+            }
+            int64_t incl = units;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int64_t o = __shfl_up_sync(FULL_MASK, incl, d);
+                if (lane >= d) incl += o;
+            }
+            const int64_t T = __shfl_sync(FULL_MASK, incl, 31);
+            const int64_t excl = incl - units;
+            // the next round's bounds are fetched while this one is walked
+            const Raw nxt_raw = row_raw(id_next);
+            id_next = row_id(k + 2);
+            if (T <= kFlatMaxEntries) {
+                __syncwarp();  // the previous round's walk has finished with L
+                L.start[lane] = static_cast<int32_t>(excl);
+                L.base[lane] = (u0 << 8) | (edge & 0xFF);
+                if (lane == 31) L.start[32] = static_cast<int32_t>(T);
+                __syncwarp();
+                warp_flat_walk<Acc, WK, VECL, VECL ? (WK == WK_HOMO ? 4 : 3) : (std::is_same<Acc, int32_t>::value && WK == WK_HOMO ? 16 : 8)>(
+                    a, L, static_cast<int32_t>(T), acc, col0, W);
+            } else {
+                // the warp walks its lanes' segments one after another, four
+                // loads in flight per lane
+                for (int l = 0; l < 32; ++l) {
+                    const int64_t c0 = __shfl_sync(FULL_MASK, b0, l);
+                    const int64_t c1 = c0 + __shfl_sync(FULL_MASK, len, l);
+                    for (int64_t j = c0 + lane; j < c1; j += 4 * 32) {
+                        int32_t c[4];
+                        float wv[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const int64_t jj = j + 32 * q;
+                            c[q] = jj < c1 ? ld_stream(a.indices + jj) : -1;
+                            wv[q] = jj < c1 ? load_weight<WK>(a.data, jj, a.w_homo) : 0.f;
                         }
-                        if (events_total && s == 0) ev += a.indptr[i + 1] - rs;
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const uint32_t kk = static_cast<uint32_t>(static_cast<int64_t>(c[q]) - col0);
+                            if (c[q] >= 0 && kk < static_cast<uint32_t>(W)) acc_add(acc + kk, event_value<Acc>(wv[q]));
+                        }
                     }
                 }
-                for (int l = 0; l < G; ++l) {
-                    const int64_t c0 = __shfl_sync(FULL_MASK, b0, l, G);
-                    const int64_t c1 = __shfl_sync(FULL_MASK, b1, l, G);
-                    if (c1 > c0) scatter_any<Acc, WK, VECL>(a.indices, a.data, a.w_homo, c0, c1, lane, G, acc, col0);
-                }
             }
-        };
-        const int G0 = VECL ? pick_group_v4(nnz, a.n_pre, S) : pick_group(nnz, a.n_pre, S);
-        const int64_t rows_here = ns > r ? (ns - r + R - 1) / R : 0;
-        // the widened walk is a separate copy, so the common walk keeps the
-        // code of the small fixed group sizes (measured: one shared copy with
-        // a run-time group size slows the large cells by 9-17 %)
-        // (batched bounds measured on the n = 1e6 cells: FP32 / BF16 weights
-        // 1-18 % faster, integer counts with 16-byte index loads 2-15 % slower,
-        // so the homogeneous form keeps the per-row chain)
-        if (rows_here * 2 * G0 <= static_cast<int64_t>(blockDim.x))
-            walk(widen_group(G0, rows_here, blockDim.x, blockDim.x));
-        else if constexpr (WK == WK_HOMO)
-            walk(G0);
-        else
-            walk_batched(G0);
+            cur = nxt_raw;
+        }
         __syncthreads();
         const int64_t rem = a.n_post - col0;
         const int lim = static_cast<int>(rem < W ? rem : W);
-        for (int t = threadIdx.x; t < lim; t += blockDim.x) {
-            const Acc v = acc[t];
-            if (v != Acc(0)) acc_add(y + col0 + t, v);
+        if constexpr (std::is_same<Acc, float>::value) {
+            // FP32 sums: one 16-byte reduction per four columns (y 16-byte
+            // aligned; col0 is a multiple of 32), the ragged tail one by one
+            if ((reinterpret_cast<uintptr_t>(y) & 15) == 0) {
+                const int lim4 = lim & ~3;
+                for (int k = 4 * t; k < lim4; k += 4 * kTileThreads) {
+                    const float4 v = *reinterpret_cast<const float4*>(acc + k);
+                    if (v.x != 0.f || v.y != 0.f || v.z != 0.f || v.w != 0.f) red_add_v4(y + col0 + k, v);
+                }
+                for (int k = lim4 + t; k < lim; k += kTileThreads)
+                    if (acc[k] != 0.f) acc_add(y + col0 + k, acc[k]);
+            } else {
+                for (int k = t; k < lim; k += kTileThreads)
+                    if (acc[k] != 0.f) acc_add(y + col0 + k, acc[k]);
+            }
+        } else {
+            for (int k = t; k < lim; k += kTileThreads) {
+                const Acc v = acc[k];
+                if (v != Acc(0)) acc_add(y + col0 + k, v);
+            }
         }
     }
     if (events_total) block_add_i64(ev, events_total);
@@ -245,7 +398,7 @@ __global__ void __launch_bounds__(kDirectThreads)
     int64_t ns = *n_spikes;
     ns = ns < max_spikes ? ns : max_spikes;
     const int64_t nnz = a.indptr[a.n_pre];
-    const int G = widen_group(VECL ? pick_group_v4(nnz, a.n_pre, 1) : pick_group(nnz, a.n_pre, 1), ns,
+    const int G = widen_group(VECL && WK != WK_F32 ? pick_group_v4(nnz, a.n_pre, 1) : pick_group(nnz, a.n_pre, 1), ns,
                               static_cast<int64_t>(gridDim.x) * blockDim.x, blockDim.x);
     const int lane = threadIdx.x % G;
     const int64_t ngroups = static_cast<int64_t>(gridDim.x) * blockDim.x / G;
@@ -255,7 +408,7 @@ __global__ void __launch_bounds__(kDirectThreads)
         if (static_cast<uint32_t>(i) >= static_cast<uint64_t>(a.n_pre)) continue;
         const int64_t b0 = a.indptr[i], b1 = a.indptr[i + 1];
         if (lane == 0) ev += b1 - b0;
-        scatter_any<Acc, WK, VECL>(a.indices, a.data, a.w_homo, b0, b1, lane, G, y, 0);
+        scatter_any<Acc, WK, VECL && WK != WK_F32>(a.indices, a.data, a.w_homo, b0, b1, lane, G, y, 0);
     }
     if (events_total) block_add_i64(ev, events_total);
 }
@@ -467,9 +620,9 @@ bp_status launch_scatter_t(const CsrArgs& a, const int32_t* spike_list, const in
         BP_LAUNCHED();
         return BP_OK;
     }
-    const size_t smem = static_cast<size_t>(W) * sizeof(Acc);
+    const size_t smem = static_cast<size_t>(W) * sizeof(Acc) + sizeof(FlatSmem);
     BP_TRY(ensure_smem_attr(reinterpret_cast<const void*>(k_csr_scatter<Acc, WK, VECL>),
-                            static_cast<int>(cap * sizeof(Acc))));
+                            static_cast<int>(cap * sizeof(Acc) + sizeof(FlatSmem))));
     // one 1024-thread CTA per SM: R row groups per tile so that S x R covers the SMs
     int64_t R = static_cast<int64_t>(sm_count()) / S;
     if (R < 1) R = 1;
@@ -485,14 +638,14 @@ bool aligned_to(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t
 template <typename Acc, int WK>
 bp_status launch_scatter_a(const CsrArgs& a, const int32_t* sl, const int32_t* ns, int64_t mx, void* y, int64_t* ev,
                            int mode, cudaStream_t s) {
-    // 16-byte index loads (aligned indices) pay off for homogeneous weights,
-    // whose events cost only the 4-byte index: with 4-byte loads too few bytes
-    // are in flight per SM.  BF16 weights take pairs (8-byte index and 4-byte
-    // weight loads: 3-9 % faster on the n = 1e6 cells, 27 % slower on the
-    // n = 1e5, p = 0.01, rho = 0.1 cell); FP32 weights stay scalar (both
-    // vector forms measured slower or mixed).
-    const bool vec = (WK == WK_HOMO && aligned_to(a.indices, 16)) ||
-                     (WK == WK_BF16 && aligned_to(a.indices, 8) && aligned_to(a.data, 4));
+    // Aligned operands: the tiled walk moves 16-byte chunks of indices (and
+    // of FP32 / 8-byte chunks of BF16 weights), reading the whole aligned
+    // chunks that hold a segment's first and last entries; the direct walk
+    // takes 16-byte index loads for homogeneous weights and pairs (8-byte
+    // index and 4-byte weight loads) for BF16 weights, and stays scalar for
+    // FP32 weights (its vector forms measured slower or mixed).
+    const bool vec = aligned_to(a.indices, 16) && (WK == WK_HOMO || (WK == WK_F32 && aligned_to(a.data, 16)) ||
+                                                   (WK == WK_BF16 && aligned_to(a.data, 8)));
     if (vec) return launch_scatter_t<Acc, WK, true>(a, sl, ns, mx, y, ev, mode, s);
     return launch_scatter_t<Acc, WK, false>(a, sl, ns, mx, y, ev, mode, s);
 }

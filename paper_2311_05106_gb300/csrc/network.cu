@@ -11,10 +11,13 @@
 // takes its spikes from a ring of per-step spike lists instead (the kernel
 // indexes it from the device step counter), so the accumulators keep their
 // two halves whatever the delay.  The optional spike-list counter alternates
-// between two slots the same way.  bp_simulate captures a chunk of steps once
-// in a CUDA graph and replays it; per-step indices that differ between
-// replays (the record row) are read from a small device control block.
+// between two slots the same way.  bp_simulate replays CUDA graphs of
+// captured steps: a 64-step chunk, and one graph per shorter remainder
+// length, each captured once (so a short call runs the same launch path as a
+// long one); per-step indices that differ between replays (the record row)
+// are read from a small device control block.
 #include <cmath>
+#include <map>
 #include <new>
 
 #include "bp_common.cuh"
@@ -26,7 +29,9 @@ struct bp_net {
     int64_t host_step;
     bp::NetCtrl* ctrl;  // device
     cudaStream_t cap_stream;
-    cudaGraphExec_t graph;
+    // captured graphs of `len` steps from an even step (the chunk, and the
+    // shorter remainders of bp_simulate calls), built on first use
+    std::map<int, cudaGraphExec_t>* graphs;
     int chunk;
 };
 
@@ -76,13 +81,19 @@ bp_status advance(bp_net* net, int64_t k, cudaStream_t s) {
     return BP_OK;
 }
 
-bp_status build_graph(bp_net* net) {
-    if (net->graph) return BP_OK;
+// Graph of `len` steps starting on an even step (counter slot 0), followed by
+// the advance of the device step counter; captured once per length and cached.
+bp_status get_graph(bp_net* net, int len, cudaGraphExec_t* out) {
+    auto it = net->graphs->find(len);
+    if (it != net->graphs->end()) {
+        *out = it->second;
+        return BP_OK;
+    }
     if (!net->cap_stream) BP_CUDA(cudaStreamCreateWithFlags(&net->cap_stream, cudaStreamNonBlocking));
     BP_CUDA(cudaStreamBeginCapture(net->cap_stream, cudaStreamCaptureModeThreadLocal));
     bp_status st = BP_OK;
-    for (int t = 0; t < net->chunk && st == BP_OK; ++t) st = enqueue_step(net, t & 1, t, net->cap_stream);
-    if (st == BP_OK) st = advance(net, net->chunk, net->cap_stream);
+    for (int t = 0; t < len && st == BP_OK; ++t) st = enqueue_step(net, t & 1, t, net->cap_stream);
+    if (st == BP_OK) st = advance(net, len, net->cap_stream);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(net->cap_stream, &g);
     if (st != BP_OK) {
@@ -93,13 +104,15 @@ bp_status build_graph(bp_net* net) {
         set_error("graph capture failed: %s", cudaGetErrorString(e));
         return BP_ERR_CUDA;
     }
-    e = cudaGraphInstantiate(&net->graph, g, 0);
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
-        net->graph = nullptr;
         set_error("graph instantiation failed: %s", cudaGetErrorString(e));
         return BP_ERR_CUDA;
     }
+    net->graphs->emplace(len, ex);
+    *out = ex;
     return BP_OK;
 }
 
@@ -187,10 +200,16 @@ bp_status bp_network_create(const bp_net_desc* desc, bp_net** out) {
     net->L = L;
     net->host_step = 0;
     net->chunk = bp::kChunk;
-    net->graph = nullptr;
+    net->graphs = new (std::nothrow) std::map<int, cudaGraphExec_t>();
     net->cap_stream = nullptr;
+    if (!net->graphs) {
+        delete net;
+        bp::set_error("host allocation failed");
+        return BP_ERR_OOM;
+    }
     cudaError_t e = cudaMalloc(&net->ctrl, sizeof(bp::NetCtrl));
     if (e != cudaSuccess) {
+        delete net->graphs;
         delete net;
         bp::set_error("cudaMalloc of the control block failed: %s", cudaGetErrorString(e));
         return BP_ERR_OOM;
@@ -199,6 +218,7 @@ bp_status bp_network_create(const bp_net_desc* desc, bp_net** out) {
     e = cudaMemset(net->ctrl, 0, sizeof(bp::NetCtrl));
     if (e != cudaSuccess) {
         cudaFree(net->ctrl);
+        delete net->graphs;
         delete net;
         bp::set_error("cudaMemset failed: %s", cudaGetErrorString(e));
         return BP_ERR_CUDA;
@@ -243,6 +263,22 @@ bp_status bp_network_step(bp_net* net, bp_stream_t stream) {
     return BP_OK;
 }
 
+bp_status bp_simulate_prepare(bp_net* net, int64_t T, bp_stream_t stream) {
+    bp::clear_error();
+    BP_REQUIRE(net, "net is NULL");
+    BP_REQUIRE(T >= 0, "T < 0");
+    // the lengths bp_simulate(T) would launch from either step parity
+    const int64_t lens[3] = {T >= net->chunk || T - 1 >= net->chunk ? net->chunk : 0, T % net->chunk,
+                             T > 0 ? (T - 1) % net->chunk : 0};
+    for (int64_t len : lens) {
+        if (len <= 0) continue;
+        cudaGraphExec_t g = nullptr;
+        BP_TRY(bp::get_graph(net, static_cast<int>(len), &g));
+        BP_CUDA(cudaGraphUpload(g, stream));
+    }
+    return BP_OK;
+}
+
 bp_status bp_simulate(bp_net* net, int64_t T, int32_t* record, bp_stream_t stream) {
     bp::clear_error();
     const bp::NvtxRange nvtx("bp_simulate");
@@ -262,16 +298,18 @@ bp_status bp_simulate(bp_net* net, int64_t T, int32_t* record, bp_stream_t strea
     }
     const int64_t chunks = (T - done) / net->chunk;
     if (chunks > 0) {
-        BP_TRY(bp::build_graph(net));
-        for (int64_t k = 0; k < chunks; ++k) BP_CUDA(cudaGraphLaunch(net->graph, stream));
+        cudaGraphExec_t g = nullptr;
+        BP_TRY(bp::get_graph(net, net->chunk, &g));
+        for (int64_t k = 0; k < chunks; ++k) BP_CUDA(cudaGraphLaunch(g, stream));
         net->host_step += chunks * net->chunk;
         done += chunks * net->chunk;
     }
+    // the remainder (host_step is even here) is one cached graph of its length
     const int64_t rem = T - done;
-    for (int64_t t = 0; t < rem; ++t)
-        BP_TRY(bp::enqueue_step(net, static_cast<int>((net->host_step + t) & 1), static_cast<int32_t>(t), stream));
     if (rem > 0) {
-        BP_TRY(bp::advance(net, rem, stream));
+        cudaGraphExec_t g = nullptr;
+        BP_TRY(bp::get_graph(net, static_cast<int>(rem), &g));
+        BP_CUDA(cudaGraphLaunch(g, stream));
         net->host_step += rem;
     }
     // detach the record so that later steps do not write into it
@@ -291,7 +329,10 @@ bp_status bp_network_stats(bp_net* net, double* out, bp_stream_t stream) {
 bp_status bp_network_destroy(bp_net* net) {
     bp::clear_error();
     if (!net) return BP_OK;
-    if (net->graph) cudaGraphExecDestroy(net->graph);
+    if (net->graphs) {
+        for (auto& kv : *net->graphs) cudaGraphExecDestroy(kv.second);
+        delete net->graphs;
+    }
     if (net->cap_stream) cudaStreamDestroy(net->cap_stream);
     if (net->ctrl) cudaFree(net->ctrl);
     delete net;

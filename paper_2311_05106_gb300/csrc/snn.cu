@@ -100,7 +100,7 @@ struct SnnK {
     float* ib_blk;       // [B][kDwBlock][n_rec]  Ibar of the steps of the current gradient block
     float* g_out;        // [B][n_rec][n_out]
     float* g_b;          // [B][n_out]
-    double* vreg;        // [B]  regulariser sums of the forward
+    float* vreg;         // [B]  regulariser sums of the forward
     int32_t stage_wout;  // the forward copies W_out into shared memory (it fits)
     unsigned long long* w_fix;  // [nnz] recurrent weights in fixed point (filled by the forward)
     int64_t nnz;
@@ -163,6 +163,21 @@ __device__ __forceinline__ int gather_inputs(const uint8_t* __restrict__ ut, int
     return *counter;
 }
 
+// Compensated (Kahan) FP32 running sum: s holds the sum, c the low-order
+// part lost so far; the result is s - c.  The regulariser's per-thread sums
+// use it so that FP32 keeps ~1e-7 relative accuracy over the T x n_rec terms
+// without FP64 arithmetic on the GPU.
+struct KahanF {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        const float y = x - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ float value() const { return s - c; }
+};
+
 // One step of the neuron state held in shared memory.  racc holds
 // W_rec^T z_{t-1} and is cleared.  Spikes are decided by the threshold, or,
 // when force_z is given, taken from those recorded bits (the backward pass
@@ -173,7 +188,7 @@ __device__ __forceinline__ int gather_inputs(const uint8_t* __restrict__ ut, int
 __device__ __forceinline__ void neuron_step(const SnnK& p, float* I, float* V, unsigned long long* racc,
                                             const int32_t* in_list,
                                             int n_act, int32_t* spk, int32_t* n_spk, float* Vp_out,
-                                            uint32_t* zbits, const uint32_t* force_z, double* reg) {
+                                            uint32_t* zbits, const uint32_t* force_z, KahanF* reg) {
     for (int jb = 0; jb < p.n_rec; jb += kSnnThreads) {
         const int j = jb + threadIdx.x;
         bool z = false;
@@ -198,7 +213,7 @@ __device__ __forceinline__ void neuron_step(const SnnK& p, float* I, float* V, u
             z = force_z ? ((force_z[j >> 5] >> (j & 31)) & 1u) != 0 : vp > p.V_th;
             V[j] = z ? p.V_reset : vp;
             if (Vp_out) Vp_out[j] = vp;
-            if (reg) *reg += static_cast<double>(penalty(p.sg, vp));
+            if (reg) reg->add(penalty(p.sg, vp));
         }
         const unsigned m = __ballot_sync(FULL_MASK, z);
         if ((threadIdx.x & 31) == 0) {
@@ -266,7 +281,7 @@ __global__ void __launch_bounds__(kSnnThreads, 1) k_snn_forward(SnnK p, const ui
         for (int e = threadIdx.x; e < p.n_rec * p.n_out; e += kSnnThreads) s_wout[e] = __ldg(p.W_out + e);
     const float* Wo = p.stage_wout ? s_wout : p.W_out;  // readout weights, shared or global
     if (threadIdx.x < p.n_out) s_y[threadIdx.x] = s_m[threadIdx.x] = 0.f;
-    double reg = 0.0;
+    KahanF reg;
     const int t_last0 = ((p.T - 1) / p.K) * p.K;  // first step of the last checkpoint segment
     __syncthreads();
     for (int t = 0; t < p.T; ++t) {
@@ -311,14 +326,14 @@ __global__ void __launch_bounds__(kSnnThreads, 1) k_snn_forward(SnnK p, const ui
     }
     if (threadIdx.x < p.n_out) m_out[static_cast<int64_t>(b) * p.n_out + threadIdx.x] = s_m[threadIdx.x] / p.T;
     if (p.sg.reg_on) {  // fixed reduction order: lanes by a tree, warps in index order
-        __shared__ double s_reg[kSnnThreads / 32];
-        reg = group_reduce_sum(reg, 32);
-        if ((threadIdx.x & 31) == 0) s_reg[threadIdx.x >> 5] = reg;
+        __shared__ float s_reg[kSnnThreads / 32];
+        const float v = group_reduce_sum(reg.value(), 32);
+        if ((threadIdx.x & 31) == 0) s_reg[threadIdx.x >> 5] = v;
         __syncthreads();
         if (threadIdx.x == 0) {
-            double acc = 0.0;
-            for (int w = 0; w < kSnnThreads / 32; ++w) acc += s_reg[w];
-            p.vreg[b] = acc;
+            KahanF acc;
+            for (int w = 0; w < kSnnThreads / 32; ++w) acc.add(s_reg[w]);
+            p.vreg[b] = acc.value();
         }
     }
 }
@@ -531,36 +546,46 @@ __global__ void k_lif_step_bwd(int64_t n, float a_m, float a_s, float R, float V
     }
 }
 
-// Mean cross-entropy of softmax(m) over the batch and its gradient.
+// Mean cross-entropy of softmax(m) over the batch and its gradient, in FP32:
+// one thread per batch element (max-subtracted log-sum-exp over the outputs
+// in index order), the per-element terms added in batch order with a
+// compensated sum, so the loss is reproducible and accurate to ~1e-7.
 __global__ void k_snn_loss(int32_t B, int32_t n_out, const float* __restrict__ m, const int64_t* __restrict__ labels,
                            float* __restrict__ loss, float* __restrict__ g_m) {
-    __shared__ double s_sum;
-    if (threadIdx.x == 0) s_sum = 0.0;
-    __syncthreads();
-    for (int b = threadIdx.x; b < B; b += blockDim.x) {
-        const float* mb = m + static_cast<int64_t>(b) * n_out;
-        double mx = mb[0];
-        for (int o = 1; o < n_out; ++o) mx = fmax(mx, static_cast<double>(mb[o]));
-        double se = 0.0;
-        for (int o = 0; o < n_out; ++o) se += exp(static_cast<double>(mb[o]) - mx);
-        const int64_t lab = labels[b];
-        const double lse = log(se) + mx;
-        atomicAdd(&s_sum, lse - mb[lab]);
-        for (int o = 0; o < n_out; ++o) {
-            const double sm = exp(static_cast<double>(mb[o]) - mx) / se;
-            g_m[static_cast<int64_t>(b) * n_out + o] = static_cast<float>((sm - (o == lab ? 1.0 : 0.0)) / B);
+    __shared__ float s_term[256];
+    KahanF total;
+    for (int b0 = 0; b0 < B; b0 += blockDim.x) {
+        const int b = b0 + threadIdx.x;
+        float term = 0.f;
+        if (b < B) {
+            const float* mb = m + static_cast<int64_t>(b) * n_out;
+            float mx = mb[0];
+            for (int o = 1; o < n_out; ++o) mx = fmaxf(mx, mb[o]);
+            float se = 0.f;
+            for (int o = 0; o < n_out; ++o) se += expf(mb[o] - mx);
+            const int64_t lab = labels[b];
+            term = (logf(se) + mx) - mb[lab];
+            const float inv = 1.f / se;
+            for (int o = 0; o < n_out; ++o) {
+                const float sm = expf(mb[o] - mx) * inv;
+                g_m[static_cast<int64_t>(b) * n_out + o] = (sm - (o == lab ? 1.f : 0.f)) / static_cast<float>(B);
+            }
         }
+        s_term[threadIdx.x] = term;
+        __syncthreads();
+        if (threadIdx.x == 0)
+            for (int k = 0; k < static_cast<int>(blockDim.x) && b0 + k < B; ++k) total.add(s_term[k]);
+        __syncthreads();
     }
-    __syncthreads();
-    if (threadIdx.x == 0) *loss = static_cast<float>(s_sum / B);
+    if (threadIdx.x == 0) *loss = total.value() / static_cast<float>(B);
 }
 
-// loss[0] += scale * sum_b vreg[b], in batch order, in FP64.
-__global__ void k_snn_reg_add(int32_t B, double scale, const double* __restrict__ vreg, float* __restrict__ loss) {
+// loss[0] += scale * sum_b vreg[b], the sum in batch order (compensated FP32).
+__global__ void k_snn_reg_add(int32_t B, float scale, const float* __restrict__ vreg, float* __restrict__ loss) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double acc = 0.0;
-    for (int b = 0; b < B; ++b) acc += vreg[b];
-    loss[0] = static_cast<float>(static_cast<double>(loss[0]) + scale * acc);
+    KahanF acc;
+    for (int b = 0; b < B; ++b) acc.add(vreg[b]);
+    loss[0] = loss[0] + scale * acc.value();
 }
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -588,7 +613,7 @@ SnnLayout snn_layout(const bp_snn_desc& d) {
     L.ib_blk = o; o = align256(o + B * static_cast<size_t>(kDwBlock) * d.n_rec * 4);
     L.g_out = o; o = align256(o + B * static_cast<size_t>(d.n_rec) * d.n_out * 4);
     L.g_b = o; o = align256(o + B * static_cast<size_t>(d.n_out) * 4);
-    L.vreg = o; o = align256(o + B * 8);
+    L.vreg = o; o = align256(o + B * 4);
     L.w_fix = o; o = align256(o + static_cast<size_t>(d.nnz > 0 ? d.nnz : 0) * 8);
     L.total = o;
     return L;
@@ -667,7 +692,7 @@ SnnK snn_kernel_args(const bp_snn_desc& d, void* ws) {
     p.ib_blk = reinterpret_cast<float*>(w + L.ib_blk);
     p.g_out = reinterpret_cast<float*>(w + L.g_out);
     p.g_b = reinterpret_cast<float*>(w + L.g_b);
-    p.vreg = reinterpret_cast<double*>(w + L.vreg);
+    p.vreg = reinterpret_cast<float*>(w + L.vreg);
     p.w_fix = reinterpret_cast<unsigned long long*>(w + L.w_fix);
     p.nnz = d.nnz;
     p.n_ck = L.n_ck;
@@ -786,8 +811,8 @@ bp_status bp_snn_reg_loss(const bp_snn_desc* d, const void* workspace, float* lo
     BP_REQUIRE((reinterpret_cast<uintptr_t>(workspace) & 255) == 0, "workspace must be 256-byte aligned");
     if (d->lambda_v == 0) return BP_OK;
     const bp::SnnLayout L = bp::snn_layout(*d);
-    const double* vreg = reinterpret_cast<const double*>(static_cast<const char*>(workspace) + L.vreg);
-    bp::k_snn_reg_add<<<1, 32, 0, stream>>>(d->B, d->lambda_v / d->B, vreg, loss);
+    const float* vreg = reinterpret_cast<const float*>(static_cast<const char*>(workspace) + L.vreg);
+    bp::k_snn_reg_add<<<1, 32, 0, stream>>>(d->B, static_cast<float>(d->lambda_v / d->B), vreg, loss);
     BP_LAUNCHED();
     return BP_OK;
 }

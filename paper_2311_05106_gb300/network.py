@@ -187,6 +187,10 @@ class CobaNetwork:
     def simulate(self, T, record=None):
         B.bp_simulate(self.handle, T, record)
 
+    def prepare(self, T):
+        """Captures and uploads the CUDA graphs a T-step simulate launches."""
+        B.bp_simulate_prepare(self.handle, T)
+
     def stats(self):
         out = torch.zeros(4, dtype=torch.float64, device=self.device)
         B.bp_network_stats(self.handle, out)
@@ -204,13 +208,34 @@ class CobaNetwork:
             pass
 
 
-class BatchedNetworks:
-    """Many independent COBA E/I networks (sizes `sizes`, seeds `seeds`, JIT
-    connectivity with p = 80/n by default) advanced together by the batched
-    persistent kernel.  State is concatenated; ``view(b)`` returns network b's
-    slice of a state array."""
+def batch_csr(sizes, seeds, off, p=None, device="cuda"):
+    """Stored rows of a batch: each network's JIT connectivity materialised
+    (as materialize_network_csr does for one network) and laid out as one CSR
+    over the padded concatenated layout, with targets local to each network;
+    padding rows are empty."""
+    total = int(off[-1])
+    lens = torch.zeros(total, dtype=torch.int64, device=device)
+    parts = []
+    for b, n in enumerate(sizes):
+        n = int(n)
+        pb = 80.0 / n if p is None else float(p[b])
+        ip, ix, _ = materialize_network_csr(int(seeds[b]), pb, n, (4 * n) // 5, device=device)
+        lens[int(off[b]):int(off[b]) + n] = ip[1:] - ip[:-1]
+        parts.append(ix)
+    indptr = torch.zeros(total + 1, dtype=torch.int64, device=device)
+    torch.cumsum(lens, 0, out=indptr[1:])
+    return indptr, torch.cat(parts)
 
-    def __init__(self, sizes, seeds, V0=None, p=None, params=None, device="cuda"):
+
+class BatchedNetworks:
+    """Many independent COBA E/I networks (sizes `sizes`, seeds `seeds`,
+    connection probability p = 80/n by default) advanced together by the
+    batched persistent kernel, with JIT rows (conn="jit") or the same rows
+    stored (conn="csr"; `csr` = (indptr, indices) over the padded layout,
+    default: batch_csr of the seeds).  State is concatenated; ``view(b)``
+    returns network b's slice of a state array."""
+
+    def __init__(self, sizes, seeds, V0=None, p=None, params=None, conn="jit", csr=None, device="cuda"):
         _require_cuda(device)
         sizes = np.ascontiguousarray(sizes, dtype=np.int64)
         if len(seeds) != len(sizes) or (p is not None and len(p) != len(sizes)):
@@ -242,8 +267,28 @@ class BatchedNetworks:
         d.coba = self.params
         d.V, d.ge, d.gi, d.ref = (t.data_ptr() for t in (self.V, self.ge, self.gi, self.ref))
         d.totals = self.totals.data_ptr()
+        if conn not in ("jit", "csr"):
+            raise ValueError("conn must be 'jit' or 'csr'")
+        self.indptr = self.indices = None
+        if conn == "csr":
+            if csr is None:
+                csr = batch_csr(sizes, self.seeds, self.off, self._p, device=device)
+            self.indptr, self.indices = csr
+            for name, t, dt in (("indptr", self.indptr, torch.int64), ("indices", self.indices, torch.int32)):
+                if not isinstance(t, torch.Tensor) or not t.is_cuda or not t.is_contiguous() or t.dtype != dt:
+                    raise ValueError("csr %s must be a contiguous CUDA %s tensor" % (name, dt))
+            if self.indptr.numel() != total + 1:
+                raise ValueError("csr indptr must have padded_total + 1 = %d entries" % (total + 1))
+            if int(self.indptr[-1].item()) > self.indices.numel():
+                raise ValueError("csr indices hold fewer entries than indptr[-1]")
+            d.indptr, d.indices = self.indptr.data_ptr(), self.indices.data_ptr()
         self.desc = d
         self.handle = B.bp_batch_create(d)
+
+    @staticmethod
+    def layout(sizes):
+        """Offsets of the padded concatenated layout (numpy int64 [n + 1])."""
+        return B.bp_batch_layout(np.ascontiguousarray(sizes, dtype=np.int64))
 
     def view(self, t, b):
         return t[int(self.off[b]):int(self.off[b]) + int(self.sizes[b])]
@@ -254,8 +299,19 @@ class BatchedNetworks:
     def simulate(self, T):
         B.bp_batch_simulate(self.handle, T)
 
+    def prepare(self, T):
+        """Captures and uploads the CUDA graph of a T-step simulate."""
+        B.bp_batch_prepare(self.handle, T)
+
     def autotune(self, probe_steps=20):
         return B.bp_batch_autotune(self.handle, probe_steps)
+
+    def tuning(self):
+        """(threads, lanes_per_row, ctas_per_sm, stored_rows)."""
+        return B.bp_batch_tuning(self.handle)
+
+    def set_tuning(self, threads, lanes_per_row, ctas_per_sm):
+        B.bp_batch_set_tuning(self.handle, threads, lanes_per_row, ctas_per_sm)
 
     def info(self):
         return B.bp_batch_info(self.handle)

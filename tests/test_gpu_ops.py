@@ -211,7 +211,7 @@ def test_event_csrmv_dense_events():
 
 
 def test_tile_index_matches_searchsorted():
-    n_pre, n_post, tc = 3000, 200000, 57344
+    n_pre, n_post, tc = 3000, 200000, B.bp_tile_cols()
     ip, ix = _csr(n_pre, n_post, 0.002, seed=9)
     tp = torch.empty(B.bp_csr_tile_index_size(n_pre, n_post, tc), dtype=torch.int32, device="cuda")
     B.bp_csr_tile_index(cuda(ip), cuda(ix), n_post, tc, tp)
@@ -505,3 +505,85 @@ def test_csr_check_counts_defects():
     bip[n_pre] = len(ix) + 100                                       # last row runs past the buffer
     B.bp_csr_check(cuda(bip), cuda(ix), n_post, out)
     assert out.cpu().tolist()[0] == 2                                # its extent, and indptr[n_pre] != nnz
+
+
+@pytest.mark.parametrize("case", [
+    # n_pre, n_post, p, rho: very short rows (most (row, tile) segments empty),
+    # dense rows (segments of a whole tile), and a single tile
+    (20000, 200000, 0.00005, 0.5),
+    (64, 120000, 1.0, 0.5),
+    (3000, 40000, 0.05, 0.9),
+])
+def test_tiled_scatter_segment_shapes(case):
+    """The tiled scatter lays each batch's (row, tile) segments end to end and
+    streams them: counts equal the oracle's bit for bit whatever the segment
+    lengths (empty, a whole tile, whole rows), and FP32 weights within 1e-5."""
+    n_pre, n_post, p, rho = case
+    ip, ix = _csr(n_pre, n_post, p, seed=n_pre + 3)
+    ev = wl.bernoulli_spikes(n_pre, rho, seed=n_pre + 4)
+    dip, dix = cuda(ip), cuda(ix)
+    tc = B.bp_tile_cols() if n_post > B.bp_tile_cols() else 0
+    tp = None
+    if tc:
+        tp = torch.empty(B.bp_csr_tile_index_size(n_pre, n_post, tc), dtype=torch.int32, device="cuda")
+        B.bp_csr_tile_index(dip, dix, n_post, tc, tp)
+    sl, ns = spike_list_of(ev)
+    y = torch.zeros(n_post, dtype=torch.int32, device="cuda")
+    B.bp_event_csrmv(dip, dix, None, 1.0, sl, ns, y, tile_ptr=tp, tile_cols=tc, flags=B.BP_ACC_SHARED)
+    assert np.array_equal(y.cpu().numpy(), orc.event_csr_count(ip, ix, ev, n_post))
+    w = wl.normal_weights(len(ix), 0.5, 0.1, seed=8)
+    yf = torch.zeros(n_post, dtype=torch.float32, device="cuda")
+    B.bp_event_csrmv(dip, dix, cuda(w), 0.0, sl, ns, yf, tile_ptr=tp, tile_cols=tc, flags=B.BP_ACC_SHARED)
+    assert rel_err(yf.cpu().numpy(), orc.event_csrmv(ip, ix, w.astype(np.float64), ev, n_post)) < RTOL_F32
+
+
+def test_tiled_scatter_repeated_columns():
+    """Sorted rows with repeated columns (a column may be hit several times by
+    one row): every repetition is an event, counted exactly."""
+    n_pre, n_post = 4000, 130000
+    rng = np.random.default_rng(12)
+    lens = rng.integers(0, 300, n_pre)
+    ip = np.zeros(n_pre + 1, np.int64)
+    np.cumsum(lens, out=ip[1:])
+    ix = np.concatenate([np.sort(rng.integers(0, n_post, int(k))) for k in lens]).astype(np.int32)
+    ix = np.repeat(ix, 2)                     # every entry twice, rows still sorted
+    ip = ip * 2
+    ev = wl.bernoulli_spikes(n_pre, 0.4, seed=13)
+    dip, dix = cuda(ip), cuda(ix)
+    tc = B.bp_tile_cols()
+    tp = torch.empty(B.bp_csr_tile_index_size(n_pre, n_post, tc), dtype=torch.int32, device="cuda")
+    B.bp_csr_tile_index(dip, dix, n_post, tc, tp)
+    sl, ns = spike_list_of(ev)
+    y = torch.zeros(n_post, dtype=torch.int32, device="cuda")
+    B.bp_event_csrmv(dip, dix, None, 1.0, sl, ns, y, tile_ptr=tp, tile_cols=tc, flags=B.BP_ACC_SHARED)
+    assert np.array_equal(y.cpu().numpy(), orc.event_csr_count(ip, ix, ev, n_post))
+
+
+def test_tiled_scatter_segments_beyond_the_flat_list():
+    """Rows whose tile segments are far longer than a tile without repeated
+    columns allows (1030 rows of 2.205e6 entries, every column of [0, 52 500)
+    repeated 42 times, n_post = 9e6 so that each tile has a single CTA, 1009
+    rows spiking): each warp's 32 segments exceed the flat list's limit, so
+    they are walked segment by segment, and every column receives exactly 42
+    events per spiking row, the other columns none (2.2e9 events in all)."""
+    n_pre, n_post, per_row, rep = 1030, 9_000_000, 2_205_000, 42
+    row = (torch.arange(per_row, dtype=torch.int64, device="cuda") // rep).to(torch.int32)
+    ix = row.repeat(n_pre)
+    ip = torch.arange(n_pre + 1, dtype=torch.int64, device="cuda") * per_row
+    del row
+    tc = B.bp_tile_cols()
+    tp = torch.empty(B.bp_csr_tile_index_size(n_pre, n_post, tc), dtype=torch.int32, device="cuda")
+    B.bp_csr_tile_index(ip, ix, n_post, tc, tp)
+    ev = np.ones(n_pre, np.uint8)
+    ev[::50] = 0
+    sl, ns = spike_list_of(ev)
+    y = torch.zeros(n_post, dtype=torch.int32, device="cuda")
+    B.bp_event_csrmv(ip, ix, None, 1.0, sl, ns, y, tile_ptr=tp, tile_cols=tc, flags=B.BP_ACC_SHARED)
+    torch.cuda.synchronize()
+    k = int(ev.sum())
+    assert k <= 1024 and k * per_row > 2**31
+    cols = per_row // rep
+    assert torch.all(y[:cols] == k * rep).item()
+    assert int(y[cols:].abs().sum().item()) == 0
+    del ix, tp
+    torch.cuda.empty_cache()
