@@ -587,3 +587,23 @@ def test_tiled_scatter_segments_beyond_the_flat_list():
     assert int(y[cols:].abs().sum().item()) == 0
     del ix, tp
     torch.cuda.empty_cache()
+
+
+def test_tiled_counts_accumulate_into_negative_outputs():
+    """Integer counts added to an output that holds negative values (the
+    tile flush adds column pairs as one 64-bit number only when the pair's
+    first word is not negative): y0 + counts bit for bit, with odd n_post."""
+    n_pre, n_post = 6000, 150001
+    ip, ix = _csr(n_pre, n_post, 0.003, seed=71)
+    ev = wl.bernoulli_spikes(n_pre, 0.3, seed=72)
+    dip, dix = cuda(ip), cuda(ix)
+    tc = B.bp_tile_cols()
+    tp = torch.empty(B.bp_csr_tile_index_size(n_pre, n_post, tc), dtype=torch.int32, device="cuda")
+    B.bp_csr_tile_index(dip, dix, n_post, tc, tp)
+    sl, ns = spike_list_of(ev)
+    y0 = np.random.default_rng(73).integers(-5, 6, n_post).astype(np.int32)
+    y = torch.from_numpy(y0).cuda()
+    B.bp_event_csrmv(dip, dix, None, 1.0, sl, ns, y, tile_ptr=tp, tile_cols=tc, flags=B.BP_ACC_SHARED)
+    expect = y0.astype(np.int64) + orc.event_csr_count(ip, ix, ev, n_post)
+    assert np.array_equal(y.cpu().numpy().astype(np.int64), expect)
+    assert (y0 < 0).sum() > 10000
