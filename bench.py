@@ -792,8 +792,11 @@ def sweep_cells(torch, sizes, probs, rhos, wsel, ops, cells=None, tile_cols=None
                     if "jit" not in ops:
                         continue
                     ms = device_timer(torch, lambda: B.bp_jitconn_event_mv(d, n, sl, ns, y), 5)
+                    # targets accumulate in shared memory when y fits a tile, else
+                    # with scattered L2 reductions, which then bound the operator
                     yield dict(op="jitconn_event_mv", n=n, p=p, rho=rho, weights=wname, us=ms * 1e3,
-                               spikes=n_spk, events=ev_jit, events_per_s=ev_jit / (ms * 1e-3), bound="alu")
+                               spikes=n_spk, events=ev_jit, events_per_s=ev_jit / (ms * 1e-3),
+                               bound="alu" if n <= B.bp_tile_cols() else "l2_red")
                 del events, sl, ns, yc, yf, yy
             del ip, ix, w32, w16, tp
             torch.cuda.empty_cache()
@@ -853,9 +856,9 @@ def bench_operator_cells(torch, roofs):
             c["roof"] = "philox" if roofs["philox_words_per_s"] <= roofs["l2_red_per_s_1e6_targets"] else "l2_red"
             c["frac_roof"] = c["events_per_s"] / roof
         out.append(c)
-    # JIT rows into n_post = 1e4 accumulators (shared memory): no L2
+    # JIT rows into n_post = 5e4 accumulators (one shared-memory tile): no L2
     # reductions, so the Philox-only draw rate is the roof (one draw per event)
-    for c in sweep_cells(torch, [10_000], [0.1], [0.1], ["homo"], ["jit"]):
+    for c in sweep_cells(torch, [50_000], [0.1], [0.1], ["homo"], ["jit"]):
         c["roof_events_per_s"] = roofs["philox_words_per_s"]
         c["roof"] = "philox"
         c["frac_roof"] = c["events_per_s"] / roofs["philox_words_per_s"]

@@ -193,6 +193,10 @@ __global__ void __launch_bounds__(kStepThreads, 4) k_step(StepArgs a) {
                 asm volatile("prefetch.global.L2 [%0];" ::"l"(a.csr.indices + j));
                 if constexpr (WK == WK_F32)
                     asm volatile("prefetch.global.L2 [%0];" ::"l"(static_cast<const float*>(a.csr.data) + j));
+                // BF16 weights: a 128-byte line holds 64 entries
+                if constexpr (WK == WK_BF16)
+                    if ((j & 63) == 0 || j == (b0 & ~int64_t(31)))
+                        asm volatile("prefetch.global.L2 [%0];" ::"l"(static_cast<const __nv_bfloat16*>(a.csr.data) + j));
             }
         }
     }
