@@ -628,6 +628,23 @@ bp_status bp_snn_loss(int32_t B, int32_t n_out, const float* m, const int64_t* l
  * result is reproducible).  Does nothing when lambda_v = 0. */
 bp_status bp_snn_reg_loss(const bp_snn_desc* d, const void* workspace, float* loss, bp_stream_t stream);
 
+/* Weight gradient of a spike-driven dense connection (Section 3.1: for
+ * y_k = W^T x_k with binary x_k the reverse-mode rule gives
+ * dW = sum_k x_k dy_k^T):
+ *   out[m][n] += sum_{k < K} [x[k][m] != 0] delta[k][n]
+ * x uint8 [K][M] (row-major; any non-zero byte is a spike), delta float
+ * [K][N], out float [M][N] (BP_OVERWRITE: out = the sum).  Computed on the
+ * tensor cores (tcgen05 BF16 MMAs, FP32 accumulation): delta enters as two
+ * BF16 terms, hi = bf16(delta) and lo = bf16(delta - hi), so each product
+ * is exact to 2^-17 relative and the sum is FP32.  The same inputs give the
+ * same result bit for bit.  work: device workspace of at least
+ * bp_spike_outer_workspace(K, M, N) bytes, 1024-byte aligned, owned by the
+ * caller (the call packs both operands into it).  K <= 2^31 - 1.  K, M or N
+ * zero: nothing to add (BP_OVERWRITE still zeroes out). */
+size_t bp_spike_outer_workspace(int64_t K, int32_t M, int32_t N);
+bp_status bp_spike_outer(const uint8_t* x, const float* delta, int64_t K, int32_t M, int32_t N, float* out,
+                         uint32_t flags, void* work, size_t work_bytes, bp_stream_t stream);
+
 /* Backward pass (BPTT with checkpointed recomputation) for an upstream
  * gradient g_m = dL/dm [B][n_out], after bp_snn_forward with the same desc,
  * inputs and workspace.  ACCUMULATES dW_in [n_in][n_rec], dw_rec [nnz] (one

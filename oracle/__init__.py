@@ -230,6 +230,15 @@ def event_csrmv_dw(indptr, indices, events, delta):
     return dw
 
 
+def spike_outer(x, delta):
+    """Weight gradient of a spike-driven dense connection (Section 3.1: the
+    reverse-mode rule of y_k = W^T x_k with binary x_k is dW = sum_k x_k dy_k^T):
+    out[m][n] = sum_k [x[k][m] != 0] delta[k][n], in FP64 (x [K][M], delta
+    [K][N])."""
+    xb = (np.asarray(x) != 0).astype(np.float64)
+    return xb.T @ np.asarray(delta, np.float64)
+
+
 # --------------------------------------------------------------------------- COBA network
 COBA_DEFAULTS = dict(dt=0.1, tau_m=20.0, tau_e=5.0, tau_i=10.0, V_rest=-60.0, V_th=-50.0, V_reset=-60.0,
                      E_e=0.0, E_i=-80.0, R=1.0, I_ext=20.0, w_e=0.6, w_i=6.7, tau_ref=5.0)

@@ -140,6 +140,8 @@ _SIGS = {
     "bp_snn_reg_loss": (c_i32, [ctypes.POINTER(SnnDesc), VP, VP, VP]),
     "bp_lif_step_bwd": (c_i32, [ctypes.POINTER(SnnDesc), c_i64, VP, VP, VP, VP, VP, VP, VP, VP]),
     "bp_snn_backward": (c_i32, [ctypes.POINTER(SnnDesc), VP, VP, VP, VP, VP, VP, VP, VP]),
+    "bp_spike_outer_workspace": (ctypes.c_size_t, [c_i64, c_i32, c_i32]),
+    "bp_spike_outer": (c_i32, [VP, VP, c_i64, c_i32, c_i32, VP, c_u32, VP, ctypes.c_size_t, VP]),
 }
 
 _lock = threading.Lock()
@@ -530,6 +532,38 @@ def bp_snn_backward(desc, u, g_m, workspace, dW_in, dw_rec, dW_out, db_out, stre
 def bp_lif_step_bwd(desc, Vp, z, Vbar, zbar, Ibar_next, Ibar, Vbar_prev, stream=None):
     _check("bp_lif_step_bwd", lib().bp_lif_step_bwd(ctypes.byref(desc), Vp.numel(), _p(Vp), _p(z), _p(Vbar), _p(zbar),
                                                     _p(Ibar_next), _p(Ibar), _p(Vbar_prev), _stream(stream)))
+
+
+def bp_spike_outer_workspace(K, M, N) -> int:
+    return int(lib().bp_spike_outer_workspace(int(K), int(M), int(N)))
+
+
+def spike_outer_workspace(K, M, N, device="cuda"):
+    """A 1024-byte aligned uint8 workspace tensor for bp_spike_outer (a view
+    into a slightly larger allocation)."""
+    nbytes = bp_spike_outer_workspace(K, M, N)
+    raw = torch.empty(nbytes + 1024, dtype=torch.uint8, device=device)
+    off = (-raw.data_ptr()) % 1024
+    return raw[off:off + nbytes]
+
+
+def bp_spike_outer(x, delta, out, overwrite=False, work=None, stream=None):
+    """out[m][n] (+)= sum_k [x[k][m] != 0] delta[k][n]; x uint8 [K][M], delta
+    float32 [K][N], out float32 [M][N] (all contiguous, on the device)."""
+    K, M = x.shape
+    K2, N = delta.shape
+    if K2 != K or tuple(out.shape) != (M, N):
+        raise ValueError("shapes: x [K][M], delta [K][N], out [M][N]")
+    if x.dtype != torch.uint8 or delta.dtype != torch.float32 or out.dtype != torch.float32:
+        raise ValueError("x uint8, delta and out float32")
+    if not (x.is_contiguous() and delta.is_contiguous() and out.is_contiguous()):
+        raise ValueError("x, delta and out must be contiguous")
+    if work is None:
+        work = spike_outer_workspace(K, M, N, device=out.device)
+    nbytes = work.numel() * work.element_size()
+    _check("bp_spike_outer", lib().bp_spike_outer(_p(x), _p(delta), int(K), int(M), int(N), _p(out),
+                                                  BP_OVERWRITE if overwrite else 0, _p(work), nbytes,
+                                                  _stream(stream)))
 
 
 # ------------------------------------------------------------------ measurement kernels

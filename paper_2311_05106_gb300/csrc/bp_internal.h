@@ -119,6 +119,17 @@ bp_status launch_event_csrmv(const CsrArgs& a, const int32_t* spike_list, const 
                              int64_t max_spikes, void* y, bool counts, int64_t* events_total, int mode,
                              cudaStream_t s);
 
+// ---- tcgemm.cu
+// G[s][a] (+)= sum_{b < B, t < T} X_bt[s] D_bt[a] on the tensor cores: D float
+// [B][T][na]; X_bt[s] = x_dense[b][t][s] != 0 for s < n_dense, bit s - n_dense
+// of z_bits[b][t - 1] (zw words per step, zero at t = 0) for the next n_bits
+// features.  G row stride ldg.  work >= tc_spike_gemm_workspace(B, T, na,
+// n_dense + n_bits) bytes, 1024-byte aligned.
+size_t tc_spike_gemm_workspace(int32_t B, int32_t T, int32_t na, int32_t ns);
+bp_status launch_tc_spike_gemm(int32_t B, int32_t T, const float* d, int32_t na, const uint8_t* x_dense,
+                               int32_t n_dense, const uint32_t* z_bits, int32_t n_bits, int32_t zw, float* g,
+                               int64_t ldg, bool accumulate, void* work, size_t work_bytes, cudaStream_t st);
+
 // ---- jitconn.cu
 // Scatter of JIT rows (row id = spike id) into y.
 bp_status launch_jit_event_mv(const JitArgs& d, int64_t n_post, const int32_t* spike_list, const int32_t* n_spikes,

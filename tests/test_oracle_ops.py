@@ -106,3 +106,31 @@ def test_jit_products_equal_materialised_csr(wkind, w0, w1):
     x_post = np.random.default_rng(8).normal(size=n_post)
     np.testing.assert_allclose(orc.jitconn_mv_t(41, K, n_pre, n_post, x_post, wkind, w0, w1), W @ x_post,
                                rtol=1e-12, atol=1e-12)
+
+
+def test_spike_outer_brute_force_and_special_cases():
+    """The spike-driven weight gradient out[m][n] = sum_k [x_km != 0] delta_kn
+    (Section 3.1's reverse-mode rule of y = W^T x with binary x): brute force on
+    a tiny case; all-ones x gives the column sums of delta in every row; a
+    single spike at (k, m) copies delta's row k into row m (so a transposed
+    operand or a swapped index fails); byte values other than 1 count as one
+    spike."""
+    rng = np.random.default_rng(3)
+    K, M, N = 7, 5, 4
+    x = (rng.random((K, M)) < 0.4).astype(np.uint8) * rng.integers(1, 255, size=(K, M)).astype(np.uint8)
+    d = rng.standard_normal((K, N))
+    want = np.zeros((M, N))
+    for k in range(K):
+        for m in range(M):
+            if x[k, m]:
+                for n in range(N):
+                    want[m, n] += d[k, n]
+    np.testing.assert_allclose(orc.spike_outer(x, d), want, rtol=0, atol=1e-12)
+    ones = np.ones((K, M), np.uint8)
+    np.testing.assert_allclose(orc.spike_outer(ones, d), np.tile(d.sum(axis=0), (M, 1)), rtol=1e-14)
+    one = np.zeros((K, M), np.uint8)
+    one[4, 2] = 1
+    g = orc.spike_outer(one, d)
+    np.testing.assert_array_equal(g[2], d[4])
+    assert np.count_nonzero(np.delete(g, 2, axis=0)) == 0
+    assert orc.spike_outer(np.zeros((0, M), np.uint8), np.zeros((0, N))).shape == (M, N)
