@@ -589,10 +589,12 @@ bp_status bp_snn_desc_default(bp_snn_desc* d);
 
 /* Device workspace (bytes, 256-byte aligned) shared by forward and backward:
  * checkpoints, the recorded spike bits of every step, one segment of
- * potentials, the gradient partials of each batch element (summed over the
- * batch in a fixed order, so gradients are reproducible bit for bit) and the
- * recurrent weights in the fixed-point form the forward delivers them in.  0
- * for an invalid desc. */
+ * potentials, Ibar of every step with the operands of the weight-gradient
+ * contraction (dW_in and dw_rec are one tensor-core contraction over batch
+ * and time, as bp_spike_outer computes it), the readout-gradient partials of
+ * each batch element (summed over the batch in a fixed order) and the
+ * recurrent weights in the fixed-point form the forward delivers them in.
+ * Every gradient is reproducible bit for bit.  0 for an invalid desc. */
 size_t bp_snn_workspace_bytes(const bp_snn_desc* d);
 
 /* Forward pass over T steps: u uint8 [B][T][n_in] (input spikes), m float

@@ -33,9 +33,14 @@
 // with a single segment, the whole run) is not recomputed.  The
 // recurrent weights are converted to fixed point once per forward call
 // (k_snn_fix_weights), so delivering an event is one integer atomic.
-// Recurrent weights are FP32 or BF16 (FP32 arithmetic); gradients are FP32,
-// accumulated per batch element and then summed over the batch in a fixed
-// order (k_snn_reduce), so they are reproducible bit for bit.
+// Recurrent weights are FP32 or BF16 (FP32 arithmetic).  The adjoint stores
+// Ibar_t of every step; the input and recurrent weight gradients are then one
+// dense contraction over batch and time on the tensor cores,
+//   G = [u_t ; z_{t-1}]^T Ibar_t  summed over (b, t)      (tcgemm.cu),
+// whose first n_in rows are dW_in and whose recurrent rows, read at the
+// stored entries, are dw_rec (k_snn_grad_scatter).  dW_out and db are kept
+// per batch element and summed over the batch in a fixed order
+// (k_snn_reduce).  Every gradient is reproducible bit for bit.
 #include <cmath>
 
 #include "bp_common.cuh"
@@ -48,11 +53,6 @@ constexpr int kSnnThreads = 1024;
 constexpr int kSnnMaxRec = 4096;
 constexpr int kSnnMaxIn = 4096;
 constexpr int kSnnMaxOut = 64;
-// The recurrent-weight gradient is summed over blocks of kDwBlock steps
-// (aligned to absolute time, so the grouping does not depend on the
-// checkpoint interval): Ibar of the block's steps is kept, and when the block
-// is complete every entry adds its block sum once.
-constexpr int kDwBlock = 32;
 
 // Surrogate derivative and voltage-regulariser constants.
 struct SgK {
@@ -95,10 +95,8 @@ struct SnnK {
     float* ck_y;         // [B][n_ck][n_out]
     uint32_t* z_all;     // [B][T][zw]  spike bits of every step (recorded by the forward)
     float* seg_Vp;       // [B][K][n_rec]
-    float* g_in;         // [B][n_in][n_rec]   per-batch-element gradient partials
-    float* g_rec;        // [B][nnz]
-    float* ib_blk;       // [B][kDwBlock][n_rec]  Ibar of the steps of the current gradient block
-    float* g_out;        // [B][n_rec][n_out]
+    float* ib_all;       // [B][T][n_rec]  Ibar_t of every step (input of the weight-gradient contraction)
+    float* g_out;        // [B][n_rec][n_out]  per-batch-element gradient partials
     float* g_b;          // [B][n_out]
     float* vreg;         // [B]  regulariser sums of the forward
     int32_t stage_wout;  // the forward copies W_out into shared memory (it fits)
@@ -345,23 +343,19 @@ __global__ void __launch_bounds__(kSnnThreads, 1) k_snn_backward(SnnK p, const u
     unsigned long long* racc = reinterpret_cast<unsigned long long*>(sh);
     float* I = reinterpret_cast<float*>(racc + p.n_rec);  // recompute state
     float* V = I + p.n_rec;
-    float* Ib_next = V + p.n_rec;     // Ibar_{t+1}
-    float* Ib = Ib_next + p.n_rec;    // Ibar_t
-    float* Vb = Ib + p.n_rec;         // Vbar_t
+    float* Ib_next = V + p.n_rec;     // Ibar_{t+1} (overwritten by Ibar_t once zbar_t is formed)
+    float* Zb = Ib_next + p.n_rec;    // zbar_t
+    float* Vb = Zb + p.n_rec;         // Vbar_t
     int32_t* spk = reinterpret_cast<int32_t*>(Vb + p.n_rec);
     int32_t* in_list = spk + p.n_rec;
     __shared__ int32_t s_cnt[2];
     __shared__ float s_yb[kSnnMaxOut], s_gm[kSnnMaxOut];
     const int b = blockIdx.x;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // this batch element's gradient partials (summed over the batch afterwards
-    // in a fixed order, so every gradient is reproducible bit for bit)
-    float* gin = p.g_in + static_cast<int64_t>(b) * p.n_in * p.n_rec;
-    float* grec = p.g_rec + static_cast<int64_t>(b) * p.nnz;
-    float* ib_keep = p.ib_blk + static_cast<int64_t>(b) * kDwBlock * p.n_rec;
+    const int lane = threadIdx.x & 31;
+    // this batch element's readout-gradient partials (summed over the batch
+    // afterwards in a fixed order) and its row of Ibar per step
     float* gout = p.g_out + static_cast<int64_t>(b) * p.n_rec * p.n_out;
-    for (int64_t e = threadIdx.x; e < static_cast<int64_t>(p.n_in) * p.n_rec; e += kSnnThreads) gin[e] = 0.f;
-    for (int64_t e = threadIdx.x; e < p.nnz; e += kSnnThreads) grec[e] = 0.f;
+    float* ib_b = p.ib_all + static_cast<int64_t>(b) * p.T * p.n_rec;
     for (int64_t e = threadIdx.x; e < static_cast<int64_t>(p.n_rec) * p.n_out; e += kSnnThreads) gout[e] = 0.f;
     for (int j = threadIdx.x; j < p.n_rec; j += kSnnThreads) Ib_next[j] = Vb[j] = 0.f;
     if (threadIdx.x < p.n_out) {
@@ -437,83 +431,24 @@ __global__ void __launch_bounds__(kSnnThreads, 1) k_snn_backward(SnnK p, const u
                             acc += p.dt * __ldg(p.W_out + static_cast<int64_t>(j) * p.n_out + oo) * s_yb[oo];
                     }
                     acc = group_reduce_sum(acc, G);
-                    if (j < p.n_rec && gl == 0) Ib[j] = acc;  // zbar_j for now
+                    if (j < p.n_rec && gl == 0) Zb[j] = acc;
                 }
             }
             __syncthreads();
             for (int j = threadIdx.x; j < p.n_rec; j += kSnnThreads) {
-                const float zbar = Ib[j];
+                const float zbar = Zb[j];
                 const bool z = (zb[j >> 5] >> (j & 31)) & 1u;
                 const float vpb = Vb[j] * (z ? 0.f : 1.f) + zbar * surrogate(p.sg, Vp[j] - p.V_th) +
                                   penalty_grad(p.sg, Vp[j]);
                 const float ib = (1.f - p.a_m) * p.R * vpb + p.a_s * Ib_next[j];
-                Ib[j] = ib;
+                Ib_next[j] = ib;  // Ibar_t is the next (earlier) step's Ibar_{t+1}; column j is this thread's
+                ib_b[static_cast<int64_t>(t) * p.n_rec + j] = ib;  // dW_in and dw_rec come from these
                 Vb[j] = p.a_m * vpb;
                 if (z) {  // dW_out[j, :] += dt ybar_t (row j belongs to this thread)
                     float* row = gout + static_cast<int64_t>(j) * p.n_out;
                     for (int oo = 0; oo < p.n_out; ++oo) row[oo] += p.dt * s_yb[oo];
                 }
             }
-            __syncthreads();
-            // dW_in[k, :] += Ibar_t for the inputs active at t (column j belongs to thread j)
-            const int n_act = gather_inputs(u + (static_cast<int64_t>(b) * p.T + t) * p.n_in, p.n_in, in_list, &s_cnt[0]);
-            for (int j = threadIdx.x; j < p.n_rec; j += kSnnThreads) {
-                const float ib = Ib[j];
-                int a = 0;
-                for (; a + 4 <= n_act; a += 4) {  // four independent read-modify-writes in flight
-                    float* r0 = gin + static_cast<int64_t>(in_list[a]) * p.n_rec + j;
-                    float* r1 = gin + static_cast<int64_t>(in_list[a + 1]) * p.n_rec + j;
-                    float* r2 = gin + static_cast<int64_t>(in_list[a + 2]) * p.n_rec + j;
-                    float* r3 = gin + static_cast<int64_t>(in_list[a + 3]) * p.n_rec + j;
-                    const float v0 = *r0, v1 = *r1, v2 = *r2, v3 = *r3;
-                    *r0 = v0 + ib;
-                    *r1 = v1 + ib;
-                    *r2 = v2 + ib;
-                    *r3 = v3 + ib;
-                }
-                for (; a < n_act; ++a) gin[static_cast<int64_t>(in_list[a]) * p.n_rec + j] += ib;
-            }
-            // dw_rec[e] += Ibar_t[col e] for the rows spiking at t - 1: Ibar_t is
-            // kept for the step's gradient block, and when the block's lowest
-            // step is done each row that spiked in the block adds, entry by
-            // entry, the block's sum in one read-modify-write (instead of one
-            // per step and spike)
-            float* ibt = ib_keep + static_cast<int64_t>(t % kDwBlock) * p.n_rec;
-            for (int j = threadIdx.x; j < p.n_rec; j += kSnnThreads) ibt[j] = Ib[j];
-            if (t % kDwBlock == 0) {
-                __syncthreads();
-                const int hi = min(p.T, t + kDwBlock);
-                for (int i = warp; i < p.n_rec; i += kSnnThreads / 32) {
-                    // steps s of the block with row i spiking at s - 1 (bit s - t)
-                    uint32_t when = 0;
-                    for (int s = max(t, 1); s < hi; ++s)
-                        when |= ((zall[static_cast<int64_t>(s - 1) * p.zw + (i >> 5)] >> (i & 31)) & 1u) << (s - t);
-                    if (!when) continue;
-                    const int64_t r0 = p.indptr[i], r1 = p.indptr[i + 1];
-                    for (int64_t e = r0 + lane; e < r1; e += 4 * 32) {
-                        int32_t c[4];
-                        float acc[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            const int64_t ee = e + 32 * u;
-                            c[u] = ee < r1 ? p.indices[ee] : 0;
-                        }
-                        // steps in increasing order: a fixed summation order
-                        for (uint32_t m = when; m; m &= m - 1) {
-                            const float* row = ib_keep + static_cast<int64_t>(__ffs(m) - 1) * p.n_rec;
-#pragma unroll
-                            for (int u = 0; u < 4; ++u) acc[u] += row[c[u]];
-                        }
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            const int64_t ee = e + 32 * u;
-                            if (ee < r1) grec[ee] += acc[u];
-                        }
-                    }
-                }
-            }
-            __syncthreads();
-            for (int j = threadIdx.x; j < p.n_rec; j += kSnnThreads) Ib_next[j] = Ib[j];
             __syncthreads();
         }
     }
@@ -527,6 +462,24 @@ __global__ void k_snn_reduce(const float* __restrict__ part, int32_t B, int64_t 
         float acc = 0.f;
         for (int b = 0; b < B; ++b) acc += part[static_cast<int64_t>(b) * n + e];
         out[e] += acc;
+    }
+}
+
+// dW_in[k][j] += G[k][j] for the n_in input rows of G; dw_rec[e] +=
+// G[n_in + i][indices[e]] for every stored entry e of recurrent row i (the
+// dense recurrent gradient read at the stored entries).
+__global__ void k_snn_grad_scatter(const float* __restrict__ G, int32_t n_in, int32_t n_rec,
+                                   const int64_t* __restrict__ indptr, const int32_t* __restrict__ indices,
+                                   float* __restrict__ dW_in, float* __restrict__ dw_rec) {
+    const int64_t tid = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    const int64_t n_w = static_cast<int64_t>(n_in) * n_rec;
+    for (int64_t e = tid; e < n_w; e += stride) dW_in[e] += G[e];
+    const int lane = threadIdx.x & 31;
+    for (int64_t i = tid >> 5; i < n_rec; i += stride >> 5) {
+        const float* g = G + (static_cast<int64_t>(n_in) + i) * n_rec;
+        const int64_t e1 = indptr[i + 1];
+        for (int64_t e = indptr[i] + lane; e < e1; e += 32) dw_rec[e] += g[indices[e]];
     }
 }
 
@@ -591,7 +544,7 @@ __global__ void k_snn_reg_add(int32_t B, float scale, const float* __restrict__ 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct SnnLayout {
-    size_t ck_I, ck_V, ck_y, z_all, seg_Vp, g_in, g_rec, ib_blk, g_out, g_b, vreg, w_fix, total;
+    size_t ck_I, ck_V, ck_y, z_all, seg_Vp, ib_all, g_full, tc_work, tc_bytes, g_out, g_b, vreg, w_fix, total;
     int32_t n_ck, zw;
 };
 
@@ -608,9 +561,13 @@ SnnLayout snn_layout(const bp_snn_desc& d) {
     L.ck_y = o; o = align256(o + B * L.n_ck * d.n_out * 4);
     L.z_all = o; o = align256(o + B * static_cast<size_t>(d.T) * L.zw * 4);
     L.seg_Vp = o; o = align256(o + B * static_cast<size_t>(K) * d.n_rec * 4);
-    L.g_in = o; o = align256(o + B * static_cast<size_t>(d.n_in) * d.n_rec * 4);
-    L.g_rec = o; o = align256(o + B * static_cast<size_t>(d.nnz > 0 ? d.nnz : 0) * 4);
-    L.ib_blk = o; o = align256(o + B * static_cast<size_t>(kDwBlock) * d.n_rec * 4);
+    L.ib_all = o; o = align256(o + B * static_cast<size_t>(d.T) * d.n_rec * 4);
+    // G = [u ; z_shifted]^T Ibar: rows n_in + n_rec, row stride n_rec
+    L.g_full = o; o = align256(o + (static_cast<size_t>(d.n_in) + d.n_rec) * d.n_rec * 4);
+    // the contraction's workspace must be 1024-byte aligned in memory, the
+    // snn workspace only 256: 768 bytes of slack let snn_kernel_args align it
+    L.tc_bytes = tc_spike_gemm_workspace(d.B, d.T, d.n_rec, d.n_in + d.n_rec);
+    L.tc_work = o; o = align256(o + L.tc_bytes + 768);
     L.g_out = o; o = align256(o + B * static_cast<size_t>(d.n_rec) * d.n_out * 4);
     L.g_b = o; o = align256(o + B * static_cast<size_t>(d.n_out) * 4);
     L.vreg = o; o = align256(o + B * 4);
@@ -687,9 +644,7 @@ SnnK snn_kernel_args(const bp_snn_desc& d, void* ws) {
     p.ck_y = reinterpret_cast<float*>(w + L.ck_y);
     p.z_all = reinterpret_cast<uint32_t*>(w + L.z_all);
     p.seg_Vp = reinterpret_cast<float*>(w + L.seg_Vp);
-    p.g_in = reinterpret_cast<float*>(w + L.g_in);
-    p.g_rec = reinterpret_cast<float*>(w + L.g_rec);
-    p.ib_blk = reinterpret_cast<float*>(w + L.ib_blk);
+    p.ib_all = reinterpret_cast<float*>(w + L.ib_all);
     p.g_out = reinterpret_cast<float*>(w + L.g_out);
     p.g_b = reinterpret_cast<float*>(w + L.g_b);
     p.vreg = reinterpret_cast<float*>(w + L.vreg);
@@ -835,9 +790,16 @@ bp_status bp_snn_backward(const bp_snn_desc* d, const uint8_t* u, const float* g
         bp::k_snn_backward<BP_W_F32><<<d->B, bp::kSnnThreads, smem, stream>>>(p, u, g_m);
     }
     BP_LAUNCHED();
+    // input and recurrent weight gradients: one contraction over batch and
+    // time on the tensor cores, G = [u_t ; z_{t-1}]^T Ibar_t
+    const bp::SnnLayout L = bp::snn_layout(*d);
+    char* wsb = static_cast<char*>(workspace);
+    float* g_full = reinterpret_cast<float*>(wsb + L.g_full);
+    const uintptr_t tw = (reinterpret_cast<uintptr_t>(wsb + L.tc_work) + 1023) & ~uintptr_t(1023);
+    BP_TRY(bp::launch_tc_spike_gemm(d->B, d->T, p.ib_all, d->n_rec, u, d->n_in, p.z_all, d->n_rec, L.zw, g_full,
+                                    d->n_rec, false, reinterpret_cast<void*>(tw), L.tc_bytes, stream));
     const int grid = bp::sm_count() * 8;
-    bp::k_snn_reduce<<<grid, 256, 0, stream>>>(p.g_in, d->B, static_cast<int64_t>(d->n_in) * d->n_rec, dW_in);
-    bp::k_snn_reduce<<<grid, 256, 0, stream>>>(p.g_rec, d->B, d->nnz, dw_rec);
+    bp::k_snn_grad_scatter<<<grid, 256, 0, stream>>>(g_full, d->n_in, d->n_rec, d->indptr, d->indices, dW_in, dw_rec);
     bp::k_snn_reduce<<<grid, 256, 0, stream>>>(p.g_out, d->B, static_cast<int64_t>(d->n_rec) * d->n_out, dW_out);
     bp::k_snn_reduce<<<1, 64, 0, stream>>>(p.g_b, d->B, d->n_out, db_out);
     BP_LAUNCHED();
