@@ -158,6 +158,18 @@ def peaks():
     return 6800.0, "fallback"
 
 
+def bf16_peak():
+    """Dense BF16 tensor rate (TFLOP/s) a kernel timed alone is compared with:
+    the measured burst figure when MEASURED_PEAKS.json exists, else 1900."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        if "bf16_tflops" in d:
+            return float(d["bf16_tflops"]), "measured"
+    return 1900.0, "fallback"
+
+
 def step_traffic_record():
     """Per-launch DRAM traffic of the fused network step from the committed ncu
     summary, valid only while the kernel's sources are unchanged (their hash is
@@ -547,6 +559,36 @@ def bench_bptt(torch, reps=3, T=1000):
     return out
 
 
+def bench_spike_outer(torch, peak_tflops, B_=128, T=1000, n_in=700, n_rec=1024):
+    """The spike-driven weight-gradient contraction of the differentiable
+    network's backward (bp_spike_outer, tcgen05 BF16 MMAs with the FP32
+    adjoint split into hi + lo terms) at its configured size: K = B T =
+    128 000 (batch x time), M = n_in + n_rec = 1724 spike rows (inputs at
+    2.75 % and recurrent spikes at 5 % per step), N = n_rec = 1024 adjoint
+    features.  Device time of the whole call (operand packing, the MMA kernel,
+    the split reduction); TFLOP/s counted both as the dense contraction's
+    2 K M N and as the MMA work executed (two BF16 terms on the padded
+    operands)."""
+    import numpy as np
+    from paper_2311_05106_gb300 import binding as B
+    K, M, N = B_ * T, n_in + n_rec, n_rec
+    g = torch.Generator(device="cuda").manual_seed(3)
+    rate = torch.cat([torch.full((n_in,), 0.0275, device="cuda"), torch.full((n_rec,), 0.05, device="cuda")])
+    x = (torch.rand((K, M), generator=g, device="cuda") < rate).to(torch.uint8)
+    d = torch.randn((K, N), generator=g, device="cuda") * 1e-3
+    out = torch.empty((M, N), dtype=torch.float32, device="cuda")
+    work = B.spike_outer_workspace(K, M, N)
+    ms = device_timer(torch, lambda: B.bp_spike_outer(x, d, out, overwrite=True, work=work), 7)
+    pad = lambda v, m: (v + m - 1) // m * m
+    flops = 2.0 * K * M * N
+    executed = 2.0 * 2.0 * pad(T, 64) * B_ * pad(M, 256) * pad(N, 128)
+    del x, d, work
+    return {"K": K, "M": M, "N": N, "ms": ms, "tflops_dense": flops / (ms * 1e-3) / 1e12,
+            "tflops_executed": executed / (ms * 1e-3) / 1e12,
+            "frac_executed_of_bf16_peak": executed / (ms * 1e-3) / 1e12 / peak_tflops,
+            "note": "whole call: operand packing + MMA kernel + split reduction"}
+
+
 # ----------------------------------------------------------------- oracle legs
 def oracle_sample(budget_s, n_sample=None):
     """The FP64 oracle (single thread, as it stands) on the same E/I network:
@@ -750,6 +792,15 @@ def sweep_cells(torch, sizes, probs, rhos, wsel, ops, cells=None, tile_cols=None
                 if tc:
                     tp = torch.empty(B.bp_csr_tile_index_size(n, n, tc), dtype=torch.int32, device="cuda")
                     B.bp_csr_tile_index(ip, ix, n, tc, tp)
+                    tp16 = None
+                    if w32 is not None:
+                        # the fixed-point tile sums' weight bound, once per matrix
+                        # (the FP32 and BF16 copies of the weights share it up to
+                        # rounding, so each gets its own index slot)
+                        B.bp_csr_tile_weight_bound(ip, ix, w32, 1.0, n, tc, tp)
+                        if w16 is not None:
+                            tp16 = tp.clone()
+                            B.bp_csr_tile_weight_bound(ip, ix, w16, 1.0, n, tc, tp16)
                 torch.cuda.synchronize()
                 x = torch.ones(n, dtype=torch.float32, device="cuda")
                 yp = torch.zeros(n, dtype=torch.float32, device="cuda")
@@ -775,14 +826,21 @@ def sweep_cells(torch, sizes, probs, rhos, wsel, ops, cells=None, tile_cols=None
                 if csr_ok:
                     lens = ip[1:] - ip[:-1]
                     ev_count = int(lens[sl[:n_spk].long()].sum().item()) if n_spk else 0
-                    for wname, wt, wb, y in (("homo", None, 0, yc), ("f32", w32, 4, yf), ("bf16", w16, 2, yf)):
+                    forms = [("homo", None, 0, yc, "int32", 0, tp)]
+                    for wname, wt, wb, tpi in (("f32", w32, 4, tp), ("bf16", w16, 2, tp16 if tc else None)):
+                        # weighted tiles: FP32 shared-memory atomics, and (with a
+                        # tile index) 32-bit fixed-point tile sums
+                        forms.append((wname, wt, wb, yf, "fp32", 0, tpi))
+                        if tc:
+                            forms.append((wname, wt, wb, yf, "fixed", B.BP_ACC_FIXED, tpi))
+                    for wname, wt, wb, y, acc, fl, tpi in forms:
                         if wname not in wsel or "csr" not in ops:
                             continue
-                        ms = device_timer(torch, lambda: B.bp_event_csrmv(ip, ix, wt, 1.0, sl, ns, y, tile_ptr=tp,
-                                                                          tile_cols=tc), 7)
+                        ms = device_timer(torch, lambda: B.bp_event_csrmv(ip, ix, wt, 1.0, sl, ns, y, tile_ptr=tpi,
+                                                                          tile_cols=tc, flags=fl), 7)
                         alg = ev_count * (4 + wb) + 16 * n_spk
-                        yield dict(op="event_csrmv", n=n, p=p, rho=rho, weights=wname, us=ms * 1e3, spikes=n_spk,
-                                   events=ev_count, events_per_s=ev_count / (ms * 1e-3), alg_bytes=alg,
+                        yield dict(op="event_csrmv", n=n, p=p, rho=rho, weights=wname, acc=acc, us=ms * 1e3,
+                                   spikes=n_spk, events=ev_count, events_per_s=ev_count / (ms * 1e-3), alg_bytes=alg,
                                    gbs=alg / ms / 1e6, frac_hbm=alg / ms / 1e6 / peak, peak_source=peak_kind,
                                    tile_cols=tc, graded=(n == 1_000_000 and (p, rho) in GRADED_CELLS))
                 yy = torch.zeros(n, dtype=torch.int32, device="cuda")
@@ -799,6 +857,8 @@ def sweep_cells(torch, sizes, probs, rhos, wsel, ops, cells=None, tile_cols=None
                                bound="alu" if n <= B.bp_tile_cols() else "l2_red")
                 del events, sl, ns, yc, yf, yy
             del ip, ix, w32, w16, tp
+            if csr_ok and tc:
+                del tp16
             torch.cuda.empty_cache()
 
 
@@ -901,7 +961,10 @@ def main():
     if args.bptt_only:
         import torch
         torch.cuda.set_device(0)
-        print(json.dumps({"bptt": bench_bptt(torch, T=args.bptt_T)}))
+        pk, pk_src = bf16_peak()
+        so = bench_spike_outer(torch, pk, T=args.bptt_T)
+        so["peak_tflops"], so["peak_source"] = pk, pk_src
+        print(json.dumps({"bptt": bench_bptt(torch, T=args.bptt_T), "spike_outer": so}))
         return 0
     if args.align_pre_only:
         import torch
@@ -1017,6 +1080,10 @@ def main():
         variants["align_pre_csr_f32"]["vs_align_post_step_time"] = \
             variants["align_pre_csr_f32"]["ms_per_step"] / (ms / args.steps)
         variants["bptt_b128_t1000"] = bench_bptt(torch)
+        pk, pk_src = bf16_peak()
+        variants["spike_outer_bptt_shape"] = bench_spike_outer(torch, pk)
+        variants["spike_outer_bptt_shape"]["peak_tflops"] = pk
+        variants["spike_outer_bptt_shape"]["peak_source"] = pk_src
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and headline:

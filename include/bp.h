@@ -69,6 +69,7 @@ typedef enum { BP_JIT_HOMO = 0, BP_JIT_UNIFORM = 1, BP_JIT_NORMAL = 2 } bp_jit_w
 #define BP_OVERWRITE 1u     /* zero the output before accumulating */
 #define BP_ACC_GLOBAL 2u    /* force direct atomic accumulation in L2 (no shared-memory tiles) */
 #define BP_ACC_SHARED 4u    /* force shared-memory tile accumulation */
+#define BP_ACC_FIXED 8u     /* float products: tile sums in 32-bit fixed point (see bp_event_csrmv) */
 
 /* --------------------------------------------------------------------------
  * Library
@@ -176,8 +177,20 @@ bp_status bp_spike_compact(int64_t n, const uint8_t* events, int32_t* spike_list
  * accumulation when n_post > bp_tile_cols().
  * Accumulation order is unspecified: FP32 results are deterministic only up to
  * rounding; int32 counts are exact.
+ * BP_ACC_FIXED (float y; needs a tile index on which
+ * bp_csr_tile_weight_bound() has recorded the weight bound b): the shared-
+ * memory tile sums are 32-bit integers.  A CTA that accumulates m spiking
+ * rows takes s = 29 - e, where m b < 2^e <= 2 m b (s kept within
+ * [-100, 100]), and adds round(w_j 2^s) per event, so no tile sum can
+ * overflow; the tile, times 2^-s, is then added to y in FP32.  Each event is
+ * off by at most 2^-(s+1) <= m b 2^-29 absolute, the order of the worst-case
+ * rounding of an FP32 sum of the same terms, and a tile's sum does not depend
+ * on the order of its events.  Direct (global-atomic) accumulation ignores
+ * the flag.  A tile index without a recorded bound makes the kernel record
+ * BP_ERR_DEVICE (bp_sync_status) and add nothing.
  * Errors: BP_ERR_INVALID for negative sizes, NULL required pointers,
- * y_is_count with a non-HOMO kind, or a tile index built for other sizes. */
+ * y_is_count with a non-HOMO kind, a tile index built for other sizes, or
+ * BP_ACC_FIXED for float y without a tile index. */
 bp_status bp_event_csrmv(int64_t n_pre, int64_t n_post,
                          const int64_t* indptr, const int32_t* indices,
                          const void* data, int32_t wkind, float w_homo,
@@ -223,15 +236,30 @@ bp_status bp_event_csrmv_dense_noalloc(int64_t n_pre, int64_t n_post,
                                        uint32_t flags, bp_stream_t stream);
 
 /* Post-column tile index for shared-memory accumulation.  With
- * S = ceil(n_post / tile_cols) tiles, writes tile_ptr int32 [n_pre * (S + 1)]:
+ * S = ceil(n_post / tile_cols) tiles, writes tile_ptr int32
+ * [n_pre * (S + 1) + 1] (bp_csr_tile_index_size entries):
  * tile_ptr[i (S+1) + s] = (first position in row i whose column is
- * >= s tile_cols) - indptr[i], for s = 0..S (so entry S is the row length).
+ * >= s tile_cols) - indptr[i], for s = 0..S (so entry S is the row length),
+ * and 0 in the last entry (the weight-bound slot of
+ * bp_csr_tile_weight_bound: no bound recorded).
  * Requires sorted rows and row lengths < 2^31.  tile_cols must be a positive
  * multiple of 32 no larger than bp_tile_cols(). */
 int64_t bp_csr_tile_index_size(int64_t n_pre, int64_t n_post, int32_t tile_cols);
 bp_status bp_csr_tile_index(int64_t n_pre, int64_t n_post, const int64_t* indptr,
                             const int32_t* indices, int32_t tile_cols, int32_t* tile_ptr,
                             bp_stream_t stream);
+
+/* Records in the tile index built by bp_csr_tile_index (same n_pre, n_post,
+ * tile_cols) the weight bound that BP_ACC_FIXED needs: b = the largest
+ * absolute sum of one row's entries in one column (the largest |w_j| when
+ * no row repeats a column; |w_homo| for BP_W_HOMO), rounded up, stored as
+ * FP32 bits in the index's last entry (bp_csr_tile_index leaves 0 there:
+ * no bound).  One device pass over the stored entries; call it again after
+ * the weights change. */
+bp_status bp_csr_tile_weight_bound(int64_t n_pre, int64_t n_post, const int64_t* indptr,
+                                   const int32_t* indices, const void* data, int32_t wkind,
+                                   float w_homo, int32_t tile_cols, int32_t* tile_ptr,
+                                   bp_stream_t stream);
 
 /* Validation of a CSR before use (the products trust their operands and do
  * not check indices on the hot path): one device pass over indices [nnz]

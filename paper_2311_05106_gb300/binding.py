@@ -19,9 +19,10 @@ import torch
 from . import _build
 
 BP_OK = 0
+BP_ERR_INVALID, BP_ERR_CUDA, BP_ERR_TIMEOUT, BP_ERR_OOM, BP_ERR_UNSUPPORTED, BP_ERR_DEVICE = 1, 2, 3, 4, 5, 6
 BP_W_HOMO, BP_W_F32, BP_W_BF16 = 0, 1, 2
 BP_JIT_HOMO, BP_JIT_UNIFORM, BP_JIT_NORMAL = 0, 1, 2
-BP_OVERWRITE, BP_ACC_GLOBAL, BP_ACC_SHARED = 1, 2, 4
+BP_OVERWRITE, BP_ACC_GLOBAL, BP_ACC_SHARED, BP_ACC_FIXED = 1, 2, 4, 8
 BP_CONN_CSR, BP_CONN_JIT = 0, 1
 
 
@@ -100,6 +101,7 @@ _SIGS = {
     "bp_event_csrmv_dense_noalloc": (c_i32, [c_i64, c_i64, VP, VP, VP, c_i32, c_f32, VP, VP, c_i32, c_u32, VP]),
     "bp_csr_tile_index_size": (c_i64, [c_i64, c_i64, c_i32]),
     "bp_csr_tile_index": (c_i32, [c_i64, c_i64, VP, VP, c_i32, VP, VP]),
+    "bp_csr_tile_weight_bound": (c_i32, [c_i64, c_i64, VP, VP, VP, c_i32, c_f32, c_i32, VP, VP]),
     "bp_csr_check": (c_i32, [c_i64, c_i64, c_i64, VP, VP, VP, VP]),
     "bp_event_csrmv_t": (c_i32, [c_i64, c_i64, VP, VP, VP, c_i32, c_f32, VP, VP, VP, c_i32, c_u32, VP]),
     "bp_event_csrmv_bwd": (c_i32, [c_i64, c_i64, VP, VP, VP, c_i32, c_f32, VP, VP, c_i64, VP, VP, VP, VP, c_i32, VP]),
@@ -212,7 +214,7 @@ def _csr_sizes(indices, data, n_pre, n_post, tile_ptr, tile_cols, spike_list=Non
     writes, a spike list of at least max_spikes entries."""
     if data is not None and indices is not None and data.numel() < indices.numel():
         raise ValueError("data holds %d weights for %d stored entries" % (data.numel(), indices.numel()))
-    if tile_ptr is not None and tile_cols > 0 and n_post > tile_cols:
+    if tile_ptr is not None and tile_cols > 0:
         need = int(lib().bp_csr_tile_index_size(n_pre, n_post, int(tile_cols)))
         if tile_ptr.dtype != torch.int32 or tile_ptr.numel() < need:
             raise ValueError("tile_ptr must be int32 with at least %d entries" % need)
@@ -327,6 +329,16 @@ def bp_csr_tile_index(indptr, indices, n_post, tile_cols, tile_ptr, stream=None)
     _csr_sizes(indices, None, indptr.numel() - 1, n_post, tile_ptr, tile_cols)
     _check("bp_csr_tile_index", lib().bp_csr_tile_index(indptr.numel() - 1, n_post, _p(indptr), _p(indices),
                                                         int(tile_cols), _p(tile_ptr), _stream(stream)))
+
+
+def bp_csr_tile_weight_bound(indptr, indices, data, w_homo, n_post, tile_cols, tile_ptr, stream=None):
+    """Records in tile_ptr's last entry the weight bound of the fixed-point
+    tile sums (BP_ACC_FIXED): the largest absolute sum of one row's entries in
+    one column, as FP32 bits."""
+    _csr_sizes(indices, data, indptr.numel() - 1, n_post, tile_ptr, tile_cols)
+    _check("bp_csr_tile_weight_bound", lib().bp_csr_tile_weight_bound(
+        indptr.numel() - 1, int(n_post), _p(indptr), _p(indices), _p(data), _wkind(data), float(w_homo),
+        int(tile_cols), _p(tile_ptr), _stream(stream)))
 
 
 def bp_csr_check(indptr, indices, n_post, out, stream=None):

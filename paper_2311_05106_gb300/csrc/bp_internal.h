@@ -62,7 +62,15 @@ struct CsrArgs {
     float w_homo;
     const int32_t* tile_ptr;
     int32_t tile_cols;
+    // the weight-bound slot at the end of the tile index (fixed-point tile
+    // sums, BP_ACC_FIXED); NULL without a tile index
+    const int32_t* w_bound = nullptr;
 };
+
+// Accumulation mode of the event CSR product (launch_event_csrmv): 0 auto,
+// 1 direct (global atomics), 2 shared tiles; kModeFixed or-ed in asks for
+// fixed-point tile sums of float products.
+constexpr int kModeFixed = 16;
 
 // JIT operand (Appendix C): key, gap range, weight law.
 struct JitArgs {

@@ -152,9 +152,20 @@ struct FlatSmem {
 // the 32-bit range.
 constexpr int64_t kFlatMaxEntries = int64_t(1) << 24;
 
-template <typename Acc, int WK, bool CHUNKS, int U>
+// One event into the shared-memory tile: an integer count, an FP32 atomic,
+// or (FX) round(w 2^s) into the tile's 32-bit fixed-point sum (fx_scale = 2^s).
+template <typename Acc, bool FX>
+__device__ __forceinline__ void tile_add(Acc* p, float w, float fx_scale) {
+    if constexpr (FX) {
+        atomicAdd(reinterpret_cast<int32_t*>(p), __float2int_rn(w * fx_scale));
+    } else {
+        acc_add(p, event_value<Acc>(w));
+    }
+}
+
+template <typename Acc, int WK, bool CHUNKS, int U, bool FX>
 __device__ __forceinline__ void warp_flat_walk(const CsrArgs& a, const WarpList& L, int32_t T,
-                                               Acc* __restrict__ acc, int64_t col0, int32_t W) {
+                                               Acc* __restrict__ acc, int64_t col0, int32_t W, float fx_scale) {
     const int lane = threadIdx.x & 31;
     int32_t e = lane;
     if (e >= T) return;
@@ -215,17 +226,18 @@ __device__ __forceinline__ void warp_flat_walk(const CsrArgs& a, const WarpList&
                 // an index outside this tile (an operand that does not match
                 // its tile index) is skipped rather than written out of the tile
                 const uint32_t c = static_cast<uint32_t>(static_cast<int64_t>(col[q][m]) - col0);
-                if (((msk[q] >> m) & 1u) && c < static_cast<uint32_t>(W)) acc_add(acc + c, event_value<Acc>(w[q][m]));
+                if (((msk[q] >> m) & 1u) && c < static_cast<uint32_t>(W)) tile_add<Acc, FX>(acc + c, w[q][m], fx_scale);
             }
         }
     }
 }
 
-template <typename Acc, int WK, bool VECL>
+template <typename Acc, int WK, bool VECL, bool FX = false>
 __global__ void __launch_bounds__(kTileThreads, 1)
     k_csr_scatter(CsrArgs a, const int32_t* __restrict__ spike_list, const int32_t* __restrict__ n_spikes,
                   int64_t max_spikes, Acc* __restrict__ y, int mode, int32_t W, int32_t S,
-                  int64_t* __restrict__ events_total) {
+                  int64_t* __restrict__ events_total, int* status) {
+    static_assert(!FX || std::is_same<Acc, float>::value, "fixed-point tiles accumulate float products");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Acc* acc = reinterpret_cast<Acc*>(smem_raw);
     FlatSmem& fs = *reinterpret_cast<FlatSmem*>(smem_raw + static_cast<size_t>(W) * sizeof(Acc));
@@ -264,6 +276,23 @@ __global__ void __launch_bounds__(kTileThreads, 1)
         // the CTA's rows are spike-list positions r + R m, m in [0, M); warp w
         // takes an equal contiguous share [m_lo, m_hi) of them, 32 per round
         const int32_t M = static_cast<int32_t>(ns > r ? (ns - r + R - 1) / R : 0);  // ns <= n_pre < 2^31
+        // fixed-point tiles: with the weight bound b, every column of this
+        // CTA's tile sums at most M b in magnitude; 2^s M b <= 2^29 keeps the
+        // sum of the rounded terms inside int32
+        float fx_scale = 1.f, fx_inv = 1.f;
+        if constexpr (FX) {
+            const float b = __int_as_float(*a.w_bound);
+            if (!(b > 0.f)) {  // no bound recorded: nothing is added
+                if (t == 0 && status) atomicExch(status, static_cast<int>(BP_ERR_DEVICE));
+                return;
+            }
+            int e = 0;
+            frexpf(static_cast<float>(M > 0 ? M : 1) * b, &e);  // M b < 2^e
+            int sx = 29 - e;
+            sx = sx < -100 ? -100 : (sx > 100 ? 100 : sx);
+            fx_scale = ldexpf(1.f, sx);
+            fx_inv = ldexpf(1.f, -sx);
+        }
         const int32_t m_lo = static_cast<int32_t>(static_cast<int64_t>(M) * warp / (kTileThreads / 32));
         const int32_t m_hi = static_cast<int32_t>(static_cast<int64_t>(M) * (warp + 1) / (kTileThreads / 32));
         auto row_id = [&](int32_t k) -> int32_t {
@@ -335,8 +364,8 @@ __global__ void __launch_bounds__(kTileThreads, 1)
                 L.base[lane] = (u0 << 8) | (edge & 0xFF);
                 if (lane == 31) L.start[32] = static_cast<int32_t>(T);
                 __syncwarp();
-                warp_flat_walk<Acc, WK, VECL, VECL ? (WK == WK_HOMO ? 4 : 3) : (std::is_same<Acc, int32_t>::value && WK == WK_HOMO ? 16 : 8)>(
-                    a, L, static_cast<int32_t>(T), acc, col0, W);
+                warp_flat_walk<Acc, WK, VECL, VECL ? (WK == WK_HOMO ? 4 : 3) : (std::is_same<Acc, int32_t>::value && WK == WK_HOMO ? 16 : 8), FX>(
+                    a, L, static_cast<int32_t>(T), acc, col0, W, fx_scale);
             } else {
                 // the warp walks its lanes' segments one after another, four
                 // loads in flight per lane
@@ -355,7 +384,7 @@ __global__ void __launch_bounds__(kTileThreads, 1)
 #pragma unroll
                         for (int q = 0; q < 4; ++q) {
                             const uint32_t kk = static_cast<uint32_t>(static_cast<int64_t>(c[q]) - col0);
-                            if (c[q] >= 0 && kk < static_cast<uint32_t>(W)) acc_add(acc + kk, event_value<Acc>(wv[q]));
+                            if (c[q] >= 0 && kk < static_cast<uint32_t>(W)) tile_add<Acc, FX>(acc + kk, wv[q], fx_scale);
                         }
                     }
                 }
@@ -365,7 +394,21 @@ __global__ void __launch_bounds__(kTileThreads, 1)
         __syncthreads();
         const int64_t rem = a.n_post - col0;
         const int lim = static_cast<int>(rem < W ? rem : W);
-        if constexpr (std::is_same<Acc, float>::value) {
+        if constexpr (FX) {
+            // fixed-point sums, times 2^-s, one 16-byte reduction per four
+            // columns (y 16-byte aligned), the ragged tail one by one
+            const int32_t* ia = reinterpret_cast<const int32_t*>(acc);
+            const bool y16 = (reinterpret_cast<uintptr_t>(y) & 15) == 0;
+            const int lim4 = y16 ? (lim & ~3) : 0;
+            for (int k = 4 * t; k < lim4; k += 4 * kTileThreads) {
+                const int4 v = *reinterpret_cast<const int4*>(ia + k);
+                if (v.x | v.y | v.z | v.w)
+                    red_add_v4(y + col0 + k, make_float4(static_cast<float>(v.x) * fx_inv, static_cast<float>(v.y) * fx_inv,
+                                                         static_cast<float>(v.z) * fx_inv, static_cast<float>(v.w) * fx_inv));
+            }
+            for (int k = lim4 + t; k < lim; k += kTileThreads)
+                if (ia[k] != 0) acc_add(y + col0 + k, static_cast<float>(ia[k]) * fx_inv);
+        } else if constexpr (std::is_same<Acc, float>::value) {
             // FP32 sums: one 16-byte reduction per four columns (y 16-byte
             // aligned; col0 is a multiple of 32), the ragged tail one by one
             if ((reinterpret_cast<uintptr_t>(y) & 15) == 0) {
@@ -592,12 +635,50 @@ __global__ void k_tile_index(int64_t n_pre, const int64_t* __restrict__ indptr, 
         }
         tile_ptr[t] = static_cast<int32_t>(lo - rs);
     }
+    if (blockIdx.x == 0 && threadIdx.x == 0) tile_ptr[total] = 0;  // weight-bound slot: no bound yet
+}
+
+// Weight bound of the fixed-point tiles: the largest absolute sum of one
+// row's entries in one column (rows sorted, so a repeated column is a run of
+// equal indices).  A warp per row; the lane at the start of each run sums the
+// run; the maximum, rounded up, goes into *slot as FP32 bits (non-negative
+// floats order like their bit patterns, so an integer maximum is a float
+// maximum).
+template <int WK>
+__global__ void __launch_bounds__(256) k_tile_weight_bound(int64_t n_pre, const int64_t* __restrict__ indptr,
+                                                          const int32_t* __restrict__ indices,
+                                                          const void* __restrict__ data, float w_homo,
+                                                          int32_t* __restrict__ slot) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
+    float best = 0.f;
+    for (int64_t i = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; i < n_pre; i += warps) {
+        const int64_t r0 = indptr[i], r1 = indptr[i + 1];
+        for (int64_t j = r0 + lane; j < r1; j += 32) {
+            const int32_t c = indices[j];
+            if (j > r0 && indices[j - 1] == c) continue;  // not the start of its run
+            float run = fabsf(load_weight<WK>(data, j, w_homo));
+            for (int64_t k = j + 1; k < r1 && indices[k] == c; ++k) run += fabsf(load_weight<WK>(data, k, w_homo));
+            best = fmaxf(best, run);
+        }
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) best = fmaxf(best, __shfl_xor_sync(FULL_MASK, best, d));
+    if (lane == 0) {
+        // a run's FP32 sum may round down: a relative 2^-16 covers runs of up
+        // to 256 repeats; never 0 (0 means no bound)
+        float up = best * (1.f + 1.f / 65536.f);
+        if (!(up >= 1.17549435e-38f)) up = 1.17549435e-38f;
+        atomicMax(slot, __float_as_int(up));
+    }
 }
 
 template <typename Acc, int WK, bool VECL>
 bp_status launch_scatter_t(const CsrArgs& a, const int32_t* spike_list, const int32_t* n_spikes, int64_t max_spikes,
                            void* y, int64_t* events_total, int mode, cudaStream_t s) {
     Acc* yy = static_cast<Acc*>(y);
+    const bool fx = (mode & kModeFixed) != 0;
+    mode &= ~kModeFixed;
     // tile geometry: one tile covers n_post if it fits, otherwise the tile index's width
     const int32_t cap = kTileCols;
     int32_t W = 0, S = 0;
@@ -621,14 +702,24 @@ bp_status launch_scatter_t(const CsrArgs& a, const int32_t* spike_list, const in
         return BP_OK;
     }
     const size_t smem = static_cast<size_t>(W) * sizeof(Acc) + sizeof(FlatSmem);
-    BP_TRY(ensure_smem_attr(reinterpret_cast<const void*>(k_csr_scatter<Acc, WK, VECL>),
-                            static_cast<int>(cap * sizeof(Acc) + sizeof(FlatSmem))));
     // one 1024-thread CTA per SM: R row groups per tile so that S x R covers the SMs
     int64_t R = static_cast<int64_t>(sm_count()) / S;
     if (R < 1) R = 1;
     const int64_t grid = R * S;
+    if constexpr (std::is_same<Acc, float>::value) {
+        if (fx) {
+            auto k = k_csr_scatter<float, WK, VECL, true>;
+            BP_TRY(ensure_smem_attr(reinterpret_cast<const void*>(k), static_cast<int>(cap * sizeof(Acc) + sizeof(FlatSmem))));
+            k<<<static_cast<unsigned>(grid), kTileThreads, smem, s>>>(at, spike_list, n_spikes, max_spikes, yy, mode, W,
+                                                                     S, events_total, device_status_ptr());
+            BP_LAUNCHED();
+            return BP_OK;
+        }
+    }
+    BP_TRY(ensure_smem_attr(reinterpret_cast<const void*>(k_csr_scatter<Acc, WK, VECL>),
+                            static_cast<int>(cap * sizeof(Acc) + sizeof(FlatSmem))));
     k_csr_scatter<Acc, WK, VECL><<<static_cast<unsigned>(grid), kTileThreads, smem, s>>>(
-        at, spike_list, n_spikes, max_spikes, yy, mode, W, S, events_total);
+        at, spike_list, n_spikes, max_spikes, yy, mode, W, S, events_total, nullptr);
     BP_LAUNCHED();
     return BP_OK;
 }
@@ -683,7 +774,12 @@ int gather_grid(int64_t n_pre) {
 bp_status launch_event_csrmv(const CsrArgs& a, const int32_t* spike_list, const int32_t* n_spikes, int64_t max_spikes,
                              void* y, bool counts, int64_t* events_total, int mode, cudaStream_t s) {
     if (max_spikes <= 0 || a.n_post == 0) return BP_OK;
-    if (counts) return launch_scatter_wk<int32_t>(a, spike_list, n_spikes, max_spikes, y, events_total, mode, s);
+    if (counts) return launch_scatter_wk<int32_t>(a, spike_list, n_spikes, max_spikes, y, events_total,
+                                                  mode & ~kModeFixed, s);
+    if ((mode & kModeFixed) && a.w_bound == nullptr) {
+        set_error("BP_ACC_FIXED needs a tile index (bp_csr_tile_index + bp_csr_tile_weight_bound)");
+        return BP_ERR_INVALID;
+    }
     return launch_scatter_wk<float>(a, spike_list, n_spikes, max_spikes, y, events_total, mode, s);
 }
 
@@ -692,9 +788,10 @@ bp_status launch_event_csrmv(const CsrArgs& a, const int32_t* spike_list, const 
 namespace {
 
 int mode_from_flags(uint32_t flags) {
-    if (flags & BP_ACC_GLOBAL) return 1;
-    if (flags & BP_ACC_SHARED) return 2;
-    return 0;
+    const int fixed = (flags & BP_ACC_FIXED) ? bp::kModeFixed : 0;
+    if (flags & BP_ACC_GLOBAL) return 1 | fixed;
+    if (flags & BP_ACC_SHARED) return 2 | fixed;
+    return fixed;
 }
 
 bp::CsrArgs make_csr(int64_t n_pre, int64_t n_post, const int64_t* indptr, const int32_t* indices, const void* data,
@@ -709,6 +806,11 @@ bp::CsrArgs make_csr(int64_t n_pre, int64_t n_post, const int64_t* indptr, const
     a.w_homo = w_homo;
     a.tile_ptr = tile_ptr;
     a.tile_cols = tile_cols;
+    a.w_bound = nullptr;
+    if (tile_ptr && tile_cols > 0 && n_pre >= 0 && n_post >= 0) {
+        const int64_t S = (n_post + tile_cols - 1) / tile_cols;
+        a.w_bound = tile_ptr + n_pre * (S + 1);  // the last entry of the index
+    }
     return a;
 }
 
@@ -761,7 +863,7 @@ bp_status bp_event_csrmv_dense(int64_t n_pre, int64_t n_post, const int64_t* ind
 int64_t bp_csr_tile_index_size(int64_t n_pre, int64_t n_post, int32_t tile_cols) {
     if (n_pre < 0 || n_post < 0 || tile_cols <= 0) return -1;
     const int64_t S = (n_post + tile_cols - 1) / tile_cols;
-    return n_pre * (S + 1);
+    return n_pre * (S + 1) + 1;  // + the weight-bound slot
 }
 
 bp_status bp_csr_tile_index(int64_t n_pre, int64_t n_post, const int64_t* indptr, const int32_t* indices,
@@ -771,13 +873,50 @@ bp_status bp_csr_tile_index(int64_t n_pre, int64_t n_post, const int64_t* indptr
     BP_REQUIRE(tile_cols > 0 && tile_cols % 32 == 0 && tile_cols <= bp::kTileCols,
                "tile_cols %d must be a positive multiple of 32 <= %d", tile_cols, bp::kTileCols);
     BP_REQUIRE(n_pre == 0 || (indptr && indices && tile_ptr), "a required pointer is NULL");
-    if (n_pre == 0) return BP_OK;
+    if (n_pre == 0) {  // only the weight-bound slot
+        if (tile_ptr) BP_CUDA(cudaMemsetAsync(tile_ptr, 0, sizeof(int32_t), stream));
+        return BP_OK;
+    }
     const int32_t S = static_cast<int32_t>((n_post + tile_cols - 1) / tile_cols);
     const int64_t total = n_pre * (S + 1);
     int64_t grid = (total + 255) / 256;
     if (grid > bp::sm_count() * 32) grid = bp::sm_count() * 32;
     bp::k_tile_index<<<static_cast<unsigned>(grid), 256, 0, stream>>>(n_pre, indptr, indices, tile_cols, S,
                                                                        tile_ptr);
+    BP_LAUNCHED();
+    return BP_OK;
+}
+
+bp_status bp_csr_tile_weight_bound(int64_t n_pre, int64_t n_post, const int64_t* indptr, const int32_t* indices,
+                                   const void* data, int32_t wkind, float w_homo, int32_t tile_cols, int32_t* tile_ptr,
+                                   bp_stream_t stream) {
+    bp::clear_error();
+    BP_REQUIRE(n_pre >= 0 && n_post >= 0 && n_pre <= INT32_MAX && n_post <= INT32_MAX, "bad sizes");
+    BP_REQUIRE(tile_cols > 0 && tile_cols % 32 == 0 && tile_cols <= bp::kTileCols,
+               "tile_cols %d must be a positive multiple of 32 <= %d", tile_cols, bp::kTileCols);
+    BP_REQUIRE(wkind >= BP_W_HOMO && wkind <= BP_W_BF16, "unknown weight kind %d", wkind);
+    BP_REQUIRE(tile_ptr != nullptr, "tile_ptr is NULL");
+    BP_REQUIRE(n_pre == 0 || (indptr && indices), "indptr or indices is NULL");
+    BP_REQUIRE(wkind == BP_W_HOMO || n_pre == 0 || data != nullptr, "weights are NULL for a non-homogeneous kind");
+    const int64_t S = (n_post + tile_cols - 1) / tile_cols;
+    int32_t* slot = tile_ptr + n_pre * (S + 1);
+    BP_CUDA(cudaMemsetAsync(slot, 0, sizeof(int32_t), stream));
+    int64_t grid = (n_pre * 32 + 255) / 256;
+    if (grid > bp::sm_count() * 16) grid = bp::sm_count() * 16;
+    if (grid < 1) grid = 1;
+    switch (wkind) {
+        case BP_W_F32:
+            bp::k_tile_weight_bound<bp::WK_F32><<<static_cast<unsigned>(grid), 256, 0, stream>>>(n_pre, indptr, indices,
+                                                                                                 data, w_homo, slot);
+            break;
+        case BP_W_BF16:
+            bp::k_tile_weight_bound<bp::WK_BF16><<<static_cast<unsigned>(grid), 256, 0, stream>>>(n_pre, indptr, indices,
+                                                                                                  data, w_homo, slot);
+            break;
+        default:
+            bp::k_tile_weight_bound<bp::WK_HOMO><<<static_cast<unsigned>(grid), 256, 0, stream>>>(n_pre, indptr, indices,
+                                                                                                  data, w_homo, slot);
+    }
     BP_LAUNCHED();
     return BP_OK;
 }

@@ -71,6 +71,7 @@ bp_status bp_event_csrmv_dense_noalloc(int64_t n_pre, int64_t n_post, const int6
     a.w_homo = w_homo;
     a.tile_ptr = nullptr;
     a.tile_cols = 0;
+    a.w_bound = nullptr;
     BP_REQUIRE(n_post >= 0 && n_post <= INT32_MAX, "bad n_post");
     BP_REQUIRE(indptr != nullptr, "indptr is NULL");
     BP_REQUIRE(wkind >= BP_W_HOMO && wkind <= BP_W_BF16, "unknown weight kind %d", wkind);

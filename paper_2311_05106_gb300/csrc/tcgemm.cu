@@ -359,12 +359,22 @@ TcShape make_shape(int32_t B, int32_t T, int32_t na, int32_t ns) {
     s.na_pad = static_cast<int32_t>(round_up(na, kTcM));
     s.ns = ns;
     s.ns_pad = static_cast<int32_t>(round_up(ns, kTcN));
+    // K splits: the fewest that minimise (waves of CTAs) x (k blocks per CTA),
+    // so that the tiles x splits CTAs fill the SMs (one CTA per SM); at most
+    // 16 splits, at least 4 k blocks each (the stage pipeline's depth)
     const int64_t tiles = static_cast<int64_t>(s.na_pad / kTcM) * (s.ns_pad / kTcN);
-    int64_t splits = sm_count() / (tiles > 0 ? tiles : 1);
-    if (splits < 1) splits = 1;
-    if (splits > 16) splits = 16;
-    if (splits > s.KB) splits = s.KB > 0 ? s.KB : 1;
-    s.splits = static_cast<int32_t>(splits);
+    const int64_t sms = sm_count();
+    int64_t best = 1, best_cost = -1;
+    for (int64_t sp = 1; sp <= 16; ++sp) {
+        if (sp > 1 && s.KB / sp < 4) break;
+        const int64_t waves = (tiles * sp + sms - 1) / sms;
+        const int64_t cost = waves * ((s.KB + sp - 1) / sp);
+        if (best_cost < 0 || cost < best_cost) {
+            best = sp;
+            best_cost = cost;
+        }
+    }
+    s.splits = static_cast<int32_t>(best);
     return s;
 }
 

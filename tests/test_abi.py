@@ -63,7 +63,7 @@ def test_host_only_helpers(libpath):
     assert B.bp_jit_desc_init(7, 80.0 / 4e6).K == 99999
     with pytest.raises(B.BpError):
         B.bp_jit_desc_init(7, 0.0)
-    assert B.bp_csr_tile_index_size(10, 100000, 57344) == 10 * 3
+    assert B.bp_csr_tile_index_size(10, 100000, 57344) == 10 * 3 + 1  # + the weight-bound slot
     import oracle as orc
     for s in (0, 2024, 2**63 + 5):
         for j in (0, 1):
@@ -148,6 +148,10 @@ def test_operator_and_constructor_host_checks(libpath):
              b"weights are NULL")
     rejected(L.bp_event_csrmv(10, 10, fake, fake, None, H, 1.0, fake, fake, 5, fake, 1, fake, 100, 0, None),
              b"tile_cols")
+    rejected(L.bp_event_csrmv(10, 10, fake, fake, fake, F32, 1.0, fake, fake, 5, fake, 0, None, 0,
+                              B.BP_ACC_FIXED, None), b"BP_ACC_FIXED")
+    rejected(L.bp_csr_tile_weight_bound(10, 10, fake, fake, None, F32, 1.0, 32, fake, None), b"weights are NULL")
+    rejected(L.bp_csr_tile_weight_bound(10, 10, fake, fake, fake, F32, 1.0, 33, fake, None), b"tile_cols")
     rejected(L.bp_event_csrmv_t(10, 10, None, fake, None, H, 1.0, fake, fake, None, 0, 0, None), b"indptr")
     rejected(L.bp_event_csrmv_t(10, 10, fake, fake, None, H, 1.0, None, fake, None, 0, 0, None), b"x_post")
     d = B.JitDesc()                      # K = 0: not initialised

@@ -216,7 +216,9 @@ def test_tile_index_matches_searchsorted():
     tp = torch.empty(B.bp_csr_tile_index_size(n_pre, n_post, tc), dtype=torch.int32, device="cuda")
     B.bp_csr_tile_index(cuda(ip), cuda(ix), n_post, tc, tp)
     S = -(-n_post // tc)
-    got = tp.cpu().numpy().reshape(n_pre, S + 1)
+    flat = tp.cpu().numpy()
+    assert flat.size == n_pre * (S + 1) + 1 and flat[-1] == 0  # the weight-bound slot starts empty
+    got = flat[:-1].reshape(n_pre, S + 1)
     for i in range(0, n_pre, 37):
         row = ix[ip[i]:ip[i + 1]]
         bounds = np.searchsorted(row, np.arange(S) * tc, side="left")
@@ -607,3 +609,123 @@ def test_tiled_counts_accumulate_into_negative_outputs():
     expect = y0.astype(np.int64) + orc.event_csr_count(ip, ix, ev, n_post)
     assert np.array_equal(y.cpu().numpy().astype(np.int64), expect)
     assert (y0 < 0).sum() > 10000
+
+
+# ---------------------------------------------------------------------- fixed-point tile sums
+def _tile_index(dip, dix, n_pre, n_post, tcols):
+    tp = torch.empty(B.bp_csr_tile_index_size(n_pre, n_post, tcols), dtype=torch.int32, device="cuda")
+    B.bp_csr_tile_index(dip, dix, n_post, tcols, tp)
+    return tp
+
+
+def _fixed_bound(counts_col, abs_col, n_spk, b):
+    """Bound on |fixed-point result - exact| per column (bp_event_csrmv,
+    BP_ACC_FIXED): each event off by at most 2^-(s+1) <= m b 2^-29 with m at
+    most the number of spiking rows, plus the FP32 conversion of each CTA's
+    tile and the FP32 adds into y (at most 152 of them per column), each
+    rounding by 2^-24 of a partial sum no larger than the column's sum of
+    absolute values."""
+    return counts_col * (n_spk * b * 2.0 ** -29) + abs_col * 2.0 ** -24 * 2 * 153 + 1e-30
+
+
+@pytest.mark.parametrize("n_pre,n_post,p,rho,tcols", [(300, 257, 0.1, 0.3, 64), (5000, 40001, 0.02, 0.05, 4096),
+                                                      (2000, 150001, 0.004, 0.2, 54944), (1, 1, 1.0, 1.0, 32)])
+@pytest.mark.parametrize("wdt", ["f32", "bf16"])
+def test_fixed_point_tiles_within_their_bound(n_pre, n_post, p, rho, tcols, wdt):
+    """BP_ACC_FIXED against the oracle's FP64 product, with weights of both
+    signs over four decades, within the bound the fixed-point arithmetic
+    gives (bp.h); the recorded weight bound is the largest |w| (rows have no
+    repeated column here), rounded up."""
+    ip, ix = _csr(n_pre, n_post, p, seed=n_pre + 31)
+    rng = np.random.default_rng(n_pre)
+    w = (rng.choice([-1.0, 1.0], size=len(ix)) * 10.0 ** rng.uniform(-3, 1, size=len(ix))).astype(np.float32)
+    ev = wl.bernoulli_spikes(n_pre, rho, seed=n_pre + 5)
+    dip, dix = cuda(ip), cuda(ix)
+    tp = _tile_index(dip, dix, n_pre, n_post, tcols)
+    dw = cuda(w) if wdt == "f32" else cuda(w).to(torch.bfloat16)
+    wref = dw.float().cpu().numpy().astype(np.float64)
+    B.bp_csr_tile_weight_bound(dip, dix, dw, 0.0, n_post, tcols, tp)
+    b = float(tp[-1:].cpu().numpy().view(np.float32)[0])
+    amax = float(np.abs(wref).max()) if len(wref) else 0.0
+    assert amax <= b <= amax * (1 + 2.0 ** -15) or (amax == 0.0 and b > 0.0)
+    sl, ns = spike_list_of(ev)
+    y = torch.zeros(n_post, dtype=torch.float32, device="cuda")
+    B.bp_event_csrmv(dip, dix, dw, 0.0, sl, ns, y, tile_ptr=tp, tile_cols=tcols,
+                     flags=B.BP_ACC_SHARED | B.BP_ACC_FIXED)
+    assert B.bp_sync_status() == 0
+    ref = orc.event_csrmv(ip, ix, wref, ev, n_post)
+    cnt = orc.event_csr_count(ip, ix, ev, n_post).astype(np.float64)
+    absc = orc.event_csrmv(ip, ix, np.abs(wref), ev, n_post)
+    err = np.abs(y.cpu().numpy().astype(np.float64) - ref)
+    assert np.all(err <= _fixed_bound(cnt, absc, int(ev.sum()), b))
+    # and typically as close as an FP32 sum
+    if ref.size and np.abs(ref).max() > 0:
+        assert rel_err(y.cpu().numpy(), ref) < RTOL_F32
+
+
+def test_fixed_point_tiles_do_not_depend_on_event_order():
+    """With one CTA per tile (as many tiles as SMs, n_post above the one-tile
+    size) every column's sum is one CTA's integer tile sum: any order of the
+    spike list gives the same result bit for bit."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    cap = B.bp_tile_cols()  # at or below this n_post one tile covers y and the index is not used
+    tcols = 32 * (-(-(cap + 1) // (32 * sms)))
+    n_post = sms * tcols
+    assert n_post > cap
+    n_pre = 3000
+    ip, ix = _csr(n_pre, n_post, 0.02, seed=77)
+    w = wl.normal_weights(len(ix), 0.5, 0.3, seed=78)
+    ev = wl.bernoulli_spikes(n_pre, 0.3, seed=79)
+    dip, dix, dw = cuda(ip), cuda(ix), cuda(w)
+    tp = _tile_index(dip, dix, n_pre, n_post, tcols)
+    B.bp_csr_tile_weight_bound(dip, dix, dw, 0.0, n_post, tcols, tp)
+    ids = np.nonzero(ev)[0].astype(np.int32)
+    outs = []
+    for perm in (ids, ids[::-1], np.random.default_rng(1).permutation(ids)):
+        sl = torch.zeros(n_pre, dtype=torch.int32, device="cuda")
+        sl[: len(perm)] = cuda(perm.astype(np.int32))
+        ns = torch.tensor([len(perm)], dtype=torch.int32, device="cuda")
+        y = torch.zeros(n_post, dtype=torch.float32, device="cuda")
+        B.bp_event_csrmv(dip, dix, dw, 0.0, sl, ns, y, tile_ptr=tp, tile_cols=tcols,
+                         flags=B.BP_ACC_SHARED | B.BP_ACC_FIXED)
+        outs.append(y.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+    assert rel_err(outs[0], orc.event_csrmv(ip, ix, w.astype(np.float64), ev, n_post)) < RTOL_F32
+
+
+def test_weight_bound_sums_repeated_columns():
+    """A row that repeats a column contributes the sum of those entries: the
+    bound is the largest such per-row, per-column absolute sum."""
+    ip = np.array([0, 3, 5], np.int64)
+    ix = np.array([2, 2, 7, 1, 1], np.int32)
+    w = np.array([0.5, -0.75, 0.25, 1.0, 0.125], np.float32)
+    tcols = 32
+    dip, dix, dw = cuda(ip), cuda(ix), cuda(w)
+    tp = _tile_index(dip, dix, 2, 40, tcols)
+    assert int(tp[-1].item()) == 0  # no bound yet
+    B.bp_csr_tile_weight_bound(dip, dix, dw, 0.0, 40, tcols, tp)
+    b = float(tp[-1:].cpu().numpy().view(np.float32)[0])
+    assert 1.25 <= b <= 1.25 * (1 + 2.0 ** -15)
+    B.bp_csr_tile_weight_bound(dip, dix, None, -3.0, 40, tcols, tp)  # homogeneous: |w| times the longest run
+    b = float(tp[-1:].cpu().numpy().view(np.float32)[0])
+    assert 6.0 <= b <= 6.0 * (1 + 2.0 ** -15)
+
+
+def test_fixed_point_without_a_bound_is_reported():
+    """BP_ACC_FIXED on a tile index whose bound was never recorded: the kernel
+    adds nothing and records BP_ERR_DEVICE; without any tile index the call
+    is rejected on the host."""
+    n_pre, n_post, tcols = 500, 4000, 1024
+    ip, ix = _csr(n_pre, n_post, 0.05, seed=3)
+    dip, dix = cuda(ip), cuda(ix)
+    dw = cuda(wl.normal_weights(len(ix), 0.5, 0.1, seed=4))
+    tp = _tile_index(dip, dix, n_pre, n_post, tcols)
+    sl, ns = spike_list_of(wl.bernoulli_spikes(n_pre, 0.5, seed=5))
+    y = torch.zeros(n_post, dtype=torch.float32, device="cuda")
+    B.bp_event_csrmv(dip, dix, dw, 0.0, sl, ns, y, tile_ptr=tp, tile_cols=tcols,
+                     flags=B.BP_ACC_SHARED | B.BP_ACC_FIXED)
+    assert B.bp_sync_status() == B.BP_ERR_DEVICE
+    assert B.bp_sync_status() == 0  # the status word was cleared
+    assert torch.count_nonzero(y).item() == 0
+    with pytest.raises(B.BpError):
+        B.bp_event_csrmv(dip, dix, dw, 0.0, sl, ns, y, flags=B.BP_ACC_SHARED | B.BP_ACC_FIXED)
