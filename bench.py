@@ -258,19 +258,10 @@ def aggregate_ranks(torch, dist, ms, events, device):
 
 
 def launches_in_simulate(steps, host_step_before):
-    """Kernels bp_simulate enqueues: one fused step kernel per step, one
-    chunk-advance per 64-step graph and per leftover group, two record set-ups."""
-    n = 2
-    done = 0
-    if host_step_before % 2 == 1 and steps > 0:
-        n += 2
-        done = 1
-    chunks = (steps - done) // 64
-    n += chunks * (64 + 1)
-    rem = steps - done - chunks * 64
-    if rem > 0:
-        n += rem + 1
-    return n
+    """Kernels bp_simulate enqueues without a record: one fused step kernel per
+    step (the last step of each graph, or an eager step, also advances the
+    device step counter, in the same kernel)."""
+    return steps
 
 
 def lif_kernel_time(torch, B, net, reps=50):

@@ -50,6 +50,8 @@ struct NetCtrl {
     int64_t record_base;   // value of `step` when the current record began
     int32_t* record;       // [T][2] or NULL
     int64_t record_len;    // T
+    uint32_t done_ctas;    // CTAs of the current step launch that have finished (the last advances `step`)
+    uint32_t pad;
 };
 
 // Stored CSR operand of the event products.
@@ -96,7 +98,7 @@ struct NetStepLaunch {
     int32_t* spike_list;   // nullable
     int32_t* n_spikes;     // [2], used with spike_list
     int64_t* totals;
-    const NetCtrl* ctrl;
+    NetCtrl* ctrl;
     bool counts;
     bool jit;
     CsrArgs csr;
@@ -115,7 +117,11 @@ bp_status launch_lif_step(const LifConst& c, int64_t n, int64_t n_e, float* V, f
                           uint8_t* ref, void* ye, void* yi, bool counts, const float* I_vec, uint8_t* spk,
                           int32_t* spike_list, int32_t* n_spikes, int32_t* clear_counter,
                           int64_t* totals, const NetCtrl* ctrl, int32_t t_local, cudaStream_t s);
-bp_status launch_network_step(const NetStepLaunch& L, int parity, int32_t t_local, cudaStream_t s);
+// advance > 0: the launch's last CTA to finish adds `advance` to the device
+// step counter and to totals[3] (the last step of a captured chunk, or an
+// eager step), so no separate kernel is needed for it.
+bp_status launch_network_step(const NetStepLaunch& L, int parity, int32_t t_local, cudaStream_t s,
+                              int32_t advance = 0);
 bp_status launch_spike_compact(int64_t n, const uint8_t* events, int32_t* spike_list, int32_t* n_spikes,
                                cudaStream_t s);
 

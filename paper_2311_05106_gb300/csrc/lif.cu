@@ -61,6 +61,9 @@ struct StepArgs {
     // delay ring: ring_slots counts, then ring_slots lists of n spike ids
     int32_t* ring;
     int32_t ring_slots, delay_e, delay_i;
+    // the step counter advance done by the launch's last CTA (0: none)
+    NetCtrl* adv_ctrl;
+    int32_t advance;
 };
 
 struct StepSmem {
@@ -71,6 +74,24 @@ struct StepSmem {
     int32_t ring_base;
     long long red[3][kStepWarps];
 };
+
+// The last CTA of the launch to finish advances the device step counter by
+// a.advance (and the step total): every CTA has finished reading the counter
+// when it counts itself done, so no CTA of this launch sees the new value.
+__device__ __forceinline__ void advance_step_counter(const StepArgs& a) {
+    if (a.advance == 0 || a.adv_ctrl == nullptr) return;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned prev = atomicAdd(&a.adv_ctrl->done_ctas, 1u);
+        if (prev == gridDim.x - 1) {
+            a.adv_ctrl->done_ctas = 0;
+            a.adv_ctrl->step += a.advance;
+            if (a.totals) a.totals[3] += a.advance;
+            __threadfence();
+        }
+    }
+}
 
 template <bool COUNTS, int VEC, int CONN, int WK, bool RING = false>
 __global__ void __launch_bounds__(kStepThreads, 4) k_step(StepArgs a) {
@@ -334,6 +355,7 @@ __global__ void __launch_bounds__(kStepThreads, 4) k_step(StepArgs a) {
             }
         }
     }
+    advance_step_counter(a);
 }
 
 struct TraceArgs {
@@ -550,8 +572,10 @@ bp_status launch_lif_step(const LifConst& c, int64_t n, int64_t n_e, float* V, f
     return launch_step(a, counts, CONN_NONE, WK_HOMO, s);
 }
 
-bp_status launch_network_step(const NetStepLaunch& L, int parity, int32_t t_local, cudaStream_t s) {
+bp_status launch_network_step(const NetStepLaunch& L, int parity, int32_t t_local, cudaStream_t s, int32_t advance) {
     StepArgs a = base_args(L.c, L.n, L.n_e, L.V, L.ge, L.gi, L.ref);
+    a.adv_ctrl = advance > 0 ? L.ctrl : nullptr;
+    a.advance = advance > 0 ? advance : 0;
     const size_t half = static_cast<size_t>(L.n) * 4;
     char* ye = static_cast<char*>(L.ye2);
     char* yi = static_cast<char*>(L.yi2);

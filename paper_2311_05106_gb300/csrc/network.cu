@@ -40,11 +40,6 @@ namespace {
 
 constexpr int kChunk = 64;  // steps per captured graph (even: the counter slots alternate)
 
-__global__ void k_advance(NetCtrl* ctrl, int64_t* totals, int64_t k) {
-    ctrl->step += k;
-    totals[3] += k;
-}
-
 __global__ void k_set_record(NetCtrl* ctrl, int32_t* record, int64_t len) {
     ctrl->record = record;
     ctrl->record_base = ctrl->step;
@@ -58,6 +53,7 @@ __global__ void k_reset_ctrl(NetCtrl* ctrl) {
     ctrl->record = nullptr;
     ctrl->record_base = 0;
     ctrl->record_len = 0;
+    ctrl->done_ctas = 0;
 }
 
 // FP64 rates from the exact integer totals.
@@ -71,18 +67,15 @@ __global__ void k_stats(const int64_t* totals, int64_t n, int64_t n_e, double dt
     out[3] = steps > 0 ? static_cast<double>(totals[2]) / steps : 0.0;
 }
 
-bp_status enqueue_step(bp_net* net, int parity, int32_t t_local, cudaStream_t s) {
-    return launch_network_step(net->L, parity, t_local, s);
+// One step; advance > 0: its last CTA also advances the device step counter
+// by `advance` (the steps this launch closes).
+bp_status enqueue_step(bp_net* net, int parity, int32_t t_local, cudaStream_t s, int32_t advance) {
+    return launch_network_step(net->L, parity, t_local, s, advance);
 }
 
-bp_status advance(bp_net* net, int64_t k, cudaStream_t s) {
-    k_advance<<<1, 1, 0, s>>>(net->ctrl, net->d.totals, k);
-    BP_LAUNCHED();
-    return BP_OK;
-}
-
-// Graph of `len` steps starting on an even step (counter slot 0), followed by
-// the advance of the device step counter; captured once per length and cached.
+// Graph of `len` steps starting on an even step (counter slot 0); the last
+// step advances the device step counter by len.  Captured once per length and
+// cached.
 bp_status get_graph(bp_net* net, int len, cudaGraphExec_t* out) {
     auto it = net->graphs->find(len);
     if (it != net->graphs->end()) {
@@ -92,8 +85,7 @@ bp_status get_graph(bp_net* net, int len, cudaGraphExec_t* out) {
     if (!net->cap_stream) BP_CUDA(cudaStreamCreateWithFlags(&net->cap_stream, cudaStreamNonBlocking));
     BP_CUDA(cudaStreamBeginCapture(net->cap_stream, cudaStreamCaptureModeThreadLocal));
     bp_status st = BP_OK;
-    for (int t = 0; t < len && st == BP_OK; ++t) st = enqueue_step(net, t & 1, t, net->cap_stream);
-    if (st == BP_OK) st = advance(net, len, net->cap_stream);
+    for (int t = 0; t < len && st == BP_OK; ++t) st = enqueue_step(net, t & 1, t, net->cap_stream, t == len - 1 ? len : 0);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(net->cap_stream, &g);
     if (st != BP_OK) {
@@ -257,8 +249,7 @@ bp_status bp_network_set_step_count(bp_net* net, int64_t step, bp_stream_t strea
 bp_status bp_network_step(bp_net* net, bp_stream_t stream) {
     bp::clear_error();
     BP_REQUIRE(net, "net is NULL");
-    BP_TRY(bp::enqueue_step(net, static_cast<int>(net->host_step & 1), 0, stream));
-    BP_TRY(bp::advance(net, 1, stream));
+    BP_TRY(bp::enqueue_step(net, static_cast<int>(net->host_step & 1), 0, stream, 1));
     net->host_step += 1;
     return BP_OK;
 }
@@ -285,14 +276,16 @@ bp_status bp_simulate(bp_net* net, int64_t T, int32_t* record, bp_stream_t strea
     BP_REQUIRE(net, "net is NULL");
     BP_REQUIRE(T >= 0, "T < 0");
     if (T == 0) return BP_OK;
-    if (record) BP_CUDA(cudaMemsetAsync(record, 0, static_cast<size_t>(T) * 2 * sizeof(int32_t), stream));
-    bp::k_set_record<<<1, 1, 0, stream>>>(net->ctrl, record, record ? T : 0);
-    BP_LAUNCHED();
+    // the record is attached only for this call (every call leaves it detached)
+    if (record) {
+        BP_CUDA(cudaMemsetAsync(record, 0, static_cast<size_t>(T) * 2 * sizeof(int32_t), stream));
+        bp::k_set_record<<<1, 1, 0, stream>>>(net->ctrl, record, T);
+        BP_LAUNCHED();
+    }
     int64_t done = 0;
     // the captured chunk starts on an even counter slot
     if (net->host_step & 1) {
-        BP_TRY(bp::enqueue_step(net, 1, 0, stream));
-        BP_TRY(bp::advance(net, 1, stream));
+        BP_TRY(bp::enqueue_step(net, 1, 0, stream, 1));
         net->host_step += 1;
         done = 1;
     }
@@ -313,8 +306,10 @@ bp_status bp_simulate(bp_net* net, int64_t T, int32_t* record, bp_stream_t strea
         net->host_step += rem;
     }
     // detach the record so that later steps do not write into it
-    bp::k_set_record<<<1, 1, 0, stream>>>(net->ctrl, nullptr, 0);
-    BP_LAUNCHED();
+    if (record) {
+        bp::k_set_record<<<1, 1, 0, stream>>>(net->ctrl, nullptr, 0);
+        BP_LAUNCHED();
+    }
     return BP_OK;
 }
 
