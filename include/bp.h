@@ -669,7 +669,8 @@ bp_status bp_snn_reg_loss(const bp_snn_desc* d, const void* workspace, float* lo
  * is exact to 2^-17 relative and the sum is FP32.  The same inputs give the
  * same result bit for bit.  work: device workspace of at least
  * bp_spike_outer_workspace(K, M, N) bytes, 1024-byte aligned, owned by the
- * caller (the call packs both operands into it).  K <= 2^31 - 1.  K, M or N
+ * caller (the call packs both operands into it).  K <= 2^31 - 1 and
+ * M N < 2^31 (BP_ERR_INVALID otherwise).  K, M or N
  * zero: nothing to add (BP_OVERWRITE still zeroes out). */
 size_t bp_spike_outer_workspace(int64_t K, int32_t M, int32_t N);
 bp_status bp_spike_outer(const uint8_t* x, const float* delta, int64_t K, int32_t M, int32_t N, float* out,

@@ -130,14 +130,16 @@ __global__ void __launch_bounds__(256) k_pack_hilo(TcShape s, const float* __res
     __shared__ float tile[kTcKB][129];
     const int64_t kb = blockIdx.x;
     const int rb = blockIdx.y;
+    // T_pad is a multiple of 64: the block's 64 k share one batch element
     const int64_t k0 = kb * kTcKB;
+    const int64_t b = k0 / s.T_pad, t0 = k0 - b * s.T_pad;
+    const float* db = d + b * s.T * static_cast<int64_t>(s.na);
     for (int e = threadIdx.x; e < kTcKB * 128; e += 256) {
-        const int kk = e / 128, r = e % 128;
-        const int64_t k = k0 + kk;
-        const int64_t b = k / s.T_pad, t = k % s.T_pad;
+        const int kk = e >> 7, r = e & 127;
+        const int64_t t = t0 + kk;
         const int a = rb * 128 + r;
         float v = 0.f;
-        if (t < s.T && a < s.na) v = d[(b * s.T + t) * s.na + a];
+        if (t < s.T && a < s.na) v = db[t * s.na + a];
         tile[kk][r] = v;
     }
     __syncthreads();
@@ -164,28 +166,37 @@ __global__ void __launch_bounds__(256) k_pack_hilo(TcShape s, const float* __res
 // Binary X -> BF16 blocks [ns_pad / 128][KB][16 KB].  Feature s < n_dense is
 // x_dense[b][t][s] != 0 (u8, row stride n_dense); feature n_dense + i is bit
 // i of z_bits[b][t - 1] (words of zw per step; zero at t = 0), i < n_bits.
+// One CTA per block: each warp takes 8 of the 64 k and, per k, forms the bits
+// of 32 features at a time with a ballot; the block's 64 x 128 bits are then
+// written out as BF16 0 / 1 in the swizzled layout.
 __global__ void __launch_bounds__(256) k_pack_spikes(TcShape s, const uint8_t* __restrict__ x_dense, int32_t n_dense,
                                                     const uint32_t* __restrict__ z_bits, int32_t n_bits, int32_t zw,
                                                     uint8_t* __restrict__ out) {
-    __shared__ uint8_t tile[kTcKB][132];
+    __shared__ uint32_t bits[kTcKB][4];  // [k][32-feature group]
     const int64_t kb = blockIdx.x;
     const int rb = blockIdx.y;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // T_pad is a multiple of 64: the block's 64 k share one batch element
     const int64_t k0 = kb * kTcKB;
-    for (int e = threadIdx.x; e < kTcKB * 128; e += 256) {
-        const int kk = e / 128, r = e % 128;
-        const int64_t k = k0 + kk;
-        const int64_t b = k / s.T_pad, t = k % s.T_pad;
-        const int f = rb * 128 + r;
-        uint8_t v = 0;
-        if (t < s.T) {
-            if (f < n_dense) {
-                v = x_dense[(b * s.T + t) * n_dense + f] != 0;
-            } else if (f - n_dense < n_bits && t > 0) {
-                const int i = f - n_dense;
-                v = (z_bits[(b * s.T + t - 1) * zw + (i >> 5)] >> (i & 31)) & 1u;
+    const int64_t b = k0 / s.T_pad, t0 = k0 - b * s.T_pad;
+    const int64_t row0 = b * s.T;  // step (b, 0)
+    for (int kk = warp; kk < kTcKB; kk += 8) {
+        const int64_t t = t0 + kk;
+#pragma unroll
+        for (int grp = 0; grp < 4; ++grp) {
+            const int f = rb * 128 + grp * 32 + lane;
+            bool v = false;
+            if (t < s.T) {
+                if (f < n_dense) {
+                    v = x_dense[(row0 + t) * n_dense + f] != 0;
+                } else if (f - n_dense < n_bits && t > 0) {
+                    const int i = f - n_dense;
+                    v = (z_bits[(row0 + t - 1) * zw + (i >> 5)] >> (i & 31)) & 1u;
+                }
             }
+            const unsigned m = __ballot_sync(FULL_MASK, v);
+            if (lane == 0) bits[kk][grp] = m;
         }
-        tile[kk][r] = v;
     }
     __syncthreads();
     uint8_t* o = out + (static_cast<int64_t>(rb) * s.KB + kb) * kTcBlock;
@@ -193,10 +204,13 @@ __global__ void __launch_bounds__(256) k_pack_spikes(TcShape s, const uint8_t* _
     for (int u = threadIdx.x; u < 1024; u += 256) {
         const int r = u >> 3, c = u & 7;
         const int kc = c ^ (r & 7);
+        const int g = r >> 5, sh = r & 31;
         uint32_t w[4];
 #pragma unroll
-        for (int p = 0; p < 4; ++p)
-            w[p] = (tile[8 * kc + 2 * p][r] ? one : 0u) | ((tile[8 * kc + 2 * p + 1][r] ? one : 0u) << 16);
+        for (int p = 0; p < 4; ++p) {
+            const uint32_t lo = (bits[8 * kc + 2 * p][g] >> sh) & 1u, hi = (bits[8 * kc + 2 * p + 1][g] >> sh) & 1u;
+            w[p] = (lo ? one : 0u) | ((hi ? one : 0u) << 16);
+        }
         reinterpret_cast<uint4*>(o)[u] = make_uint4(w[0], w[1], w[2], w[3]);
     }
 }
@@ -333,15 +347,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_spike_gemm(TcShape s, cons
     }
 }
 
-// G[s][a] (+)= sum over splits of part[split][s][a] (splits in order).
+// G[s][a] (+)= sum over splits of part[split][s][a] (splits in order), one
+// element per thread and pass (32-bit index arithmetic: ns na < 2^31 is
+// checked at launch).
 __global__ void k_tc_reduce(TcShape s, const float* __restrict__ part, float* __restrict__ g, int64_t ldg,
                             int32_t accumulate) {
-    const int64_t n = static_cast<int64_t>(s.ns) * s.na;
-    for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < n;
-         e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int64_t r = e / s.na, c = e % s.na;
+    const int32_t n = s.ns * s.na;
+    const int64_t plane = static_cast<int64_t>(s.ns_pad) * s.na_pad;
+    for (int32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        const int32_t r = e / s.na, c = e - r * s.na;
+        const float* pr = part + static_cast<int64_t>(r) * s.na_pad + c;
         float acc = 0.f;
-        for (int p = 0; p < s.splits; ++p) acc += part[(static_cast<int64_t>(p) * s.ns_pad + r) * s.na_pad + c];
+        for (int p = 0; p < s.splits; ++p) acc += pr[p * plane];
         float* o = g + r * ldg + c;
         *o = accumulate ? *o + acc : acc;
     }
@@ -420,6 +437,8 @@ bp_status launch_tc_spike_gemm(int32_t B, int32_t T, const float* d, int32_t na,
                work_bytes);
     BP_REQUIRE((reinterpret_cast<uintptr_t>(work) & 1023u) == 0, "workspace must be 1024-byte aligned");
     BP_REQUIRE(s.KB <= 0x7FFFFFFF, "too many k blocks");
+    BP_REQUIRE(static_cast<int64_t>(ns) * na < (int64_t(1) << 31), "the output's rows x columns must be below 2^31");
+    BP_REQUIRE(s.na_pad / 128 <= 65535 && s.ns_pad / 128 <= 65535, "more than 8 388 480 features on one side");
     k_pack_hilo<<<dim3(static_cast<unsigned>(s.KB), s.na_pad / 128), 256, 0, st>>>(s, d, w.dhi, w.dlo);
     BP_LAUNCHED();
     k_pack_spikes<<<dim3(static_cast<unsigned>(s.KB), s.ns_pad / 128), 256, 0, st>>>(s, x_dense, n_dense, z_bits,
@@ -429,9 +448,8 @@ bp_status launch_tc_spike_gemm(int32_t B, int32_t T, const float* d, int32_t na,
     const int grid = (s.na_pad / kTcM) * (s.ns_pad / kTcN) * s.splits;
     k_tc_spike_gemm<<<grid, kTcThreads, kTcSmem, st>>>(s, w.dhi, w.dlo, w.xs, w.part, device_status_ptr());
     BP_LAUNCHED();
-    const int64_t n = static_cast<int64_t>(ns) * na;
-    int64_t rg = (n + 255) / 256;
-    if (rg > static_cast<int64_t>(sm_count()) * 8) rg = static_cast<int64_t>(sm_count()) * 8;
+    int64_t rg = (static_cast<int64_t>(ns) * na + 255) / 256;
+    if (rg > static_cast<int64_t>(sm_count()) * 16) rg = static_cast<int64_t>(sm_count()) * 16;
     k_tc_reduce<<<static_cast<unsigned>(rg), 256, 0, st>>>(s, w.part, g, ldg, accumulate ? 1 : 0);
     BP_LAUNCHED();
     return BP_OK;
