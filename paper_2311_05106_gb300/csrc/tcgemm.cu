@@ -180,32 +180,24 @@ __global__ void __launch_bounds__(256) k_pack_spikes(TcShape s, const uint8_t* _
     const int64_t k0 = kb * kTcKB;
     const int64_t b = k0 / s.T_pad, t0 = k0 - b * s.T_pad;
     const int64_t row0 = b * s.T;  // step (b, 0)
-    // all 32 of the lane's loads are issued before the first ballot
-    bool v[kTcKB / 8][4];
-#pragma unroll
-    for (int j = 0; j < kTcKB / 8; ++j) {
-        const int64_t t = t0 + warp + 8 * j;
+    for (int kk = warp; kk < kTcKB; kk += 8) {
+        const int64_t t = t0 + kk;
 #pragma unroll
         for (int grp = 0; grp < 4; ++grp) {
             const int f = rb * 128 + grp * 32 + lane;
-            v[j][grp] = false;
+            bool v = false;
             if (t < s.T) {
                 if (f < n_dense) {
-                    v[j][grp] = x_dense[(row0 + t) * n_dense + f] != 0;
+                    v = x_dense[(row0 + t) * n_dense + f] != 0;
                 } else if (f - n_dense < n_bits && t > 0) {
                     const int i = f - n_dense;
-                    v[j][grp] = (z_bits[(row0 + t - 1) * zw + (i >> 5)] >> (i & 31)) & 1u;
+                    v = (z_bits[(row0 + t - 1) * zw + (i >> 5)] >> (i & 31)) & 1u;
                 }
             }
+            const unsigned m = __ballot_sync(FULL_MASK, v);
+            if (lane == 0) bits[kk][grp] = m;
         }
     }
-#pragma unroll
-    for (int j = 0; j < kTcKB / 8; ++j)
-#pragma unroll
-        for (int grp = 0; grp < 4; ++grp) {
-            const unsigned m = __ballot_sync(FULL_MASK, v[j][grp]);
-            if (lane == 0) bits[warp + 8 * j][grp] = m;
-        }
     __syncthreads();
     uint8_t* o = out + (static_cast<int64_t>(rb) * s.KB + kb) * kTcBlock;
     constexpr uint32_t one = 0x3F80u;  // BF16 1.0
