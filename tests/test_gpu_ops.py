@@ -729,3 +729,40 @@ def test_fixed_point_without_a_bound_is_reported():
     assert torch.count_nonzero(y).item() == 0
     with pytest.raises(B.BpError):
         B.bp_event_csrmv(dip, dix, dw, 0.0, sl, ns, y, flags=B.BP_ACC_SHARED | B.BP_ACC_FIXED)
+
+
+@pytest.mark.parametrize("off", [0, 1, 2, 4, 8])
+@pytest.mark.parametrize("wdt", [None, torch.float32, torch.bfloat16])
+def test_tiled_scatter_operand_alignments(off, wdt):
+    """The tiled walk picks its unit by the operands' alignment (8 entries for
+    32-byte aligned BF16 weights, 4 for 16-byte aligned operands, single
+    entries otherwise): index and weight buffers offset by `off` elements
+    reach every unit size, each against the oracle (counts exactly), with FP32
+    atomics and with fixed-point tile sums."""
+    n_pre, n_post, tc = 3000, 150001, B.bp_tile_cols()
+    ip, ix = _csr(n_pre, n_post, 0.004, seed=41)
+    ev = wl.bernoulli_spikes(n_pre, 0.2, seed=42)
+    nnz = len(ix)
+    ixb = torch.zeros(nnz + 16, dtype=torch.int32, device="cuda")
+    ixb[off:off + nnz] = cuda(ix)
+    dix = ixb[off:off + nnz]
+    dip = cuda(ip)
+    tp = torch.empty(B.bp_csr_tile_index_size(n_pre, n_post, tc), dtype=torch.int32, device="cuda")
+    B.bp_csr_tile_index(dip, dix, n_post, tc, tp)
+    sl, ns = spike_list_of(ev)
+    if wdt is None:
+        y = torch.zeros(n_post, dtype=torch.int32, device="cuda")
+        B.bp_event_csrmv(dip, dix, None, 1.0, sl, ns, y, tile_ptr=tp, tile_cols=tc, flags=B.BP_ACC_SHARED)
+        assert np.array_equal(y.cpu().numpy(), orc.event_csr_count(ip, ix, ev, n_post))
+        return
+    w = wl.normal_weights(nnz, 0.5, 0.1, seed=43)
+    wb = torch.zeros(nnz + 16, dtype=wdt, device="cuda")
+    wb[off:off + nnz] = cuda(w).to(wdt)
+    dw = wb[off:off + nnz]
+    ref = orc.event_csrmv(ip, ix, dw.float().cpu().numpy().astype(np.float64), ev, n_post)
+    B.bp_csr_tile_weight_bound(dip, dix, dw, 0.0, n_post, tc, tp)
+    for fl in (B.BP_ACC_SHARED, B.BP_ACC_SHARED | B.BP_ACC_FIXED):
+        y = torch.zeros(n_post, dtype=torch.float32, device="cuda")
+        B.bp_event_csrmv(dip, dix, dw, 0.0, sl, ns, y, tile_ptr=tp, tile_cols=tc, flags=fl)
+        assert B.bp_sync_status() == 0
+        assert rel_err(y.cpu().numpy(), ref) < RTOL_F32
