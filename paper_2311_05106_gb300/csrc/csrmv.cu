@@ -192,10 +192,30 @@ __device__ __forceinline__ void tile_add(Acc* p, float w, float fx_scale) {
     }
 }
 
+// The same, as one predicated shared-memory reduction at the tile's 32-bit
+// shared address (computed once per walk): no branch around the update and
+// no generic-to-shared conversion per event.  `on` false: nothing is added.
+template <typename Acc, bool FX>
+__device__ __forceinline__ void tile_red(uint32_t acc_s, uint32_t c, float w, float fx_scale, bool on) {
+    const uint32_t addr = acc_s + 4u * c;
+    if constexpr (FX || std::is_same<Acc, int32_t>::value) {
+        const int32_t v = FX ? __float2int_rn(w * fx_scale) : 1;
+        asm volatile("{\n .reg .pred q;\n setp.ne.u32 q, %2, 0;\n @q red.shared.add.u32 [%0], %1;\n}" ::"r"(addr),
+                     "r"(v), "r"(static_cast<uint32_t>(on))
+                     : "memory");
+    } else {
+        asm volatile("{\n .reg .pred q;\n setp.ne.u32 q, %2, 0;\n @q red.shared.add.f32 [%0], %1;\n}" ::"r"(addr),
+                     "f"(w), "r"(static_cast<uint32_t>(on))
+                     : "memory");
+    }
+}
+
 template <typename Acc, int WK, int EPU, int U, bool FX>
 __device__ __forceinline__ void warp_flat_walk(const CsrArgs& a, const WarpList& L, int32_t T,
                                                Acc* __restrict__ acc, int64_t col0, int32_t W, float fx_scale) {
     const int lane = threadIdx.x & 31;
+    const uint32_t acc_s = static_cast<uint32_t>(__cvta_generic_to_shared(acc));
+    const uint32_t col0_u = static_cast<uint32_t>(col0);
     int32_t e = lane;
     if (e >= T) return;
     int k_lo = 0, k_hi = 32;  // start[k_lo] <= e < start[k_hi]
@@ -261,8 +281,10 @@ __device__ __forceinline__ void warp_flat_walk(const CsrArgs& a, const WarpList&
             for (int m = 0; m < EPU; ++m) {
                 // an index outside this tile (an operand that does not match
                 // its tile index) is skipped rather than written out of the tile
-                const uint32_t c = static_cast<uint32_t>(static_cast<int64_t>(col[q][m]) - col0);
-                if (((msk[q] >> m) & 1u) && c < static_cast<uint32_t>(W)) tile_add<Acc, FX>(acc + c, w[q][m], fx_scale);
+                // modulo 2^32: a column outside [col0, col0 + W) maps to >= W
+                // (n_post < 2^31), so one unsigned compare bounds it
+                const uint32_t c = static_cast<uint32_t>(col[q][m]) - col0_u;
+                tile_red<Acc, FX>(acc_s, c, w[q][m], fx_scale, ((msk[q] >> m) & 1u) && c < static_cast<uint32_t>(W));
             }
         }
     }
