@@ -180,12 +180,13 @@ bp_status bp_spike_compact(int64_t n, const uint8_t* events, int32_t* spike_list
  * BP_ACC_FIXED (float y; needs a tile index on which
  * bp_csr_tile_weight_bound() has recorded the weight bound b): the shared-
  * memory tile sums are 32-bit integers.  A CTA that accumulates m spiking
- * rows takes s = 29 - e, where m b < 2^e <= 2 m b (s kept within
- * [-100, 100]), and adds round(w_j 2^s) per event, so no tile sum can
- * overflow; the tile, times 2^-s, is then added to y in FP32.  Each event is
- * off by at most 2^-(s+1) <= m b 2^-29 absolute, the order of the worst-case
- * rounding of an FP32 sum of the same terms, and a tile's sum does not depend
- * on the order of its events.  Direct (global-atomic) accumulation ignores
+ * rows takes s = 29 - e_m - e_b, where m < 2^e_m <= 2 m and
+ * b < 2^e_b <= 2 b (s kept within [-126, 126]), and adds round(w_j 2^s) per
+ * event, so no tile sum can overflow; the tile, times 2^-s, is then added to
+ * y in FP32.  Each event is off by at most 2^-(s+1) <= max(2 m b 2^-29,
+ * 2^-127) absolute, the order of the worst-case rounding of an FP32 sum of
+ * the same terms (the second term only for weight bounds below 2^-97 / m),
+ * and a tile's sum does not depend on the order of its events.  Direct (global-atomic) accumulation ignores
  * the flag.  A tile index without a recorded bound makes the kernel record
  * BP_ERR_DEVICE (bp_sync_status) and add nothing.
  * Errors: BP_ERR_INVALID for negative sizes, NULL required pointers,

@@ -344,10 +344,16 @@ __global__ void __launch_bounds__(kTileThreads, 1)
                 if (t == 0 && status) atomicExch(status, static_cast<int>(BP_ERR_DEVICE));
                 return;
             }
-            int e = 0;
-            frexpf(static_cast<float>(M > 0 ? M : 1) * b, &e);  // M b < 2^e
-            int sx = 29 - e;
-            sx = sx < -100 ? -100 : (sx > 100 ? 100 : sx);
+            // M b < 2^(em + eb), from the two exponents (M b itself may
+            // overflow FP32 for weights near its range)
+            int em = 0, eb = 0;
+            frexpf(static_cast<float>(M > 0 ? M : 1), &em);
+            frexpf(b, &eb);
+            int sx = 29 - em - eb;
+            // 2^s must stay a normal float both ways: for bounds below
+            // 2^-97 / M the scale stops at 2^126 (events then carry an
+            // absolute error up to 2^-127)
+            sx = sx < -126 ? -126 : (sx > 126 ? 126 : sx);
             fx_scale = ldexpf(1.f, sx);
             fx_inv = ldexpf(1.f, -sx);
         }

@@ -620,12 +620,13 @@ def _tile_index(dip, dix, n_pre, n_post, tcols):
 
 def _fixed_bound(counts_col, abs_col, n_spk, b):
     """Bound on |fixed-point result - exact| per column (bp_event_csrmv,
-    BP_ACC_FIXED): each event off by at most 2^-(s+1) <= m b 2^-29 with m at
-    most the number of spiking rows, plus the FP32 conversion of each CTA's
-    tile and the FP32 adds into y (at most 152 of them per column), each
-    rounding by 2^-24 of a partial sum no larger than the column's sum of
-    absolute values."""
-    return counts_col * (n_spk * b * 2.0 ** -29) + abs_col * 2.0 ** -24 * 2 * 153 + 1e-30
+    BP_ACC_FIXED): each event off by at most 2^-(s+1) <= max(2 m b 2^-29,
+    2^-127) with m at most the number of spiking rows, plus the FP32
+    conversion of each CTA's tile and the FP32 adds into y (at most 152 of
+    them per column), each rounding by 2^-24 of a partial sum no larger than
+    the column's sum of absolute values."""
+    per_event = max(2.0 * n_spk * b * 2.0 ** -29, 2.0 ** -127)
+    return counts_col * per_event + abs_col * 2.0 ** -24 * 2 * 153 + 1e-300
 
 
 @pytest.mark.parametrize("n_pre,n_post,p,rho,tcols", [(300, 257, 0.1, 0.3, 64), (5000, 40001, 0.02, 0.05, 4096),
@@ -766,3 +767,33 @@ def test_tiled_scatter_operand_alignments(off, wdt):
         B.bp_event_csrmv(dip, dix, dw, 0.0, sl, ns, y, tile_ptr=tp, tile_cols=tc, flags=fl)
         assert B.bp_sync_status() == 0
         assert rel_err(y.cpu().numpy(), ref) < RTOL_F32
+
+
+@pytest.mark.parametrize("scale", [1e-30, 1e30])
+def test_fixed_point_tiles_extreme_weight_magnitudes(scale):
+    """Weight bounds near the ends of the FP32 range: the fixed-point scale is
+    taken from the exponents of m and b separately (m b may overflow FP32)
+    and stays a normal float, and the result keeps the bound of the
+    arithmetic against the oracle."""
+    n_pre, n_post, tc = 2000, 60001, 4096
+    ip, ix = _csr(n_pre, n_post, 0.01, seed=51)
+    rng = np.random.default_rng(52)
+    w = (rng.choice([-1.0, 1.0], size=len(ix)) * rng.uniform(0.1, 1.0, size=len(ix)) * scale).astype(np.float32)
+    ev = wl.bernoulli_spikes(n_pre, 0.3, seed=53)
+    dip, dix, dw = cuda(ip), cuda(ix), cuda(w)
+    tp = _tile_index(dip, dix, n_pre, n_post, tc)
+    B.bp_csr_tile_weight_bound(dip, dix, dw, 0.0, n_post, tc, tp)
+    b = float(tp[-1:].cpu().numpy().view(np.float32)[0])
+    sl, ns = spike_list_of(ev)
+    y = torch.zeros(n_post, dtype=torch.float32, device="cuda")
+    B.bp_event_csrmv(dip, dix, dw, 0.0, sl, ns, y, tile_ptr=tp, tile_cols=tc, flags=B.BP_ACC_SHARED | B.BP_ACC_FIXED)
+    assert B.bp_sync_status() == 0
+    wref = w.astype(np.float64)
+    ref = orc.event_csrmv(ip, ix, wref, ev, n_post)
+    cnt = orc.event_csr_count(ip, ix, ev, n_post).astype(np.float64)
+    absc = orc.event_csrmv(ip, ix, np.abs(wref), ev, n_post)
+    got = y.cpu().numpy().astype(np.float64)
+    assert np.all(np.isfinite(got))
+    assert np.all(np.abs(got - ref) <= _fixed_bound(cnt, absc, int(ev.sum()), b))
+    assert rel_err(got, ref) < RTOL_F32
+
