@@ -289,7 +289,10 @@ def e2e_run(torch, net, host_ckpt, steps):
     after the settle period).  Inside the timed region: the upload of that
     state (CobaNetwork.restore, non-blocking copies), bp_simulate over the
     steps with a per-step spike record, and the download of the record and of
-    the final potentials.  `steps` = W + K."""
+    the final potentials.  `steps` = W + K.  The whole replay runs once
+    untimed first: a first call pays one-off costs (first launches, first
+    transfers through newly pinned buffers; once measured at 7.5 ms against
+    1.35 ms for the same 25 steps) that a repeated job does not pay."""
     f32 = torch.float32
     n = net.n
     rec = torch.zeros((steps, 2), dtype=torch.int32, device="cuda")
@@ -297,16 +300,22 @@ def e2e_run(torch, net, host_ckpt, steps):
     hVout = torch.zeros(n, dtype=f32).pin_memory()
     net.prepare(steps)
     stream = torch.cuda.current_stream()
+
+    def replay():
+        net.restore(host_ckpt, non_blocking=True)
+        before = net.totals.clone()
+        net.simulate(steps, rec)
+        events = net.totals[2] - before[2]
+        hrec.copy_(rec, non_blocking=True)
+        hVout.copy_(net.V, non_blocking=True)
+        return events
+
+    replay()
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    net.restore(host_ckpt, non_blocking=True)
-    before = net.totals.clone()
-    net.simulate(steps, rec)
-    events = net.totals[2] - before[2]
-    hrec.copy_(rec, non_blocking=True)
-    hVout.copy_(net.V, non_blocking=True)
+    events = replay()
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
@@ -1032,7 +1041,8 @@ def main():
                "h2d_bytes_per_step": h2d / n_e2e, "d2h_bytes_per_step": d2h / n_e2e,
                "ms": e2e_ms, "events": e2e_events, "steps": n_e2e,
                "note": "the W warm-up and K timed steps replayed through the public API from the post-settle "
-                       "state uploaded from pinned host memory; upload, steps and downloads inside the timed region"}
+                       "state uploaded from pinned host memory; upload, steps and downloads inside the timed region; "
+                       "the same replay run once untimed before (first use of the pinned buffers)"}
     net.close()
     del net
     torch.cuda.empty_cache()
