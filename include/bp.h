@@ -459,10 +459,10 @@ int64_t bp_network_step_count(const bp_net* net);
 bp_status bp_network_set_step_count(bp_net* net, int64_t step, bp_stream_t stream);
 
 /* T steps, launched as CUDA graphs on `stream`: T is split into 64-step
- * chunks and a shorter remainder (plus one single step first when the step
- * count is odd); the graph of each length is captured once, on a private
- * stream, on first use and cached with the network.  record int32 [T][2]
- * (nullable) receives the E and I spike counts of each step. */
+ * chunks and a shorter remainder; the graph of each length is captured once
+ * per parity of the starting step count, on a private stream, on first use
+ * and cached with the network.  record int32 [T][2] (nullable) receives the
+ * E and I spike counts of each step. */
 bp_status bp_simulate(bp_net* net, int64_t T, int32_t* record, bp_stream_t stream);
 
 /* Captures (if not cached yet) and uploads to the device, on `stream`, the

@@ -13,9 +13,10 @@
 // two halves whatever the delay.  The optional spike-list counter alternates
 // between two slots the same way.  bp_simulate replays CUDA graphs of
 // captured steps: a 64-step chunk, and one graph per shorter remainder
-// length, each captured once (so a short call runs the same launch path as a
-// long one); per-step indices that differ between replays (the record row)
-// are read from a small device control block.
+// length, each captured once per starting parity (so a short call runs the
+// same launch path as a long one, and a call launches graphs only); per-step
+// indices that differ between replays (the record row) are read from a small
+// device control block.
 #include <cmath>
 #include <map>
 #include <new>
@@ -29,16 +30,17 @@ struct bp_net {
     int64_t host_step;
     bp::NetCtrl* ctrl;  // device
     cudaStream_t cap_stream;
-    // captured graphs of `len` steps from an even step (the chunk, and the
-    // shorter remainders of bp_simulate calls), built on first use
-    std::map<int, cudaGraphExec_t>* graphs;
+    // captured graphs of `len` steps (the chunk, and the shorter remainders
+    // of bp_simulate calls) from a step of either parity, keyed 2 len +
+    // parity, built on first use
+    std::map<int64_t, cudaGraphExec_t>* graphs;
     int chunk;
 };
 
 namespace bp {
 namespace {
 
-constexpr int kChunk = 64;  // steps per captured graph (even: the counter slots alternate)
+constexpr int kChunk = 64;  // steps per captured graph (even: a chunk keeps the parity of the step count)
 
 __global__ void k_set_record(NetCtrl* ctrl, int32_t* record, int64_t len) {
     ctrl->record = record;
@@ -73,11 +75,12 @@ bp_status enqueue_step(bp_net* net, int parity, int32_t t_local, cudaStream_t s,
     return launch_network_step(net->L, parity, t_local, s, advance);
 }
 
-// Graph of `len` steps starting on an even step (counter slot 0); the last
-// step advances the device step counter by len.  Captured once per length and
-// cached.
-bp_status get_graph(bp_net* net, int len, cudaGraphExec_t* out) {
-    auto it = net->graphs->find(len);
+// Graph of `len` steps starting on a step of the given parity (accumulator
+// half and counter slot `parity` read first); the last step advances the
+// device step counter by len.  Captured once per (length, parity) and cached.
+bp_status get_graph(bp_net* net, int len, int parity, cudaGraphExec_t* out) {
+    const int64_t key = 2 * static_cast<int64_t>(len) + (parity & 1);
+    auto it = net->graphs->find(key);
     if (it != net->graphs->end()) {
         *out = it->second;
         return BP_OK;
@@ -85,7 +88,8 @@ bp_status get_graph(bp_net* net, int len, cudaGraphExec_t* out) {
     if (!net->cap_stream) BP_CUDA(cudaStreamCreateWithFlags(&net->cap_stream, cudaStreamNonBlocking));
     BP_CUDA(cudaStreamBeginCapture(net->cap_stream, cudaStreamCaptureModeThreadLocal));
     bp_status st = BP_OK;
-    for (int t = 0; t < len && st == BP_OK; ++t) st = enqueue_step(net, t & 1, t, net->cap_stream, t == len - 1 ? len : 0);
+    for (int t = 0; t < len && st == BP_OK; ++t)
+        st = enqueue_step(net, (parity + t) & 1, t, net->cap_stream, t == len - 1 ? len : 0);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(net->cap_stream, &g);
     if (st != BP_OK) {
@@ -103,7 +107,7 @@ bp_status get_graph(bp_net* net, int len, cudaGraphExec_t* out) {
         set_error("graph instantiation failed: %s", cudaGetErrorString(e));
         return BP_ERR_CUDA;
     }
-    net->graphs->emplace(len, ex);
+    net->graphs->emplace(key, ex);
     *out = ex;
     return BP_OK;
 }
@@ -192,7 +196,7 @@ bp_status bp_network_create(const bp_net_desc* desc, bp_net** out) {
     net->L = L;
     net->host_step = 0;
     net->chunk = bp::kChunk;
-    net->graphs = new (std::nothrow) std::map<int, cudaGraphExec_t>();
+    net->graphs = new (std::nothrow) std::map<int64_t, cudaGraphExec_t>();
     net->cap_stream = nullptr;
     if (!net->graphs) {
         delete net;
@@ -258,14 +262,16 @@ bp_status bp_simulate_prepare(bp_net* net, int64_t T, bp_stream_t stream) {
     bp::clear_error();
     BP_REQUIRE(net, "net is NULL");
     BP_REQUIRE(T >= 0, "T < 0");
-    // the lengths bp_simulate(T) would launch from either step parity
-    const int64_t lens[3] = {T >= net->chunk || T - 1 >= net->chunk ? net->chunk : 0, T % net->chunk,
-                             T > 0 ? (T - 1) % net->chunk : 0};
-    for (int64_t len : lens) {
-        if (len <= 0) continue;
-        cudaGraphExec_t g = nullptr;
-        BP_TRY(bp::get_graph(net, static_cast<int>(len), &g));
-        BP_CUDA(cudaGraphUpload(g, stream));
+    // the graphs bp_simulate(T) would launch from a step of either parity
+    // (the step count may change before the call, e.g. by a restore)
+    const int64_t lens[2] = {T >= net->chunk ? net->chunk : 0, T % net->chunk};
+    for (int parity = 0; parity < 2; ++parity) {
+        for (int64_t len : lens) {
+            if (len <= 0) continue;
+            cudaGraphExec_t g = nullptr;
+            BP_TRY(bp::get_graph(net, static_cast<int>(len), parity, &g));
+            BP_CUDA(cudaGraphUpload(g, stream));
+        }
     }
     return BP_OK;
 }
@@ -283,25 +289,22 @@ bp_status bp_simulate(bp_net* net, int64_t T, int32_t* record, bp_stream_t strea
         BP_LAUNCHED();
     }
     int64_t done = 0;
-    // the captured chunk starts on an even counter slot
-    if (net->host_step & 1) {
-        BP_TRY(bp::enqueue_step(net, 1, 0, stream, 1));
-        net->host_step += 1;
-        done = 1;
-    }
-    const int64_t chunks = (T - done) / net->chunk;
+    // every graph starts at the current parity (a chunk is even, so it
+    // leaves the parity unchanged)
+    const int parity = static_cast<int>(net->host_step & 1);
+    const int64_t chunks = T / net->chunk;
     if (chunks > 0) {
         cudaGraphExec_t g = nullptr;
-        BP_TRY(bp::get_graph(net, net->chunk, &g));
+        BP_TRY(bp::get_graph(net, net->chunk, parity, &g));
         for (int64_t k = 0; k < chunks; ++k) BP_CUDA(cudaGraphLaunch(g, stream));
         net->host_step += chunks * net->chunk;
         done += chunks * net->chunk;
     }
-    // the remainder (host_step is even here) is one cached graph of its length
+    // the remainder is one cached graph of its length
     const int64_t rem = T - done;
     if (rem > 0) {
         cudaGraphExec_t g = nullptr;
-        BP_TRY(bp::get_graph(net, static_cast<int>(rem), &g));
+        BP_TRY(bp::get_graph(net, static_cast<int>(rem), parity, &g));
         BP_CUDA(cudaGraphLaunch(g, stream));
         net->host_step += rem;
     }

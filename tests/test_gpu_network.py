@@ -144,6 +144,20 @@ def test_simulate_graph_equals_step_loop(conn):
     for _ in range(37):
         b.step()
     assert torch.equal(a.V, b.V)
+    # a call from an odd step count (graphs captured for that parity: two
+    # 64-step chunks and a remainder) with a record
+    T2 = 131
+    rec2 = torch.zeros((T2, 2), dtype=torch.int32, device="cuda")
+    a.simulate(T2, rec2)
+    counts = []
+    for _ in range(T2):
+        before = b.totals[:2].clone()
+        b.step()
+        counts.append((b.totals[:2] - before).cpu().numpy())
+    assert np.array_equal(rec2.cpu().numpy(), np.array(counts, np.int32))
+    assert torch.equal(a.V, b.V) and torch.equal(a.ge, b.ge) and torch.equal(a.gi, b.gi)
+    assert torch.equal(a.ye, b.ye) and torch.equal(a.yi, b.yi) and torch.equal(a.totals, b.totals)
+    assert B.bp_network_step_count(a.handle) == B.bp_network_step_count(b.handle) == T + 37 + T2
 
 
 def test_stored_float_weights_network_close_to_counts():
@@ -265,7 +279,7 @@ def test_delayed_simulate_equals_single_steps(conn):
     V0 = wl.coba_v0(n, seed=3)
     a = CobaNetwork(n, conn=conn, seed=seed, p=p, V0=V0, delay_e=5, delay_i=10)
     b = CobaNetwork(n, conn=conn, seed=seed, p=p, V0=V0, delay_e=5, delay_i=10)
-    a.step()            # odd start: the simulate call begins with one single step
+    a.step()            # odd start: the simulate call launches graphs captured from an odd step
     a.simulate(T - 1)
     for _ in range(T):
         b.step()
