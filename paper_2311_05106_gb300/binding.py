@@ -193,9 +193,18 @@ def _p(t):
     return VP(t.data_ptr())
 
 
+# the current stream's raw handle without building a torch Stream object
+# (0.1 us against ~3 us per call; the public route where torch lacks it)
+_raw_stream = getattr(torch._C, "_cuda_getCurrentRawStream", None)
+_cur_device = getattr(torch._C, "_cuda_getDevice", None)
+
+
 def _stream(stream=None):
-    s = torch.cuda.current_stream() if stream is None else stream
-    return VP(s.cuda_stream)
+    if stream is None:
+        if _raw_stream is not None and _cur_device is not None:
+            return VP(_raw_stream(_cur_device()))
+        stream = torch.cuda.current_stream()
+    return VP(stream.cuda_stream)
 
 
 def _wkind(data):

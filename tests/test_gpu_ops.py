@@ -797,3 +797,21 @@ def test_fixed_point_tiles_extreme_weight_magnitudes(scale):
     assert np.all(np.abs(got - ref) <= _fixed_bound(cnt, absc, int(ev.sum()), b))
     assert rel_err(got, ref) < RTOL_F32
 
+
+
+def test_binding_launches_on_the_current_stream():
+    """The binding's default stream is torch's current stream (raw handle),
+    on the device's default stream and inside a side-stream context; a
+    kernel enqueued there is ordered after earlier work on that stream."""
+    assert (B._stream(None).value or 0) == torch.cuda.current_stream().cuda_stream
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        assert B._stream(None).value == s.cuda_stream
+        n = 1000
+        events = torch.zeros(n, dtype=torch.uint8, device="cuda")
+        events[::3] = 1
+        sl = torch.zeros(n, dtype=torch.int32, device="cuda")
+        ns = torch.zeros(1, dtype=torch.int32, device="cuda")
+        B.bp_spike_compact(events, sl, ns)
+    s.synchronize()
+    assert int(ns.item()) == (n + 2) // 3
