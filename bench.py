@@ -788,7 +788,7 @@ def sweep_cells(torch, sizes, probs, rhos, wsel, ops, cells=None, tile_cols=None
                 ip, ix, w32 = B.jit_materialize(dn, n, n, data_dtype=torch.float32 if stored else None)
                 nnz = ix.numel()
                 w16 = w32.to(torch.bfloat16) if "bf16" in wsel else None
-                tc = (tile_cols or B.bp_tile_cols()) if n > B.bp_tile_cols() else 0
+                tc = (tile_cols or B.bp_tile_cols_for(n)) if n > B.bp_tile_cols() else 0
                 if tc:
                     tp = torch.empty(B.bp_csr_tile_index_size(n, n, tc), dtype=torch.int32, device="cuda")
                     B.bp_csr_tile_index(ip, ix, n, tc, tp)

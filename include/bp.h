@@ -92,6 +92,14 @@ bp_status bp_sync_status(bp_stream_t stream);
  * bytes per post neuron. */
 int32_t bp_tile_cols(void);
 
+/* A tile width for an index over n_post post columns: the fewest tiles of
+ * at most bp_tile_cols() columns, S = ceil(n_post / bp_tile_cols()), made
+ * equal, ceil(n_post / S) rounded up to a multiple of 32 (32 when
+ * n_post <= 0).  The tiled products give each of the S tiles the same
+ * number of CTAs, so equal tiles give every CTA the same share of a uniform
+ * matrix (with full-width tiles the last one can be nearly empty). */
+int32_t bp_tile_cols_for(int64_t n_post);
+
 /* --------------------------------------------------------------------------
  * a1-a4. LIF / exponential conductance synapse / COBA step.
  * Appendix E (exponential synapse: g <- exp(-dt/tau) g, then g <- g + w per

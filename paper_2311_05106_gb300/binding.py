@@ -88,6 +88,7 @@ _SIGS = {
     "bp_last_error": (ctypes.c_char_p, []),
     "bp_sync_status": (c_i32, [VP]),
     "bp_tile_cols": (c_i32, []),
+    "bp_tile_cols_for": (c_i32, [c_i64]),
     "bp_coba_params_default": (c_i32, [ctypes.POINTER(CobaParams)]),
     "bp_lif_step": (c_i32, [ctypes.POINTER(CobaParams), c_i64, c_i64, VP, VP, VP, VP, VP, VP, c_i32, VP, VP, VP, VP,
                             VP, VP]),
@@ -246,6 +247,11 @@ def bp_sync_status(stream=None) -> int:
 
 def bp_tile_cols() -> int:
     return int(lib().bp_tile_cols())
+
+
+def bp_tile_cols_for(n_post) -> int:
+    """Equal tiles of at most bp_tile_cols() columns over n_post columns."""
+    return int(lib().bp_tile_cols_for(int(n_post)))
 
 
 def bp_coba_params_default(**overrides) -> CobaParams:

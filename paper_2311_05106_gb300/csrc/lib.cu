@@ -142,6 +142,15 @@ const char* bp_last_error(void) { return g_msg; }
 
 int32_t bp_tile_cols(void) { return bp::kTileCols; }
 
+int32_t bp_tile_cols_for(int64_t n_post) {
+    const int64_t cap = bp::kTileCols;
+    if (n_post <= 0) return 32;
+    const int64_t S = (n_post + cap - 1) / cap;
+    int64_t W = (n_post + S - 1) / S;
+    W = (W + 31) & ~int64_t(31);  // cap is a multiple of 32, so W stays <= cap
+    return static_cast<int32_t>(W < cap ? W : cap);
+}
+
 bp_status bp_sync_status(bp_stream_t stream) {
     bp::clear_error();
     cudaError_t e = cudaStreamSynchronize(stream);

@@ -64,6 +64,16 @@ def test_host_only_helpers(libpath):
     with pytest.raises(B.BpError):
         B.bp_jit_desc_init(7, 0.0)
     assert B.bp_csr_tile_index_size(10, 100000, 57344) == 10 * 3 + 1  # + the weight-bound slot
+    # equal tiles: the fewest tiles of at most bp_tile_cols() columns, each a
+    # multiple of 32 columns, none of them nearly empty
+    cap = B.bp_tile_cols()
+    for n_post in (1, 31, 32, 1000, cap - 1, cap, cap + 1, 2 * cap, 2 * cap + 7, 1_000_000, 4_000_000, 2**31 - 1):
+        W = B.bp_tile_cols_for(n_post)
+        S = -(-n_post // cap)
+        assert W % 32 == 0 and 0 < W <= cap
+        assert -(-n_post // W) == S
+        assert n_post - (S - 1) * W >= W - 32 * S  # the last tile is within 32 S columns of the others
+    assert B.bp_tile_cols_for(1_000_000) == 52640 and B.bp_tile_cols_for(0) == 32
     import oracle as orc
     for s in (0, 2024, 2**63 + 5):
         for j in (0, 1):
