@@ -156,30 +156,65 @@ class CobaNetwork:
         names = ("V", "ge", "gi", "ref", "ye", "yi", "n_spikes", "totals", "spk", "spike_list", "delay_buf", "trace")
         return {k: getattr(self, k) for k in names if getattr(self, k, None) is not None}
 
+    def _live_half(self, step):
+        """Index (0 / 1) of the accumulator half the next step reads, or None
+        when both halves are kept.  Step t reads half t mod 2 and clears it
+        while it delivers into the other, so between steps the half that is
+        not read next is all zero and a checkpoint needs only the live one
+        (AlignPre networks recompute their accumulators every step and keep
+        both)."""
+        return None if self.align == "pre" else int(step) & 1
+
+    def _checkpoint_views(self, step):
+        h = self._live_half(step)
+        out = {}
+        for k, t in self.state_tensors().items():
+            if h is not None and k in ("ye", "yi"):
+                t = t[h * self.n:(h + 1) * self.n]
+            out[k] = t
+        return out
+
     def checkpoint(self):
-        """A copy of the state (device tensors) and the step count."""
-        return {"step": B.bp_network_step_count(self.handle),
-                "state": {k: t.clone() for k, t in self.state_tensors().items()}}
+        """A copy of the state (device tensors) and the step count: every
+        state buffer, the event accumulators as their live half only."""
+        step = B.bp_network_step_count(self.handle)
+        return {"step": step, "live_half": self._live_half(step),
+                "state": {k: t.clone() for k, t in self._checkpoint_views(step).items()}}
 
     def checkpoint_to_host(self):
         """A checkpoint in pinned host memory (for restoring from the host
         later, e.g. to resume a run in another process)."""
         torch.cuda.synchronize()
-        return {"step": B.bp_network_step_count(self.handle),
-                "state": {k: t.to("cpu").pin_memory() for k, t in self.state_tensors().items()}}
+        step = B.bp_network_step_count(self.handle)
+        return {"step": step, "live_half": self._live_half(step),
+                "state": {k: t.to("cpu").pin_memory() for k, t in self._checkpoint_views(step).items()}}
 
     def restore(self, ckpt, non_blocking=False):
         """Writes a checkpoint back (into this network or a new one of the
-        same configuration) so that the simulation resumes where it was taken.
-        With non_blocking and a pinned host checkpoint the copies are enqueued
-        on the current stream without waiting for them."""
+        same configuration) so that the simulation resumes where it was taken:
+        the saved buffers are copied in and the other accumulator half is
+        zeroed on the device.  With non_blocking and a pinned host checkpoint
+        the copies are enqueued on the current stream without waiting for
+        them."""
+        h = ckpt.get("live_half")
+        if h is not None and h != self._live_half(ckpt["step"]):
+            raise ValueError("checkpoint accumulator half does not match its step count")
         for k, t in self.state_tensors().items():
-            t.copy_(ckpt["state"][k], non_blocking=non_blocking)
+            if h is not None and k in ("ye", "yi"):
+                t[h * self.n:(h + 1) * self.n].copy_(ckpt["state"][k], non_blocking=non_blocking)
+                t[(1 - h) * self.n:(2 - h) * self.n].zero_()
+            else:
+                t.copy_(ckpt["state"][k], non_blocking=non_blocking)
         B.bp_network_set_step_count(self.handle, ckpt["step"])
 
     def state_bytes(self):
-        """Bytes of the caller-owned state buffers (what a restore copies)."""
+        """Bytes of the caller-owned state buffers."""
         return sum(t.numel() * t.element_size() for t in self.state_tensors().values())
+
+    def checkpoint_bytes(self):
+        """Bytes a checkpoint holds (what a restore copies in)."""
+        step = B.bp_network_step_count(self.handle)
+        return sum(t.numel() * t.element_size() for t in self._checkpoint_views(step).values())
 
     def step(self):
         B.bp_network_step(self.handle)
