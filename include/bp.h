@@ -186,15 +186,17 @@ bp_status bp_spike_compact(int64_t n, const uint8_t* events, int32_t* spike_list
  * Accumulation order is unspecified: FP32 results are deterministic only up to
  * rounding; int32 counts are exact.
  * BP_ACC_FIXED (float y; needs a tile index on which
- * bp_csr_tile_weight_bound() has recorded the weight bound b): the shared-
- * memory tile sums are 32-bit integers.  A CTA that accumulates m spiking
- * rows takes s = 29 - e_m - e_b, where m < 2^e_m <= 2 m and
- * b < 2^e_b <= 2 b (s kept within [-126, 126]), and adds round(w_j 2^s) per
- * event, so no tile sum can overflow; the tile, times 2^-s, is then added to
- * y in FP32.  Each event is off by at most 2^-(s+1) <= max(2 m b 2^-29,
- * 2^-127) absolute, the order of the worst-case rounding of an FP32 sum of
- * the same terms (the second term only for weight bounds below 2^-97 / m),
- * and a tile's sum does not depend on the order of its events.  Direct (global-atomic) accumulation ignores
+ * bp_csr_tile_weight_bound() has recorded the weight bound b and the column
+ * count c_max): the shared-memory tile sums are 32-bit integers.  A CTA that
+ * accumulates M spiking rows bounds every column of its tile by m b, with
+ * m = min(M, c_max) (a column receives at most one run of entries per row),
+ * takes s = 29 - e_m - e_b, where m < 2^e_m <= 2 m and b < 2^e_b <= 2 b
+ * (s kept within [-126, 126]), and adds round(w_j 2^s) per event, so no
+ * tile sum can overflow; the tile, times 2^-s, is then added to y in FP32.
+ * Each event is off by at most 2^-(s+1) <= max(2 m b 2^-29, 2^-127)
+ * absolute, the order of the worst-case rounding of an FP32 sum of the same
+ * terms (the second term only for weight bounds below 2^-97 / m), and a
+ * tile's sum does not depend on the order of its events.  Direct (global-atomic) accumulation ignores
  * the flag.  A tile index without a recorded bound makes the kernel record
  * BP_ERR_DEVICE (bp_sync_status) and add nothing.
  * Errors: BP_ERR_INVALID for negative sizes, NULL required pointers,
@@ -249,7 +251,7 @@ bp_status bp_event_csrmv_dense_noalloc(int64_t n_pre, int64_t n_post,
  * [n_pre * (S + 1) + 1] (bp_csr_tile_index_size entries):
  * tile_ptr[i (S+1) + s] = (first position in row i whose column is
  * >= s tile_cols) - indptr[i], for s = 0..S (so entry S is the row length),
- * and 0 in the last entry (the weight-bound slot of
+ * and 0 in the last two entries (the bound slots of
  * bp_csr_tile_weight_bound: no bound recorded).
  * Requires sorted rows and row lengths < 2^31.  tile_cols must be a positive
  * multiple of 32 no larger than bp_tile_cols(). */
@@ -259,16 +261,21 @@ bp_status bp_csr_tile_index(int64_t n_pre, int64_t n_post, const int64_t* indptr
                             bp_stream_t stream);
 
 /* Records in the tile index built by bp_csr_tile_index (same n_pre, n_post,
- * tile_cols) the weight bound that BP_ACC_FIXED needs: b = the largest
- * absolute sum of one row's entries in one column (the largest |w_j| when
- * no row repeats a column; |w_homo| for BP_W_HOMO), rounded up, stored as
- * FP32 bits in the index's last entry (bp_csr_tile_index leaves 0 there:
- * no bound).  One device pass over the stored entries; call it again after
- * the weights change. */
+ * tile_cols) the bounds that BP_ACC_FIXED needs, in its last two entries:
+ * b = the largest absolute sum of one row's entries in one column (the
+ * largest |w_j| when no row repeats a column; |w_homo| for BP_W_HOMO),
+ * rounded up, as FP32 bits at index n_pre (S+1); and c_max = the largest
+ * number of rows with an entry in one column, as an int32 at index
+ * n_pre (S+1) + 1 (bp_csr_tile_index leaves 0 in both: no bound).
+ * work int32 [n_post]: caller-owned scratch (the per-column row counts),
+ * overwritten; it may be NULL only when n_post = 0.  One device pass over
+ * the stored entries and one over the columns; call it again after the
+ * weights or the indices change.  Column indices outside [0, n_post) are
+ * not counted. */
 bp_status bp_csr_tile_weight_bound(int64_t n_pre, int64_t n_post, const int64_t* indptr,
                                    const int32_t* indices, const void* data, int32_t wkind,
                                    float w_homo, int32_t tile_cols, int32_t* tile_ptr,
-                                   bp_stream_t stream);
+                                   int32_t* work, bp_stream_t stream);
 
 /* Validation of a CSR before use (the products trust their operands and do
  * not check indices on the hot path): one device pass over indices [nnz]

@@ -102,7 +102,7 @@ _SIGS = {
     "bp_event_csrmv_dense_noalloc": (c_i32, [c_i64, c_i64, VP, VP, VP, c_i32, c_f32, VP, VP, c_i32, c_u32, VP]),
     "bp_csr_tile_index_size": (c_i64, [c_i64, c_i64, c_i32]),
     "bp_csr_tile_index": (c_i32, [c_i64, c_i64, VP, VP, c_i32, VP, VP]),
-    "bp_csr_tile_weight_bound": (c_i32, [c_i64, c_i64, VP, VP, VP, c_i32, c_f32, c_i32, VP, VP]),
+    "bp_csr_tile_weight_bound": (c_i32, [c_i64, c_i64, VP, VP, VP, c_i32, c_f32, c_i32, VP, VP, VP]),
     "bp_csr_check": (c_i32, [c_i64, c_i64, c_i64, VP, VP, VP, VP]),
     "bp_event_csrmv_t": (c_i32, [c_i64, c_i64, VP, VP, VP, c_i32, c_f32, VP, VP, VP, c_i32, c_u32, VP]),
     "bp_event_csrmv_bwd": (c_i32, [c_i64, c_i64, VP, VP, VP, c_i32, c_f32, VP, VP, c_i64, VP, VP, VP, VP, c_i32, VP]),
@@ -346,14 +346,19 @@ def bp_csr_tile_index(indptr, indices, n_post, tile_cols, tile_ptr, stream=None)
                                                         int(tile_cols), _p(tile_ptr), _stream(stream)))
 
 
-def bp_csr_tile_weight_bound(indptr, indices, data, w_homo, n_post, tile_cols, tile_ptr, stream=None):
-    """Records in tile_ptr's last entry the weight bound of the fixed-point
+def bp_csr_tile_weight_bound(indptr, indices, data, w_homo, n_post, tile_cols, tile_ptr, work=None, stream=None):
+    """Records in tile_ptr's last two entries the bounds of the fixed-point
     tile sums (BP_ACC_FIXED): the largest absolute sum of one row's entries in
-    one column, as FP32 bits."""
+    one column (FP32 bits) and the most rows with an entry in one column.
+    work: int32 [n_post] device scratch (allocated here when None)."""
     _csr_sizes(indices, data, indptr.numel() - 1, n_post, tile_ptr, tile_cols)
+    if work is None:
+        work = torch.empty(max(int(n_post), 1), dtype=torch.int32, device=indptr.device)
+    if work.dtype != torch.int32 or work.numel() < int(n_post):
+        raise ValueError("work must hold n_post = %d int32 values" % int(n_post))
     _check("bp_csr_tile_weight_bound", lib().bp_csr_tile_weight_bound(
         indptr.numel() - 1, int(n_post), _p(indptr), _p(indices), _p(data), _wkind(data), float(w_homo),
-        int(tile_cols), _p(tile_ptr), _stream(stream)))
+        int(tile_cols), _p(tile_ptr), _p(work), _stream(stream)))
 
 
 def bp_csr_check(indptr, indices, n_post, out, stream=None):

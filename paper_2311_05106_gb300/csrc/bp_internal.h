@@ -64,8 +64,10 @@ struct CsrArgs {
     float w_homo;
     const int32_t* tile_ptr;
     int32_t tile_cols;
-    // the weight-bound slot at the end of the tile index (fixed-point tile
-    // sums, BP_ACC_FIXED); NULL without a tile index
+    // the two bound slots at the end of the tile index (fixed-point tile
+    // sums, BP_ACC_FIXED): [0] the weight bound b as FP32 bits, [1] the most
+    // rows with an entry in one column (0: not recorded); NULL without a
+    // tile index
     const int32_t* w_bound = nullptr;
 };
 

@@ -335,19 +335,24 @@ __global__ void __launch_bounds__(kTileThreads, 1)
         // takes an equal contiguous share [m_lo, m_hi) of them, 32 per round
         const int32_t M = static_cast<int32_t>(ns > r ? (ns - r + R - 1) / R : 0);  // ns <= n_pre < 2^31
         // fixed-point tiles: with the weight bound b, every column of this
-        // CTA's tile sums at most M b in magnitude; 2^s M b <= 2^29 keeps the
-        // sum of the rounded terms inside int32
+        // CTA's tile sums at most m b in magnitude (m below); 2^s m b <= 2^29
+        // keeps the sum of the rounded terms inside int32
         float fx_scale = 1.f, fx_inv = 1.f;
         if constexpr (FX) {
-            const float b = __int_as_float(*a.w_bound);
+            const float b = __int_as_float(a.w_bound[0]);
             if (!(b > 0.f)) {  // no bound recorded: nothing is added
                 if (t == 0 && status) atomicExch(status, static_cast<int>(BP_ERR_DEVICE));
                 return;
             }
-            // M b < 2^(em + eb), from the two exponents (M b itself may
+            // a column receives at most one run of entries from each row, so
+            // at most m = min(M, cmax) runs here, cmax = the most rows with an
+            // entry in one column (0: not recorded)
+            const int32_t cmax = a.w_bound[1];
+            const int32_t m = cmax > 0 && cmax < M ? cmax : M;
+            // m b < 2^(em + eb), from the two exponents (m b itself may
             // overflow FP32 for weights near its range)
             int em = 0, eb = 0;
-            frexpf(static_cast<float>(M > 0 ? M : 1), &em);
+            frexpf(static_cast<float>(m > 0 ? m : 1), &em);
             frexpf(b, &eb);
             int sx = 29 - em - eb;
             // 2^s must stay a normal float both ways: for bounds below
@@ -706,7 +711,10 @@ __global__ void k_tile_index(int64_t n_pre, const int64_t* __restrict__ indptr, 
         }
         tile_ptr[t] = static_cast<int32_t>(lo - rs);
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) tile_ptr[total] = 0;  // weight-bound slot: no bound yet
+    if (blockIdx.x == 0 && threadIdx.x == 0) {  // the bound slots: no bound yet
+        tile_ptr[total] = 0;
+        tile_ptr[total + 1] = 0;
+    }
 }
 
 // Weight bound of the fixed-point tiles: the largest absolute sum of one
@@ -714,12 +722,14 @@ __global__ void k_tile_index(int64_t n_pre, const int64_t* __restrict__ indptr, 
 // equal indices).  A warp per row; the lane at the start of each run sums the
 // run; the maximum, rounded up, goes into *slot as FP32 bits (non-negative
 // floats order like their bit patterns, so an integer maximum is a float
-// maximum).
+// maximum).  Each run also counts its row in its column: cnt[c] = the number
+// of rows with an entry in column c (exact int32 counts).
 template <int WK>
-__global__ void __launch_bounds__(256) k_tile_weight_bound(int64_t n_pre, const int64_t* __restrict__ indptr,
+__global__ void __launch_bounds__(256) k_tile_weight_bound(int64_t n_pre, int64_t n_post,
+                                                          const int64_t* __restrict__ indptr,
                                                           const int32_t* __restrict__ indices,
                                                           const void* __restrict__ data, float w_homo,
-                                                          int32_t* __restrict__ slot) {
+                                                          int32_t* __restrict__ slot, int32_t* __restrict__ cnt) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
     float best = 0.f;
@@ -728,6 +738,7 @@ __global__ void __launch_bounds__(256) k_tile_weight_bound(int64_t n_pre, const 
         for (int64_t j = r0 + lane; j < r1; j += 32) {
             const int32_t c = indices[j];
             if (j > r0 && indices[j - 1] == c) continue;  // not the start of its run
+            if (static_cast<uint32_t>(c) < static_cast<uint64_t>(n_post)) atomicAdd(cnt + c, 1);
             float run = fabsf(load_weight<WK>(data, j, w_homo));
             for (int64_t k = j + 1; k < r1 && indices[k] == c; ++k) run += fabsf(load_weight<WK>(data, k, w_homo));
             best = fmaxf(best, run);
@@ -742,6 +753,19 @@ __global__ void __launch_bounds__(256) k_tile_weight_bound(int64_t n_pre, const 
         if (!(up >= 1.17549435e-38f)) up = 1.17549435e-38f;
         atomicMax(slot, __float_as_int(up));
     }
+}
+
+// *slot = max over c of cnt[c] (the largest number of rows with an entry in
+// one column).
+__global__ void __launch_bounds__(256) k_max_count(int64_t n, const int32_t* __restrict__ cnt,
+                                                  int32_t* __restrict__ slot) {
+    int32_t best = 0;
+    for (int64_t c = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; c < n;
+         c += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        best = max(best, cnt[c]);
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) best = max(best, __shfl_xor_sync(FULL_MASK, best, d));
+    if ((threadIdx.x & 31) == 0 && best > 0) atomicMax(slot, best);
 }
 
 template <typename Acc, int WK, bool VECL, bool WIDE = false>
@@ -888,7 +912,7 @@ bp::CsrArgs make_csr(int64_t n_pre, int64_t n_post, const int64_t* indptr, const
     a.w_bound = nullptr;
     if (tile_ptr && tile_cols > 0 && n_pre >= 0 && n_post >= 0) {
         const int64_t S = (n_post + tile_cols - 1) / tile_cols;
-        a.w_bound = tile_ptr + n_pre * (S + 1);  // the last entry of the index
+        a.w_bound = tile_ptr + n_pre * (S + 1);  // the two bound slots at the end of the index
     }
     return a;
 }
@@ -942,7 +966,7 @@ bp_status bp_event_csrmv_dense(int64_t n_pre, int64_t n_post, const int64_t* ind
 int64_t bp_csr_tile_index_size(int64_t n_pre, int64_t n_post, int32_t tile_cols) {
     if (n_pre < 0 || n_post < 0 || tile_cols <= 0) return -1;
     const int64_t S = (n_post + tile_cols - 1) / tile_cols;
-    return n_pre * (S + 1) + 1;  // + the weight-bound slot
+    return n_pre * (S + 1) + 2;  // + the two bound slots
 }
 
 bp_status bp_csr_tile_index(int64_t n_pre, int64_t n_post, const int64_t* indptr, const int32_t* indices,
@@ -952,8 +976,8 @@ bp_status bp_csr_tile_index(int64_t n_pre, int64_t n_post, const int64_t* indptr
     BP_REQUIRE(tile_cols > 0 && tile_cols % 32 == 0 && tile_cols <= bp::kTileCols,
                "tile_cols %d must be a positive multiple of 32 <= %d", tile_cols, bp::kTileCols);
     BP_REQUIRE(n_pre == 0 || (indptr && indices && tile_ptr), "a required pointer is NULL");
-    if (n_pre == 0) {  // only the weight-bound slot
-        if (tile_ptr) BP_CUDA(cudaMemsetAsync(tile_ptr, 0, sizeof(int32_t), stream));
+    if (n_pre == 0) {  // only the bound slots
+        if (tile_ptr) BP_CUDA(cudaMemsetAsync(tile_ptr, 0, 2 * sizeof(int32_t), stream));
         return BP_OK;
     }
     const int32_t S = static_cast<int32_t>((n_post + tile_cols - 1) / tile_cols);
@@ -968,7 +992,7 @@ bp_status bp_csr_tile_index(int64_t n_pre, int64_t n_post, const int64_t* indptr
 
 bp_status bp_csr_tile_weight_bound(int64_t n_pre, int64_t n_post, const int64_t* indptr, const int32_t* indices,
                                    const void* data, int32_t wkind, float w_homo, int32_t tile_cols, int32_t* tile_ptr,
-                                   bp_stream_t stream) {
+                                   int32_t* work, bp_stream_t stream) {
     bp::clear_error();
     BP_REQUIRE(n_pre >= 0 && n_post >= 0 && n_pre <= INT32_MAX && n_post <= INT32_MAX, "bad sizes");
     BP_REQUIRE(tile_cols > 0 && tile_cols % 32 == 0 && tile_cols <= bp::kTileCols,
@@ -977,26 +1001,34 @@ bp_status bp_csr_tile_weight_bound(int64_t n_pre, int64_t n_post, const int64_t*
     BP_REQUIRE(tile_ptr != nullptr, "tile_ptr is NULL");
     BP_REQUIRE(n_pre == 0 || (indptr && indices), "indptr or indices is NULL");
     BP_REQUIRE(wkind == BP_W_HOMO || n_pre == 0 || data != nullptr, "weights are NULL for a non-homogeneous kind");
+    BP_REQUIRE(n_post == 0 || work != nullptr, "work is NULL");
     const int64_t S = (n_post + tile_cols - 1) / tile_cols;
     int32_t* slot = tile_ptr + n_pre * (S + 1);
-    BP_CUDA(cudaMemsetAsync(slot, 0, sizeof(int32_t), stream));
+    BP_CUDA(cudaMemsetAsync(slot, 0, 2 * sizeof(int32_t), stream));
+    if (n_post > 0) BP_CUDA(cudaMemsetAsync(work, 0, static_cast<size_t>(n_post) * sizeof(int32_t), stream));
     int64_t grid = (n_pre * 32 + 255) / 256;
     if (grid > bp::sm_count() * 16) grid = bp::sm_count() * 16;
     if (grid < 1) grid = 1;
     switch (wkind) {
         case BP_W_F32:
-            bp::k_tile_weight_bound<bp::WK_F32><<<static_cast<unsigned>(grid), 256, 0, stream>>>(n_pre, indptr, indices,
-                                                                                                 data, w_homo, slot);
+            bp::k_tile_weight_bound<bp::WK_F32><<<static_cast<unsigned>(grid), 256, 0, stream>>>(n_pre, n_post, indptr, indices,
+                                                                                                 data, w_homo, slot, work);
             break;
         case BP_W_BF16:
-            bp::k_tile_weight_bound<bp::WK_BF16><<<static_cast<unsigned>(grid), 256, 0, stream>>>(n_pre, indptr, indices,
-                                                                                                  data, w_homo, slot);
+            bp::k_tile_weight_bound<bp::WK_BF16><<<static_cast<unsigned>(grid), 256, 0, stream>>>(n_pre, n_post, indptr, indices,
+                                                                                                  data, w_homo, slot, work);
             break;
         default:
-            bp::k_tile_weight_bound<bp::WK_HOMO><<<static_cast<unsigned>(grid), 256, 0, stream>>>(n_pre, indptr, indices,
-                                                                                                  data, w_homo, slot);
+            bp::k_tile_weight_bound<bp::WK_HOMO><<<static_cast<unsigned>(grid), 256, 0, stream>>>(n_pre, n_post, indptr, indices,
+                                                                                                  data, w_homo, slot, work);
     }
     BP_LAUNCHED();
+    if (n_post > 0) {
+        int64_t g2 = (n_post + 255) / 256;
+        if (g2 > bp::sm_count() * 8) g2 = bp::sm_count() * 8;
+        bp::k_max_count<<<static_cast<unsigned>(g2), 256, 0, stream>>>(n_post, work, slot + 1);
+        BP_LAUNCHED();
+    }
     return BP_OK;
 }
 

@@ -63,7 +63,7 @@ def test_host_only_helpers(libpath):
     assert B.bp_jit_desc_init(7, 80.0 / 4e6).K == 99999
     with pytest.raises(B.BpError):
         B.bp_jit_desc_init(7, 0.0)
-    assert B.bp_csr_tile_index_size(10, 100000, 57344) == 10 * 3 + 1  # + the weight-bound slot
+    assert B.bp_csr_tile_index_size(10, 100000, 57344) == 10 * 3 + 2  # + the two bound slots
     # equal tiles: the fewest tiles of at most bp_tile_cols() columns, each a
     # multiple of 32 columns, none of them nearly empty
     cap = B.bp_tile_cols()
@@ -160,8 +160,9 @@ def test_operator_and_constructor_host_checks(libpath):
              b"tile_cols")
     rejected(L.bp_event_csrmv(10, 10, fake, fake, fake, F32, 1.0, fake, fake, 5, fake, 0, None, 0,
                               B.BP_ACC_FIXED, None), b"BP_ACC_FIXED")
-    rejected(L.bp_csr_tile_weight_bound(10, 10, fake, fake, None, F32, 1.0, 32, fake, None), b"weights are NULL")
-    rejected(L.bp_csr_tile_weight_bound(10, 10, fake, fake, fake, F32, 1.0, 33, fake, None), b"tile_cols")
+    rejected(L.bp_csr_tile_weight_bound(10, 10, fake, fake, None, F32, 1.0, 32, fake, fake, None), b"weights are NULL")
+    rejected(L.bp_csr_tile_weight_bound(10, 10, fake, fake, fake, F32, 1.0, 33, fake, fake, None), b"tile_cols")
+    rejected(L.bp_csr_tile_weight_bound(10, 10, fake, fake, fake, F32, 1.0, 32, fake, None, None), b"work is NULL")
     rejected(L.bp_event_csrmv_t(10, 10, None, fake, None, H, 1.0, fake, fake, None, 0, 0, None), b"indptr")
     rejected(L.bp_event_csrmv_t(10, 10, fake, fake, None, H, 1.0, None, fake, None, 0, 0, None), b"x_post")
     d = B.JitDesc()                      # K = 0: not initialised

@@ -217,8 +217,8 @@ def test_tile_index_matches_searchsorted():
     B.bp_csr_tile_index(cuda(ip), cuda(ix), n_post, tc, tp)
     S = -(-n_post // tc)
     flat = tp.cpu().numpy()
-    assert flat.size == n_pre * (S + 1) + 1 and flat[-1] == 0  # the weight-bound slot starts empty
-    got = flat[:-1].reshape(n_pre, S + 1)
+    assert flat.size == n_pre * (S + 1) + 2 and flat[-1] == 0 and flat[-2] == 0  # the bound slots start empty
+    got = flat[:-2].reshape(n_pre, S + 1)
     for i in range(0, n_pre, 37):
         row = ix[ip[i]:ip[i + 1]]
         bounds = np.searchsorted(row, np.arange(S) * tc, side="left")
@@ -462,24 +462,46 @@ def test_full_size_operator_cell():
     """A graded operator cell at full size: n = 1e6, p = 0.001 (1e9 stored
     entries), rho = 0.1 (about 1e8 events), matrix = the JIT rows
     materialised.  The scatter's integer counts equal the oracle's over the
-    whole output vector bit for bit (tiled shared-memory path, as timed), and
-    the tiled gather of a random x matches the oracle's sequential sum."""
+    whole output vector bit for bit (tiled shared-memory path, as timed: the
+    equal tiles of bp_tile_cols_for, and full-width tiles with a short last
+    one); FP32 and BF16 weights N(0.5, 0.1) with fixed-point tiles (as timed)
+    stay within the fixed-point bound of the oracle's FP64 product; the tiled
+    gather of a random x matches the oracle's sequential sum."""
     n, p, seed = 1_000_000, 0.001, 1000 + 1_000_000 % 997 + 10
     d = B.bp_jit_desc_init(seed, p)
     ip, ix, _ = B.jit_materialize(d, n, n)
-    tc = B.bp_tile_cols()
-    tp = torch.empty(B.bp_csr_tile_index_size(n, n, tc), dtype=torch.int32, device="cuda")
-    B.bp_csr_tile_index(ip, ix, n, tc, tp)
     ev = wl.bernoulli_spikes(n, 0.1, seed=seed + 1000)
     sl, ns = spike_list_of(ev)
-    y = torch.zeros(n, dtype=torch.int32, device="cuda")
-    B.bp_event_csrmv(ip, ix, None, 1.0, sl, ns, y, tile_ptr=tp, tile_cols=tc)
     h_ip, h_ix = ip.cpu().numpy(), ix.cpu().numpy()
     expect = orc.event_csr_count(h_ip, h_ix, ev, n)
-    assert np.array_equal(y.cpu().numpy(), expect.astype(np.int64))
+    tiles = {}
+    for tc in (B.bp_tile_cols_for(n), B.bp_tile_cols()):
+        tp = torch.empty(B.bp_csr_tile_index_size(n, n, tc), dtype=torch.int32, device="cuda")
+        B.bp_csr_tile_index(ip, ix, n, tc, tp)
+        tiles[tc] = tp
+        y = torch.zeros(n, dtype=torch.int32, device="cuda")
+        B.bp_event_csrmv(ip, ix, None, 1.0, sl, ns, y, tile_ptr=tp, tile_cols=tc)
+        assert np.array_equal(y.cpu().numpy(), expect.astype(np.int64)), tc
+    tc = B.bp_tile_cols_for(n)
+    rng = np.random.default_rng(12)
+    w = (0.5 + 0.1 * rng.standard_normal(len(h_ix))).astype(np.float32)
+    cnt = expect.astype(np.float64)
+    for dw in (cuda(w), cuda(w).to(torch.bfloat16)):
+        wref = dw.float().cpu().numpy().astype(np.float64)
+        tp = tiles[tc].clone()
+        B.bp_csr_tile_weight_bound(ip, ix, dw, 0.0, n, tc, tp)
+        b = float(tp[-2:-1].cpu().numpy().view(np.float32)[0])
+        y = torch.zeros(n, dtype=torch.float32, device="cuda")
+        B.bp_event_csrmv(ip, ix, dw, 0.0, sl, ns, y, tile_ptr=tp, tile_cols=tc, flags=B.BP_ACC_FIXED)
+        assert B.bp_sync_status() == 0
+        ref = orc.event_csrmv(h_ip, h_ix, wref, ev, n)
+        absc = orc.event_csrmv(h_ip, h_ix, np.abs(wref), ev, n)
+        err = np.abs(y.cpu().numpy().astype(np.float64) - ref)
+        assert np.all(err <= _fixed_bound(cnt, absc, int(ev.sum()), b)), str(dw.dtype)
+        assert rel_err(y.cpu().numpy(), ref) < RTOL_F32
     x = np.random.default_rng(11).normal(size=n).astype(np.float32)
     yp = torch.zeros(n, dtype=torch.float32, device="cuda")
-    B.bp_event_csrmv_t(ip, ix, None, 1.0, cuda(x), yp, tile_ptr=tp, tile_cols=tc)
+    B.bp_event_csrmv_t(ip, ix, None, 1.0, cuda(x), yp, tile_ptr=tiles[tc], tile_cols=tc)
     ref = orc.csrmv_t(h_ip, h_ix, None, x.astype(np.float64))
     assert rel_err(yp.cpu().numpy(), ref) < RTOL_F32
 
@@ -646,7 +668,7 @@ def test_fixed_point_tiles_within_their_bound(n_pre, n_post, p, rho, tcols, wdt)
     dw = cuda(w) if wdt == "f32" else cuda(w).to(torch.bfloat16)
     wref = dw.float().cpu().numpy().astype(np.float64)
     B.bp_csr_tile_weight_bound(dip, dix, dw, 0.0, n_post, tcols, tp)
-    b = float(tp[-1:].cpu().numpy().view(np.float32)[0])
+    b = float(tp[-2:-1].cpu().numpy().view(np.float32)[0])
     amax = float(np.abs(wref).max()) if len(wref) else 0.0
     assert amax <= b <= amax * (1 + 2.0 ** -15) or (amax == 0.0 and b > 0.0)
     sl, ns = spike_list_of(ev)
@@ -703,13 +725,36 @@ def test_weight_bound_sums_repeated_columns():
     tcols = 32
     dip, dix, dw = cuda(ip), cuda(ix), cuda(w)
     tp = _tile_index(dip, dix, 2, 40, tcols)
-    assert int(tp[-1].item()) == 0  # no bound yet
+    assert int(tp[-1].item()) == 0 and int(tp[-2].item()) == 0  # no bound yet
     B.bp_csr_tile_weight_bound(dip, dix, dw, 0.0, 40, tcols, tp)
-    b = float(tp[-1:].cpu().numpy().view(np.float32)[0])
+    b = float(tp[-2:-1].cpu().numpy().view(np.float32)[0])
     assert 1.25 <= b <= 1.25 * (1 + 2.0 ** -15)
+    assert int(tp[-1].item()) == 1  # no column holds entries of both rows
     B.bp_csr_tile_weight_bound(dip, dix, None, -3.0, 40, tcols, tp)  # homogeneous: |w| times the longest run
-    b = float(tp[-1:].cpu().numpy().view(np.float32)[0])
+    b = float(tp[-2:-1].cpu().numpy().view(np.float32)[0])
     assert 6.0 <= b <= 6.0 * (1 + 2.0 ** -15)
+
+
+@pytest.mark.parametrize("n_pre,n_post,p", [(3000, 700, 0.05), (50, 100000, 0.2), (1, 5, 1.0)])
+def test_column_bound_counts_rows_per_column(n_pre, n_post, p):
+    """The second bound slot holds the largest number of rows with an entry
+    in one column (a row that repeats a column counts once; indices outside
+    [0, n_post) are not counted), against a brute-force count."""
+    ip, ix = _csr(n_pre, n_post, p, seed=n_pre + 77)
+    ix = ix.copy()
+    lens = np.diff(ip)
+    rows = np.nonzero(lens >= 2)[0]
+    if len(rows):
+        r = int(rows[0])
+        ix[ip[r] + 1] = ix[ip[r]]  # a repeated column (rows stay sorted)
+    dip, dix = cuda(ip), cuda(ix)
+    tcols = 32 * max(1, min(B.bp_tile_cols() // 32, (n_post + 31) // 32))
+    tp = _tile_index(dip, dix, n_pre, n_post, tcols)
+    B.bp_csr_tile_weight_bound(dip, dix, None, 1.0, n_post, tcols, tp)
+    per_col = np.zeros(n_post, np.int64)
+    for i in range(n_pre):
+        per_col[np.unique(ix[ip[i]:ip[i + 1]])] += 1
+    assert int(tp[-1].item()) == int(per_col.max())
 
 
 def test_fixed_point_without_a_bound_is_reported():
@@ -783,7 +828,7 @@ def test_fixed_point_tiles_extreme_weight_magnitudes(scale):
     dip, dix, dw = cuda(ip), cuda(ix), cuda(w)
     tp = _tile_index(dip, dix, n_pre, n_post, tc)
     B.bp_csr_tile_weight_bound(dip, dix, dw, 0.0, n_post, tc, tp)
-    b = float(tp[-1:].cpu().numpy().view(np.float32)[0])
+    b = float(tp[-2:-1].cpu().numpy().view(np.float32)[0])
     sl, ns = spike_list_of(ev)
     y = torch.zeros(n_post, dtype=torch.float32, device="cuda")
     B.bp_event_csrmv(dip, dix, dw, 0.0, sl, ns, y, tile_ptr=tp, tile_cols=tc, flags=B.BP_ACC_SHARED | B.BP_ACC_FIXED)
