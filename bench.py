@@ -322,7 +322,7 @@ def e2e_run(torch, net, host_ckpt, steps):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
-    h2d = sum(t.numel() * t.element_size() for t in host_ckpt["state"].values())
+    h2d = net.host_checkpoint_bytes(host_ckpt)
     d2h = 8 * steps + 4 * n
     return ms, int(events.item()), h2d, d2h
 

@@ -491,6 +491,19 @@ bp_status bp_simulate_prepare(bp_net* net, int64_t T, bp_stream_t stream);
  * the int64 totals accumulated since the last reset. */
 bp_status bp_network_stats(bp_net* net, double* out, bp_stream_t stream);
 
+/* Sparse form of a checkpointed event accumulator (between steps the live
+ * half holds the deliveries of the last step's spikes, mostly zero).
+ * bp_words_compact: the nonzero 32-bit words of x [n] (int32 counts or FP32
+ * bits; -0.0f counts as nonzero) into idx int32 [n] and val uint32 [n]
+ * (capacity n, caller-owned), their number into *count (device int32, set
+ * by the call); pairs are in no particular order.  bp_words_scatter:
+ * x[idx[k]] = val[k] for k < count (host count; indices outside [0, n)
+ * are skipped); the other words of x are left as they are.  n < 2^31. */
+bp_status bp_words_compact(const void* x, int64_t n, int32_t* idx, uint32_t* val, int32_t* count,
+                           bp_stream_t stream);
+bp_status bp_words_scatter(const int32_t* idx, const uint32_t* val, int64_t count, void* x, int64_t n,
+                           bp_stream_t stream);
+
 bp_status bp_network_destroy(bp_net* net);
 
 /* --------------------------------------------------------------------------

@@ -119,6 +119,8 @@ _SIGS = {
     "bp_network_set_step_count": (c_i32, [VP, c_i64, VP]),
     "bp_simulate": (c_i32, [VP, c_i64, VP, VP]),
     "bp_simulate_prepare": (c_i32, [VP, c_i64, VP]),
+    "bp_words_compact": (c_i32, [VP, c_i64, VP, VP, VP, VP]),
+    "bp_words_scatter": (c_i32, [VP, VP, c_i64, VP, c_i64, VP]),
     "bp_network_stats": (c_i32, [VP, VP, VP]),
     "bp_network_destroy": (c_i32, [VP]),
     "bp_batch_layout": (c_i64, [c_i32, VP, VP]),
@@ -464,6 +466,23 @@ def bp_simulate(net, T, record=None, stream=None):
 
 def bp_simulate_prepare(net, T, stream=None):
     _check("bp_simulate_prepare", lib().bp_simulate_prepare(net, int(T), _stream(stream)))
+
+
+def bp_words_compact(x, idx, val, count, stream=None):
+    """Nonzero 32-bit words of x as (idx, val) pairs; count (int32 [1]) gets
+    their number."""
+    n = x.numel() * x.element_size() // 4
+    if x.element_size() * x.numel() != 4 * n or idx.numel() < n or val.numel() < n or count.numel() < 1:
+        raise ValueError("x must hold whole 32-bit words; idx and val need room for n = %d pairs" % n)
+    _check("bp_words_compact", lib().bp_words_compact(_p(x), n, _p(idx), _p(val), _p(count), _stream(stream)))
+
+
+def bp_words_scatter(idx, val, count, x, stream=None):
+    """x[idx[k]] = val[k] (as 32-bit words) for k < count."""
+    n = x.numel() * x.element_size() // 4
+    if int(count) > min(idx.numel(), val.numel()):
+        raise ValueError("count exceeds the pairs given")
+    _check("bp_words_scatter", lib().bp_words_scatter(_p(idx), _p(val), int(count), _p(x), n, _stream(stream)))
 
 
 def bp_network_stats(net, out, stream=None):

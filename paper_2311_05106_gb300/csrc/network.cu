@@ -50,6 +50,40 @@ __global__ void k_set_record(NetCtrl* ctrl, int32_t* record, int64_t len) {
 
 __global__ void k_set_step(NetCtrl* ctrl, int64_t step) { ctrl->step = step; }
 
+// The nonzero 32-bit words of x[0, n) as (index, word) pairs: a warp ballot
+// per 32 words and one counter atomic per warp; the pairs of a warp are in
+// index order, the warps in arrival order.  *count must start at 0.
+__global__ void k_compact_words(const uint32_t* __restrict__ x, int64_t n, int32_t* __restrict__ idx,
+                                uint32_t* __restrict__ val, int32_t* __restrict__ count) {
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    // every lane of a warp runs the same number of iterations (the ballot)
+    const int64_t base0 = static_cast<int64_t>(blockIdx.x) * blockDim.x + (threadIdx.x & ~31);
+    for (int64_t b = base0; b < n; b += stride) {
+        const int64_t i = b + lane;
+        const uint32_t w = i < n ? x[i] : 0u;
+        const unsigned m = __ballot_sync(FULL_MASK, w != 0u);
+        if (m == 0u) continue;
+        int pos = 0;
+        if (lane == 0) pos = atomicAdd(count, __popc(m));
+        pos = __shfl_sync(FULL_MASK, pos, 0) + __popc(m & lanemask_lt());
+        if (w != 0u) {
+            idx[pos] = static_cast<int32_t>(i);
+            val[pos] = w;
+        }
+    }
+}
+
+// x[idx[k]] = val[k] for k < count (indices outside [0, n) are skipped).
+__global__ void k_scatter_words(const int32_t* __restrict__ idx, const uint32_t* __restrict__ val, int64_t count,
+                                uint32_t* __restrict__ x, int64_t n) {
+    for (int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; k < count;
+         k += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int32_t i = idx[k];
+        if (i >= 0 && i < n) x[i] = val[k];
+    }
+}
+
 __global__ void k_reset_ctrl(NetCtrl* ctrl) {
     ctrl->step = 0;
     ctrl->record = nullptr;
@@ -313,6 +347,35 @@ bp_status bp_simulate(bp_net* net, int64_t T, int32_t* record, bp_stream_t strea
         bp::k_set_record<<<1, 1, 0, stream>>>(net->ctrl, nullptr, 0);
         BP_LAUNCHED();
     }
+    return BP_OK;
+}
+
+bp_status bp_words_compact(const void* x, int64_t n, int32_t* idx, uint32_t* val, int32_t* count,
+                           bp_stream_t stream) {
+    bp::clear_error();
+    BP_REQUIRE(n >= 0 && n <= INT32_MAX, "n must be in [0, 2^31 - 1]");
+    BP_REQUIRE(count != nullptr, "count is NULL");
+    BP_REQUIRE(n == 0 || (x && idx && val), "a required pointer is NULL");
+    BP_CUDA(cudaMemsetAsync(count, 0, sizeof(int32_t), stream));
+    if (n == 0) return BP_OK;
+    int64_t grid = (n + 255) / 256;
+    if (grid > bp::sm_count() * 8) grid = bp::sm_count() * 8;
+    bp::k_compact_words<<<static_cast<unsigned>(grid), 256, 0, stream>>>(static_cast<const uint32_t*>(x), n, idx, val,
+                                                                        count);
+    BP_LAUNCHED();
+    return BP_OK;
+}
+
+bp_status bp_words_scatter(const int32_t* idx, const uint32_t* val, int64_t count, void* x, int64_t n,
+                           bp_stream_t stream) {
+    bp::clear_error();
+    BP_REQUIRE(count >= 0 && n >= 0, "negative size");
+    BP_REQUIRE(count == 0 || (idx && val && x), "a required pointer is NULL");
+    if (count == 0) return BP_OK;
+    int64_t grid = (count + 255) / 256;
+    if (grid > bp::sm_count() * 8) grid = bp::sm_count() * 8;
+    bp::k_scatter_words<<<static_cast<unsigned>(grid), 256, 0, stream>>>(idx, val, count, static_cast<uint32_t*>(x), n);
+    BP_LAUNCHED();
     return BP_OK;
 }
 

@@ -183,24 +183,47 @@ class CobaNetwork:
 
     def checkpoint_to_host(self):
         """A checkpoint in pinned host memory (for restoring from the host
-        later, e.g. to resume a run in another process)."""
+        later, e.g. to resume a run in another process).  The live halves of
+        the event accumulators are stored as their nonzero words only (index,
+        word pairs: between steps they hold the deliveries of the last step's
+        spikes, a small share of the neurons)."""
         torch.cuda.synchronize()
         step = B.bp_network_step_count(self.handle)
-        return {"step": step, "live_half": self._live_half(step),
-                "state": {k: t.to("cpu").pin_memory() for k, t in self._checkpoint_views(step).items()}}
+        views = self._checkpoint_views(step)
+        sparse = {}
+        if self._live_half(step) is not None:
+            for k in ("ye", "yi"):
+                x = views.pop(k)
+                idx = torch.empty(x.numel(), dtype=torch.int32, device=x.device)
+                val = torch.empty(x.numel(), dtype=torch.int32, device=x.device)
+                cnt = torch.zeros(1, dtype=torch.int32, device=x.device)
+                B.bp_words_compact(x, idx, val, cnt)
+                c = int(cnt.item())
+                sparse[k] = (idx[:c].to("cpu").pin_memory(), val[:c].to("cpu").pin_memory())
+        return {"step": step, "live_half": self._live_half(step), "sparse": sparse,
+                "state": {k: t.to("cpu").pin_memory() for k, t in views.items()}}
 
     def restore(self, ckpt, non_blocking=False):
         """Writes a checkpoint back (into this network or a new one of the
         same configuration) so that the simulation resumes where it was taken:
         the saved buffers are copied in and the other accumulator half is
-        zeroed on the device.  With non_blocking and a pinned host checkpoint
+        zeroed on the device (sparse accumulators: zeroed, then their saved
+        words scattered back by bp_words_scatter).  With non_blocking and a pinned host checkpoint
         the copies are enqueued on the current stream without waiting for
         them."""
         h = ckpt.get("live_half")
         if h is not None and h != self._live_half(ckpt["step"]):
             raise ValueError("checkpoint accumulator half does not match its step count")
+        sparse = ckpt.get("sparse", {})
         for k, t in self.state_tensors().items():
-            if h is not None and k in ("ye", "yi"):
+            if k in sparse:
+                # zero, then the saved words into the live half
+                idx, val = sparse[k]
+                t.zero_()
+                di = idx.to(t.device, non_blocking=non_blocking)
+                dv = val.to(t.device, non_blocking=non_blocking)
+                B.bp_words_scatter(di, dv, idx.numel(), t[h * self.n:(h + 1) * self.n])
+            elif h is not None and k in ("ye", "yi"):
                 t[h * self.n:(h + 1) * self.n].copy_(ckpt["state"][k], non_blocking=non_blocking)
                 t[(1 - h) * self.n:(2 - h) * self.n].zero_()
             else:
@@ -212,9 +235,16 @@ class CobaNetwork:
         return sum(t.numel() * t.element_size() for t in self.state_tensors().values())
 
     def checkpoint_bytes(self):
-        """Bytes a checkpoint holds (what a restore copies in)."""
+        """Bytes a device checkpoint holds (what a restore copies in)."""
         step = B.bp_network_step_count(self.handle)
         return sum(t.numel() * t.element_size() for t in self._checkpoint_views(step).values())
+
+    @staticmethod
+    def host_checkpoint_bytes(ckpt):
+        """Bytes of a checkpoint_to_host checkpoint (what a restore uploads)."""
+        n = sum(t.numel() * t.element_size() for t in ckpt["state"].values())
+        return n + sum(a.numel() * a.element_size() + b.numel() * b.element_size()
+                       for a, b in ckpt.get("sparse", {}).values())
 
     def step(self):
         B.bp_network_step(self.handle)

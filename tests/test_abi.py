@@ -163,6 +163,11 @@ def test_operator_and_constructor_host_checks(libpath):
     rejected(L.bp_csr_tile_weight_bound(10, 10, fake, fake, None, F32, 1.0, 32, fake, fake, None), b"weights are NULL")
     rejected(L.bp_csr_tile_weight_bound(10, 10, fake, fake, fake, F32, 1.0, 33, fake, fake, None), b"tile_cols")
     rejected(L.bp_csr_tile_weight_bound(10, 10, fake, fake, fake, F32, 1.0, 32, fake, None, None), b"work is NULL")
+    rejected(L.bp_words_compact(fake, -1, fake, fake, fake, None), b"n must be")
+    rejected(L.bp_words_compact(fake, 10, fake, fake, None, None), b"count is NULL")
+    rejected(L.bp_words_compact(None, 10, fake, fake, fake, None), b"required pointer")
+    rejected(L.bp_words_scatter(fake, fake, -1, fake, 10, None), b"negative size")
+    rejected(L.bp_words_scatter(None, fake, 5, fake, 10, None), b"required pointer")
     rejected(L.bp_event_csrmv_t(10, 10, None, fake, None, H, 1.0, fake, fake, None, 0, 0, None), b"indptr")
     rejected(L.bp_event_csrmv_t(10, 10, fake, fake, None, H, 1.0, None, fake, None, 0, 0, None), b"x_post")
     d = B.JitDesc()                      # K = 0: not initialised

@@ -426,12 +426,27 @@ def test_checkpoint_resume_bit_exact(conn, d_e, d_i):
     ck = a.checkpoint()
     assert ck["step"] == 137 and ck["live_half"] == 1 and ck["state"]["ye"].numel() == n
     assert a.checkpoint_bytes() == a.state_bytes() - 2 * n * a.ye.element_size()
+    # the host checkpoint keeps the live accumulator halves as their nonzero words
+    hk = a.checkpoint_to_host()
+    live = slice(n, 2 * n)
+    for k in ("ye", "yi"):
+        idx, val = hk["sparse"][k]
+        buf = getattr(a, k)[live]
+        nz = torch.nonzero(buf.view(torch.int32)).flatten().cpu()
+        assert torch.equal(torch.sort(idx.long()).values, nz)
+        assert torch.equal(val.cuda(), buf.view(torch.int32)[idx.cuda().long()])
+    assert CobaNetwork.host_checkpoint_bytes(hk) < a.checkpoint_bytes()
     a.simulate(90)
     b = CobaNetwork(n, **kw)
     b.restore(ck)
     b.simulate(90)
+    c = CobaNetwork(n, **kw)
+    c.simulate(3)  # state and accumulators to be overwritten
+    c.restore(hk, non_blocking=True)
+    c.simulate(90)
     for name in ("V", "ge", "gi", "ref", "ye", "yi", "totals"):
         assert torch.equal(getattr(a, name), getattr(b, name)), name
+        assert torch.equal(getattr(a, name), getattr(c, name)), name
     after = {k: t.clone() for k, t in a.state_tensors().items()}
     a.restore(ck)
     a.simulate(90)
@@ -440,3 +455,34 @@ def test_checkpoint_resume_bit_exact(conn, d_e, d_i):
     assert int(a.totals[0].item()) > 0
     a.close()
     b.close()
+    c.close()
+
+
+@pytest.mark.parametrize("dtype", [torch.int32, torch.float32])
+def test_words_compact_and_scatter_round_trip(dtype):
+    """bp_words_compact keeps exactly the nonzero 32-bit words (a -0.0 FP32
+    word included) with their indices; bp_words_scatter writes them back into
+    a zeroed buffer bit for bit, skipping indices outside the buffer."""
+    n = 300_001
+    g = torch.Generator().manual_seed(5)
+    x = torch.zeros(n, dtype=dtype)
+    pos = torch.randperm(n, generator=g)[:12_345]
+    if dtype == torch.int32:
+        x[pos] = torch.randint(-1000, 1000, (len(pos),), generator=g, dtype=torch.int32)
+    else:
+        x[pos] = torch.randn(len(pos), generator=g)
+        x[pos[0]] = -0.0
+    x = x.cuda()
+    idx = torch.empty(n, dtype=torch.int32, device="cuda")
+    val = torch.empty(n, dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+    B.bp_words_compact(x, idx, val, cnt)
+    c = int(cnt.item())
+    words = x.view(torch.int32)
+    assert c == int((words != 0).sum().item())
+    assert torch.equal(torch.sort(idx[:c].long()).values, torch.nonzero(words).flatten())
+    assert torch.equal(val[:c], words[idx[:c].long()])
+    y = torch.zeros_like(x)
+    bad = torch.tensor([-1, n], dtype=torch.int32, device="cuda")
+    B.bp_words_scatter(torch.cat([idx[:c], bad]), torch.cat([val[:c], val[:2]]), c + 2, y)
+    assert torch.equal(y.view(torch.int32), words)
