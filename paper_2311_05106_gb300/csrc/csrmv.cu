@@ -152,23 +152,38 @@ struct FlatSmem {
 // the 32-bit range.
 constexpr int64_t kFlatMaxEntries = int64_t(1) << 24;
 
+// The walk's index and weight loads ask L2 to fetch 256 bytes around each
+// request (a lane's next units follow 32 units later in the same segment
+// when it is long, and neighbouring lanes read the bytes between): measured
+// +1.4-1.9 % on 52-entry segments, +0.3-1.1 % on 526-entry ones.
+#define BP_PFX ".L2::256B"
+
 // Eight consecutive indices (and weights) of a 32-byte aligned unit, one
 // streaming 256-bit load each (BF16 weights: one 128-bit load).
 __device__ __forceinline__ void ld_stream8(const int32_t* p, int32_t c[8]) {
-    asm volatile("ld.global.cs.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+    asm volatile("ld.global.cs" BP_PFX ".v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
                  : "=r"(c[0]), "=r"(c[1]), "=r"(c[2]), "=r"(c[3]), "=r"(c[4]), "=r"(c[5]), "=r"(c[6]), "=r"(c[7])
                  : "l"(p));
+}
+
+// 16 bytes, streaming, with the same L2 fetch-size hint.
+__device__ __forceinline__ uint4 ld_stream16_pf(const void* p) {
+    uint4 v;
+    asm volatile("ld.global.cs" BP_PFX ".v4.b32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p));
+    return v;
 }
 
 template <int WK>
 __device__ __forceinline__ void load_weight8(const void* data, int64_t j, float w_homo, float w[8]) {
     if constexpr (WK == WK_F32) {
         const float* p = static_cast<const float*>(data) + j;
-        asm volatile("ld.global.cs.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        asm volatile("ld.global.cs" BP_PFX ".v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
                      : "=f"(w[0]), "=f"(w[1]), "=f"(w[2]), "=f"(w[3]), "=f"(w[4]), "=f"(w[5]), "=f"(w[6]), "=f"(w[7])
                      : "l"(p));
     } else if constexpr (WK == WK_BF16) {
-        const uint4 v = __ldcs(reinterpret_cast<const uint4*>(static_cast<const __nv_bfloat16*>(data) + j));
+        const uint4 v = ld_stream16_pf(static_cast<const __nv_bfloat16*>(data) + j);
         const uint32_t u[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -257,8 +272,17 @@ __device__ __forceinline__ void warp_flat_walk(const CsrArgs& a, const WarpList&
                     ld_stream8(a.indices + 8 * g, col[q]);
                     load_weight8<WK>(a.data, 8 * g, a.w_homo, w[q]);
                 } else if constexpr (EPU == 4) {
-                    const int4 c4 = ld_stream4(a.indices + 4 * g);
-                    const float4 w4 = load_weight4<WK>(a.data, 4 * g, a.w_homo);
+                    const uint4 cu = ld_stream16_pf(a.indices + 4 * g);
+                    const int4 c4 = make_int4(static_cast<int32_t>(cu.x), static_cast<int32_t>(cu.y),
+                                              static_cast<int32_t>(cu.z), static_cast<int32_t>(cu.w));
+                    float4 w4;
+                    if constexpr (WK == WK_F32) {
+                        const uint4 wu = ld_stream16_pf(static_cast<const float*>(a.data) + 4 * g);
+                        w4 = make_float4(__uint_as_float(wu.x), __uint_as_float(wu.y), __uint_as_float(wu.z),
+                                         __uint_as_float(wu.w));
+                    } else {
+                        w4 = load_weight4<WK>(a.data, 4 * g, a.w_homo);
+                    }
                     col[q][0] = c4.x, col[q][1] = c4.y, col[q][2] = c4.z, col[q][3] = c4.w;
                     w[q][0] = w4.x, w[q][1] = w4.y, w[q][2] = w4.z, w[q][3] = w4.w;
                 }
