@@ -816,7 +816,8 @@ def sweep_cells(torch, sizes, probs, rhos, wsel, ops, cells=None, tile_cols=None
                     alg = nnz * (4 + wb) + 8 * (n + 1)
                     for form, fl in (("tiles", 0), ("l2", B.BP_ACC_GLOBAL)) if tc else (("l2", 0),):
                         ms = device_timer(torch, lambda: B.bp_event_csrmv_t(ip, ix, wt, 1.0, x, yp, flags=fl,
-                                                                            tile_ptr=tp, tile_cols=tc), 5)
+                                                                            tile_ptr=tp, tile_cols=tc), 5,
+                                          graph=True)
                         yield dict(op="event_csrmv_t", form=form, n=n, p=p, weights=wname, us=ms * 1e3, nnz=nnz,
                                    alg_bytes=alg, gbs=alg / ms / 1e6, frac_hbm=alg / ms / 1e6 / peak,
                                    peak_source=peak_kind)
@@ -859,7 +860,7 @@ def sweep_cells(torch, sizes, probs, rhos, wsel, ops, cells=None, tile_cols=None
                 for wname, d, y in (("homo", dh, yc), ("normal", dn, yf)):
                     if "jit" not in ops:
                         continue
-                    ms = device_timer(torch, lambda: B.bp_jitconn_event_mv(d, n, sl, ns, y), 5)
+                    ms = device_timer(torch, lambda: B.bp_jitconn_event_mv(d, n, sl, ns, y), 5, graph=True)
                     # targets accumulate in shared memory when y fits a tile, else
                     # with scattered L2 reductions, which then bound the operator
                     yield dict(op="jitconn_event_mv", n=n, p=p, rho=rho, weights=wname, us=ms * 1e3,
