@@ -38,3 +38,19 @@ def test_two_rank_aggregation_gloo():
     out = mgr.dict()
     mp.spawn(_worker, args=(2, port, out), nprocs=2, join=True)
     assert out[0] == out[1] == (15.0, 3000)
+
+
+def test_failed_variant_child_is_reported():
+    """A network variant whose child process fails (here: an unknown variant,
+    rejected by the child's own argument handling) raises in the parent with
+    the child's error text, which the bench records in that variant's entry
+    instead of ending the run."""
+    import argparse
+    import importlib
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sys.path.insert(0, root)
+    bench = importlib.import_module("bench")
+    args = argparse.Namespace(steps=1, warmup=0, settle=0)
+    with pytest.raises(RuntimeError, match="variant no_such_variant failed"):
+        bench.network_variant("no_such_variant", args, 0)
